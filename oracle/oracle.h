@@ -1,0 +1,88 @@
+/*
+ * FP64 CPU oracle of the batched quasi-Newton dwell-time optimisation (gL-BFGS) of
+ * "A GPU-based multi-criteria optimization algorithm for HDR brachytherapy".
+ *
+ * TEST INFRASTRUCTURE ONLY.  This library is a plain, slow, obviously correct restatement
+ * of the paper's arithmetic in double precision.  Only the test-suite, the smoke check and
+ * the benchmark's CPU-baseline / reference leg load it; the product path (the CUDA library
+ * under paper_1904_01567_b300/) never does, and the two share no code.
+ *
+ * Layouts (all row-major, plan-major):
+ *   A       n_pnt x n_dwell   dose rate of dwell l at point i (Gy/s), Eq. (dose)
+ *   sid     n_pnt             structure id of each point, 0 <= sid < n_struct
+ *   params  n_struct x 4      (w_min, D_min, D_max, w_max) per structure, Eq. (1);
+ *                             D_min = -inf or D_max = +inf makes the penalty one-sided
+ *   w       n_struct          hidden weights of one plan, Eq. (obj)
+ *   x       n_dwell           dwell weights, t = x*x (Sec. 2.1.2)
+ *   T, T0   P x n_dwell       dwell times of P plans (one row per plan)
+ *
+ * Parity status of each function is stated beside it; every function here is pinned by a
+ * test in tests/test_oracle_*.py against something other than itself.
+ */
+#ifndef GMCO_ORACLE_H
+#define GMCO_ORACLE_H
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+enum { ORACLE_CONVERGED = 0, ORACLE_MAXITER = 1, ORACLE_LSFAIL = 2, ORACLE_NONFINITE = 3 };
+
+/* Eq. (dose): d_i = sum_l A_il t_l.  Pinned: closed-form single source, exact sums. */
+void oracle_dose(const double *A, int64_t n_pnt, int64_t n_dwell, const double *t, double *d);
+
+/* Eq. (1): piecewise quadratic penalty of one dose value, and its derivative in d. */
+double oracle_point_penalty(double d, const double *prm);
+double oracle_point_dpenalty(double d, const double *prm);
+
+/* Eq. (obj) with Eq. (dose) at t = x*x, and the gradient of Eq. (2) summed over points:
+ *   F = sum_s w_s / N_s sum_{i in s} f_i(d_i)
+ *   dF/dx_l = 2 x_l sum_i A_il (w_s(i) / N_s(i)) f'_i(d_i)
+ * Structures without points contribute nothing.  grad_x, dose, f_struct may be NULL;
+ * f_struct[s] = (1/N_s) sum_{i in s} f_i (the unweighted per-structure objective).
+ * Returns 0, or -1 on invalid arguments. */
+int oracle_objective(const double *A, int64_t n_pnt, int64_t n_dwell, const int32_t *sid,
+                     int32_t n_struct, const double *params, const double *w, const double *x,
+                     double *F, double *grad_x, double *dose, double *f_struct);
+
+/* L-BFGS two-loop recursion (Nocedal & Wright, Algorithm 7.4) with H0 = gamma I,
+ * gamma = s'y / y'y of the newest pair.  History is a ring of m slots (S, Y: m x n,
+ * rho: m) holding `count` pairs, the newest at slot `newest`.  Writes p = -H g.
+ * count == 0 gives p = -g. */
+void oracle_two_loop(int64_t n, int32_t m, int32_t count, int32_t newest, const double *S,
+                     const double *Y, const double *rho, const double *g, double *p);
+
+/* One plan, the whole method (x = sqrt(t0); L-BFGS with backtracking Armijo line search;
+ * stop on relative objective change).  t0 may be NULL (uniform 1 s).
+ * trace (optional, 3 x (max_iters + 1) doubles): for each accepted iteration k the
+ * objective F_k, the accepted step alpha_k and the directional derivative g'p; row 0 holds
+ * F_0.  n_evals counts objective evaluations.  Returns 0 or -1 on invalid arguments. */
+int oracle_lbfgs(const double *A, int64_t n_pnt, int64_t n_dwell, const int32_t *sid,
+                 int32_t n_struct, const double *params, const double *w, const double *t0,
+                 int32_t max_iters, double tol, int32_t m, double c1, int32_t max_ls,
+                 double *t_out, double *F_out, int32_t *iters_out, int32_t *status_out,
+                 double *trace, int64_t *n_evals);
+
+/* P independent plans (rows of W and T0), one plan per OpenMP thread.  T0 may be NULL.
+ * n_threads <= 0 uses the OpenMP default.  Returns 0 or -1. */
+int oracle_lbfgs_batch(const double *A, int64_t n_pnt, int64_t n_dwell, const int32_t *sid,
+                       int32_t n_struct, const double *params, const double *W, int64_t P,
+                       const double *T0, int32_t max_iters, double tol, int32_t m, double c1,
+                       int32_t max_ls, double *T_out, double *F_out, int32_t *iters_out,
+                       int32_t *status_out, int64_t *n_evals, int32_t n_threads);
+
+/* DVH indices of one dose vector (Sec. 2.3.1 definitions), rx = prescription (Gy):
+ *   out[0] V100 of structure 0 (% of its points with d >= rx)
+ *   out[1] D90  of structure 0 (% of rx): k-th largest dose, k = ceil(0.9 N_0)
+ *   out[2] D10  of structure 1 (% of rx): k-th largest dose, k = ceil(0.1 N_1)
+ *   out[3] V75  of structure 2 (% of its points with d >= 0.75 rx)
+ *   out[4] V75  of structure 3 (same)
+ * An index whose structure is absent or empty is NaN. */
+void oracle_dvh(const double *d, const int32_t *sid, int64_t n_pnt, int32_t n_struct, double rx,
+                double *out);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

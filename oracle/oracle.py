@@ -1,0 +1,158 @@
+"""ctypes wrapper of the FP64 C oracle (oracle.c).  Test infrastructure only.
+
+Every function takes and returns numpy float64 / int32 arrays; inputs are converted with
+np.ascontiguousarray so callers may pass float32 (the values are widened exactly).
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import subprocess
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "oracle.c")
+_LIB = os.path.join(_HERE, "liboracle.so")
+
+CONVERGED, MAXITER, LSFAIL, NONFINITE = 0, 1, 2, 3
+
+_lib = None
+_dp = ctypes.POINTER(ctypes.c_double)
+_ip = ctypes.POINTER(ctypes.c_int32)
+_lp = ctypes.POINTER(ctypes.c_int64)
+_i64 = ctypes.c_int64
+_i32 = ctypes.c_int32
+_f64 = ctypes.c_double
+
+
+def build(force: bool = False) -> str:
+    """Compile liboracle.so with gcc (plain -O2, OpenMP over plans)."""
+    if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < max(
+            os.path.getmtime(_SRC), os.path.getmtime(os.path.join(_HERE, "oracle.h"))):
+        cmd = ["gcc", "-O2", "-std=c11", "-fopenmp", "-fPIC", "-shared", "-o", _LIB, _SRC, "-lm"]
+        subprocess.run(cmd, check=True)
+    return _LIB
+
+
+def load():
+    global _lib
+    if _lib is None:
+        build()
+        lib = ctypes.CDLL(_LIB)
+        lib.oracle_dose.argtypes = [_dp, _i64, _i64, _dp, _dp]
+        lib.oracle_dose.restype = None
+        lib.oracle_point_penalty.argtypes = [_f64, _dp]
+        lib.oracle_point_penalty.restype = _f64
+        lib.oracle_point_dpenalty.argtypes = [_f64, _dp]
+        lib.oracle_point_dpenalty.restype = _f64
+        lib.oracle_objective.argtypes = [_dp, _i64, _i64, _ip, _i32, _dp, _dp, _dp, _dp, _dp, _dp, _dp]
+        lib.oracle_objective.restype = ctypes.c_int
+        lib.oracle_two_loop.argtypes = [_i64, _i32, _i32, _i32, _dp, _dp, _dp, _dp, _dp]
+        lib.oracle_two_loop.restype = None
+        lib.oracle_lbfgs.argtypes = [_dp, _i64, _i64, _ip, _i32, _dp, _dp, _dp, _i32, _f64, _i32,
+                                     _f64, _i32, _dp, _dp, _ip, _ip, _dp, _lp]
+        lib.oracle_lbfgs.restype = ctypes.c_int
+        lib.oracle_lbfgs_batch.argtypes = [_dp, _i64, _i64, _ip, _i32, _dp, _dp, _i64, _dp, _i32,
+                                           _f64, _i32, _f64, _i32, _dp, _dp, _ip, _ip, _lp, _i32]
+        lib.oracle_lbfgs_batch.restype = ctypes.c_int
+        lib.oracle_dvh.argtypes = [_dp, _ip, _i64, _i32, _f64, _dp]
+        lib.oracle_dvh.restype = None
+        _lib = lib
+    return _lib
+
+
+def _d(a):
+    return np.ascontiguousarray(a, dtype=np.float64)
+
+
+def _i(a):
+    return np.ascontiguousarray(a, dtype=np.int32)
+
+
+def _p(a, t=_dp):
+    return None if a is None else a.ctypes.data_as(t)
+
+
+def dose(A, t):
+    A = _d(A); t = _d(t)
+    out = np.empty(A.shape[0])
+    load().oracle_dose(_p(A), A.shape[0], A.shape[1], _p(t), _p(out))
+    return out
+
+
+def point_penalty(d, prm):
+    return load().oracle_point_penalty(float(d), _p(_d(prm)))
+
+
+def point_dpenalty(d, prm):
+    return load().oracle_point_dpenalty(float(d), _p(_d(prm)))
+
+
+def objective(A, sid, params, w, x, want_grad=True):
+    """Returns (F, grad_x, dose, f_struct)."""
+    A = _d(A); sid = _i(sid); params = _d(params); w = _d(w); x = _d(x)
+    S = params.shape[0]
+    F = np.zeros(1)
+    g = np.empty(A.shape[1]) if want_grad else None
+    dd = np.empty(A.shape[0])
+    fs = np.empty(S)
+    rc = load().oracle_objective(_p(A), A.shape[0], A.shape[1], _p(sid, _ip), S, _p(params),
+                                 _p(w), _p(x), _p(F), _p(g), _p(dd), _p(fs))
+    if rc != 0:
+        raise ValueError("oracle_objective: invalid arguments")
+    return float(F[0]), g, dd, fs
+
+
+def two_loop(S, Y, rho, count, newest, g):
+    S = _d(S); Y = _d(Y); rho = _d(rho); g = _d(g)
+    m, n = S.shape
+    p = np.empty(n)
+    load().oracle_two_loop(n, m, count, newest, _p(S), _p(Y), _p(rho), _p(g), _p(p))
+    return p
+
+
+def lbfgs(A, sid, params, w, t0=None, max_iters=200, tol=1e-6, m=10, c1=1e-4, max_ls=30,
+          trace=False):
+    """One plan.  Returns dict(t, F, iters, status, evals[, trace])."""
+    A = _d(A); sid = _i(sid); params = _d(params); w = _d(w)
+    t0 = None if t0 is None else _d(t0)
+    n = A.shape[1]
+    t = np.empty(n); F = np.zeros(1); it = np.zeros(1, np.int32); st = np.zeros(1, np.int32)
+    ev = np.zeros(1, np.int64)
+    tr = np.full(3 * (max_iters + 1), np.nan) if trace else None
+    rc = load().oracle_lbfgs(_p(A), A.shape[0], n, _p(sid, _ip), params.shape[0], _p(params),
+                             _p(w), _p(t0), max_iters, tol, m, c1, max_ls, _p(t), _p(F),
+                             _p(it, _ip), _p(st, _ip), _p(tr), _p(ev, _lp))
+    if rc != 0:
+        raise ValueError("oracle_lbfgs: invalid arguments")
+    out = dict(t=t, F=float(F[0]), iters=int(it[0]), status=int(st[0]), evals=int(ev[0]))
+    if trace:
+        k = out["iters"]
+        out["trace"] = tr.reshape(-1, 3)[:k + 1]
+    return out
+
+
+def lbfgs_batch(A, sid, params, W, T0=None, max_iters=200, tol=1e-6, m=10, c1=1e-4, max_ls=30,
+                n_threads=0):
+    """P plans, one per OpenMP thread.  Returns dict(T, F, iters, status, evals)."""
+    A = _d(A); sid = _i(sid); params = _d(params); W = _d(W)
+    P = W.shape[0]
+    n = A.shape[1]
+    T0 = None if T0 is None else _d(T0)
+    T = np.empty((P, n)); F = np.empty(P); it = np.empty(P, np.int32); st = np.empty(P, np.int32)
+    ev = np.empty(P, np.int64)
+    rc = load().oracle_lbfgs_batch(_p(A), A.shape[0], n, _p(sid, _ip), params.shape[0],
+                                   _p(params), _p(W), P, _p(T0), max_iters, tol, m, c1, max_ls,
+                                   _p(T), _p(F), _p(it, _ip), _p(st, _ip), _p(ev, _lp),
+                                   int(n_threads))
+    if rc != 0:
+        raise ValueError("oracle_lbfgs_batch: invalid arguments")
+    return dict(T=T, F=F, iters=it, status=st, evals=ev)
+
+
+def dvh(d, sid, n_struct=4, rx=15.0):
+    d = _d(d); sid = _i(sid)
+    out = np.empty(5)
+    load().oracle_dvh(_p(d), _p(sid, _ip), d.shape[0], n_struct, rx, _p(out))
+    return out
