@@ -1,0 +1,159 @@
+/*
+ * gmco.h - C ABI of the batched gL-BFGS Pareto-plan optimiser for HDR prostate
+ * brachytherapy on NVIDIA B300 (sm_103a).
+ *
+ * Method: Belanger, Cui et al., "A GPU-based multi-criteria optimization algorithm for HDR
+ * brachytherapy" (arXiv 1904.01567).  Each plan p of a batch has its own hidden weights w_p
+ * (Eq. (obj)); the library minimises, for every plan at once,
+ *
+ *     F_p(x) = sum_s w_ps / N_s  sum_{i in s} f_s(d_i),      d = A t,   t = x*x,
+ *
+ * with f_s the piecewise quadratic penalty of Eq. (1), the dose of Eq. (dose), the
+ * non-negativity substitution t = x^2 of Sec. 2.1.2 and the gradient of Eq. (2), by
+ * limited-memory BFGS (Sec. 2.2.2) with a backtracking Armijo line search, stopping on the
+ * relative variation of the objective (Sec. 2.2.3).  DVH indices follow Sec. 2.3.1.
+ *
+ * Conventions for every call:
+ *   - Pointers may be host or device memory (checked with cudaPointerGetAttributes).
+ *     Host buffers are staged through device memory inside the call.
+ *   - All matrices are row-major.  Batched per-plan data is plan-major: row p holds plan p
+ *     (so T, an n_dwell x P matrix with one column per plan, is stored as P x n_dwell).
+ *   - Calls return a gmco_status and never abort or throw; per-plan numerical outcomes are
+ *     reported as gmco_plan_status values.
+ *   - One problem is used by one host thread and one stream at a time.  Calls that take a
+ *     stream run on it and return after their results are in the caller's buffers.
+ *   - Nothing falls back to the CPU: without a usable CUDA device every call that needs one
+ *     returns GMCO_ECUDA.
+ */
+#ifndef GMCO_H
+#define GMCO_H
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct gmco_problem gmco_problem;
+
+typedef enum {
+    GMCO_OK = 0,
+    GMCO_EINVAL = 1,       /* bad shape, null pointer, non-finite or negative input */
+    GMCO_ENOMEM = 2,       /* device allocation failed */
+    GMCO_ECUDA = 3,        /* CUDA runtime error, or no usable device */
+    GMCO_ETIMEOUT = 4,     /* the solve hit its step budget with plans still running */
+    GMCO_EUNSUPPORTED = 5  /* valid request this build cannot serve (e.g. too many dwells) */
+} gmco_status;
+
+typedef enum {
+    GMCO_PLAN_CONVERGED = 0, /* relative objective change <= tol, F == 0 or gradient == 0 */
+    GMCO_PLAN_MAXITER = 1,   /* max_iters accepted iterations without meeting tol */
+    GMCO_PLAN_LSFAIL = 2,    /* line search failed along steepest descent; x kept */
+    GMCO_PLAN_NONFINITE = 3  /* objective or gradient not finite */
+} gmco_plan_status;
+
+typedef enum {
+    GMCO_PREC_FP32 = 0,   /* A in FP32, FP32 SIMT dose and gradient contractions */
+    GMCO_PREC_BF16 = 1,   /* A in BF16 with a per-point power-of-two scale; tcgen05 BF16 MMA
+                             (FP32 accumulate) with two-term BF16 splits of t and of dF/dd */
+    GMCO_PREC_FP8 = 2,    /* A quantised to FP8 E4M3 with a per-point power-of-two scale, run
+                             on the BF16 tensor-core path (E4M3 values are exact in BF16) */
+    GMCO_PREC_BF16X2 = 3, /* A, t and dF/dd each split into two BF16 terms (about 16 bits) */
+    GMCO_PREC_BF16X3 = 4  /* three BF16 terms each (24 bits, the FP32 significand): products
+                             with term orders i + j <= 4, FP32 accuracy on the tensor cores */
+} gmco_precision;
+
+/* Number of DVH indices written per plan, in this order (Sec. 2.3.1; structure 0 is the
+ * target, 1 the urethra, 2 and 3 the rectum and bladder):
+ *   0 V100 of structure 0, % of its points receiving >= rx_gy
+ *   1 D90  of structure 0, % of rx_gy (k-th largest dose, k = ceil(0.9 N_0))
+ *   2 D10  of structure 1, % of rx_gy (k = ceil(0.1 N_1))
+ *   3 V75  of structure 2, % of its points receiving >= 0.75 rx_gy
+ *   4 V75  of structure 3, same
+ * Indices of absent structures are NaN. */
+#define GMCO_DVH_K 5
+
+typedef struct {
+    int32_t precision;     /* gmco_precision, default GMCO_PREC_FP32 */
+    int32_t m;             /* L-BFGS history pairs, 1..16, default 10 */
+    double c1;             /* Armijo sufficient-decrease constant, default 1e-4 */
+    int32_t max_ls;        /* line-search trials per direction, 1..60, default 30 */
+    double rx_gy;          /* prescription dose for the DVH indices, default 15 Gy */
+    int32_t refine_iters;  /* after a BF16/FP8 solve, up to this many further iterations
+                              with the FP32 evaluation (history kept); default 0 */
+    int32_t steps_per_poll;/* device steps between host checks for completion, default 16 */
+} gmco_options;
+
+/* Fills *opt with the defaults above. */
+void gmco_default_options(gmco_options *opt);
+
+/* Creates a problem on the current CUDA device.
+ *   A               n_pnt x n_dwell dose-rate matrix, Gy/s, finite and >= 0 (Eq. (dose));
+ *                   copied (and quantised for BF16/FP8), the caller may free it afterwards
+ *   structure_ids   n_pnt values in [0, n_struct); every structure needs >= 1 point
+ *   penalty_params  n_struct x 4: (w_min, D_min, D_max, w_max) of Eq. (1), Gy; weights
+ *                   finite and >= 0, D_min <= D_max, D_min may be -inf, D_max may be +inf
+ *   opt             options, or NULL for the defaults
+ * 1 <= n_dwell <= 1024, 1 <= n_pnt, 1 <= n_struct <= 16; the tensor-core precisions need
+ * n_dwell <= 384 and n_struct <= 8 (GMCO_EUNSUPPORTED otherwise).  Returns GMCO_EINVAL on bad
+ * arguments, GMCO_ENOMEM / GMCO_ECUDA on device failure; *out is NULL unless GMCO_OK. */
+gmco_status gmco_create_problem(const float *A, int64_t n_pnt, int64_t n_dwell,
+                                const int32_t *structure_ids, int32_t n_struct,
+                                const double *penalty_params, const gmco_options *opt,
+                                gmco_problem **out);
+
+/* Releases every device buffer of the problem.  NULL is allowed. */
+void gmco_destroy_problem(gmco_problem *prob);
+
+/* Solves P plans at once (gMCO, Sec. 2.3.2): plan p minimises F_p with hidden weights
+ * penalty_weights[p, :] from the start t0[p, :].
+ *   penalty_weights P x n_struct, finite and >= 0
+ *   t0              P x n_dwell start dwell times (s), finite and >= 0, or NULL for 1 s
+ *   max_iters       accepted iterations per plan, >= 0
+ *   tol             relative objective change that ends a plan, >= 0
+ * Outputs (any may be NULL except none of them needs to be given):
+ *   T_out           P x n_dwell final dwell times t = x^2 (s)
+ *   objectives      P final objectives F_p; with BF16/FP8 precision they are re-evaluated
+ *                   with the FP32 path at the final T
+ *   dvh             P x GMCO_DVH_K indices of the final doses (FP32 path)
+ *   iters_out       P accepted iterations
+ *   plan_status     P gmco_plan_status values
+ * Returns GMCO_ETIMEOUT when plans were still running after the step budget
+ * (max_iters * (max_ls + 1) + 2 steps); outputs then hold the current iterates. */
+gmco_status gmco_solve_batch(gmco_problem *prob, const float *penalty_weights, int64_t P,
+                             const float *t0, int32_t max_iters, double tol, float *T_out,
+                             double *objectives, float *dvh, int32_t *iters_out,
+                             int32_t *plan_status, void *cuda_stream);
+
+/* One evaluation at given dwell weights X (P x n_dwell), with the problem's precision:
+ *   objectives  P values of Eq. (obj)
+ *   grad_x      P x n_dwell gradient of Eq. (2) summed over points (dF/dx)
+ *   dose        P x n_pnt doses of Eq. (dose)
+ *   dvh         P x GMCO_DVH_K DVH indices of those doses
+ * Any output may be NULL.  All outputs come from the problem's precision form (the dose of
+ * a tensor-core form is that form's dose GEMM), so this call measures each form's error. */
+gmco_status gmco_evaluate(gmco_problem *prob, const float *penalty_weights, int64_t P,
+                          const float *X, double *objectives, float *grad_x, float *dose,
+                          float *dvh, void *cuda_stream);
+
+/* DVH indices (GMCO_DVH_K per plan, see above) of given doses: dose is P x n_pnt (Gy).
+ * Exact on the given FP32 values: counts and k-th largest values, no interpolation. */
+gmco_status gmco_dvh_from_dose(gmco_problem *prob, const float *dose, int64_t P, float *dvh,
+                               void *cuda_stream);
+
+/* Problem sizes as stored (after validation). */
+gmco_status gmco_problem_info(const gmco_problem *prob, int64_t *n_pnt, int64_t *n_dwell,
+                              int32_t *n_struct, int32_t *precision);
+
+/* Kernel launches made by the most recent solve or evaluate call on this problem. */
+int64_t gmco_last_launch_count(const gmco_problem *prob);
+
+/* Static description of a status code. */
+const char *gmco_status_string(gmco_status s);
+
+/* Text of the most recent error on the calling host thread (empty if none). */
+const char *gmco_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

@@ -1,0 +1,24 @@
+"""B300-native batched gL-BFGS Pareto-plan optimiser (arXiv 1904.01567, gMCO).
+
+The compute path is the CUDA library libgmco.so (paper_1904_01567_b300/csrc, C ABI in
+include/gmco.h); this package only marshals arguments to it.
+"""
+from .gmco import (  # noqa: F401
+    Problem,
+    GmcoError,
+    create_problem,
+    destroy_problem,
+    solve_batch,
+    evaluate,
+    dvh_from_dose,
+    problem_info,
+    last_launch_count,
+    status_string,
+    default_options,
+    load,
+    LIB_PATH,
+    PREC,
+    PLAN_STATUS,
+    DVH_K,
+    DVH_NAMES,
+)

@@ -1,0 +1,101 @@
+// Internal declarations shared by the CUDA translation units of libgmco.
+// Device buffers, launch helpers and the solver's per-plan state layout.
+#pragma once
+#include <cuda_runtime.h>
+#include <cuda_bf16.h>
+#include <stdint.h>
+
+#include "gmco.h"
+
+namespace gmco {
+
+constexpr int kMaxStruct = 16;
+constexpr int kMaxHist = 16;
+constexpr int kMaxDwell = 1024;
+
+// Per-plan solver state machine (one evaluation per step for every plan not DONE).
+enum PlanState : int32_t { ST_INIT = 0, ST_TRIAL = 1, ST_DONE = 2 };
+
+inline int64_t round_up(int64_t a, int64_t b) { return (a + b - 1) / b * b; }
+inline int64_t ceil_div(int64_t a, int64_t b) { return (a + b - 1) / b; }
+
+// Problem data resident on the device.
+struct DevProblem {
+    int64_t n_pnt = 0, n_dwell = 0;
+    int64_t np_pad = 0;   // points padded to a multiple of 256 (padding rows of A are 0, sid -1)
+    int64_t nd_pad = 0;   // dwells padded to a multiple of 32 (padding columns of A are 0)
+    int32_t n_struct = 0;
+    float *A32 = nullptr;          // np_pad x nd_pad, Gy/s
+    float *row_scale = nullptr;    // np_pad, power-of-two scale of each point's row of A
+    int8_t *sid = nullptr;         // np_pad, -1 on padding points
+    // tensor-core forms: A / row_scale split into tc_terms BF16 terms, row-major and transposed
+    int32_t tc_terms = 0;          // 0 = FP32 SIMT form
+    int64_t kpad = 0;              // dwells padded to a multiple of 64 (BF16 row length)
+    __nv_bfloat16 *Ah[3] = {nullptr, nullptr, nullptr};    // np_pad x kpad
+    __nv_bfloat16 *AhT[3] = {nullptr, nullptr, nullptr};   // kpad x np_pad
+    float4 *sparams = nullptr;     // n_struct x (w_min, D_min, D_max, w_max)
+    float *inv_count = nullptr;    // n_struct, 1 / N_s
+};
+
+// Buffers of one evaluation pass over `rows` compact plan rows.
+struct EvalArgs {
+    DevProblem pb;           // by value: kernels read the problem's pointers and sizes
+    const int32_t *n_rows;   // device scalar: number of valid compact rows
+    int32_t cap;             // allocated compact rows
+    const float *Tt;         // cap x nd_pad trial dwell times
+    const float *dT;         // cap x nd_pad change of dwell times vs the base point, or null
+    const float *Wc;         // cap x n_struct, w_ps / N_s
+    float *G;                // cap x np_pad, dF/dd per point (mode G) or dose (mode D)
+    float *Fpart;            // n_ptiles x cap, per point tile partial of F
+    float *dFpart;           // n_ptiles x cap, partial of F(trial) - F(base)
+    float *gpart;            // n_split x cap x nd_pad, partial of A^T G
+    int32_t n_split;
+};
+
+// Plan-indexed solver state (capacity P).
+struct SolverState {
+    int32_t P = 0, m = 10, nd_pad = 0, n_struct = 0;
+    float *x = nullptr, *g = nullptr, *p = nullptr, *xt = nullptr, *gt = nullptr;  // P x nd_pad
+    float *S = nullptr, *Y = nullptr;   // P x m x nd_pad
+    double *rho = nullptr;              // P x m
+    double *gamma = nullptr;            // P
+    double *F = nullptr, *Ft = nullptr, *dFt = nullptr, *gtp = nullptr, *alpha = nullptr;
+    int32_t *state = nullptr, *status = nullptr, *iters = nullptr, *maxit = nullptr;
+    int32_t *ls = nullptr, *hcount = nullptr, *hnewest = nullptr;
+    float *Wn = nullptr;                // P x n_struct, w / N_s
+    int32_t *list = nullptr;            // compact row -> plan
+    int32_t *n_act = nullptr;           // device scalar
+    int32_t *n_live = nullptr;          // device scalar: plans not DONE after the last update
+};
+
+struct UpdateParams {
+    double c1, tol;
+    int32_t max_ls;
+};
+
+// ---- launchers (return cudaError_t of the launch) ----
+cudaError_t launch_solver_init(const SolverState &s, const DevProblem &pb, const float *W,
+                               const float *t0, int32_t max_iters, cudaStream_t st);
+cudaError_t launch_compact(const SolverState &s, int32_t mode, cudaStream_t st);
+cudaError_t launch_prep_fp32(const SolverState &s, const DevProblem &pb, float *Tc, float *dTc,
+                             float *Wc, bool force_base, cudaStream_t st);
+cudaError_t launch_finish(const SolverState &s, const EvalArgs &e, int32_t n_ptiles,
+                          cudaStream_t st);
+cudaError_t launch_update(const SolverState &s, const UpdateParams &u, cudaStream_t st);
+cudaError_t launch_count_live(const SolverState &s, cudaStream_t st);
+cudaError_t launch_reopen(const SolverState &s, int32_t extra_iters, cudaStream_t st);
+cudaError_t launch_square(const float *x, float *t, int64_t rows, int64_t nd, int64_t nd_pad,
+                          cudaStream_t st);
+
+// SIMT FP32 evaluation
+enum EvalMode : int32_t { MODE_G = 0, MODE_DOSE = 1 };
+int32_t simt_n_ptiles(const DevProblem &pb);
+int32_t simt_pts_per_split(const DevProblem &pb, int32_t n_split);
+cudaError_t launch_gemm1_simt(const EvalArgs &e, int32_t mode, cudaStream_t st);
+cudaError_t launch_gemm2_simt(const EvalArgs &e, cudaStream_t st);
+
+// DVH indices of P dose rows (P x np_pad, row stride ld)
+cudaError_t launch_dvh(const DevProblem &pb, const float *D, int64_t ld, const int32_t *rows,
+                       int32_t P, double rx, float *dvh_out, cudaStream_t st);
+
+}  // namespace gmco

@@ -1,0 +1,480 @@
+// Batched L-BFGS machinery (Sec. 2.2.2 of the paper, whose L-BFGS details are omitted there;
+// this follows Nocedal & Wright's two-loop recursion with backtracking Armijo search).
+//
+// Every plan runs the same per-plan state machine; one "step" evaluates every plan that is
+// not DONE exactly once:
+//   INIT  : evaluate at x0 = sqrt(t0), then choose the first direction
+//   TRIAL : evaluate at x + alpha p; accept (Armijo) -> curvature pair, stop test, next
+//           direction; or reject -> alpha /= 2 and stay TRIAL
+//   DONE  : frozen
+// The Armijo and stop tests use dF = F(x + alpha p) - F(x) evaluated from the dose change
+// A (t_trial - t), with t_trial - t = alpha p (2 x + alpha p), instead of a difference of
+// two rounded objective values (see the evaluation kernels).
+#include <cuda_runtime.h>
+#include <math.h>
+
+#include <algorithm>
+
+#include "common.cuh"
+
+namespace gmco {
+
+namespace {
+
+constexpr unsigned kFull = 0xffffffffu;
+
+__device__ __forceinline__ float warp_sum_f(float v)
+{
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(kFull, v, o);
+    return __shfl_sync(kFull, v, 0);
+}
+
+__device__ __forceinline__ double warp_sum_d(double v)
+{
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(kFull, v, o);
+    return __shfl_sync(kFull, v, 0);
+}
+
+__device__ __forceinline__ float warp_max_f(float v)
+{
+    for (int o = 16; o > 0; o >>= 1) v = fmaxf(v, __shfl_down_sync(kFull, v, o));
+    return __shfl_sync(kFull, v, 0);
+}
+
+__global__ void k_solver_init(SolverState s, const float *__restrict__ W,
+                              const float *__restrict__ t0, const float *__restrict__ inv_count,
+                              int32_t nd, int32_t max_iters)
+{
+    const int j = blockIdx.x;
+    if (j >= s.P) return;
+    const size_t base = (size_t)j * s.nd_pad;
+    for (int l = threadIdx.x; l < s.nd_pad; l += blockDim.x) {
+        float xv = 0.0f;
+        if (l < nd) xv = t0 ? sqrtf(t0[(size_t)j * nd + l]) : 1.0f;
+        s.x[base + l] = xv;
+        s.xt[base + l] = xv;
+        s.g[base + l] = 0.0f;
+        s.gt[base + l] = 0.0f;
+        s.p[base + l] = 0.0f;
+    }
+    if (threadIdx.x < s.n_struct)
+        s.Wn[(size_t)j * s.n_struct + threadIdx.x] =
+            W[(size_t)j * s.n_struct + threadIdx.x] * inv_count[threadIdx.x];
+    if (threadIdx.x == 0) {
+        s.state[j] = ST_INIT;
+        s.status[j] = GMCO_PLAN_MAXITER;
+        s.iters[j] = 0;
+        s.maxit[j] = max_iters;
+        s.ls[j] = 0;
+        s.hcount[j] = 0;
+        s.hnewest[j] = s.m - 1;
+        s.F[j] = 0.0;
+        s.Ft[j] = 0.0;
+        s.dFt[j] = 0.0;
+        s.gtp[j] = 0.0;
+        s.alpha[j] = 0.0;
+        s.gamma[j] = 1.0;
+    }
+}
+
+// Single-block stream compaction of the plans that need an evaluation this step, in plan
+// order (mode 0: INIT or TRIAL; mode 1: every plan).  Writes list[] and *n_act.
+__global__ void k_compact(SolverState s, int32_t mode)
+{
+    __shared__ int32_t wsum[32];
+    const int P = s.P;
+    const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
+    const int chunk = (P + blockDim.x - 1) / blockDim.x;
+    const int b = min(tid * chunk, P), e = min(b + chunk, P);
+    int c = 0;
+    for (int j = b; j < e; ++j) {
+        const int st = s.state[j];
+        c += (mode == 1) || st == ST_INIT || st == ST_TRIAL;
+    }
+    int incl = c;
+    for (int o = 1; o < 32; o <<= 1) {
+        int v = __shfl_up_sync(kFull, incl, o);
+        if (lane >= o) incl += v;
+    }
+    if (lane == 31) wsum[wid] = incl;
+    __syncthreads();
+    if (wid == 0) {
+        const int nw = blockDim.x >> 5;
+        int v = lane < nw ? wsum[lane] : 0;
+        for (int o = 1; o < 32; o <<= 1) {
+            int u = __shfl_up_sync(kFull, v, o);
+            if (lane >= o) v += u;
+        }
+        if (lane < nw) wsum[lane] = v;  // inclusive warp totals
+    }
+    __syncthreads();
+    int off = incl - c + (wid > 0 ? wsum[wid - 1] : 0);
+    for (int j = b; j < e; ++j) {
+        const int st = s.state[j];
+        if ((mode == 1) || st == ST_INIT || st == ST_TRIAL) s.list[off++] = j;
+    }
+    if (tid == blockDim.x - 1) *s.n_act = off;
+}
+
+// Trial point of each compact row: x_t = x + alpha p and dT = t_t - t = alpha p (2 x + alpha p)
+// (rows in INIT or DONE state are evaluated at x itself, dT = 0).  FP32 layout.
+__global__ void k_prep_fp32(SolverState s, float *__restrict__ Tc, float *__restrict__ dTc,
+                            float *__restrict__ Wc, int32_t force_base)
+{
+    const int i = blockIdx.x;
+    if (i >= *s.n_act) return;
+    const int j = s.list[i];
+    const bool trial = !force_base && s.state[j] == ST_TRIAL;
+    const float a = trial ? (float)s.alpha[j] : 0.0f;
+    const size_t pb = (size_t)j * s.nd_pad, cb = (size_t)i * s.nd_pad;
+    for (int l = threadIdx.x; l < s.nd_pad; l += blockDim.x) {
+        const float xv = s.x[pb + l];
+        float xt = xv, dt = 0.0f;
+        if (trial) {
+            const float ap = a * s.p[pb + l];
+            xt = xv + ap;
+            dt = ap * (2.0f * xv + ap);
+        }
+        s.xt[pb + l] = xt;
+        Tc[cb + l] = xt * xt;
+        if (dTc) dTc[cb + l] = dt;
+    }
+    if (threadIdx.x < s.n_struct)
+        Wc[(size_t)i * s.n_struct + threadIdx.x] = s.Wn[(size_t)j * s.n_struct + threadIdx.x];
+}
+
+// gt = 2 x_t * sum_split gpart (chain rule of t = x^2, Eq. (2)); Ft, dFt = fixed-order FP64
+// sums of the per-tile partials.
+__global__ void k_finish(SolverState s, EvalArgs e, int32_t n_ptiles)
+{
+    const int i = blockIdx.x;
+    if (i >= *e.n_rows) return;
+    const int j = s.list[i];
+    const int nd = s.nd_pad;
+    if (e.gpart) {
+        for (int l = threadIdx.x; l < nd; l += blockDim.x) {
+            float acc = 0.0f;
+            for (int q = 0; q < e.n_split; ++q) acc += e.gpart[((size_t)q * e.cap + i) * nd + l];
+            s.gt[(size_t)j * nd + l] = 2.0f * s.xt[(size_t)j * nd + l] * acc;
+        }
+    }
+    __shared__ double red[2][128];
+    double f = 0.0, df = 0.0;
+    for (int t = threadIdx.x; t < n_ptiles; t += blockDim.x) {
+        f += (double)e.Fpart[(size_t)t * e.cap + i];
+        if (e.dFpart) df += (double)e.dFpart[(size_t)t * e.cap + i];
+    }
+    red[0][threadIdx.x] = f;
+    red[1][threadIdx.x] = df;
+    __syncthreads();
+    for (int w = blockDim.x / 2; w > 0; w >>= 1) {
+        if (threadIdx.x < w) {
+            red[0][threadIdx.x] += red[0][threadIdx.x + w];
+            red[1][threadIdx.x] += red[1][threadIdx.x + w];
+        }
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) {
+        s.Ft[j] = red[0][0];
+        s.dFt[j] = red[1][0];
+    }
+}
+
+__device__ __forceinline__ void plan_done(const SolverState &s, int j, int status, int lane)
+{
+    if (lane == 0) {
+        s.state[j] = ST_DONE;
+        s.status[j] = status;
+    }
+}
+
+// Warp-per-plan update: Armijo acceptance, curvature pair, stop test, two-loop direction.
+template <int EPL>
+__global__ void __launch_bounds__(256) k_update(SolverState s, UpdateParams u)
+{
+    const int j = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int lane = threadIdx.x & 31;
+    if (j >= s.P) return;
+    const int st = s.state[j];
+    if (st != ST_INIT && st != ST_TRIAL) return;
+    const int nd = s.nd_pad, epl = nd >> 5, m = s.m;
+    const size_t vb = (size_t)j * nd;
+    float *x = s.x + vb, *g = s.g + vb, *p = s.p + vb;
+    const float *xt = s.xt + vb, *gt = s.gt + vb;
+
+    float gv[EPL];
+    float gmax = 0.0f;
+    int it = s.iters[j];
+    int cnt = s.hcount[j];
+    int nw = s.hnewest[j];
+    bool need_dir = false;
+
+    if (st == ST_INIT) {
+        const double F = s.Ft[j];
+        bool fin = isfinite(F);
+#pragma unroll
+        for (int e = 0; e < EPL; ++e) {
+            gv[e] = 0.0f;
+            if (e < epl) {
+                const int l = lane + 32 * e;
+                gv[e] = gt[l];
+                g[l] = gv[e];
+                fin = fin && isfinite(gv[e]);
+                gmax = fmaxf(gmax, fabsf(gv[e]));
+            }
+        }
+        fin = __all_sync(kFull, fin);
+        gmax = warp_max_f(gmax);
+        if (lane == 0) s.F[j] = F;
+        if (!fin) { plan_done(s, j, GMCO_PLAN_NONFINITE, lane); return; }
+        if (F == 0.0 || gmax == 0.0f) { plan_done(s, j, GMCO_PLAN_CONVERGED, lane); return; }
+        need_dir = true;
+    } else {
+        const double dF = s.dFt[j], Ft = s.Ft[j], alpha = s.alpha[j], gtp = s.gtp[j];
+        const bool ok = isfinite(dF) && isfinite(Ft) && dF <= u.c1 * alpha * gtp;
+        if (ok) {
+            float sv[EPL], yv[EPL];
+            double sy = 0.0, yy = 0.0;
+            bool fin = true;
+#pragma unroll
+            for (int e = 0; e < EPL; ++e) {
+                sv[e] = 0.0f;
+                yv[e] = 0.0f;
+                gv[e] = 0.0f;
+                if (e < epl) {
+                    const int l = lane + 32 * e;
+                    const float xo = x[l], xn = xt[l], go = g[l], gn = gt[l];
+                    sv[e] = xn - xo;
+                    yv[e] = gn - go;
+                    sy += (double)sv[e] * (double)yv[e];
+                    yy += (double)yv[e] * (double)yv[e];
+                    fin = fin && isfinite(gn);
+                    gmax = fmaxf(gmax, fabsf(gn));
+                    x[l] = xn;
+                    g[l] = gn;
+                    gv[e] = gn;
+                }
+            }
+            sy = warp_sum_d(sy);   // curvature products in FP64
+            yy = warp_sum_d(yy);
+            fin = __all_sync(kFull, fin);
+            gmax = warp_max_f(gmax);
+            if (fin && sy > 1e-12 * yy) {
+                nw = (nw + 1) % m;
+                float *Sd = s.S + ((size_t)j * m + nw) * nd;
+                float *Yd = s.Y + ((size_t)j * m + nw) * nd;
+#pragma unroll
+                for (int e = 0; e < EPL; ++e)
+                    if (e < epl) {
+                        Sd[lane + 32 * e] = sv[e];
+                        Yd[lane + 32 * e] = yv[e];
+                    }
+                cnt = min(cnt + 1, m);
+                if (lane == 0) {
+                    s.rho[(size_t)j * m + nw] = 1.0 / sy;
+                    s.gamma[j] = sy / yy;
+                }
+            }
+            const double Fprev = s.F[j];
+            ++it;
+            if (lane == 0) {
+                s.F[j] = Fprev + dF;
+                s.iters[j] = it;
+                s.hcount[j] = cnt;
+                s.hnewest[j] = nw;
+            }
+            if (!fin) { plan_done(s, j, GMCO_PLAN_NONFINITE, lane); return; }
+            if (Ft == 0.0 || gmax == 0.0f || fabs(dF) <= u.tol * fmax(fabs(Fprev), 1e-300)) {
+                plan_done(s, j, GMCO_PLAN_CONVERGED, lane);
+                return;
+            }
+            need_dir = true;
+        } else {
+            const int lsn = s.ls[j] + 1;
+            if (lsn >= u.max_ls) {
+                if (cnt > 0) {   // retry once along steepest descent with a fresh history
+                    cnt = 0;
+                    need_dir = true;
+#pragma unroll
+                    for (int e = 0; e < EPL; ++e) {
+                        gv[e] = 0.0f;
+                        if (e < epl) {
+                            gv[e] = g[lane + 32 * e];
+                            gmax = fmaxf(gmax, fabsf(gv[e]));
+                        }
+                    }
+                    gmax = warp_max_f(gmax);
+                    if (lane == 0) s.hcount[j] = 0;
+                } else {
+                    plan_done(s, j, GMCO_PLAN_LSFAIL, lane);
+                    return;
+                }
+            } else {
+                if (lane == 0) {
+                    s.alpha[j] = alpha * 0.5;
+                    s.ls[j] = lsn;
+                }
+                return;
+            }
+        }
+    }
+
+    if (!need_dir) return;
+    if (it >= s.maxit[j]) { plan_done(s, j, GMCO_PLAN_MAXITER, lane); return; }
+
+    // two-loop recursion, q in registers (FP32 vectors, FP32 dot products)
+    float q[EPL];
+#pragma unroll
+    for (int e = 0; e < EPL; ++e) q[e] = gv[e];
+    if (cnt > 0) {
+        float al[kMaxHist];
+#pragma unroll
+        for (int k = 0; k < kMaxHist; ++k) {
+            al[k] = 0.0f;
+            if (k < cnt) {
+                const int i = (nw - k + m) % m;
+                const float *Si = s.S + ((size_t)j * m + i) * nd;
+                const float *Yi = s.Y + ((size_t)j * m + i) * nd;
+                float d = 0.0f;
+#pragma unroll
+                for (int e = 0; e < EPL; ++e)
+                    if (e < epl) d += Si[lane + 32 * e] * q[e];
+                const float a = (float)s.rho[(size_t)j * m + i] * warp_sum_f(d);
+                al[k] = a;
+#pragma unroll
+                for (int e = 0; e < EPL; ++e)
+                    if (e < epl) q[e] -= a * Yi[lane + 32 * e];
+            }
+        }
+        const float gam = (float)s.gamma[j];
+#pragma unroll
+        for (int e = 0; e < EPL; ++e) q[e] *= gam;
+#pragma unroll
+        for (int k = kMaxHist - 1; k >= 0; --k) {
+            if (k < cnt) {
+                const int i = (nw - k + m) % m;
+                const float *Si = s.S + ((size_t)j * m + i) * nd;
+                const float *Yi = s.Y + ((size_t)j * m + i) * nd;
+                float d = 0.0f;
+#pragma unroll
+                for (int e = 0; e < EPL; ++e)
+                    if (e < epl) d += Yi[lane + 32 * e] * q[e];
+                const float b = (float)s.rho[(size_t)j * m + i] * warp_sum_f(d);
+#pragma unroll
+                for (int e = 0; e < EPL; ++e)
+                    if (e < epl) q[e] += Si[lane + 32 * e] * (al[k] - b);
+            }
+        }
+    }
+    double gtp = 0.0;
+#pragma unroll
+    for (int e = 0; e < EPL; ++e)
+        if (e < epl) gtp += (double)gv[e] * (double)(-q[e]);
+    gtp = warp_sum_d(gtp);   // directional derivative for the Armijo test, FP64
+    double alpha0 = (cnt == 0) ? fmin(1.0, 1.0 / (double)gmax) : 1.0;
+    if (!(gtp < 0.0)) {       // not a descent direction: steepest descent, fresh history
+        cnt = 0;
+        double gg = 0.0;
+#pragma unroll
+        for (int e = 0; e < EPL; ++e) {
+            q[e] = gv[e];
+            if (e < epl) gg += (double)gv[e] * (double)gv[e];
+        }
+        gtp = -warp_sum_d(gg);
+        alpha0 = fmin(1.0, 1.0 / (double)gmax);
+    }
+#pragma unroll
+    for (int e = 0; e < EPL; ++e)
+        if (e < epl) p[lane + 32 * e] = -q[e];
+    if (lane == 0) {
+        s.gtp[j] = gtp;
+        s.alpha[j] = alpha0;
+        s.ls[j] = 0;
+        s.hcount[j] = cnt;
+        s.state[j] = ST_TRIAL;
+    }
+}
+
+// Re-open finished plans for further iterations (FP32 refinement after a BF16/FP8 solve).
+__global__ void k_reopen(SolverState s, int32_t extra)
+{
+    const int j = blockIdx.x * blockDim.x + threadIdx.x;
+    if (j >= s.P) return;
+    if (s.state[j] == ST_DONE && s.status[j] != GMCO_PLAN_NONFINITE) {
+        s.state[j] = ST_INIT;
+        s.status[j] = GMCO_PLAN_MAXITER;
+        s.maxit[j] = s.iters[j] + extra;
+    }
+}
+
+__global__ void k_square(const float *__restrict__ x, float *__restrict__ t, int64_t rows,
+                         int64_t nd, int64_t nd_pad)
+{
+    const int64_t n = rows * nd;
+    for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < n;
+         k += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t r = k / nd, l = k - r * nd;
+        const float v = x[r * nd_pad + l];
+        t[k] = v * v;
+    }
+}
+
+}  // namespace
+
+cudaError_t launch_solver_init(const SolverState &s, const DevProblem &pb, const float *W,
+                               const float *t0, int32_t max_iters, cudaStream_t st)
+{
+    k_solver_init<<<s.P, 128, 0, st>>>(s, W, t0, pb.inv_count, (int32_t)pb.n_dwell, max_iters);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_compact(const SolverState &s, int32_t mode, cudaStream_t st)
+{
+    k_compact<<<1, 1024, 0, st>>>(s, mode);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_prep_fp32(const SolverState &s, const DevProblem &pb, float *Tc, float *dTc,
+                             float *Wc, bool force_base, cudaStream_t st)
+{
+    (void)pb;
+    k_prep_fp32<<<s.P, 128, 0, st>>>(s, Tc, dTc, Wc, force_base ? 1 : 0);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_finish(const SolverState &s, const EvalArgs &e, int32_t n_ptiles,
+                          cudaStream_t st)
+{
+    k_finish<<<s.P, 128, 0, st>>>(s, e, n_ptiles);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_update(const SolverState &s, const UpdateParams &u, cudaStream_t st)
+{
+    const int epl = s.nd_pad / 32;
+    const int blocks = (int)ceil_div((int64_t)s.P * 32, 256);
+    if (epl <= 4) k_update<4><<<blocks, 256, 0, st>>>(s, u);
+    else if (epl <= 8) k_update<8><<<blocks, 256, 0, st>>>(s, u);
+    else if (epl <= 12) k_update<12><<<blocks, 256, 0, st>>>(s, u);
+    else if (epl <= 16) k_update<16><<<blocks, 256, 0, st>>>(s, u);
+    else k_update<32><<<blocks, 256, 0, st>>>(s, u);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_reopen(const SolverState &s, int32_t extra_iters, cudaStream_t st)
+{
+    k_reopen<<<(int)ceil_div(s.P, 256), 256, 0, st>>>(s, extra_iters);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_square(const float *x, float *t, int64_t rows, int64_t nd, int64_t nd_pad,
+                          cudaStream_t st)
+{
+    const int64_t n = rows * nd;
+    const int blocks = (int)std::min<int64_t>(ceil_div(n, 256), 148 * 16);
+    if (n == 0) return cudaSuccess;
+    k_square<<<blocks, 256, 0, st>>>(x, t, rows, nd, nd_pad);
+    return cudaGetLastError();
+}
+
+}  // namespace gmco

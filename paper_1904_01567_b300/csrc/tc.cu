@@ -1,0 +1,805 @@
+// Tensor-core evaluation of Eq. (dose), Eq. (1), Eq. (obj) and Eq. (2) on sm_103a:
+// tcgen05.mma (kind::f16, BF16 operands, FP32 accumulators in TMEM), operands staged by TMA
+// (cp.async.bulk.tensor, 128-byte swizzle) through an mbarrier ring, one elected thread
+// issuing the MMAs, eight epilogue warps reading TMEM with tcgen05.ld.
+//
+// A row i of A is scaled by a power of two s_i (exact) and split into BF16 terms
+// A/s = A1 + A2 + A3; t and dF/dd are split the same way.  Products A_i T_j are exact in FP32,
+// and keeping the pairs with i + j <= n + 1 (n = number of terms) leaves an error of the
+// order of the last kept term: 2^-8 relative for one term, 2^-16 for two, 2^-24 for three.
+//
+// Dose GEMM (rows = plans, columns = points, K = dwells):
+//   acc0 = sum_{i,j} T_j A_i^T            -> d = s * acc0
+//   acc1 = sum_i dT A_i^T                 -> dd = s * acc1, the dose change of the step
+//   epilogue: Eq. (1) penalty, per-plan partial of F and of F(t) - F(t - dT) (factored, see
+//   eval_simt.cu), and G = s * dF/dd split into BF16 terms for the gradient GEMM.
+// Gradient GEMM (rows = plans, columns = dwells, K = points, split over point ranges):
+//   acc0 = sum_{i,j} G_j A_i               -> partial of A^T G, reduced by k_finish.
+#include <cuda.h>
+#include <cuda_bf16.h>
+#include <cuda_fp8.h>
+#include <cuda_runtime.h>
+#include <math.h>
+
+#include <algorithm>
+
+#include "tc.cuh"
+
+namespace gmco {
+
+namespace {
+
+constexpr int BM = 128;                 // plan rows per tile (TMEM lanes)
+constexpr int BK = 64;                  // K elements per stage: 128 bytes of BF16
+constexpr int A_TILE = BM * BK * 2;     // bytes of one A-operand tile
+constexpr int BN1 = 256;                // points per dose-GEMM tile
+constexpr int NTHREADS = 384;           // warps 0-7 epilogue, 8 TMA, 9 MMA, 10 TMEM owner
+constexpr int MAX_STAGES = 4;
+constexpr int SMEM_BUDGET = 208 * 1024;   // dynamic ring; static shared memory adds ~7 KB
+constexpr long long kSpinCycles = 2000000000LL;   // about 1 s at 2 GHz
+
+struct Group {
+    int32_t b_map, n_a;
+    int32_t a_map[4], acc[4];
+};
+
+struct Job {
+    int32_t n_groups;
+    Group g[3];
+    int32_t b_boxes, b_box_rows;
+    int32_t n_mma, n_part0, n_part1;
+    int32_t acc_cols, tmem_cols;
+    int32_t n_stages, stage_bytes, b_bytes;
+    int32_t b_row_step;
+    int32_t kb_step, kb_total;
+    int32_t k16_total;
+};
+
+struct EpiArgs {
+    const int32_t *n_rows;
+    int32_t cap;
+    int64_t np_pad;
+    // dose GEMM
+    const int8_t *sid;
+    const float *scale;
+    const float4 *sparams;
+    int32_t n_struct;
+    const float *Wc;
+    __nv_bfloat16 *G[3];
+    int32_t nG;
+    float *dose_out;
+    float *Fpart, *dFpart;
+    int32_t has_dT;
+    // gradient GEMM
+    float *gpart;
+    int32_t nd_pad, n_total;
+    int32_t *err;
+};
+
+// ------------------------------------------------------------------ PTX wrappers
+__device__ __forceinline__ uint32_t smem_u32(const void *p)
+{
+    return (uint32_t)__cvta_generic_to_shared(p);
+}
+
+__device__ __forceinline__ void mbar_init(uint32_t bar, uint32_t count)
+{
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar), "r"(count) : "memory");
+}
+
+__device__ __forceinline__ void mbar_expect_tx(uint32_t bar, uint32_t bytes)
+{
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes)
+                 : "memory");
+}
+
+__device__ __forceinline__ bool mbar_test(uint32_t bar, uint32_t parity)
+{
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.b32 %0, 1, 0, p;\n\t}"
+        : "=r"(ok)
+        : "r"(bar), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+
+// Waits for the phase with the given parity; gives up after about a second, records `code`
+// in *err and returns false so that the kernel can still wind down and free its TMEM.
+__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, int32_t *err, int code)
+{
+    if (mbar_test(bar, parity)) return true;
+    const long long t0 = clock64();
+    while (!mbar_test(bar, parity)) {
+        if (clock64() - t0 > kSpinCycles) {
+            atomicExch(err, code);
+            return false;
+        }
+    }
+    return true;
+}
+
+__device__ __forceinline__ void tma_load_2d(uint32_t dst, const CUtensorMap *map, int c0, int c1,
+                                            uint32_t bar)
+{
+    asm volatile(
+        "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes"
+        " [%0], [%1, {%2, %3}], [%4];" ::"r"(dst),
+        "l"((uint64_t)map), "r"(c0), "r"(c1), "r"(bar)
+        : "memory");
+}
+
+__device__ __forceinline__ void tmem_alloc(uint32_t holder, uint32_t ncols)
+{
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(holder),
+                 "r"(ncols)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+}
+
+__device__ __forceinline__ void tmem_dealloc(uint32_t taddr, uint32_t ncols)
+{
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(taddr), "r"(ncols)
+                 : "memory");
+}
+
+__device__ __forceinline__ void fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
+
+// Shared-memory matrix descriptor: K-major operand, 128-byte swizzle, 8-row atoms of
+// 1024 bytes (stride-dimension byte offset 1024), descriptor version 1.
+__device__ __forceinline__ uint64_t sw128_desc(uint32_t saddr)
+{
+    return (uint64_t)((saddr & 0x3FFFFu) >> 4) | ((uint64_t)1 << 16) |
+           ((uint64_t)(1024 >> 4) << 32) | ((uint64_t)1 << 46) | ((uint64_t)2 << 61);
+}
+
+// Instruction descriptor, kind::f16: FP32 accumulator, BF16 A and B, both K-major, M = 128.
+__device__ __forceinline__ uint32_t idesc_bf16(int n)
+{
+    return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(n >> 3) << 17) |
+           ((uint32_t)(BM >> 4) << 24);
+}
+
+__device__ __forceinline__ void mma_bf16(uint32_t d, uint64_t a, uint64_t b, uint32_t idesc,
+                                         uint32_t accum)
+{
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "setp.ne.b32 p, %4, 0;\n\t"
+        "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(d),
+        "l"(a), "l"(b), "r"(idesc), "r"(accum)
+        : "memory");
+}
+
+__device__ __forceinline__ void mma_commit(uint32_t bar)
+{
+    asm volatile(
+        "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar)
+        : "memory");
+}
+
+__device__ __forceinline__ void tmem_ld16(uint32_t taddr, uint32_t (&r)[16])
+{
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x16.b32 "
+        "{%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
+          "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]),
+          "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+        : "r"(taddr));
+}
+
+__device__ __forceinline__ void tmem_ld_wait() { asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory"); }
+
+// ------------------------------------------------------------------ penalty (Eq. (1))
+__device__ __forceinline__ void penalty(float d, float4 prm, float c, float &f, float &df)
+{
+    const float u = prm.y - d, o = d - prm.z;
+    f = 0.0f;
+    df = 0.0f;
+    if (u > 0.0f) {
+        f = c * prm.x * u * u;
+        df = -2.0f * c * prm.x * u;
+    } else if (o > 0.0f) {
+        f = c * prm.w * o * o;
+        df = 2.0f * c * prm.w * o;
+    }
+}
+
+__device__ __forceinline__ float penalty_delta(float dt, float dd, float4 prm, float c)
+{
+    const float db = dt - dd;
+    float lo = 0.0f, up = 0.0f;
+    const float ut = prm.y - dt, ub = prm.y - db;
+    if (ut > 0.0f && ub > 0.0f) lo = -dd * (ut + ub);
+    else if (ut > 0.0f) lo = ut * ut;
+    else if (ub > 0.0f) lo = -ub * ub;
+    const float ot = dt - prm.z, ob = db - prm.z;
+    if (ot > 0.0f && ob > 0.0f) up = dd * (ot + ob);
+    else if (ot > 0.0f) up = ot * ot;
+    else if (ob > 0.0f) up = -ob * ob;
+    return c * (prm.x * lo + prm.w * up);
+}
+
+__device__ __forceinline__ uint32_t pack_bf16(float a, float b)
+{
+    const __nv_bfloat162 v = __floats2bfloat162_rn(a, b);
+    return *reinterpret_cast<const uint32_t *>(&v);
+}
+
+// ------------------------------------------------------------------ the GEMM kernel
+template <int KIND>   // 1: dose GEMM with penalty epilogue, 2: gradient GEMM
+__global__ void __launch_bounds__(NTHREADS, 1)
+    k_tc(const __grid_constant__ TcMaps maps, const Job job, const EpiArgs ep)
+{
+    extern __shared__ uint8_t smem_raw[];
+    uint8_t *smem = reinterpret_cast<uint8_t *>(
+        (reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~static_cast<uintptr_t>(1023));
+    __shared__ __align__(8) uint64_t full_bar[MAX_STAGES], empty_bar[MAX_STAGES], acc_bar;
+    __shared__ uint32_t tmem_holder;
+    __shared__ int8_t s_sid[BN1];
+    __shared__ float s_scale[BN1];
+    __shared__ float4 s_prm[8];
+    __shared__ float s_w[BM][8];
+    __shared__ float s_half[2][BM];
+
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int n_rows = *ep.n_rows;
+    const int row0 = blockIdx.y * BM;
+    if (row0 >= n_rows) return;   // the whole CTA leaves before any barrier or TMEM use
+
+    int kb0 = 0, kb1 = job.kb_total;
+    if (job.kb_step > 0) {
+        kb0 = blockIdx.x * job.kb_step;
+        kb1 = min(kb0 + job.kb_step, job.kb_total);
+    }
+    const int b_row0 = blockIdx.x * job.b_row_step;
+
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < job.n_stages; ++s) {
+            mbar_init(smem_u32(&full_bar[s]), 1);
+            mbar_init(smem_u32(&empty_bar[s]), 1);
+        }
+        mbar_init(smem_u32(&acc_bar), 1);
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    if (warp == 10) tmem_alloc(smem_u32(&tmem_holder), (uint32_t)job.tmem_cols);
+    if (KIND == 1 && threadIdx.x < 256) {
+        const int i = threadIdx.x;
+        const int64_t p = (int64_t)b_row0 + i;
+        s_sid[i] = p < ep.np_pad ? ep.sid[p] : (int8_t)-1;
+        s_scale[i] = p < ep.np_pad ? ep.scale[p] : 0.0f;
+        if (i < ep.n_struct) s_prm[i] = ep.sparams[i];
+        if (i < BM) {
+            const int row = row0 + i;
+            for (int s = 0; s < ep.n_struct; ++s)
+                s_w[i][s] = row < n_rows ? ep.Wc[(size_t)row * ep.n_struct + s] : 0.0f;
+        }
+    }
+    fence_before();
+    __syncthreads();
+    fence_after();
+    const uint32_t tmem = tmem_holder;
+
+    if (warp == 8) {
+        // ---------------- TMA producer
+        if (lane == 0) {
+            int it = 0;
+            bool ok = true;
+            for (int gi = 0; gi < job.n_groups && ok; ++gi) {
+                const Group &g = job.g[gi];
+                for (int kb = kb0; kb < kb1; ++kb, ++it) {
+                    const int s = it % job.n_stages;
+                    const uint32_t ph = (uint32_t)(it / job.n_stages) & 1u;
+                    if (!mbar_wait(smem_u32(&empty_bar[s]), ph ^ 1u, ep.err, 1)) { ok = false; break; }
+                    uint8_t *st = smem + (size_t)s * job.stage_bytes;
+                    const uint32_t fb = smem_u32(&full_bar[s]);
+                    mbar_expect_tx(fb, (uint32_t)(job.b_bytes + g.n_a * A_TILE));
+                    for (int b = 0; b < job.b_boxes; ++b)
+                        tma_load_2d(smem_u32(st + b * job.b_box_rows * 128), &maps.m[g.b_map],
+                                    kb * BK, b_row0 + b * job.b_box_rows, fb);
+                    for (int t = 0; t < g.n_a; ++t)
+                        tma_load_2d(smem_u32(st + job.b_bytes + t * A_TILE), &maps.m[g.a_map[t]],
+                                    kb * BK, row0, fb);
+                }
+            }
+        }
+    } else if (warp == 9) {
+        // ---------------- MMA issuer (one thread)
+        if (lane == 0) {
+            int it = 0;
+            bool started[2] = {false, false};
+            bool ok = true;
+            for (int gi = 0; gi < job.n_groups && ok; ++gi) {
+                const Group &g = job.g[gi];
+                for (int kb = kb0; kb < kb1; ++kb, ++it) {
+                    const int s = it % job.n_stages;
+                    const uint32_t ph = (uint32_t)(it / job.n_stages) & 1u;
+                    if (!mbar_wait(smem_u32(&full_bar[s]), ph, ep.err, 2)) { ok = false; break; }
+                    fence_after();
+                    const uint32_t st = smem_u32(smem + (size_t)s * job.stage_bytes);
+                    const int k16n = KIND == 1 ? min(4, job.k16_total - kb * 4) : 4;
+                    for (int k16 = 0; k16 < k16n; ++k16) {
+                        for (int t = 0; t < g.n_a; ++t) {
+                            const uint64_t ad = sw128_desc(st + job.b_bytes + t * A_TILE + k16 * 32);
+                            const int acc = g.acc[t];
+                            const uint32_t accum = started[acc] ? 1u : 0u;
+                            mma_bf16(tmem + (uint32_t)(acc * job.acc_cols), ad,
+                                     sw128_desc(st + k16 * 32), idesc_bf16(job.n_part0), accum);
+                            if (job.n_mma > 1)
+                                mma_bf16(tmem + (uint32_t)(acc * job.acc_cols + job.n_part0), ad,
+                                         sw128_desc(st + job.n_part0 * 128 + k16 * 32),
+                                         idesc_bf16(job.n_part1), accum);
+                            started[acc] = true;
+                        }
+                    }
+                    mma_commit(smem_u32(&empty_bar[s]));   // stage free once these MMAs finish
+                }
+            }
+            mma_commit(smem_u32(&acc_bar));
+        }
+    } else if (warp < 8) {
+        // ---------------- epilogue: TMEM lane quarter q, column half h
+        const int q = warp & 3, h = warp >> 2;
+        const int r = q * 32 + lane;
+        const int row = row0 + r;
+        const bool valid = row < n_rows;
+        const uint32_t lane_addr = tmem + ((uint32_t)(q * 32) << 16);
+        const bool ok = mbar_wait(smem_u32(&acc_bar), 0u, ep.err, 3);
+        fence_after();
+        if (KIND == 1) {
+            float fsum = 0.0f, dfsum = 0.0f;
+            if (ok) {
+                for (int c = h * (BN1 / 2); c < (h + 1) * (BN1 / 2); c += 16) {
+                    uint32_t dv[16], ddv[16];
+                    tmem_ld16(lane_addr + (uint32_t)c, dv);
+                    if (ep.has_dT) tmem_ld16(lane_addr + (uint32_t)(job.acc_cols + c), ddv);
+                    tmem_ld_wait();
+                    float out[16];
+#pragma unroll
+                    for (int i = 0; i < 16; ++i) {
+                        const int sv = s_sid[c + i];
+                        const float sc = s_scale[c + i];
+                        const float d = sc * __uint_as_float(dv[i]);
+                        out[i] = 0.0f;
+                        if (sv >= 0) {
+                            const float4 prm = s_prm[sv];
+                            const float cw = s_w[r][sv];
+                            float f, df;
+                            penalty(d, prm, cw, f, df);
+                            fsum += f;
+                            out[i] = ep.dose_out ? d : df * sc;
+                            if (ep.has_dT)
+                                dfsum += penalty_delta(d, sc * __uint_as_float(ddv[i]), prm, cw);
+                        }
+                    }
+                    if (valid) {
+                        const size_t off = (size_t)row * ep.np_pad + b_row0 + c;
+                        if (ep.dose_out) {
+                            float4 *o = reinterpret_cast<float4 *>(ep.dose_out + off);
+#pragma unroll
+                            for (int v = 0; v < 4; ++v)
+                                o[v] = make_float4(out[4 * v], out[4 * v + 1], out[4 * v + 2],
+                                                   out[4 * v + 3]);
+                        } else {
+                            for (int j = 0; j < ep.nG; ++j) {
+                                uint32_t pk[8];
+#pragma unroll
+                                for (int v = 0; v < 8; ++v) {
+                                    const __nv_bfloat16 a = __float2bfloat16_rn(out[2 * v]);
+                                    const __nv_bfloat16 b = __float2bfloat16_rn(out[2 * v + 1]);
+                                    pk[v] = pack_bf16(__bfloat162float(a), __bfloat162float(b));
+                                    out[2 * v] -= __bfloat162float(a);
+                                    out[2 * v + 1] -= __bfloat162float(b);
+                                }
+                                uint4 *o = reinterpret_cast<uint4 *>(ep.G[j] + off);
+                                o[0] = make_uint4(pk[0], pk[1], pk[2], pk[3]);
+                                o[1] = make_uint4(pk[4], pk[5], pk[6], pk[7]);
+                            }
+                        }
+                    }
+                }
+            }
+            if (h == 1) {
+                s_half[0][r] = fsum;
+                s_half[1][r] = dfsum;
+            }
+            asm volatile("bar.sync 1, 256;" ::: "memory");
+            if (h == 0 && valid) {
+                ep.Fpart[(size_t)blockIdx.x * ep.cap + row] = fsum + s_half[0][r];
+                if (ep.dFpart) ep.dFpart[(size_t)blockIdx.x * ep.cap + row] = dfsum + s_half[1][r];
+            }
+        } else {
+            const int nch = ep.n_total / 16;
+            const int c_beg = h == 0 ? 0 : (nch + 1) / 2;
+            const int c_end = h == 0 ? (nch + 1) / 2 : nch;
+            float *out = ep.gpart + ((size_t)blockIdx.x * ep.cap + row) * ep.nd_pad;
+            if (ok) {
+                for (int ch = c_beg; ch < c_end; ++ch) {
+                    uint32_t v[16];
+                    tmem_ld16(lane_addr + (uint32_t)(ch * 16), v);
+                    tmem_ld_wait();
+                    if (valid) {
+                        float4 *o = reinterpret_cast<float4 *>(out + ch * 16);
+#pragma unroll
+                        for (int k = 0; k < 4; ++k)
+                            o[k] = make_float4(__uint_as_float(v[4 * k]), __uint_as_float(v[4 * k + 1]),
+                                               __uint_as_float(v[4 * k + 2]),
+                                               __uint_as_float(v[4 * k + 3]));
+                    }
+                }
+            }
+            if (h == 1 && valid)
+                for (int c = ep.n_total; c < ep.nd_pad; ++c) out[c] = 0.0f;
+        }
+    }
+    fence_before();
+    __syncthreads();
+    if (warp == 10) {
+        fence_after();
+        tmem_dealloc(tmem, (uint32_t)job.tmem_cols);
+    }
+}
+
+// ------------------------------------------------------------------ operand preparation
+// Row scale (power of two, so that A / s is exact) and the BF16 split terms of A / s; for the
+// E4M3 form the single term is A / s rounded to E4M3 (stored as BF16, exactly).
+__global__ void k_split_A(const float *__restrict__ A32, int64_t nd, int64_t nd_pad, int64_t kpad,
+                          int32_t terms, int32_t fp8, float *__restrict__ scale,
+                          __nv_bfloat16 *A1, __nv_bfloat16 *A2, __nv_bfloat16 *A3)
+{
+    const int64_t row = blockIdx.x;
+    const float *a = A32 + row * nd_pad;
+    __shared__ float red[128];
+    float mx = 0.0f;
+    for (int64_t l = threadIdx.x; l < nd; l += blockDim.x) mx = fmaxf(mx, a[l]);
+    red[threadIdx.x] = mx;
+    __syncthreads();
+    for (int w = 64; w > 0; w >>= 1) {
+        if ((int)threadIdx.x < w) red[threadIdx.x] = fmaxf(red[threadIdx.x], red[threadIdx.x + w]);
+        __syncthreads();
+    }
+    mx = red[0];
+    float s = 1.0f;
+    if (mx > 0.0f) s = exp2f(ceilf(log2f(fp8 ? mx / 448.0f : mx)));
+    if (threadIdx.x == 0) scale[row] = s;
+    for (int64_t l = threadIdx.x; l < kpad; l += blockDim.x) {
+        const float v = l < nd ? a[l] / s : 0.0f;   // exact: s is a power of two
+        const size_t o = (size_t)row * kpad + l;
+        if (fp8) {
+            const __nv_fp8_e4m3 q(v);
+            A1[o] = __float2bfloat16_rn(float(q));
+            continue;
+        }
+        const __nv_bfloat16 t1 = __float2bfloat16_rn(v);
+        A1[o] = t1;
+        const float r1 = v - __bfloat162float(t1);
+        if (terms > 1) {
+            const __nv_bfloat16 t2 = __float2bfloat16_rn(r1);
+            A2[o] = t2;
+            if (terms > 2) A3[o] = __float2bfloat16_rn(r1 - __bfloat162float(t2));
+        }
+    }
+}
+
+__global__ void k_transpose_bf16(const __nv_bfloat16 *__restrict__ in, int64_t rows, int64_t cols,
+                                 __nv_bfloat16 *__restrict__ out)
+{
+    __shared__ __nv_bfloat16 tile[32][33];
+    const int64_t c0 = blockIdx.x * 32, r0 = blockIdx.y * 32;
+    for (int k = threadIdx.y; k < 32; k += blockDim.y) {
+        const int64_t r = r0 + k, c = c0 + threadIdx.x;
+        tile[k][threadIdx.x] = (r < rows && c < cols) ? in[r * cols + c] : __float2bfloat16_rn(0.0f);
+    }
+    __syncthreads();
+    for (int k = threadIdx.y; k < 32; k += blockDim.y) {
+        const int64_t c = c0 + k, r = r0 + threadIdx.x;
+        if (c < cols && r < rows) out[c * rows + r] = tile[threadIdx.x][k];
+    }
+}
+
+// Trial point of each compact row, as in k_prep_fp32, written as BF16 split terms of t and
+// one BF16 term of dT.
+__global__ void k_prep_tc(SolverState s, TcBuffers b, int32_t nT, int64_t kpad, int32_t force_base)
+{
+    const int i = blockIdx.x;
+    if (i >= *s.n_act) return;
+    const int j = s.list[i];
+    const bool trial = !force_base && s.state[j] == ST_TRIAL;
+    const float a = trial ? (float)s.alpha[j] : 0.0f;
+    const size_t pb = (size_t)j * s.nd_pad, cb = (size_t)i * kpad;
+    for (int64_t l = threadIdx.x; l < kpad; l += blockDim.x) {
+        float t = 0.0f, dt = 0.0f;
+        if (l < s.nd_pad) {
+            const float xv = s.x[pb + l];
+            float xt = xv;
+            if (trial) {
+                const float ap = a * s.p[pb + l];
+                xt = xv + ap;
+                dt = ap * (2.0f * xv + ap);
+            }
+            s.xt[pb + l] = xt;
+            t = xt * xt;
+        }
+        const __nv_bfloat16 t1 = __float2bfloat16_rn(t);
+        b.T[0][cb + l] = t1;
+        const float r1 = t - __bfloat162float(t1);
+        if (nT > 1) {
+            const __nv_bfloat16 t2 = __float2bfloat16_rn(r1);
+            b.T[1][cb + l] = t2;
+            if (nT > 2) b.T[2][cb + l] = __float2bfloat16_rn(r1 - __bfloat162float(t2));
+        }
+        b.dT[cb + l] = __float2bfloat16_rn(dt);
+    }
+    if (threadIdx.x < s.n_struct)
+        b.Wc[(size_t)i * s.n_struct + threadIdx.x] = s.Wn[(size_t)j * s.n_struct + threadIdx.x];
+}
+
+// ------------------------------------------------------------------ host helpers
+// cuTensorMapEncodeTiled is resolved through the runtime's driver entry-point query, so the
+// library does not link libcuda directly (it still needs the driver at run time).
+using EncodeTiledFn = CUresult (*)(CUtensorMap *, CUtensorMapDataType, cuuint32_t, void *,
+                                   const cuuint64_t *, const cuuint64_t *, const cuuint32_t *,
+                                   const cuuint32_t *, CUtensorMapInterleave, CUtensorMapSwizzle,
+                                   CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+EncodeTiledFn encode_fn()
+{
+    static EncodeTiledFn fn = nullptr;
+    if (!fn) {
+        void *p = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault,
+                                             &q) == cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = reinterpret_cast<EncodeTiledFn>(p);
+    }
+    return fn;
+}
+
+bool encode_map(CUtensorMap *m, const void *ptr, uint64_t cols, uint64_t rows,
+                uint32_t box_cols, uint32_t box_rows)
+{
+    cuuint64_t dims[2] = {cols, rows};
+    cuuint64_t strides[1] = {cols * 2};
+    cuuint32_t box[2] = {box_cols, box_rows};
+    cuuint32_t es[2] = {1, 1};
+    EncodeTiledFn enc = encode_fn();
+    if (!enc) return false;
+    return enc(m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<void *>(ptr),
+                                  dims, strides, box, es, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                                  CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                                  CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
+int n_t_terms(const DevProblem &pb) { return std::max(pb.tc_terms, 2); }
+
+// pairs (i, j) of split terms kept in a product: i + j <= max(nA, nB) + 1 (1-based)
+bool keep_pair(int i, int j, int nA, int nB) { return (i + 1) + (j + 1) <= std::max(nA, nB) + 1; }
+
+int tmem_cols_for(int cols)
+{
+    int c = 32;
+    while (c < cols) c <<= 1;
+    return c;
+}
+
+void finish_stages(Job &job, int max_a)
+{
+    job.stage_bytes = job.b_bytes + max_a * A_TILE;
+    job.n_stages = std::max(1, std::min(MAX_STAGES, SMEM_BUDGET / job.stage_bytes));
+}
+
+Job make_dose_job(const DevProblem &pb, bool with_dT)
+{
+    Job job{};
+    const int nA = pb.tc_terms, nT = n_t_terms(pb);
+    int max_a = 0;
+    job.n_groups = nA;
+    for (int i = 0; i < nA; ++i) {
+        Group &g = job.g[i];
+        g.b_map = i;
+        g.n_a = 0;
+        for (int j = 0; j < nT; ++j)
+            if (keep_pair(i, j, nA, nT)) {
+                g.a_map[g.n_a] = 3 + j;
+                g.acc[g.n_a++] = 0;
+            }
+        if (with_dT) {
+            g.a_map[g.n_a] = 6;
+            g.acc[g.n_a++] = 1;
+        }
+        max_a = std::max(max_a, g.n_a);
+    }
+    job.b_boxes = 1;
+    job.b_box_rows = BN1;
+    job.n_mma = 1;
+    job.n_part0 = BN1;
+    job.n_part1 = 0;
+    job.acc_cols = BN1;
+    job.tmem_cols = with_dT ? 2 * BN1 : BN1;
+    job.b_bytes = BN1 * 128;
+    finish_stages(job, max_a);
+    job.b_row_step = BN1;
+    job.kb_step = 0;
+    job.kb_total = (int32_t)(pb.kpad / BK);
+    job.k16_total = (int32_t)(round_up(pb.n_dwell, 16) / 16);
+    return job;
+}
+
+Job make_grad_job(const DevProblem &pb, const TcBuffers &b)
+{
+    Job job{};
+    const int nA = pb.tc_terms, nG = n_t_terms(pb);
+    int max_a = 0;
+    job.n_groups = nA;
+    for (int i = 0; i < nA; ++i) {
+        Group &g = job.g[i];
+        g.b_map = i;
+        g.n_a = 0;
+        for (int j = 0; j < nG; ++j)
+            if (keep_pair(i, j, nA, nG)) {
+                g.a_map[g.n_a] = 3 + j;
+                g.acc[g.n_a++] = 0;
+            }
+        max_a = std::max(max_a, g.n_a);
+    }
+    const int n16 = (int)round_up(pb.n_dwell, 16);
+    job.n_mma = n16 > 256 ? 2 : 1;
+    job.n_part0 = job.n_mma == 1 ? n16 : (int)round_up(ceil_div(n16, 2), 16);
+    job.n_part1 = n16 - job.n_part0;
+    job.b_boxes = (int)ceil_div(n16, 256);
+    job.b_box_rows = (int)round_up(ceil_div(n16, job.b_boxes), 8);
+    job.acc_cols = 0;
+    job.tmem_cols = tmem_cols_for(n16);
+    job.b_bytes = job.b_boxes * job.b_box_rows * 128;
+    finish_stages(job, max_a);
+    job.b_row_step = 0;
+    job.kb_step = b.kbps;
+    job.kb_total = (int32_t)(pb.np_pad / BK);
+    job.k16_total = job.kb_total * 4;
+    return job;
+}
+
+size_t dyn_smem(const Job &job) { return (size_t)job.n_stages * job.stage_bytes + 1024; }
+
+}  // namespace
+
+int32_t tc_n_ptiles(const DevProblem &pb) { return (int32_t)(pb.np_pad / BN1); }
+int32_t tc_max_split(const DevProblem &pb) { return (int32_t)std::min<int64_t>(148, pb.np_pad / BK); }
+int64_t tc_launches_per_eval() { return 4; }
+
+cudaError_t tc_prepare_problem(DevProblem *pb, int precision, cudaStream_t st,
+                               const AllocFn &alloc)
+{
+    if (pb->n_dwell > 384 || pb->n_struct > 8) return cudaErrorNotSupported;
+    const int terms = precision == GMCO_PREC_BF16X3 ? 3 : precision == GMCO_PREC_BF16X2 ? 2 : 1;
+    pb->tc_terms = terms;
+    pb->kpad = round_up(pb->n_dwell, 64);
+    const size_t n = (size_t)pb->np_pad * pb->kpad;
+    for (int i = 0; i < terms; ++i) {
+        cudaError_t e = alloc(reinterpret_cast<void **>(&pb->Ah[i]), n * sizeof(__nv_bfloat16));
+        if (e != cudaSuccess) return e;
+        e = alloc(reinterpret_cast<void **>(&pb->AhT[i]), n * sizeof(__nv_bfloat16));
+        if (e != cudaSuccess) return e;
+    }
+    k_split_A<<<(unsigned)pb->np_pad, 128, 0, st>>>(pb->A32, pb->n_dwell, pb->nd_pad, pb->kpad,
+                                                    terms, precision == GMCO_PREC_FP8 ? 1 : 0,
+                                                    pb->row_scale, pb->Ah[0], pb->Ah[1], pb->Ah[2]);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    for (int i = 0; i < terms; ++i) {
+        dim3 grid((unsigned)ceil_div(pb->kpad, 32), (unsigned)ceil_div(pb->np_pad, 32));
+        k_transpose_bf16<<<grid, dim3(32, 8), 0, st>>>(pb->Ah[i], pb->np_pad, pb->kpad, pb->AhT[i]);
+        e = cudaGetLastError();
+        if (e != cudaSuccess) return e;
+    }
+    static bool attr_set = false;
+    if (!attr_set) {
+        e = cudaFuncSetAttribute(k_tc<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_BUDGET + 1024);
+        if (e != cudaSuccess) return e;
+        e = cudaFuncSetAttribute(k_tc<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_BUDGET + 1024);
+        if (e != cudaSuccess) return e;
+        attr_set = true;
+    }
+    return cudaSuccess;
+}
+
+cudaError_t tc_alloc(const DevProblem &pb, int32_t cap, TcBuffers *b, const AllocFn &alloc)
+{
+    *b = TcBuffers{};
+    b->cap = cap;
+    const int nT = n_t_terms(pb);
+    const size_t tn = (size_t)cap * pb.kpad, gn = (size_t)cap * pb.np_pad;
+    cudaError_t e;
+    for (int j = 0; j < nT; ++j) {
+        if ((e = alloc(reinterpret_cast<void **>(&b->T[j]), tn * 2)) != cudaSuccess) return e;
+        if ((e = alloc(reinterpret_cast<void **>(&b->G[j]), gn * 2)) != cudaSuccess) return e;
+    }
+    if ((e = alloc(reinterpret_cast<void **>(&b->dT), tn * 2)) != cudaSuccess) return e;
+    if ((e = alloc(reinterpret_cast<void **>(&b->Wc), (size_t)cap * pb.n_struct * 4)) != cudaSuccess)
+        return e;
+    if ((e = alloc(reinterpret_cast<void **>(&b->err), 4)) != cudaSuccess) return e;
+    if ((e = cudaMemset(b->err, 0, 4)) != cudaSuccess) return e;
+    // point splits of the gradient GEMM: about one CTA per SM in total
+    const int64_t kb_total = pb.np_pad / BK;
+    const int64_t plan_tiles = ceil_div(cap, BM);
+    const int64_t target = std::max<int64_t>(1, 148 / plan_tiles);
+    b->kbps = (int32_t)ceil_div(kb_total, target);
+    b->n_split = (int32_t)ceil_div(kb_total, b->kbps);
+    // tensor maps
+    const int nA = pb.tc_terms;
+    const int n16 = (int)round_up(pb.n_dwell, 16);
+    const int boxes = (int)ceil_div(n16, 256);
+    const uint32_t box_rows2 = (uint32_t)round_up(ceil_div(n16, boxes), 8);
+    bool ok = true;
+    for (int i = 0; i < nA; ++i) {
+        ok = ok && encode_map(&b->maps1.m[i], pb.Ah[i], pb.kpad, pb.np_pad, BK, BN1);
+        ok = ok && encode_map(&b->maps2.m[i], pb.AhT[i], pb.np_pad, pb.kpad, BK, box_rows2);
+    }
+    for (int j = 0; j < nT; ++j) {
+        ok = ok && encode_map(&b->maps1.m[3 + j], b->T[j], pb.kpad, cap, BK, BM);
+        ok = ok && encode_map(&b->maps2.m[3 + j], b->G[j], pb.np_pad, cap, BK, BM);
+    }
+    ok = ok && encode_map(&b->maps1.m[6], b->dT, pb.kpad, cap, BK, BM);
+    return ok ? cudaSuccess : cudaErrorInvalidValue;
+}
+
+cudaError_t tc_launch_eval(const DevProblem &pb, const SolverState &s, const TcBuffers &b,
+                           float *Fpart, float *dFpart, float *gpart, int32_t cap, bool with_dT,
+                           float *dose_out, bool force_base, cudaStream_t st, int32_t *n_launches)
+{
+    int nl = 0;
+    k_prep_tc<<<cap, 128, 0, st>>>(s, b, n_t_terms(pb), pb.kpad, force_base ? 1 : 0);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    ++nl;
+    EpiArgs ep{};
+    ep.n_rows = s.n_act;
+    ep.cap = cap;
+    ep.np_pad = pb.np_pad;
+    ep.sid = pb.sid;
+    ep.scale = pb.row_scale;
+    ep.sparams = pb.sparams;
+    ep.n_struct = pb.n_struct;
+    ep.Wc = b.Wc;
+    for (int j = 0; j < 3; ++j) ep.G[j] = b.G[j];
+    ep.nG = n_t_terms(pb);
+    ep.dose_out = dose_out;
+    ep.Fpart = Fpart;
+    ep.dFpart = with_dT ? dFpart : nullptr;
+    ep.has_dT = with_dT ? 1 : 0;
+    ep.gpart = gpart;
+    ep.nd_pad = (int32_t)pb.nd_pad;
+    ep.n_total = (int32_t)round_up(pb.n_dwell, 16);
+    ep.err = b.err;
+    const Job j1 = make_dose_job(pb, with_dT);
+    dim3 g1((unsigned)(pb.np_pad / BN1), (unsigned)ceil_div(cap, BM));
+    k_tc<1><<<g1, NTHREADS, dyn_smem(j1), st>>>(b.maps1, j1, ep);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    ++nl;
+    if (!dose_out) {
+        const Job j2 = make_grad_job(pb, b);
+        dim3 g2((unsigned)b.n_split, (unsigned)ceil_div(cap, BM));
+        k_tc<2><<<g2, NTHREADS, dyn_smem(j2), st>>>(b.maps2, j2, ep);
+        if ((e = cudaGetLastError()) != cudaSuccess) return e;
+        ++nl;
+    }
+    EvalArgs fe{};
+    fe.pb = pb;
+    fe.n_rows = s.n_act;
+    fe.cap = cap;
+    fe.Fpart = Fpart;
+    fe.dFpart = with_dT ? dFpart : nullptr;
+    fe.gpart = dose_out ? nullptr : gpart;
+    fe.n_split = b.n_split;
+    if ((e = launch_finish(s, fe, tc_n_ptiles(pb), st)) != cudaSuccess) return e;
+    ++nl;
+    *n_launches = nl;
+    return cudaSuccess;
+}
+
+}  // namespace gmco

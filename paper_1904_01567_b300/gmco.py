@@ -1,0 +1,267 @@
+"""Thin ctypes binding of libgmco.so (include/gmco.h).  Argument marshalling only.
+
+Functions carry the C names without the ``gmco_`` prefix.  Arrays may be numpy arrays
+(host memory) or torch tensors (host or CUDA memory); outputs are allocated where the
+inputs live (torch CUDA tensors on the current device, numpy arrays otherwise).  Every
+computation runs in the CUDA library: there is no CPU fallback, and a missing or unloadable
+library raises at first use.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libgmco.so")
+
+PREC = {"fp32": 0, "bf16": 1, "fp8": 2, "bf16x2": 3, "bf16x3": 4}
+PLAN_STATUS = {0: "converged", 1: "maxiter", 2: "lsfail", 3: "nonfinite"}
+DVH_K = 5
+DVH_NAMES = ("V100_pct", "D90_pct_rx", "urethra_D10_pct_rx", "rectum_V75_pct", "bladder_V75_pct")
+
+OK, EINVAL, ENOMEM, ECUDA, ETIMEOUT, EUNSUPPORTED = 0, 1, 2, 3, 4, 5
+
+
+class GmcoError(RuntimeError):
+    def __init__(self, status, where, detail=""):
+        super().__init__(f"{where}: {status_string(status)} ({status}) {detail}".strip())
+        self.status = status
+
+
+class _Options(ctypes.Structure):
+    _fields_ = [("precision", ctypes.c_int32), ("m", ctypes.c_int32), ("c1", ctypes.c_double),
+                ("max_ls", ctypes.c_int32), ("rx_gy", ctypes.c_double),
+                ("refine_iters", ctypes.c_int32), ("steps_per_poll", ctypes.c_int32)]
+
+
+_lib = None
+_vp = ctypes.c_void_p
+_i64 = ctypes.c_int64
+_i32 = ctypes.c_int32
+
+
+def load():
+    """Loads libgmco.so (built in-tree by paper_1904_01567_b300.build)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError(f"{LIB_PATH} is missing: run python -m paper_1904_01567_b300.build")
+        lib = ctypes.CDLL(LIB_PATH)
+        lib.gmco_default_options.argtypes = [ctypes.POINTER(_Options)]
+        lib.gmco_default_options.restype = None
+        lib.gmco_create_problem.argtypes = [_vp, _i64, _i64, _vp, _i32, _vp,
+                                            ctypes.POINTER(_Options), ctypes.POINTER(_vp)]
+        lib.gmco_create_problem.restype = ctypes.c_int
+        lib.gmco_destroy_problem.argtypes = [_vp]
+        lib.gmco_destroy_problem.restype = None
+        lib.gmco_solve_batch.argtypes = [_vp, _vp, _i64, _vp, _i32, ctypes.c_double, _vp, _vp,
+                                         _vp, _vp, _vp, _vp]
+        lib.gmco_solve_batch.restype = ctypes.c_int
+        lib.gmco_evaluate.argtypes = [_vp, _vp, _i64, _vp, _vp, _vp, _vp, _vp, _vp]
+        lib.gmco_evaluate.restype = ctypes.c_int
+        lib.gmco_dvh_from_dose.argtypes = [_vp, _vp, _i64, _vp, _vp]
+        lib.gmco_dvh_from_dose.restype = ctypes.c_int
+        lib.gmco_problem_info.argtypes = [_vp, ctypes.POINTER(_i64), ctypes.POINTER(_i64),
+                                          ctypes.POINTER(_i32), ctypes.POINTER(_i32)]
+        lib.gmco_problem_info.restype = ctypes.c_int
+        lib.gmco_last_launch_count.argtypes = [_vp]
+        lib.gmco_last_launch_count.restype = _i64
+        lib.gmco_status_string.argtypes = [ctypes.c_int]
+        lib.gmco_status_string.restype = ctypes.c_char_p
+        lib.gmco_last_error.argtypes = []
+        lib.gmco_last_error.restype = ctypes.c_char_p
+        _lib = lib
+    return _lib
+
+
+def status_string(status: int) -> str:
+    return load().gmco_status_string(int(status)).decode()
+
+
+def last_error() -> str:
+    return load().gmco_last_error().decode()
+
+
+def _check(status, where):
+    if status != OK:
+        raise GmcoError(status, where, last_error())
+
+
+# ---------------------------------------------------------------- marshalling helpers
+def _is_torch(a):
+    return type(a).__module__.startswith("torch")
+
+
+def _prep(a, np_dtype, torch_name):
+    """Contiguous array of the right dtype; returns (keepalive, pointer, is_cuda)."""
+    if a is None:
+        return None, None, False
+    if _is_torch(a):
+        import torch
+        t = a.detach().to(getattr(torch, torch_name)).contiguous()
+        return t, t.data_ptr(), t.is_cuda
+    arr = np.ascontiguousarray(a, dtype=np_dtype)
+    return arr, arr.ctypes.data, False
+
+
+def _alloc(shape, np_dtype, torch_name, cuda):
+    if cuda:
+        import torch
+        t = torch.empty(shape, dtype=getattr(torch, torch_name), device="cuda")
+        return t, t.data_ptr()
+    arr = np.empty(shape, dtype=np_dtype)
+    return arr, arr.ctypes.data
+
+
+def _stream_ptr(stream, cuda):
+    if stream is not None:
+        return int(getattr(stream, "cuda_stream", stream))
+    if cuda:
+        import torch
+        return torch.cuda.current_stream().cuda_stream
+    return 0
+
+
+# ---------------------------------------------------------------- C ABI mirrors
+def default_options(**overrides) -> _Options:
+    o = _Options()
+    load().gmco_default_options(ctypes.byref(o))
+    for k, v in overrides.items():
+        if k == "precision" and isinstance(v, str):
+            v = PREC[v]
+        setattr(o, k, v)
+    return o
+
+
+def create_problem(A, structure_ids, penalty_params, **options):
+    """gmco_create_problem.  Returns an opaque handle (int)."""
+    lib = load()
+    a_keep, a_ptr, _ = _prep(A, np.float32, "float32")
+    s_keep, s_ptr, _ = _prep(structure_ids, np.int32, "int32")
+    p_keep, p_ptr, _ = _prep(penalty_params, np.float64, "float64")
+    n_pnt, n_dwell = (int(x) for x in a_keep.shape)
+    n_struct = int(p_keep.shape[0])
+    opt = default_options(**options)
+    h = _vp()
+    _check(lib.gmco_create_problem(a_ptr, n_pnt, n_dwell, s_ptr, n_struct, p_ptr,
+                                   ctypes.byref(opt), ctypes.byref(h)), "gmco_create_problem")
+    return h.value
+
+
+def destroy_problem(h):
+    if h:
+        load().gmco_destroy_problem(h)
+
+
+def problem_info(h):
+    n_pnt, n_dwell, n_struct, prec = _i64(), _i64(), _i32(), _i32()
+    _check(load().gmco_problem_info(h, ctypes.byref(n_pnt), ctypes.byref(n_dwell),
+                                    ctypes.byref(n_struct), ctypes.byref(prec)),
+           "gmco_problem_info")
+    return dict(n_pnt=n_pnt.value, n_dwell=n_dwell.value, n_struct=n_struct.value,
+                precision=prec.value)
+
+
+def last_launch_count(h) -> int:
+    return int(load().gmco_last_launch_count(h))
+
+
+def solve_batch(h, penalty_weights, t0=None, max_iters=500, tol=1e-6, stream=None,
+                want=("T", "objectives", "dvh", "iters", "status"), allow_timeout=False):
+    """gmco_solve_batch.  Returns a dict with the requested outputs."""
+    info = problem_info(h)
+    w_keep, w_ptr, cuda = _prep(penalty_weights, np.float32, "float32")
+    P = int(w_keep.shape[0])
+    t_keep, t_ptr, _ = _prep(t0, np.float32, "float32")
+    out, ptrs = {}, {}
+    shapes = dict(T=((P, info["n_dwell"]), np.float32, "float32"),
+                  objectives=((P,), np.float64, "float64"),
+                  dvh=((P, DVH_K), np.float32, "float32"),
+                  iters=((P,), np.int32, "int32"), status=((P,), np.int32, "int32"))
+    for k in ("T", "objectives", "dvh", "iters", "status"):
+        if k in want:
+            out[k], ptrs[k] = _alloc(*shapes[k], cuda)
+        else:
+            ptrs[k] = None
+    st = load().gmco_solve_batch(h, w_ptr, P, t_ptr, int(max_iters), float(tol), ptrs["T"],
+                                 ptrs["objectives"], ptrs["dvh"], ptrs["iters"], ptrs["status"],
+                                 _stream_ptr(stream, cuda))
+    if st == ETIMEOUT and allow_timeout:
+        out["timeout"] = True
+    else:
+        _check(st, "gmco_solve_batch")
+    del w_keep, t_keep
+    return out
+
+
+def evaluate(h, penalty_weights, X, objectives=True, grad=True, dose=False, dvh=False,
+             stream=None):
+    """gmco_evaluate at dwell weights X (P x n_dwell)."""
+    info = problem_info(h)
+    w_keep, w_ptr, cuda = _prep(penalty_weights, np.float32, "float32")
+    x_keep, x_ptr, _ = _prep(X, np.float32, "float32")
+    P = int(w_keep.shape[0])
+    out, ptrs = {}, {}
+    spec = dict(objectives=(objectives, (P,), np.float64, "float64"),
+                grad=(grad, (P, info["n_dwell"]), np.float32, "float32"),
+                dose=(dose, (P, info["n_pnt"]), np.float32, "float32"),
+                dvh=(dvh, (P, DVH_K), np.float32, "float32"))
+    for k, (on, shape, nd_, td_) in spec.items():
+        if on:
+            out[k], ptrs[k] = _alloc(shape, nd_, td_, cuda)
+        else:
+            ptrs[k] = None
+    _check(load().gmco_evaluate(h, w_ptr, P, x_ptr, ptrs["objectives"], ptrs["grad"],
+                                ptrs["dose"], ptrs["dvh"], _stream_ptr(stream, cuda)),
+           "gmco_evaluate")
+    del w_keep, x_keep
+    return out
+
+
+def dvh_from_dose(h, dose, stream=None):
+    """gmco_dvh_from_dose: DVH indices of given doses (P x n_pnt)."""
+    d_keep, d_ptr, cuda = _prep(dose, np.float32, "float32")
+    P = int(d_keep.shape[0])
+    out, optr = _alloc((P, DVH_K), np.float32, "float32", cuda)
+    _check(load().gmco_dvh_from_dose(h, d_ptr, P, optr, _stream_ptr(stream, cuda)),
+           "gmco_dvh_from_dose")
+    return out
+
+
+class Problem:
+    """Owning wrapper of a problem handle."""
+
+    def __init__(self, A, structure_ids, penalty_params, **options):
+        self.handle = create_problem(A, structure_ids, penalty_params, **options)
+        self.info = problem_info(self.handle)
+
+    def solve_batch(self, penalty_weights, t0=None, max_iters=500, tol=1e-6, **kw):
+        return solve_batch(self.handle, penalty_weights, t0, max_iters, tol, **kw)
+
+    def evaluate(self, penalty_weights, X, **kw):
+        return evaluate(self.handle, penalty_weights, X, **kw)
+
+    def dvh_from_dose(self, dose, **kw):
+        return dvh_from_dose(self.handle, dose, **kw)
+
+    def last_launch_count(self):
+        return last_launch_count(self.handle)
+
+    def close(self):
+        if self.handle:
+            destroy_problem(self.handle)
+            self.handle = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

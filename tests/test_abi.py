@@ -1,0 +1,54 @@
+"""The C ABI library: loads, exports every declared entry point, validates on the host."""
+import ctypes
+import os
+import re
+
+import numpy as np
+import pytest
+
+from tests.conftest import ROOT
+
+
+def _declared():
+    txt = open(os.path.join(ROOT, "include", "gmco.h")).read()
+    txt = re.sub(r"/\*.*?\*/", "", txt, flags=re.S)
+    return sorted(set(re.findall(r"\b(gmco_[a-z_0-9]+)\s*\(", txt)))
+
+
+def test_library_exports_every_declared_symbol(gmco_mod):
+    lib = ctypes.CDLL(gmco_mod.LIB_PATH)
+    names = _declared()
+    assert "gmco_solve_batch" in names and "gmco_create_problem" in names
+    for n in names:
+        assert hasattr(lib, n), n
+
+
+def test_status_strings(gmco_mod):
+    assert gmco_mod.status_string(0) == "ok"
+    assert "invalid" in gmco_mod.status_string(1)
+    assert gmco_mod.status_string(99) == "unknown status"
+
+
+def test_host_validation_before_device_use(gmco_mod):
+    # rejected on the host before any CUDA call: zero dwells, ids out of range
+    A = np.ones((4, 3), np.float32)
+    prm = np.array([[1.0, 15.0, np.inf, 1.0]])
+    with pytest.raises(gmco_mod.GmcoError) as e:
+        gmco_mod.create_problem(np.ones((4, 0), np.float32), np.zeros(4, np.int32), prm)
+    assert e.value.status == 1
+
+
+def test_options_defaults(gmco_mod):
+    o = gmco_mod.default_options()
+    assert (o.precision, o.m, o.c1, o.max_ls, o.rx_gy) == (0, 10, 1e-4, 30, 15.0)
+    assert gmco_mod.default_options(precision="bf16").precision == 1
+
+
+def test_no_cpu_fallback_without_device(gmco_mod):
+    import torch
+    if torch.cuda.is_available():
+        pytest.skip("a CUDA device is present")
+    with pytest.raises(gmco_mod.GmcoError) as e:
+        gmco_mod.create_problem(np.ones((4, 3), np.float32), np.zeros(4, np.int32),
+                                np.array([[1.0, 15.0, np.inf, 1.0]]))
+    assert e.value.status == 3   # GMCO_ECUDA: the library never computes on the host
