@@ -81,6 +81,8 @@ typedef struct {
     int32_t refine_iters;  /* after a BF16/FP8 solve, up to this many further iterations
                               with the FP32 evaluation (history kept); default 0 */
     int32_t steps_per_poll;/* device steps between host checks for completion, default 16 */
+    int32_t stop_window;   /* a plan converges after this many consecutive accepted
+                              iterations each with |F_prev - F| <= tol |F_prev|; default 1 */
 } gmco_options;
 
 /* Fills *opt with the defaults above. */
@@ -139,6 +141,18 @@ gmco_status gmco_evaluate(gmco_problem *prob, const float *penalty_weights, int6
  * Exact on the given FP32 values: counts and k-th largest values, no interpolation. */
 gmco_status gmco_dvh_from_dose(gmco_problem *prob, const float *dose, int64_t P, float *dvh,
                                void *cuda_stream);
+
+/* Measurement aid: times one evaluation of P plans at a line-search trial point
+ * (x_trial = 1.01 X, so both the dose and the dose change are computed) `reps` times after
+ * one warm-up, with CUDA events between its kernels on the problem's stream.
+ *   ms     4 averages (milliseconds): trial-point preparation, dose GEMM with the penalty
+ *          epilogue, gradient GEMM, reduction of partial sums
+ *   flops  4 values or NULL: algorithmic FLOPs of the dose GEMM (d and dd, 4 P n_pnt n_dwell)
+ *          and of the gradient GEMM (2 P n_pnt n_dwell), then the FLOPs the kernels issue
+ *          (tensor-core split terms over padded tiles; equal to the algorithmic for FP32).
+ * Synchronous. */
+gmco_status gmco_profile_evaluate(gmco_problem *prob, const float *penalty_weights, int64_t P,
+                                  const float *X, int32_t reps, double *ms, double *flops);
 
 /* Problem sizes as stored (after validation). */
 gmco_status gmco_problem_info(const gmco_problem *prob, int64_t *n_pnt, int64_t *n_dwell,

@@ -142,11 +142,11 @@ void oracle_two_loop(int64_t n, int32_t m, int32_t count, int32_t newest, const 
 int oracle_lbfgs(const double *A, int64_t n_pnt, int64_t n_dwell, const int32_t *sid,
                  int32_t n_struct, const double *params, const double *w, const double *t0,
                  int32_t max_iters, double tol, int32_t m, double c1, int32_t max_ls,
-                 double *t_out, double *F_out, int32_t *iters_out, int32_t *status_out,
-                 double *trace, int64_t *n_evals)
+                 int32_t stop_window, double *t_out, double *F_out, int32_t *iters_out,
+                 int32_t *status_out, double *trace, int64_t *n_evals)
 {
-    if (m < 1 || m > 64 || max_ls < 1 || max_iters < 0 || !t_out || !F_out || !iters_out ||
-        !status_out)
+    if (m < 1 || m > 64 || max_ls < 1 || max_iters < 0 || stop_window < 1 || !t_out || !F_out ||
+        !iters_out || !status_out)
         return -1;
     const int64_t n = n_dwell;
     const size_t vb = (size_t)(n > 0 ? n : 1) * sizeof(double);
@@ -167,7 +167,7 @@ int oracle_lbfgs(const double *A, int64_t n_pnt, int64_t n_dwell, const int32_t 
     evals++;
     if (trace) { trace[0] = F; trace[1] = 0.0; trace[2] = 0.0; }
 
-    int32_t k = 0, status;
+    int32_t k = 0, status, n_small = 0;
     int32_t count = 0, newest = m - 1;
     if (!isfinite(F) || !all_finite(n, g)) { status = ORACLE_NONFINITE; goto finish; }
     if (F == 0.0 || norm_inf(n, g) == 0.0) { status = ORACLE_CONVERGED; goto finish; }
@@ -222,9 +222,10 @@ int oracle_lbfgs(const double *A, int64_t n_pnt, int64_t n_dwell, const int32_t 
         k++;
         if (trace) { trace[3 * k] = F; trace[3 * k + 1] = alpha; trace[3 * k + 2] = gtp; }
         if (!all_finite(n, g)) { status = ORACLE_NONFINITE; break; }
-        /* stop on the relative variation of the objective (Sec. 2.2.3) */
-        if (F == 0.0 || norm_inf(n, g) == 0.0 ||
-            fabs(Fprev - F) <= tol * fmax(fabs(Fprev), 1e-300)) {
+        /* stop on the relative variation of the objective (Sec. 2.2.3), over stop_window
+         * consecutive iterations */
+        n_small = fabs(Fprev - F) <= tol * fmax(fabs(Fprev), 1e-300) ? n_small + 1 : 0;
+        if (F == 0.0 || norm_inf(n, g) == 0.0 || n_small >= stop_window) {
             status = ORACLE_CONVERGED;
             break;
         }
@@ -243,8 +244,9 @@ done:
 int oracle_lbfgs_batch(const double *A, int64_t n_pnt, int64_t n_dwell, const int32_t *sid,
                        int32_t n_struct, const double *params, const double *W, int64_t P,
                        const double *T0, int32_t max_iters, double tol, int32_t m, double c1,
-                       int32_t max_ls, double *T_out, double *F_out, int32_t *iters_out,
-                       int32_t *status_out, int64_t *n_evals, int32_t n_threads)
+                       int32_t max_ls, int32_t stop_window, double *T_out, double *F_out,
+                       int32_t *iters_out, int32_t *status_out, int64_t *n_evals,
+                       int32_t n_threads)
 {
     int bad = 0;
 #ifdef _OPENMP
@@ -255,7 +257,7 @@ int oracle_lbfgs_batch(const double *A, int64_t n_pnt, int64_t n_dwell, const in
         int64_t ev = 0;
         int r = oracle_lbfgs(A, n_pnt, n_dwell, sid, n_struct, params, W + j * n_struct,
                              T0 ? T0 + j * n_dwell : NULL, max_iters, tol, m, c1, max_ls,
-                             T_out + j * n_dwell, F_out + j, iters_out + j, status_out + j,
+                             stop_window, T_out + j * n_dwell, F_out + j, iters_out + j, status_out + j,
                              NULL, &ev);
         if (n_evals) n_evals[j] = ev;
         bad |= (r != 0);

@@ -51,10 +51,11 @@ def load():
         lib.oracle_two_loop.argtypes = [_i64, _i32, _i32, _i32, _dp, _dp, _dp, _dp, _dp]
         lib.oracle_two_loop.restype = None
         lib.oracle_lbfgs.argtypes = [_dp, _i64, _i64, _ip, _i32, _dp, _dp, _dp, _i32, _f64, _i32,
-                                     _f64, _i32, _dp, _dp, _ip, _ip, _dp, _lp]
+                                     _f64, _i32, _i32, _dp, _dp, _ip, _ip, _dp, _lp]
         lib.oracle_lbfgs.restype = ctypes.c_int
         lib.oracle_lbfgs_batch.argtypes = [_dp, _i64, _i64, _ip, _i32, _dp, _dp, _i64, _dp, _i32,
-                                           _f64, _i32, _f64, _i32, _dp, _dp, _ip, _ip, _lp, _i32]
+                                           _f64, _i32, _f64, _i32, _i32, _dp, _dp, _ip, _ip, _lp,
+                                           _i32]
         lib.oracle_lbfgs_batch.restype = ctypes.c_int
         lib.oracle_dvh.argtypes = [_dp, _ip, _i64, _i32, _f64, _dp]
         lib.oracle_dvh.restype = None
@@ -113,7 +114,7 @@ def two_loop(S, Y, rho, count, newest, g):
 
 
 def lbfgs(A, sid, params, w, t0=None, max_iters=200, tol=1e-6, m=10, c1=1e-4, max_ls=30,
-          trace=False):
+          trace=False, stop_window=1):
     """One plan.  Returns dict(t, F, iters, status, evals[, trace])."""
     A = _d(A); sid = _i(sid); params = _d(params); w = _d(w)
     t0 = None if t0 is None else _d(t0)
@@ -122,7 +123,7 @@ def lbfgs(A, sid, params, w, t0=None, max_iters=200, tol=1e-6, m=10, c1=1e-4, ma
     ev = np.zeros(1, np.int64)
     tr = np.full(3 * (max_iters + 1), np.nan) if trace else None
     rc = load().oracle_lbfgs(_p(A), A.shape[0], n, _p(sid, _ip), params.shape[0], _p(params),
-                             _p(w), _p(t0), max_iters, tol, m, c1, max_ls, _p(t), _p(F),
+                             _p(w), _p(t0), max_iters, tol, m, c1, max_ls, stop_window, _p(t), _p(F),
                              _p(it, _ip), _p(st, _ip), _p(tr), _p(ev, _lp))
     if rc != 0:
         raise ValueError("oracle_lbfgs: invalid arguments")
@@ -134,7 +135,7 @@ def lbfgs(A, sid, params, w, t0=None, max_iters=200, tol=1e-6, m=10, c1=1e-4, ma
 
 
 def lbfgs_batch(A, sid, params, W, T0=None, max_iters=200, tol=1e-6, m=10, c1=1e-4, max_ls=30,
-                n_threads=0):
+                n_threads=0, stop_window=1):
     """P plans, one per OpenMP thread.  Returns dict(T, F, iters, status, evals)."""
     A = _d(A); sid = _i(sid); params = _d(params); W = _d(W)
     P = W.shape[0]
@@ -144,7 +145,7 @@ def lbfgs_batch(A, sid, params, W, T0=None, max_iters=200, tol=1e-6, m=10, c1=1e
     ev = np.empty(P, np.int64)
     rc = load().oracle_lbfgs_batch(_p(A), A.shape[0], n, _p(sid, _ip), params.shape[0],
                                    _p(params), _p(W), P, _p(T0), max_iters, tol, m, c1, max_ls,
-                                   _p(T), _p(F), _p(it, _ip), _p(st, _ip), _p(ev, _lp),
+                                   stop_window, _p(T), _p(F), _p(it, _ip), _p(st, _ip), _p(ev, _lp),
                                    int(n_threads))
     if rc != 0:
         raise ValueError("oracle_lbfgs_batch: invalid arguments")

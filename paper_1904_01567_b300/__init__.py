@@ -11,6 +11,7 @@ from .gmco import (  # noqa: F401
     solve_batch,
     evaluate,
     dvh_from_dose,
+    profile_evaluate,
     problem_info,
     last_launch_count,
     status_string,

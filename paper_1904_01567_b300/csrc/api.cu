@@ -105,12 +105,12 @@ struct gmco_problem {
 
     // cached step graphs, one per evaluation form
     struct GraphKey {
-        int32_t P = -1, form = -1, max_ls = -1, steps = -1;
+        int32_t P = -1, form = -1, max_ls = -1, steps = -1, window = -1;
         double tol = -1, c1 = -1;
         bool operator==(const GraphKey &o) const
         {
             return P == o.P && form == o.form && max_ls == o.max_ls && steps == o.steps &&
-                   tol == o.tol && c1 == o.c1;
+                   window == o.window && tol == o.tol && c1 == o.c1;
         }
     };
     GraphKey gkey[2];
@@ -184,7 +184,7 @@ gmco_status ensure_workspace(gmco_problem *pr, int32_t P)
     CK(a.alloc(&s.state, (size_t)cap)); CK(a.alloc(&s.status, (size_t)cap));
     CK(a.alloc(&s.iters, (size_t)cap)); CK(a.alloc(&s.maxit, (size_t)cap));
     CK(a.alloc(&s.ls, (size_t)cap)); CK(a.alloc(&s.hcount, (size_t)cap));
-    CK(a.alloc(&s.hnewest, (size_t)cap));
+    CK(a.alloc(&s.hnewest, (size_t)cap)); CK(a.alloc(&s.nsmall, (size_t)cap));
     CK(a.alloc(&s.Wn, (size_t)cap * S));
     CK(a.alloc(&s.list, (size_t)cap)); CK(a.alloc(&s.n_act, 1)); CK(a.alloc(&s.n_live, 1));
     CK(cudaMemset(s.S, 0, vn * m * sizeof(float)));
@@ -223,11 +223,13 @@ gmco_status ensure_workspace(gmco_problem *pr, int32_t P)
 // Launches one evaluation of every compact row (rows from s.list / s.n_act) in `form`
 // (0 = FP32 SIMT, 1 = tensor-core BF16) with F, dF and the gradient.
 gmco_status launch_eval(gmco_problem *pr, SolverState s, int form, bool with_dT,
-                        cudaStream_t st)
+                        cudaStream_t st, cudaEvent_t *ev = nullptr)
 {
     const DevProblem &pb = pr->pb;
     if (form == 0) {
+        if (ev) CK(cudaEventRecord(ev[0], st));
         CK(launch_prep_fp32(s, pb, pr->Tc, with_dT ? pr->dTc : nullptr, pr->Wc, false, st));
+        if (ev) CK(cudaEventRecord(ev[1], st));
         EvalArgs e{};
         e.pb = pb;
         e.n_rows = s.n_act;
@@ -241,13 +243,16 @@ gmco_status launch_eval(gmco_problem *pr, SolverState s, int form, bool with_dT,
         e.gpart = pr->gpart;
         e.n_split = pr->n_split;
         CK(launch_gemm1_simt(e, MODE_G, st));
+        if (ev) CK(cudaEventRecord(ev[2], st));
         CK(launch_gemm2_simt(e, st));
+        if (ev) CK(cudaEventRecord(ev[3], st));
         CK(launch_finish(s, e, pr->n_ptiles, st));
+        if (ev) CK(cudaEventRecord(ev[4], st));
         pr->launches += 4;
     } else {
         int32_t nl = 0;
         CK(tc_launch_eval(pb, s, pr->tcb, pr->Fpart, pr->dFpart, pr->gpart, pr->cap, with_dT,
-                          nullptr, false, st, &nl));
+                          nullptr, false, st, &nl, ev));
         pr->launches += nl;
     }
     return GMCO_OK;
@@ -302,6 +307,7 @@ gmco_status run_loop(gmco_problem *pr, int form, int32_t P, const UpdateParams &
     key.form = form;
     key.max_ls = u.max_ls;
     key.steps = steps;
+    key.window = u.stop_window;
     key.tol = u.tol;
     key.c1 = u.c1;
     if (!(pr->gkey[form] == key) || !pr->gexec[form]) {
@@ -398,6 +404,7 @@ void gmco_default_options(gmco_options *opt)
     opt->rx_gy = 15.0;
     opt->refine_iters = 0;
     opt->steps_per_poll = 16;
+    opt->stop_window = 1;
 }
 
 const char *gmco_status_string(gmco_status s)
@@ -433,7 +440,7 @@ gmco_status gmco_create_problem(const float *A, int64_t n_pnt, int64_t n_dwell,
     if (o.precision < 0 || o.precision > 4 || o.m < 1 || o.m > kMaxHist || !(o.c1 > 0.0) ||
         !(o.c1 < 1.0) || o.max_ls < 1 || o.max_ls > 60 || !(o.rx_gy > 0.0) ||
         !isfinite(o.rx_gy) || o.refine_iters < 0 || o.steps_per_poll < 1 ||
-        o.steps_per_poll > 1024) {
+        o.steps_per_poll > 1024 || o.stop_window < 1) {
         set_error_msg("gmco_create_problem: bad options");
         return GMCO_EINVAL;
     }
@@ -621,7 +628,7 @@ gmco_status gmco_solve_batch(gmco_problem *pr, const float *penalty_weights, int
 
     CK(launch_solver_init(s, pb, pr->dW, t0 ? pr->dT0 : nullptr, max_iters, pr->stream));
     pr->launches++;
-    UpdateParams u{pr->opt.c1, tol, pr->opt.max_ls};
+    UpdateParams u{pr->opt.c1, tol, pr->opt.max_ls, pr->opt.stop_window};
     const int form = pr->opt.precision == GMCO_PREC_FP32 ? 0 : 1;
     const int64_t budget = ((int64_t)max_iters + pr->opt.refine_iters + 1) * (pr->opt.max_ls + 1) + 4;
     int64_t steps = 0;
@@ -734,6 +741,74 @@ gmco_status gmco_evaluate(gmco_problem *pr, const float *penalty_weights, int64_
     }
     CKS(check_tc_error(pr));
     CKS(end_call(pr, cuda_stream));
+    return GMCO_OK;
+}
+
+gmco_status gmco_profile_evaluate(gmco_problem *pr, const float *penalty_weights, int64_t P,
+                                  const float *X, int32_t reps, double *ms, double *flops)
+{
+    if (!pr || !penalty_weights || !X || !ms || P < 1 || P > (1 << 20) || reps < 1) {
+        set_error_msg("gmco_profile_evaluate: bad arguments");
+        return GMCO_EINVAL;
+    }
+    pr->launches = 0;
+    CKS(begin_call(pr, nullptr));
+    CKS(ensure_workspace(pr, (int32_t)P));
+    const DevProblem &pb = pr->pb;
+    const int32_t S = pb.n_struct;
+    CKS(stage_in(pr, penalty_weights, pr->dW, (size_t)P * S * sizeof(float)));
+    CKS(stage_in(pr, X, pr->dT0, (size_t)P * pb.n_dwell * sizeof(float)));
+    SolverState s = pr->s;
+    s.P = (int32_t)P;
+    SolverState saved = pr->s;
+    pr->s = s;
+    struct Restore {
+        gmco_problem *p;
+        SolverState st;
+        ~Restore() { p->s = st; }
+    } restore{pr, saved};
+    CK(launch_solver_init(s, pb, pr->dW, nullptr, 0, pr->stream));
+    CK(cudaMemcpy2DAsync(s.x, pb.nd_pad * sizeof(float), pr->dT0, pb.n_dwell * sizeof(float),
+                         pb.n_dwell * sizeof(float), P, cudaMemcpyDeviceToDevice, pr->stream));
+    CK(launch_profile_setup(s, pr->stream));
+    CK(launch_compact(s, 0, pr->stream));
+    const int form = pr->opt.precision == GMCO_PREC_FP32 ? 0 : 1;
+    cudaEvent_t ev[5];
+    for (int k = 0; k < 5; ++k) CK(cudaEventCreate(&ev[k]));
+    double acc[4] = {0, 0, 0, 0};
+    gmco_status rs = GMCO_OK;
+    for (int r = 0; r < reps + 1 && rs == GMCO_OK; ++r) {   // first repetition is warm-up
+        rs = launch_eval(pr, s, form, true, pr->stream, ev);
+        if (rs != GMCO_OK) break;
+        if (cudaStreamSynchronize(pr->stream) != cudaSuccess) { rs = GMCO_ECUDA; break; }
+        if (r == 0) continue;
+        for (int k = 0; k < 4; ++k) {
+            float t = 0.0f;
+            cudaEventElapsedTime(&t, ev[k], ev[k + 1]);
+            acc[k] += t;
+        }
+    }
+    for (int k = 0; k < 5; ++k) cudaEventDestroy(ev[k]);
+    if (rs != GMCO_OK) return rs;
+    for (int k = 0; k < 4; ++k) ms[k] = acc[k] / reps;
+    if (flops) {
+        // algorithmic: dose d and dose change dd (2 contractions), gradient (1 contraction)
+        const double c = 2.0 * (double)P * (double)pb.n_pnt * (double)pb.n_dwell;
+        flops[0] = 2.0 * c;
+        flops[1] = c;
+        // issued on the tensor cores (split terms, padded tiles); FP32 form: algorithmic
+        if (form == 1) {
+            const double cp = 2.0 * (double)round_up(P, 128) * (double)pb.np_pad *
+                              (double)round_up(pb.n_dwell, 16);
+            flops[2] = tc_mma_units(pb, true, 1) * cp;
+            flops[3] = tc_mma_units(pb, true, 2) * cp;
+        } else {
+            flops[2] = flops[0];
+            flops[3] = flops[1];
+        }
+    }
+    CKS(check_tc_error(pr));
+    CKS(end_call(pr, nullptr));
     return GMCO_OK;
 }
 

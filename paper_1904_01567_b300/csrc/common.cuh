@@ -62,6 +62,7 @@ struct SolverState {
     double *F = nullptr, *Ft = nullptr, *dFt = nullptr, *gtp = nullptr, *alpha = nullptr;
     int32_t *state = nullptr, *status = nullptr, *iters = nullptr, *maxit = nullptr;
     int32_t *ls = nullptr, *hcount = nullptr, *hnewest = nullptr;
+    int32_t *nsmall = nullptr;          // consecutive iterations below the stop tolerance
     float *Wn = nullptr;                // P x n_struct, w / N_s
     int32_t *list = nullptr;            // compact row -> plan
     int32_t *n_act = nullptr;           // device scalar
@@ -71,6 +72,7 @@ struct SolverState {
 struct UpdateParams {
     double c1, tol;
     int32_t max_ls;
+    int32_t stop_window;
 };
 
 // ---- launchers (return cudaError_t of the launch) ----
@@ -84,6 +86,7 @@ cudaError_t launch_finish(const SolverState &s, const EvalArgs &e, int32_t n_pti
 cudaError_t launch_update(const SolverState &s, const UpdateParams &u, cudaStream_t st);
 cudaError_t launch_count_live(const SolverState &s, cudaStream_t st);
 cudaError_t launch_reopen(const SolverState &s, int32_t extra_iters, cudaStream_t st);
+cudaError_t launch_profile_setup(const SolverState &s, cudaStream_t st);
 cudaError_t launch_square(const float *x, float *t, int64_t rows, int64_t nd, int64_t nd_pad,
                           cudaStream_t st);
 

@@ -68,6 +68,7 @@ __global__ void k_solver_init(SolverState s, const float *__restrict__ W,
         s.ls[j] = 0;
         s.hcount[j] = 0;
         s.hnewest[j] = s.m - 1;
+        s.nsmall[j] = 0;
         s.F[j] = 0.0;
         s.Ft[j] = 0.0;
         s.dFt[j] = 0.0;
@@ -284,7 +285,9 @@ __global__ void __launch_bounds__(256) k_update(SolverState s, UpdateParams u)
                 s.hnewest[j] = nw;
             }
             if (!fin) { plan_done(s, j, GMCO_PLAN_NONFINITE, lane); return; }
-            if (Ft == 0.0 || gmax == 0.0f || fabs(dF) <= u.tol * fmax(fabs(Fprev), 1e-300)) {
+            const int nsm = fabs(dF) <= u.tol * fmax(fabs(Fprev), 1e-300) ? s.nsmall[j] + 1 : 0;
+            if (lane == 0) s.nsmall[j] = nsm;
+            if (Ft == 0.0 || gmax == 0.0f || nsm >= u.stop_window) {
                 plan_done(s, j, GMCO_PLAN_CONVERGED, lane);
                 return;
             }
@@ -395,6 +398,19 @@ __global__ void __launch_bounds__(256) k_update(SolverState s, UpdateParams u)
     }
 }
 
+// Measurement set-up: every plan in a line-search trial at x + 0.01 x (t_trial != t).
+__global__ void k_profile_setup(SolverState s)
+{
+    const int j = blockIdx.x;
+    if (j >= s.P) return;
+    for (int l = threadIdx.x; l < s.nd_pad; l += blockDim.x)
+        s.p[(size_t)j * s.nd_pad + l] = s.x[(size_t)j * s.nd_pad + l];
+    if (threadIdx.x == 0) {
+        s.state[j] = ST_TRIAL;
+        s.alpha[j] = 0.01;
+    }
+}
+
 // Re-open finished plans for further iterations (FP32 refinement after a BF16/FP8 solve).
 __global__ void k_reopen(SolverState s, int32_t extra)
 {
@@ -404,6 +420,7 @@ __global__ void k_reopen(SolverState s, int32_t extra)
         s.state[j] = ST_INIT;
         s.status[j] = GMCO_PLAN_MAXITER;
         s.maxit[j] = s.iters[j] + extra;
+        s.nsmall[j] = 0;
     }
 }
 
@@ -458,6 +475,12 @@ cudaError_t launch_update(const SolverState &s, const UpdateParams &u, cudaStrea
     else if (epl <= 12) k_update<12><<<blocks, 256, 0, st>>>(s, u);
     else if (epl <= 16) k_update<16><<<blocks, 256, 0, st>>>(s, u);
     else k_update<32><<<blocks, 256, 0, st>>>(s, u);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_profile_setup(const SolverState &s, cudaStream_t st)
+{
+    k_profile_setup<<<s.P, 128, 0, st>>>(s);
     return cudaGetLastError();
 }
 

@@ -669,6 +669,15 @@ size_t dyn_smem(const Job &job) { return (size_t)job.n_stages * job.stage_bytes 
 }  // namespace
 
 int32_t tc_n_ptiles(const DevProblem &pb) { return (int32_t)(pb.np_pad / BN1); }
+
+double tc_mma_units(const DevProblem &pb, bool with_dT, int which)
+{
+    const int nA = pb.tc_terms, nT = n_t_terms(pb);
+    int pairs = 0;
+    for (int i = 0; i < nA; ++i)
+        for (int j = 0; j < nT; ++j) pairs += keep_pair(i, j, nA, nT);
+    return which == 1 ? pairs + (with_dT ? nA : 0) : pairs;
+}
 int32_t tc_max_split(const DevProblem &pb) { return (int32_t)std::min<int64_t>(148, pb.np_pad / BK); }
 int64_t tc_launches_per_eval() { return 4; }
 
@@ -750,13 +759,16 @@ cudaError_t tc_alloc(const DevProblem &pb, int32_t cap, TcBuffers *b, const Allo
 
 cudaError_t tc_launch_eval(const DevProblem &pb, const SolverState &s, const TcBuffers &b,
                            float *Fpart, float *dFpart, float *gpart, int32_t cap, bool with_dT,
-                           float *dose_out, bool force_base, cudaStream_t st, int32_t *n_launches)
+                           float *dose_out, bool force_base, cudaStream_t st, int32_t *n_launches,
+                           cudaEvent_t *ev)
 {
     int nl = 0;
+    if (ev) cudaEventRecord(ev[0], st);
     k_prep_tc<<<cap, 128, 0, st>>>(s, b, n_t_terms(pb), pb.kpad, force_base ? 1 : 0);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     ++nl;
+    if (ev) cudaEventRecord(ev[1], st);
     EpiArgs ep{};
     ep.n_rows = s.n_act;
     ep.cap = cap;
@@ -781,6 +793,7 @@ cudaError_t tc_launch_eval(const DevProblem &pb, const SolverState &s, const TcB
     k_tc<1><<<g1, NTHREADS, dyn_smem(j1), st>>>(b.maps1, j1, ep);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
     ++nl;
+    if (ev) cudaEventRecord(ev[2], st);
     if (!dose_out) {
         const Job j2 = make_grad_job(pb, b);
         dim3 g2((unsigned)b.n_split, (unsigned)ceil_div(cap, BM));
@@ -788,6 +801,7 @@ cudaError_t tc_launch_eval(const DevProblem &pb, const SolverState &s, const TcB
         if ((e = cudaGetLastError()) != cudaSuccess) return e;
         ++nl;
     }
+    if (ev) cudaEventRecord(ev[3], st);
     EvalArgs fe{};
     fe.pb = pb;
     fe.n_rows = s.n_act;
@@ -798,6 +812,7 @@ cudaError_t tc_launch_eval(const DevProblem &pb, const SolverState &s, const TcB
     fe.n_split = b.n_split;
     if ((e = launch_finish(s, fe, tc_n_ptiles(pb), st)) != cudaSuccess) return e;
     ++nl;
+    if (ev) cudaEventRecord(ev[4], st);
     *n_launches = nl;
     return cudaSuccess;
 }

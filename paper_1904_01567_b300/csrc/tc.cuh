@@ -31,6 +31,8 @@ struct TcBuffers {
 int32_t tc_n_ptiles(const DevProblem &pb);
 int32_t tc_max_split(const DevProblem &pb);
 int64_t tc_launches_per_eval();
+// MMA products per output element issued by the dose GEMM (which = 1) or gradient GEMM (2).
+double tc_mma_units(const DevProblem &pb, bool with_dT, int which);
 // Splits A / row_scale into pb->tc_terms BF16 terms (precision 1, 3, 4) or the E4M3 grid
 // (precision 2) and builds the transposed copies.  cudaErrorNotSupported when the sizes are
 // beyond the tensor-core path (n_dwell > 384 or n_struct > 8).
@@ -43,6 +45,6 @@ cudaError_t tc_alloc(const DevProblem &pb, int32_t cap, TcBuffers *b, const Allo
 cudaError_t tc_launch_eval(const DevProblem &pb, const SolverState &s, const TcBuffers &b,
                            float *Fpart, float *dFpart, float *gpart, int32_t cap, bool with_dT,
                            float *dose_out, bool force_base, cudaStream_t st,
-                           int32_t *n_launches);
+                           int32_t *n_launches, cudaEvent_t *ev = nullptr);
 
 }  // namespace gmco

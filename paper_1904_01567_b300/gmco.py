@@ -33,7 +33,8 @@ class GmcoError(RuntimeError):
 class _Options(ctypes.Structure):
     _fields_ = [("precision", ctypes.c_int32), ("m", ctypes.c_int32), ("c1", ctypes.c_double),
                 ("max_ls", ctypes.c_int32), ("rx_gy", ctypes.c_double),
-                ("refine_iters", ctypes.c_int32), ("steps_per_poll", ctypes.c_int32)]
+                ("refine_iters", ctypes.c_int32), ("steps_per_poll", ctypes.c_int32),
+                ("stop_window", ctypes.c_int32)]
 
 
 _lib = None
@@ -63,6 +64,8 @@ def load():
         lib.gmco_evaluate.restype = ctypes.c_int
         lib.gmco_dvh_from_dose.argtypes = [_vp, _vp, _i64, _vp, _vp]
         lib.gmco_dvh_from_dose.restype = ctypes.c_int
+        lib.gmco_profile_evaluate.argtypes = [_vp, _vp, _i64, _vp, _i32, _vp, _vp]
+        lib.gmco_profile_evaluate.restype = ctypes.c_int
         lib.gmco_problem_info.argtypes = [_vp, ctypes.POINTER(_i64), ctypes.POINTER(_i64),
                                           ctypes.POINTER(_i32), ctypes.POINTER(_i32)]
         lib.gmco_problem_info.restype = ctypes.c_int
@@ -220,6 +223,20 @@ def evaluate(h, penalty_weights, X, objectives=True, grad=True, dose=False, dvh=
     return out
 
 
+def profile_evaluate(h, penalty_weights, X, reps=20):
+    """gmco_profile_evaluate: per-kernel milliseconds of one evaluation and its FLOPs."""
+    w_keep, w_ptr, _ = _prep(penalty_weights, np.float32, "float32")
+    x_keep, x_ptr, _ = _prep(X, np.float32, "float32")
+    ms = np.zeros(4)
+    fl = np.zeros(4)
+    _check(load().gmco_profile_evaluate(h, w_ptr, int(w_keep.shape[0]), x_ptr, int(reps),
+                                        ms.ctypes.data, fl.ctypes.data), "gmco_profile_evaluate")
+    del w_keep, x_keep
+    return dict(ms=dict(prep=ms[0], dose_gemm=ms[1], grad_gemm=ms[2], finish=ms[3]),
+                flops=dict(dose_algorithmic=fl[0], grad_algorithmic=fl[1], dose_issued=fl[2],
+                           grad_issued=fl[3]))
+
+
 def dvh_from_dose(h, dose, stream=None):
     """gmco_dvh_from_dose: DVH indices of given doses (P x n_pnt)."""
     d_keep, d_ptr, cuda = _prep(dose, np.float32, "float32")
@@ -245,6 +262,9 @@ class Problem:
 
     def dvh_from_dose(self, dose, **kw):
         return dvh_from_dose(self.handle, dose, **kw)
+
+    def profile_evaluate(self, penalty_weights, X, reps=20):
+        return profile_evaluate(self.handle, penalty_weights, X, reps)
 
     def last_launch_count(self):
         return last_launch_count(self.handle)
