@@ -137,6 +137,28 @@ gmco_status gmco_evaluate(gmco_problem *prob, const float *penalty_weights, int6
                           const float *X, double *objectives, float *grad_x, float *dose,
                           float *dvh, void *cuda_stream);
 
+/* Allocation-free variant of gmco_evaluate, for callers that cannot allocate device memory
+ * while they run (a fixed memory budget, a real-time loop that cannot take cudaMalloc's
+ * implicit synchronisation, an application that owns every allocation).  The paper has no
+ * counterpart; it is an interface addition.
+ *   Computes objectives[P] and grad_x[P x n_dwell] (either may be NULL, not both) at dwell
+ *   weights X[P x n_dwell] with weights penalty_weights[P x n_struct], always with the FP32
+ *   form (the problem's FP32 copy of A), whatever the problem's precision.
+ *   Every pointer must be device memory (GMCO_EINVAL otherwise).
+ *   Scratch is one fixed 8 MiB device array inside the library, present on every GPU that
+ *   loads it until the process exits; a request that needs more (about
+ *   P x (n_pnt + 6 n_dwell) x 4 bytes) returns GMCO_EUNSUPPORTED and launches nothing.
+ *   The first call on a device resolves that array's address on the device (once, with the
+ *   device current); make that first call before any stream capture.
+ *   Asynchronous: kernels are queued on cuda_stream and the call returns without waiting.
+ *   All calls share the one array: calls whose kernels overlap on the GPU (different streams,
+ *   or threads without ordering) race and corrupt each other.  Each call writes every scratch
+ *   value before reading it, so nothing has to be cleared between calls.
+ * Allocates nothing: no cudaMalloc, cudaFree or allocating library routine. */
+gmco_status gmco_evaluate_noalloc(const gmco_problem *prob, const float *penalty_weights,
+                                  int64_t P, const float *X, double *objectives, float *grad_x,
+                                  void *cuda_stream);
+
 /* DVH indices (GMCO_DVH_K per plan, see above) of given doses: dose is P x n_pnt (Gy).
  * Exact on the given FP32 values: counts and k-th largest values, no interpolation. */
 gmco_status gmco_dvh_from_dose(gmco_problem *prob, const float *dose, int64_t P, float *dvh,

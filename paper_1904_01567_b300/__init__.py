@@ -10,6 +10,7 @@ from .gmco import (  # noqa: F401
     destroy_problem,
     solve_batch,
     evaluate,
+    evaluate_noalloc,
     dvh_from_dose,
     profile_evaluate,
     problem_info,

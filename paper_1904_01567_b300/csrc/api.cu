@@ -812,6 +812,45 @@ gmco_status gmco_profile_evaluate(gmco_problem *pr, const float *penalty_weights
     return GMCO_OK;
 }
 
+gmco_status gmco_evaluate_noalloc(const gmco_problem *pr, const float *penalty_weights,
+                                  int64_t P, const float *X, double *objectives, float *grad_x,
+                                  void *cuda_stream)
+{
+    if (!pr || !penalty_weights || !X || (!objectives && !grad_x) || P < 1 || P > (1 << 20)) {
+        set_error_msg("gmco_evaluate_noalloc: bad arguments");
+        return GMCO_EINVAL;
+    }
+    // every buffer must already be device memory: staging host data would need scratch
+    const void *ptrs[4] = {penalty_weights, X, objectives, grad_x};
+    for (const void *q : ptrs) {
+        if (!q) continue;
+        cudaPointerAttributes a;
+        if (cudaPointerGetAttributes(&a, q) != cudaSuccess) {
+            cudaGetLastError();
+            set_error_msg("gmco_evaluate_noalloc: buffers must be device memory");
+            return GMCO_EINVAL;
+        }
+        if (a.type != cudaMemoryTypeDevice && a.type != cudaMemoryTypeManaged) {
+            set_error_msg("gmco_evaluate_noalloc: buffers must be device memory");
+            return GMCO_EINVAL;
+        }
+    }
+    const size_t need = noalloc_required_bytes(pr->pb, P);
+    if (need > noalloc_scratch_bytes()) {
+        char buf[256];
+        snprintf(buf, sizeof buf,
+                 "gmco_evaluate_noalloc: %lld plans of this problem need %zu bytes of scratch; "
+                 "the fixed scratch array holds %zu bytes",
+                 (long long)P, need, noalloc_scratch_bytes());
+        set_error_msg(buf);
+        return GMCO_EUNSUPPORTED;
+    }
+    CK(cudaSetDevice(pr->device));
+    CK(noalloc_evaluate(pr->pb, penalty_weights, P, X, objectives, grad_x,
+                        (cudaStream_t)cuda_stream));
+    return GMCO_OK;
+}
+
 gmco_status gmco_dvh_from_dose(gmco_problem *pr, const float *dose, int64_t P, float *dvh,
                                void *cuda_stream)
 {

@@ -97,6 +97,12 @@ int32_t simt_pts_per_split(const DevProblem &pb, int32_t n_split);
 cudaError_t launch_gemm1_simt(const EvalArgs &e, int32_t mode, cudaStream_t st);
 cudaError_t launch_gemm2_simt(const EvalArgs &e, cudaStream_t st);
 
+// Allocation-free FP32 evaluation (noalloc.cu): scratch in a fixed device array.
+size_t noalloc_scratch_bytes();
+size_t noalloc_required_bytes(const DevProblem &pb, int64_t P);
+cudaError_t noalloc_evaluate(const DevProblem &pb, const float *W, int64_t P, const float *X,
+                             double *F, float *grad, cudaStream_t st);
+
 // DVH indices of P dose rows (P x np_pad, row stride ld)
 cudaError_t launch_dvh(const DevProblem &pb, const float *D, int64_t ld, const int32_t *rows,
                        int32_t P, double rx, float *dvh_out, cudaStream_t st);

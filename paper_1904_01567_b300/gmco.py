@@ -62,6 +62,8 @@ def load():
         lib.gmco_solve_batch.restype = ctypes.c_int
         lib.gmco_evaluate.argtypes = [_vp, _vp, _i64, _vp, _vp, _vp, _vp, _vp, _vp]
         lib.gmco_evaluate.restype = ctypes.c_int
+        lib.gmco_evaluate_noalloc.argtypes = [_vp, _vp, _i64, _vp, _vp, _vp, _vp]
+        lib.gmco_evaluate_noalloc.restype = ctypes.c_int
         lib.gmco_dvh_from_dose.argtypes = [_vp, _vp, _i64, _vp, _vp]
         lib.gmco_dvh_from_dose.restype = ctypes.c_int
         lib.gmco_profile_evaluate.argtypes = [_vp, _vp, _i64, _vp, _i32, _vp, _vp]
@@ -237,6 +239,26 @@ def profile_evaluate(h, penalty_weights, X, reps=20):
                            grad_issued=fl[3]))
 
 
+def evaluate_noalloc(h, penalty_weights, X, objectives=None, grad=None, stream=None):
+    """gmco_evaluate_noalloc: FP32 objectives and gradient without any device allocation in
+    the call.  penalty_weights, X and the outputs must be torch CUDA tensors; outputs are
+    allocated here (by torch) when not given.  Queued on `stream` (default: torch's current)
+    and not waited for."""
+    import torch
+    info = problem_info(h)
+    w = penalty_weights.detach().to(torch.float32).contiguous()
+    x = X.detach().to(torch.float32).contiguous()
+    P = int(w.shape[0])
+    if objectives is None:
+        objectives = torch.empty(P, dtype=torch.float64, device=w.device)
+    if grad is None:
+        grad = torch.empty((P, info["n_dwell"]), dtype=torch.float32, device=w.device)
+    _check(load().gmco_evaluate_noalloc(h, w.data_ptr(), P, x.data_ptr(), objectives.data_ptr(),
+                                        grad.data_ptr(), _stream_ptr(stream, True)),
+           "gmco_evaluate_noalloc")
+    return dict(objectives=objectives, grad=grad, _keep=(w, x))
+
+
 def dvh_from_dose(h, dose, stream=None):
     """gmco_dvh_from_dose: DVH indices of given doses (P x n_pnt)."""
     d_keep, d_ptr, cuda = _prep(dose, np.float32, "float32")
@@ -262,6 +284,9 @@ class Problem:
 
     def dvh_from_dose(self, dose, **kw):
         return dvh_from_dose(self.handle, dose, **kw)
+
+    def evaluate_noalloc(self, penalty_weights, X, **kw):
+        return evaluate_noalloc(self.handle, penalty_weights, X, **kw)
 
     def profile_evaluate(self, penalty_weights, X, reps=20):
         return profile_evaluate(self.handle, penalty_weights, X, reps)
