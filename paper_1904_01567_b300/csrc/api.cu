@@ -95,7 +95,7 @@ struct gmco_problem {
     SolverState s{};
     float *Tc = nullptr, *dTc = nullptr, *Wc = nullptr, *G = nullptr;
     float *Fpart = nullptr, *dFpart = nullptr, *gpart = nullptr;
-    int32_t n_split = 1, n_ptiles = 1;
+    int32_t n_ptiles = 1;
     TcBuffers tcb{};
     float *dW = nullptr, *dT0 = nullptr, *dTout = nullptr, *dDvh = nullptr;
     double *dObj = nullptr;
@@ -147,13 +147,16 @@ void destroy_graphs(gmco_problem *pr)
     }
 }
 
-int32_t choose_split(const DevProblem &pb, int32_t cap)
+// Largest number of gradient-partial rows (splits x rows) any row count up to cap can use.
+int64_t max_split_rows(const SplitPlan &sp, int32_t cap)
 {
-    // enough CTAs for ~4 waves of 2 CTAs/SM on 148 SMs in the gradient GEMM
-    const int64_t base = ceil_div(pb.nd_pad, 128) * ceil_div(std::max(cap, 1), 64);
-    int64_t sp = ceil_div(148 * 2 * 4, std::max<int64_t>(base, 1));
-    sp = std::max<int64_t>(1, std::min<int64_t>(sp, pb.np_pad / 128));
-    return (int32_t)sp;
+    int64_t best = 0;
+    for (int32_t n = 1; n <= cap; ++n) {
+        int32_t kbps, ns;
+        split_plan(sp, n, &kbps, &ns);
+        best = std::max<int64_t>(best, (int64_t)ns * n);
+    }
+    return best;
 }
 
 gmco_status ensure_workspace(gmco_problem *pr, int32_t P)
@@ -185,19 +188,23 @@ gmco_status ensure_workspace(gmco_problem *pr, int32_t P)
     CK(a.alloc(&s.iters, (size_t)cap)); CK(a.alloc(&s.maxit, (size_t)cap));
     CK(a.alloc(&s.ls, (size_t)cap)); CK(a.alloc(&s.hcount, (size_t)cap));
     CK(a.alloc(&s.hnewest, (size_t)cap)); CK(a.alloc(&s.nsmall, (size_t)cap));
+    CK(a.alloc(&s.slot_of, (size_t)cap)); CK(a.alloc(&s.cnt, 2));
     CK(a.alloc(&s.Wn, (size_t)cap * S));
-    CK(a.alloc(&s.list, (size_t)cap)); CK(a.alloc(&s.n_act, 1)); CK(a.alloc(&s.n_live, 1));
+    CK(a.alloc(&s.list, (size_t)cap)); CK(a.alloc(&s.n_live, 1));
+    s.n_act = s.cnt;   // the compaction's row count is the even-step counter
     CK(cudaMemset(s.S, 0, vn * m * sizeof(float)));
     CK(cudaMemset(s.Y, 0, vn * m * sizeof(float)));
 
     pr->n_ptiles = simt_n_ptiles(pb);
-    pr->n_split = choose_split(pb, cap);
     CK(a.alloc(&pr->Tc, vn)); CK(a.alloc(&pr->dTc, vn)); CK(a.alloc(&pr->Wc, (size_t)cap * S));
     CK(a.alloc(&pr->G, (size_t)cap * pb.np_pad));
     const int32_t nparts = std::max(pr->n_ptiles, tc_n_ptiles(pb));
     CK(a.alloc(&pr->Fpart, (size_t)nparts * cap));
     CK(a.alloc(&pr->dFpart, (size_t)nparts * cap));
-    CK(a.alloc(&pr->gpart, (size_t)std::max(pr->n_split, tc_max_split(pb)) * vn));
+    int64_t grows = max_split_rows(simt_split_plan(pb), cap);
+    if (pr->opt.precision != GMCO_PREC_FP32)
+        grows = std::max(grows, max_split_rows(tc_split_plan(pb), cap));
+    CK(a.alloc(&pr->gpart, (size_t)grows * pb.nd_pad));
     if (pr->opt.precision != GMCO_PREC_FP32) {
         cudaError_t e = tc_alloc(pb, cap, &pr->tcb, [&](void **p, size_t bytes) {
             unsigned char *q = nullptr;
@@ -241,7 +248,7 @@ gmco_status launch_eval(gmco_problem *pr, SolverState s, int form, bool with_dT,
         e.Fpart = pr->Fpart;
         e.dFpart = pr->dFpart;
         e.gpart = pr->gpart;
-        e.n_split = pr->n_split;
+        e.sp = simt_split_plan(pb);
         CK(launch_gemm1_simt(e, MODE_G, st));
         if (ev) CK(cudaEventRecord(ev[2], st));
         CK(launch_gemm2_simt(e, st));
@@ -277,23 +284,67 @@ gmco_status launch_dose_eval(gmco_problem *pr, cudaStream_t st)
     e.Fpart = pr->Fpart;
     e.dFpart = nullptr;
     e.gpart = nullptr;
-    e.n_split = 0;
+    e.sp = simt_split_plan(pb);
     CK(launch_gemm1_simt(e, MODE_DOSE, st));
     CK(launch_finish(s, e, pr->n_ptiles, st));
     pr->launches += 4;
     return GMCO_OK;
 }
 
+// One solver step = the form's dose and gradient GEMMs over this step's compact rows, the
+// reset of the next step's row counter, and the fused update (k_step) that writes the next
+// step's rows.  Step k uses counter k % 2; `steps` is even so a graph starts on counter 0.
 gmco_status record_steps(gmco_problem *pr, int form, int steps, const UpdateParams &u,
                          cudaStream_t st)
 {
     SolverState s = pr->s;
+    const DevProblem &pb = pr->pb;
     for (int k = 0; k < steps; ++k) {
-        CK(launch_compact(s, 0, st));
-        CKS(launch_eval(pr, s, form, true, st));
-        CK(launch_update(s, u, st));
+        int32_t *cur = s.cnt + (k & 1), *next = s.cnt + ((k + 1) & 1);
+        StepArgs a{};
+        a.Fpart = pr->Fpart;
+        a.dFpart = pr->dFpart;
+        a.gpart = pr->gpart;
+        a.cap = pr->cap;
+        a.rows_cur = cur;
+        a.rows_next = next;
+        if (form == 0) {
+            EvalArgs e{};
+            e.pb = pb;
+            e.n_rows = cur;
+            e.cap = pr->cap;
+            e.Tt = pr->Tc;
+            e.dT = pr->dTc;
+            e.Wc = pr->Wc;
+            e.G = pr->G;
+            e.Fpart = pr->Fpart;
+            e.dFpart = pr->dFpart;
+            e.gpart = pr->gpart;
+            e.sp = simt_split_plan(pb);
+            CK(launch_gemm1_simt(e, MODE_G, st));
+            CK(launch_gemm2_simt(e, st));
+            a.n_ptiles = pr->n_ptiles;
+            a.sp = e.sp;
+            a.fmt = 0;
+            a.Tc = pr->Tc;
+            a.dTc = pr->dTc;
+            a.Wc = pr->Wc;
+        } else {
+            int32_t nl = 0;
+            CK(tc_launch_gemms(pb, pr->tcb, cur, pr->Fpart, pr->dFpart, pr->gpart, pr->cap, true,
+                               nullptr, st, &nl));
+            a.n_ptiles = tc_n_ptiles(pb);
+            a.sp = tc_split_plan(pb);
+            a.fmt = 1;
+            for (int j = 0; j < 3; ++j) a.Tb[j] = pr->tcb.T[j];
+            a.dTb = pr->tcb.dT;
+            a.nT = std::max(pb.tc_terms, 2);
+            a.kpad = (int32_t)pb.kpad;
+            a.Wc = pr->tcb.Wc;
+        }
+        CK(cudaMemsetAsync(next, 0, sizeof(int32_t), st));
+        CK(launch_step(s, u, a, st));
     }
-    CK(launch_compact(s, 0, st));
     return GMCO_OK;
 }
 
@@ -301,7 +352,18 @@ gmco_status record_steps(gmco_problem *pr, int form, int steps, const UpdatePara
 gmco_status run_loop(gmco_problem *pr, int form, int32_t P, const UpdateParams &u,
                      int64_t max_steps, int64_t *steps_done)
 {
-    const int steps = std::max(1, pr->opt.steps_per_poll);
+    const int steps = (int)round_up(std::max(2, pr->opt.steps_per_poll), 2);
+    // rows of the first step: every plan in INIT or TRIAL, by compaction and preparation
+    {
+        SolverState s0 = pr->s;
+        CK(launch_compact(s0, 0, pr->stream));
+        if (form == 0) {
+            CK(launch_prep_fp32(s0, pr->pb, pr->Tc, pr->dTc, pr->Wc, false, pr->stream));
+        } else {
+            CK(tc_launch_prep(pr->pb, s0, pr->tcb, pr->cap, false, pr->stream));
+        }
+        pr->launches += 2;
+    }
     gmco_problem::GraphKey key;
     key.P = P;
     key.form = form;
@@ -329,9 +391,8 @@ gmco_status run_loop(gmco_problem *pr, int form, int32_t P, const UpdateParams &
         CK(ei);
         pr->gkey[form] = key;
     }
-    // launches per graph: steps x (compact + eval + update) + trailing compact
-    const int64_t per_eval = form == 0 ? 4 : tc_launches_per_eval();
-    const int64_t per_graph = (int64_t)steps * (2 + per_eval) + 1;
+    // launches per graph: steps x (dose GEMM + gradient GEMM + k_step); memsets not counted
+    const int64_t per_graph = (int64_t)steps * 3;
     int64_t done = 0;
     for (;;) {
         CK(cudaGraphLaunch(pr->gexec[form], pr->stream));

@@ -30,12 +30,37 @@ struct DevProblem {
     int8_t *sid = nullptr;         // np_pad, -1 on padding points
     // tensor-core forms: A / row_scale split into tc_terms BF16 terms, row-major and transposed
     int32_t tc_terms = 0;          // 0 = FP32 SIMT form
+    float4 *pt4 = nullptr;         // np_pad: (D_min, D_max, scale, id) per point, dose epilogue
+    int32_t *chunk = nullptr;      // np_pad / 16: epilogue mode of each run of 16 points
     int64_t kpad = 0;              // dwells padded to a multiple of 64 (BF16 row length)
     __nv_bfloat16 *Ah[3] = {nullptr, nullptr, nullptr};    // np_pad x kpad
     __nv_bfloat16 *AhT[3] = {nullptr, nullptr, nullptr};   // kpad x np_pad
     float4 *sparams = nullptr;     // n_struct x (w_min, D_min, D_max, w_max)
     float *inv_count = nullptr;    // n_struct, 1 / N_s
 };
+
+// Point splits of a gradient GEMM, chosen at run time from the number of rows so that a small
+// batch still spreads over the SMs.  Shared by the GEMM kernels and the kernels that read
+// their partial sums, which must agree on it.
+struct SplitPlan {
+    int32_t rows_per_tile;   // plan rows per CTA tile
+    int32_t other_tiles;     // CTA tiles along the output columns
+    int32_t kb_total;        // K blocks (of points) in total
+    int32_t target_ctas;     // CTAs to aim for
+    int32_t max_split;       // grid extent along the split dimension
+};
+
+__host__ __device__ inline void split_plan(const SplitPlan &p, int32_t n_rows, int32_t *kbps,
+                                           int32_t *n_split)
+{
+    int32_t tiles = (n_rows + p.rows_per_tile - 1) / p.rows_per_tile;
+    tiles = (tiles < 1 ? 1 : tiles) * (p.other_tiles < 1 ? 1 : p.other_tiles);
+    int32_t target = p.target_ctas / tiles;
+    target = target < 1 ? 1 : (target > p.max_split ? p.max_split : target);
+    const int32_t k = (p.kb_total + target - 1) / target;
+    *kbps = k;
+    *n_split = (p.kb_total + k - 1) / k;
+}
 
 // Buffers of one evaluation pass over `rows` compact plan rows.
 struct EvalArgs {
@@ -48,8 +73,8 @@ struct EvalArgs {
     float *G;                // cap x np_pad, dF/dd per point (mode G) or dose (mode D)
     float *Fpart;            // n_ptiles x cap, per point tile partial of F
     float *dFpart;           // n_ptiles x cap, partial of F(trial) - F(base)
-    float *gpart;            // n_split x cap x nd_pad, partial of A^T G
-    int32_t n_split;
+    float *gpart;            // n_split x rows x nd_pad, partial of A^T G (rows = *n_rows)
+    SplitPlan sp;            // split plan of the gradient GEMM that wrote gpart
 };
 
 // Plan-indexed solver state (capacity P).
@@ -63,10 +88,29 @@ struct SolverState {
     int32_t *state = nullptr, *status = nullptr, *iters = nullptr, *maxit = nullptr;
     int32_t *ls = nullptr, *hcount = nullptr, *hnewest = nullptr;
     int32_t *nsmall = nullptr;          // consecutive iterations below the stop tolerance
+    int32_t *slot_of = nullptr;         // compact row of each plan in the current evaluation
+    int32_t *cnt = nullptr;             // 2 counters: rows of even and odd steps
     float *Wn = nullptr;                // P x n_struct, w / N_s
     int32_t *list = nullptr;            // compact row -> plan
     int32_t *n_act = nullptr;           // device scalar
     int32_t *n_live = nullptr;          // device scalar: plans not DONE after the last update
+};
+
+// Inputs of a fused solver step: the evaluation's partial sums and where the next step's
+// compact rows go.
+struct StepArgs {
+    const float *Fpart, *dFpart;     // n_ptiles x cap
+    const float *gpart;              // n_split x rows x nd_pad
+    int32_t n_ptiles, cap;
+    SplitPlan sp;
+    const int32_t *rows_cur;         // rows evaluated this step
+    int32_t *rows_next;              // slot counter of the next step
+    int32_t fmt;                     // 0: FP32 rows (Tc, dTc), 1: BF16 split rows (Tb, dTb)
+    float *Tc, *dTc;
+    __nv_bfloat16 *Tb[3];
+    __nv_bfloat16 *dTb;
+    int32_t nT, kpad;
+    float *Wc;
 };
 
 struct UpdateParams {
@@ -83,7 +127,8 @@ cudaError_t launch_prep_fp32(const SolverState &s, const DevProblem &pb, float *
                              float *Wc, bool force_base, cudaStream_t st);
 cudaError_t launch_finish(const SolverState &s, const EvalArgs &e, int32_t n_ptiles,
                           cudaStream_t st);
-cudaError_t launch_update(const SolverState &s, const UpdateParams &u, cudaStream_t st);
+cudaError_t launch_step(const SolverState &s, const UpdateParams &u, const StepArgs &a,
+                        cudaStream_t st);
 cudaError_t launch_count_live(const SolverState &s, cudaStream_t st);
 cudaError_t launch_reopen(const SolverState &s, int32_t extra_iters, cudaStream_t st);
 cudaError_t launch_profile_setup(const SolverState &s, cudaStream_t st);
@@ -93,7 +138,7 @@ cudaError_t launch_square(const float *x, float *t, int64_t rows, int64_t nd, in
 // SIMT FP32 evaluation
 enum EvalMode : int32_t { MODE_G = 0, MODE_DOSE = 1 };
 int32_t simt_n_ptiles(const DevProblem &pb);
-int32_t simt_pts_per_split(const DevProblem &pb, int32_t n_split);
+SplitPlan simt_split_plan(const DevProblem &pb);
 cudaError_t launch_gemm1_simt(const EvalArgs &e, int32_t mode, cudaStream_t st);
 cudaError_t launch_gemm2_simt(const EvalArgs &e, cudaStream_t st);
 

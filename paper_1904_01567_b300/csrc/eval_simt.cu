@@ -197,19 +197,22 @@ __global__ void __launch_bounds__(NT, 2) k_gemm1(EvalArgs e, int32_t mode)
     }
 }
 
-__global__ void __launch_bounds__(NT, 2) k_gemm2(EvalArgs e, int32_t pts_per_split)
+__global__ void __launch_bounds__(NT, 2) k_gemm2(EvalArgs e)
 {
     __shared__ __align__(16) float Gs[2][BK][SP];
     __shared__ __align__(16) float As[2][BK][BN];
     const int n_rows = *e.n_rows;
     const int row0 = blockIdx.y * BM;
     if (row0 >= n_rows) return;
+    int kbps, n_split;
+    split_plan(e.sp, n_rows, &kbps, &n_split);
+    const int split = blockIdx.z;
+    if (split >= n_split) return;
     const DevProblem &pb = e.pb;
     const int nd = (int)pb.nd_pad;
     const int d0 = blockIdx.x * BN;
-    const int split = blockIdx.z;
-    const int n_beg = split * pts_per_split;
-    const int n_end = min((int)pb.np_pad, n_beg + pts_per_split);
+    const int n_beg = split * kbps * BK;
+    const int n_end = min((int)pb.np_pad, n_beg + kbps * BK);
     const int tid = threadIdx.x;
     const int tr = tid >> 4, tc = tid & 15;
 
@@ -269,7 +272,7 @@ __global__ void __launch_bounds__(NT, 2) k_gemm2(EvalArgs e, int32_t pts_per_spl
     for (int r = 0; r < 4; ++r) {
         const int row = row0 + tr * 4 + r;
         if (row >= n_rows) continue;
-        float *out = e.gpart + ((size_t)split * e.cap + row) * nd + d0;
+        float *out = e.gpart + ((size_t)split * n_rows + row) * nd + d0;
         if (d0 + tc * 4 < nd)
             *reinterpret_cast<float4 *>(out + tc * 4) =
                 make_float4(acc[r][0], acc[r][1], acc[r][2], acc[r][3]);
@@ -283,9 +286,15 @@ __global__ void __launch_bounds__(NT, 2) k_gemm2(EvalArgs e, int32_t pts_per_spl
 
 int32_t simt_n_ptiles(const DevProblem &pb) { return (int32_t)(pb.np_pad / BN); }
 
-int32_t simt_pts_per_split(const DevProblem &pb, int32_t n_split)
+SplitPlan simt_split_plan(const DevProblem &pb)
 {
-    return (int32_t)round_up(ceil_div(pb.np_pad, n_split), BK);
+    SplitPlan p{};
+    p.rows_per_tile = BM;
+    p.other_tiles = (int32_t)ceil_div(pb.nd_pad, BN);
+    p.kb_total = (int32_t)(pb.np_pad / BK);
+    p.target_ctas = 148 * 2 * 2;     // two CTAs per SM, two waves
+    p.max_split = (int32_t)std::min<int64_t>(148, p.kb_total);
+    return p;
 }
 
 cudaError_t launch_gemm1_simt(const EvalArgs &e, int32_t mode, cudaStream_t st)
@@ -300,10 +309,9 @@ cudaError_t launch_gemm1_simt(const EvalArgs &e, int32_t mode, cudaStream_t st)
 cudaError_t launch_gemm2_simt(const EvalArgs &e, cudaStream_t st)
 {
     const DevProblem &hpb = e.pb;
-    const int32_t pps = simt_pts_per_split(hpb, e.n_split);
     dim3 grid((unsigned)ceil_div(hpb.nd_pad, BN), (unsigned)ceil_div(e.cap, BM),
-              (unsigned)e.n_split);
-    k_gemm2<<<grid, NT, 0, st>>>(e, pps);
+              (unsigned)e.sp.max_split);
+    k_gemm2<<<grid, NT, 0, st>>>(e);
     return cudaGetLastError();
 }
 

@@ -137,7 +137,9 @@ cudaError_t noalloc_evaluate(const DevProblem &pb, const float *W, int64_t P, co
     ea.Fpart = reinterpret_cast<float *>(b + L.Fpart);
     ea.dFpart = nullptr;
     ea.gpart = reinterpret_cast<float *>(b + L.gpart);
-    ea.n_split = kSplit;
+    ea.sp = simt_split_plan(pb);
+    ea.sp.target_ctas = 1 << 30;     // always exactly kSplit point splits
+    ea.sp.max_split = kSplit;
     k_na_prep<<<(unsigned)P, 128, 0, st>>>(X, W, pb.inv_count, (int32_t)P, (int32_t)pb.n_dwell,
                                            (int32_t)pb.nd_pad, pb.n_struct, Tc, Wc, n_rows);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;

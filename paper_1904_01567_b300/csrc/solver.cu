@@ -142,6 +142,7 @@ __global__ void k_prep_fp32(SolverState s, float *__restrict__ Tc, float *__rest
     }
     if (threadIdx.x < s.n_struct)
         Wc[(size_t)i * s.n_struct + threadIdx.x] = s.Wn[(size_t)j * s.n_struct + threadIdx.x];
+    if (threadIdx.x == 0) s.slot_of[j] = i;
 }
 
 // gt = 2 x_t * sum_split gpart (chain rule of t = x^2, Eq. (2)); Ft, dFt = fixed-order FP64
@@ -153,9 +154,12 @@ __global__ void k_finish(SolverState s, EvalArgs e, int32_t n_ptiles)
     const int j = s.list[i];
     const int nd = s.nd_pad;
     if (e.gpart) {
+        const int R = *e.n_rows;
+        int kbps, n_split;
+        split_plan(e.sp, R, &kbps, &n_split);
         for (int l = threadIdx.x; l < nd; l += blockDim.x) {
             float acc = 0.0f;
-            for (int q = 0; q < e.n_split; ++q) acc += e.gpart[((size_t)q * e.cap + i) * nd + l];
+            for (int q = 0; q < n_split; ++q) acc += e.gpart[((size_t)q * R + i) * nd + l];
             s.gt[(size_t)j * nd + l] = 2.0f * s.xt[(size_t)j * nd + l] * acc;
         }
     }
@@ -189,9 +193,58 @@ __device__ __forceinline__ void plan_done(const SolverState &s, int j, int statu
     }
 }
 
-// Warp-per-plan update: Armijo acceptance, curvature pair, stop test, two-loop direction.
+// Next trial row of plan j in compact slot `slot`: x_t = x + alpha p, t = x_t^2 and
+// dT = alpha p (2 x + alpha p), written in the evaluation form's operand layout.
 template <int EPL>
-__global__ void __launch_bounds__(256) k_update(SolverState s, UpdateParams u)
+__device__ __forceinline__ void write_trial_row(const SolverState &s, const StepArgs &a, int j,
+                                                int slot, float alpha, int lane)
+{
+    const int nd = s.nd_pad, epl = nd >> 5;
+    const size_t vb = (size_t)j * nd;
+#pragma unroll
+    for (int e = 0; e < EPL; ++e) {
+        if (e >= epl) continue;
+        const int l = lane + 32 * e;
+        const float xv = s.x[vb + l];
+        const float ap = alpha * s.p[vb + l];
+        const float xn = xv + ap;
+        const float dt = ap * (2.0f * xv + ap);
+        s.xt[vb + l] = xn;
+        const float t = xn * xn;
+        if (a.fmt == 0) {
+            a.Tc[(size_t)slot * nd + l] = t;
+            a.dTc[(size_t)slot * nd + l] = dt;
+        } else {
+            const size_t o = (size_t)slot * a.kpad + l;
+            const __nv_bfloat16 t1 = __float2bfloat16_rn(t);
+            a.Tb[0][o] = t1;
+            const float r1 = t - __bfloat162float(t1);
+            if (a.nT > 1) {
+                const __nv_bfloat16 t2 = __float2bfloat16_rn(r1);
+                a.Tb[1][o] = t2;
+                if (a.nT > 2) a.Tb[2][o] = __float2bfloat16_rn(r1 - __bfloat162float(t2));
+            }
+            a.dTb[o] = __float2bfloat16_rn(dt);
+        }
+    }
+    if (a.fmt != 0) {   // BF16 rows are kpad long: keep the columns past nd_pad at zero
+        for (int l = nd + lane; l < a.kpad; l += 32) {
+            const size_t o = (size_t)slot * a.kpad + l;
+            for (int k = 0; k < a.nT; ++k) a.Tb[k][o] = __float2bfloat16_rn(0.0f);
+            a.dTb[o] = __float2bfloat16_rn(0.0f);
+        }
+    }
+    if (lane < s.n_struct)
+        a.Wc[(size_t)slot * s.n_struct + lane] = s.Wn[(size_t)j * s.n_struct + lane];
+}
+
+// One solver step for plan j (warp per plan), after the evaluation of its compact row:
+//   sum the per-tile objective partials and the per-split gradient partials (gt = 2 x_t A^T G),
+//   INIT: take F, g; TRIAL: Armijo test on dF (FP64), curvature pair (FP64 s'y, y'y), stop test;
+//   new direction by the two-loop recursion; then, if the plan still runs, claim a slot of the
+//   next step's compact rows and write its next trial point there.
+template <int EPL>
+__global__ void __launch_bounds__(256) k_step(SolverState s, UpdateParams u, StepArgs a)
 {
     const int j = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int lane = threadIdx.x & 31;
@@ -201,7 +254,31 @@ __global__ void __launch_bounds__(256) k_update(SolverState s, UpdateParams u)
     const int nd = s.nd_pad, epl = nd >> 5, m = s.m;
     const size_t vb = (size_t)j * nd;
     float *x = s.x + vb, *g = s.g + vb, *p = s.p + vb;
-    const float *xt = s.xt + vb, *gt = s.gt + vb;
+    const float *xt = s.xt + vb;
+
+    // ---- results of this step's evaluation (fixed summation order)
+    const int slot = s.slot_of[j];
+    const int R = *a.rows_cur;
+    double fsum = 0.0, dfsum = 0.0;
+    for (int t = lane; t < a.n_ptiles; t += 32) {
+        fsum += (double)a.Fpart[(size_t)t * a.cap + slot];
+        if (st == ST_TRIAL) dfsum += (double)a.dFpart[(size_t)t * a.cap + slot];
+    }
+    const double Ft = warp_sum_d(fsum);
+    const double dF = warp_sum_d(dfsum);
+    int kbps, n_split;
+    split_plan(a.sp, R, &kbps, &n_split);
+    float gtv[EPL];
+#pragma unroll
+    for (int e = 0; e < EPL; ++e) {
+        gtv[e] = 0.0f;
+        if (e < epl) {
+            const int l = lane + 32 * e;
+            float acc = 0.0f;
+            for (int q = 0; q < n_split; ++q) acc += a.gpart[((size_t)q * R + slot) * nd + l];
+            gtv[e] = 2.0f * xt[l] * acc;
+        }
+    }
 
     float gv[EPL];
     float gmax = 0.0f;
@@ -209,29 +286,32 @@ __global__ void __launch_bounds__(256) k_update(SolverState s, UpdateParams u)
     int cnt = s.hcount[j];
     int nw = s.hnewest[j];
     bool need_dir = false;
+    bool retry = false;          // line search continues with a halved step
+    double alpha_next = 0.0;
 
     if (st == ST_INIT) {
-        const double F = s.Ft[j];
-        bool fin = isfinite(F);
+        bool fin = isfinite(Ft);
 #pragma unroll
         for (int e = 0; e < EPL; ++e) {
             gv[e] = 0.0f;
             if (e < epl) {
-                const int l = lane + 32 * e;
-                gv[e] = gt[l];
-                g[l] = gv[e];
+                gv[e] = gtv[e];
+                g[lane + 32 * e] = gv[e];
                 fin = fin && isfinite(gv[e]);
                 gmax = fmaxf(gmax, fabsf(gv[e]));
             }
         }
         fin = __all_sync(kFull, fin);
         gmax = warp_max_f(gmax);
-        if (lane == 0) s.F[j] = F;
+        if (lane == 0) {
+            s.F[j] = Ft;
+            s.Ft[j] = Ft;
+        }
         if (!fin) { plan_done(s, j, GMCO_PLAN_NONFINITE, lane); return; }
-        if (F == 0.0 || gmax == 0.0f) { plan_done(s, j, GMCO_PLAN_CONVERGED, lane); return; }
+        if (Ft == 0.0 || gmax == 0.0f) { plan_done(s, j, GMCO_PLAN_CONVERGED, lane); return; }
         need_dir = true;
     } else {
-        const double dF = s.dFt[j], Ft = s.Ft[j], alpha = s.alpha[j], gtp = s.gtp[j];
+        const double alpha = s.alpha[j], gtp = s.gtp[j];
         const bool ok = isfinite(dF) && isfinite(Ft) && dF <= u.c1 * alpha * gtp;
         if (ok) {
             float sv[EPL], yv[EPL];
@@ -244,7 +324,7 @@ __global__ void __launch_bounds__(256) k_update(SolverState s, UpdateParams u)
                 gv[e] = 0.0f;
                 if (e < epl) {
                     const int l = lane + 32 * e;
-                    const float xo = x[l], xn = xt[l], go = g[l], gn = gt[l];
+                    const float xo = x[l], xn = xt[l], go = g[l], gn = gtv[e];
                     sv[e] = xn - xo;
                     yv[e] = gn - go;
                     sy += (double)sv[e] * (double)yv[e];
@@ -280,6 +360,7 @@ __global__ void __launch_bounds__(256) k_update(SolverState s, UpdateParams u)
             ++it;
             if (lane == 0) {
                 s.F[j] = Fprev + dF;
+                s.Ft[j] = Ft;
                 s.iters[j] = it;
                 s.hcount[j] = cnt;
                 s.hnewest[j] = nw;
@@ -313,88 +394,143 @@ __global__ void __launch_bounds__(256) k_update(SolverState s, UpdateParams u)
                     return;
                 }
             } else {
+                retry = true;
+                alpha_next = alpha * 0.5;
                 if (lane == 0) {
-                    s.alpha[j] = alpha * 0.5;
+                    s.alpha[j] = alpha_next;
                     s.ls[j] = lsn;
                 }
-                return;
             }
         }
     }
 
-    if (!need_dir) return;
-    if (it >= s.maxit[j]) { plan_done(s, j, GMCO_PLAN_MAXITER, lane); return; }
+    if (need_dir) {
+        if (it >= s.maxit[j]) { plan_done(s, j, GMCO_PLAN_MAXITER, lane); return; }
 
-    // two-loop recursion, q in registers (FP32 vectors, FP32 dot products)
-    float q[EPL];
+        // two-loop recursion, q in registers (FP32 vectors and dot products); the next
+        // history pair is loaded while the current dot product is reduced
+        float q[EPL];
 #pragma unroll
-    for (int e = 0; e < EPL; ++e) q[e] = gv[e];
-    if (cnt > 0) {
-        float al[kMaxHist];
+        for (int e = 0; e < EPL; ++e) q[e] = gv[e];
+        if (cnt > 0) {
+            float al[kMaxHist];
+            float sc[EPL], yc[EPL];
+            {
+                const int i0 = nw;
+                const float *Si = s.S + ((size_t)j * m + i0) * nd;
+                const float *Yi = s.Y + ((size_t)j * m + i0) * nd;
 #pragma unroll
-        for (int k = 0; k < kMaxHist; ++k) {
-            al[k] = 0.0f;
-            if (k < cnt) {
-                const int i = (nw - k + m) % m;
-                const float *Si = s.S + ((size_t)j * m + i) * nd;
-                const float *Yi = s.Y + ((size_t)j * m + i) * nd;
-                float d = 0.0f;
+                for (int e = 0; e < EPL; ++e) {
+                    sc[e] = e < epl ? Si[lane + 32 * e] : 0.0f;
+                    yc[e] = e < epl ? Yi[lane + 32 * e] : 0.0f;
+                }
+            }
 #pragma unroll
-                for (int e = 0; e < EPL; ++e)
-                    if (e < epl) d += Si[lane + 32 * e] * q[e];
-                const float a = (float)s.rho[(size_t)j * m + i] * warp_sum_f(d);
-                al[k] = a;
+            for (int k = 0; k < kMaxHist; ++k) {
+                al[k] = 0.0f;
+                if (k < cnt) {
+                    const int i = (nw - k + m) % m;
+                    float sn[EPL], yn[EPL];
+                    const bool more = k + 1 < cnt;
+                    const int i1 = (nw - k - 1 + m) % m;
+                    const float *Sn = s.S + ((size_t)j * m + i1) * nd;
+                    const float *Yn = s.Y + ((size_t)j * m + i1) * nd;
 #pragma unroll
-                for (int e = 0; e < EPL; ++e)
-                    if (e < epl) q[e] -= a * Yi[lane + 32 * e];
+                    for (int e = 0; e < EPL; ++e) {
+                        sn[e] = (more && e < epl) ? Sn[lane + 32 * e] : 0.0f;
+                        yn[e] = (more && e < epl) ? Yn[lane + 32 * e] : 0.0f;
+                    }
+                    float d = 0.0f;
+#pragma unroll
+                    for (int e = 0; e < EPL; ++e) d += sc[e] * q[e];
+                    const float av = (float)s.rho[(size_t)j * m + i] * warp_sum_f(d);
+                    al[k] = av;
+#pragma unroll
+                    for (int e = 0; e < EPL; ++e) {
+                        q[e] -= av * yc[e];
+                        sc[e] = sn[e];
+                        yc[e] = yn[e];
+                    }
+                }
+            }
+            const float gam = (float)s.gamma[j];
+#pragma unroll
+            for (int e = 0; e < EPL; ++e) q[e] *= gam;
+            {
+                const int io = (nw - (cnt - 1) + m) % m;   // oldest pair first
+                const float *Si = s.S + ((size_t)j * m + io) * nd;
+                const float *Yi = s.Y + ((size_t)j * m + io) * nd;
+#pragma unroll
+                for (int e = 0; e < EPL; ++e) {
+                    sc[e] = e < epl ? Si[lane + 32 * e] : 0.0f;
+                    yc[e] = e < epl ? Yi[lane + 32 * e] : 0.0f;
+                }
+            }
+#pragma unroll
+            for (int k = kMaxHist - 1; k >= 0; --k) {
+                if (k < cnt) {
+                    const int i = (nw - k + m) % m;
+                    float sn[EPL], yn[EPL];
+                    const bool more = k > 0;
+                    const int i1 = (nw - k + 1 + m) % m;
+                    const float *Sn = s.S + ((size_t)j * m + i1) * nd;
+                    const float *Yn = s.Y + ((size_t)j * m + i1) * nd;
+#pragma unroll
+                    for (int e = 0; e < EPL; ++e) {
+                        sn[e] = (more && e < epl) ? Sn[lane + 32 * e] : 0.0f;
+                        yn[e] = (more && e < epl) ? Yn[lane + 32 * e] : 0.0f;
+                    }
+                    float d = 0.0f;
+#pragma unroll
+                    for (int e = 0; e < EPL; ++e) d += yc[e] * q[e];
+                    const float b = (float)s.rho[(size_t)j * m + i] * warp_sum_f(d);
+#pragma unroll
+                    for (int e = 0; e < EPL; ++e) {
+                        q[e] += sc[e] * (al[k] - b);
+                        sc[e] = sn[e];
+                        yc[e] = yn[e];
+                    }
+                }
             }
         }
-        const float gam = (float)s.gamma[j];
+        double gtp = 0.0;
 #pragma unroll
-        for (int e = 0; e < EPL; ++e) q[e] *= gam;
+        for (int e = 0; e < EPL; ++e)
+            if (e < epl) gtp += (double)gv[e] * (double)(-q[e]);
+        gtp = warp_sum_d(gtp);   // directional derivative for the Armijo test, FP64
+        double alpha0 = (cnt == 0) ? fmin(1.0, 1.0 / (double)gmax) : 1.0;
+        if (!(gtp < 0.0)) {       // not a descent direction: steepest descent, fresh history
+            cnt = 0;
+            double gg = 0.0;
 #pragma unroll
-        for (int k = kMaxHist - 1; k >= 0; --k) {
-            if (k < cnt) {
-                const int i = (nw - k + m) % m;
-                const float *Si = s.S + ((size_t)j * m + i) * nd;
-                const float *Yi = s.Y + ((size_t)j * m + i) * nd;
-                float d = 0.0f;
-#pragma unroll
-                for (int e = 0; e < EPL; ++e)
-                    if (e < epl) d += Yi[lane + 32 * e] * q[e];
-                const float b = (float)s.rho[(size_t)j * m + i] * warp_sum_f(d);
-#pragma unroll
-                for (int e = 0; e < EPL; ++e)
-                    if (e < epl) q[e] += Si[lane + 32 * e] * (al[k] - b);
+            for (int e = 0; e < EPL; ++e) {
+                q[e] = gv[e];
+                if (e < epl) gg += (double)gv[e] * (double)gv[e];
             }
+            gtp = -warp_sum_d(gg);
+            alpha0 = fmin(1.0, 1.0 / (double)gmax);
         }
-    }
-    double gtp = 0.0;
 #pragma unroll
-    for (int e = 0; e < EPL; ++e)
-        if (e < epl) gtp += (double)gv[e] * (double)(-q[e]);
-    gtp = warp_sum_d(gtp);   // directional derivative for the Armijo test, FP64
-    double alpha0 = (cnt == 0) ? fmin(1.0, 1.0 / (double)gmax) : 1.0;
-    if (!(gtp < 0.0)) {       // not a descent direction: steepest descent, fresh history
-        cnt = 0;
-        double gg = 0.0;
-#pragma unroll
-        for (int e = 0; e < EPL; ++e) {
-            q[e] = gv[e];
-            if (e < epl) gg += (double)gv[e] * (double)gv[e];
+        for (int e = 0; e < EPL; ++e)
+            if (e < epl) p[lane + 32 * e] = -q[e];
+        if (lane == 0) {
+            s.gtp[j] = gtp;
+            s.alpha[j] = alpha0;
+            s.ls[j] = 0;
+            s.hcount[j] = cnt;
+            s.state[j] = ST_TRIAL;
         }
-        gtp = -warp_sum_d(gg);
-        alpha0 = fmin(1.0, 1.0 / (double)gmax);
+        alpha_next = alpha0;
+        retry = true;
     }
-#pragma unroll
-    for (int e = 0; e < EPL; ++e)
-        if (e < epl) p[lane + 32 * e] = -q[e];
-    if (lane == 0) {
-        s.gtp[j] = gtp;
-        s.alpha[j] = alpha0;
-        s.ls[j] = 0;
-        s.hcount[j] = cnt;
-        s.state[j] = ST_TRIAL;
+
+    if (retry) {   // still running: next trial point into a slot of the next step's rows
+        int ns = 0;
+        if (lane == 0) ns = atomicAdd(a.rows_next, 1);
+        ns = __shfl_sync(kFull, ns, 0);
+        if (lane == 0) s.slot_of[j] = ns;
+        __syncwarp();
+        write_trial_row<EPL>(s, a, j, ns, (float)alpha_next, lane);
     }
 }
 
@@ -466,15 +602,16 @@ cudaError_t launch_finish(const SolverState &s, const EvalArgs &e, int32_t n_pti
     return cudaGetLastError();
 }
 
-cudaError_t launch_update(const SolverState &s, const UpdateParams &u, cudaStream_t st)
+cudaError_t launch_step(const SolverState &s, const UpdateParams &u, const StepArgs &a,
+                        cudaStream_t st)
 {
     const int epl = s.nd_pad / 32;
     const int blocks = (int)ceil_div((int64_t)s.P * 32, 256);
-    if (epl <= 4) k_update<4><<<blocks, 256, 0, st>>>(s, u);
-    else if (epl <= 8) k_update<8><<<blocks, 256, 0, st>>>(s, u);
-    else if (epl <= 12) k_update<12><<<blocks, 256, 0, st>>>(s, u);
-    else if (epl <= 16) k_update<16><<<blocks, 256, 0, st>>>(s, u);
-    else k_update<32><<<blocks, 256, 0, st>>>(s, u);
+    if (epl <= 4) k_step<4><<<blocks, 256, 0, st>>>(s, u, a);
+    else if (epl <= 8) k_step<8><<<blocks, 256, 0, st>>>(s, u, a);
+    else if (epl <= 12) k_step<12><<<blocks, 256, 0, st>>>(s, u, a);
+    else if (epl <= 16) k_step<16><<<blocks, 256, 0, st>>>(s, u, a);
+    else k_step<32><<<blocks, 256, 0, st>>>(s, u, a);
     return cudaGetLastError();
 }
 

@@ -32,8 +32,10 @@ namespace {
 constexpr int BM = 128;                 // plan rows per tile (TMEM lanes)
 constexpr int BK = 64;                  // K elements per stage: 128 bytes of BF16
 constexpr int A_TILE = BM * BK * 2;     // bytes of one A-operand tile
-constexpr int BN1 = 256;                // points per dose-GEMM tile
-constexpr int NTHREADS = 384;           // warps 0-7 epilogue, 8 TMA, 9 MMA, 10 TMEM owner
+constexpr int BN1 = 128;                // points per dose-GEMM tile
+constexpr int EPI_WARPS = 16;           // 4 per TMEM lane quarter
+constexpr int W_TMA = EPI_WARPS, W_MMA = EPI_WARPS + 1, W_TMEM = EPI_WARPS + 2;
+constexpr int NTHREADS = (EPI_WARPS + 3) * 32;   // epilogue, TMA, MMA, TMEM owner
 constexpr int MAX_STAGES = 4;
 constexpr int SMEM_BUDGET = 208 * 1024;   // dynamic ring; static shared memory adds ~7 KB
 constexpr long long kSpinCycles = 2000000000LL;   // about 1 s at 2 GHz
@@ -49,6 +51,8 @@ struct Job {
     int32_t b_boxes, b_box_rows;
     int32_t n_mma, n_part0, n_part1;
     int32_t acc_cols, tmem_cols;
+    int32_t n_bufs, buf_cols;        // TMEM accumulator buffers and their column stride
+    int32_t n_ptiles;                // dose GEMM: point tiles
     int32_t n_stages, stage_bytes, b_bytes;
     int32_t b_row_step;
     int32_t kb_step, kb_total;
@@ -60,8 +64,8 @@ struct EpiArgs {
     int32_t cap;
     int64_t np_pad;
     // dose GEMM
-    const int8_t *sid;
-    const float *scale;
+    const float4 *pt4;       // per point: D_min, D_max, scale, structure id (padding: -inf, inf, 0, 0)
+    const int32_t *chunk;    // per 16 points: (structure id << 3) | mode, see k_chunk_info
     const float4 *sparams;
     int32_t n_struct;
     const float *Wc;
@@ -73,6 +77,7 @@ struct EpiArgs {
     // gradient GEMM
     float *gpart;
     int32_t nd_pad, n_total;
+    SplitPlan sp;            // gradient GEMM: point splits from the row count
     int32_t *err;
 };
 
@@ -194,43 +199,45 @@ __device__ __forceinline__ void tmem_ld16(uint32_t taddr, uint32_t (&r)[16])
 
 __device__ __forceinline__ void tmem_ld_wait() { asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory"); }
 
-// ------------------------------------------------------------------ penalty (Eq. (1))
-__device__ __forceinline__ void penalty(float d, float4 prm, float c, float &f, float &df)
+__device__ __forceinline__ void tmem_ld8(uint32_t taddr, uint32_t (&r)[8])
 {
-    const float u = prm.y - d, o = d - prm.z;
-    f = 0.0f;
-    df = 0.0f;
-    if (u > 0.0f) {
-        f = c * prm.x * u * u;
-        df = -2.0f * c * prm.x * u;
-    } else if (o > 0.0f) {
-        f = c * prm.w * o * o;
-        df = 2.0f * c * prm.w * o;
-    }
+    asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
+                 : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]),
+                   "=r"(r[6]), "=r"(r[7])
+                 : "r"(taddr));
 }
 
-__device__ __forceinline__ float penalty_delta(float dt, float dd, float4 prm, float c)
+__device__ __forceinline__ void tmem_ld_wait_regs8(uint32_t (&a)[8], uint32_t (&b)[8])
 {
-    const float db = dt - dd;
-    float lo = 0.0f, up = 0.0f;
-    const float ut = prm.y - dt, ub = prm.y - db;
-    if (ut > 0.0f && ub > 0.0f) lo = -dd * (ut + ub);
-    else if (ut > 0.0f) lo = ut * ut;
-    else if (ub > 0.0f) lo = -ub * ub;
-    const float ot = dt - prm.z, ob = db - prm.z;
-    if (ot > 0.0f && ob > 0.0f) up = dd * (ot + ob);
-    else if (ot > 0.0f) up = ot * ot;
-    else if (ob > 0.0f) up = -ob * ob;
-    return c * (prm.x * lo + prm.w * up);
+    asm volatile("tcgen05.wait::ld.sync.aligned;"
+                 : "+r"(a[0]), "+r"(a[1]), "+r"(a[2]), "+r"(a[3]), "+r"(a[4]), "+r"(a[5]),
+                   "+r"(a[6]), "+r"(a[7]), "+r"(b[0]), "+r"(b[1]), "+r"(b[2]), "+r"(b[3]),
+                   "+r"(b[4]), "+r"(b[5]), "+r"(b[6]), "+r"(b[7])
+                 :
+                 : "memory");
 }
 
-__device__ __forceinline__ uint32_t pack_bf16(float a, float b)
+// Waits for outstanding tcgen05.ld and tells the compiler that the given registers are only
+// valid from here on (an asynchronous load's destinations must not be read or copied earlier).
+__device__ __forceinline__ void tmem_ld_wait_regs(uint32_t (&a)[16], uint32_t (&b)[16])
 {
-    const __nv_bfloat162 v = __floats2bfloat162_rn(a, b);
-    return *reinterpret_cast<const uint32_t *>(&v);
+    asm volatile("tcgen05.wait::ld.sync.aligned;"
+                 : "+r"(a[0]), "+r"(a[1]), "+r"(a[2]), "+r"(a[3]), "+r"(a[4]), "+r"(a[5]),
+                   "+r"(a[6]), "+r"(a[7]), "+r"(a[8]), "+r"(a[9]), "+r"(a[10]), "+r"(a[11]),
+                   "+r"(a[12]), "+r"(a[13]), "+r"(a[14]), "+r"(a[15]), "+r"(b[0]), "+r"(b[1]),
+                   "+r"(b[2]), "+r"(b[3]), "+r"(b[4]), "+r"(b[5]), "+r"(b[6]), "+r"(b[7]),
+                   "+r"(b[8]), "+r"(b[9]), "+r"(b[10]), "+r"(b[11]), "+r"(b[12]), "+r"(b[13]),
+                   "+r"(b[14]), "+r"(b[15])
+                 :
+                 : "memory");
 }
 
 // ------------------------------------------------------------------ the GEMM kernel
+// Persistent: the grid is one CTA per SM, and each CTA walks work items derived from the
+// number of compact rows at run time (dose GEMM: plan tile x point tile; gradient GEMM: plan
+// tile x point split).  The TMA ring continues across items; accumulators live in n_bufs TMEM
+// buffers handed between the MMA thread and the epilogue warps through acc_full / acc_empty
+// barriers, so the epilogue of one item overlaps the MMAs of the next.
 template <int KIND>   // 1: dose GEMM with penalty epilogue, 2: gradient GEMM
 __global__ void __launch_bounds__(NTHREADS, 1)
     k_tc(const __grid_constant__ TcMaps maps, const Job job, const EpiArgs ep)
@@ -238,207 +245,312 @@ __global__ void __launch_bounds__(NTHREADS, 1)
     extern __shared__ uint8_t smem_raw[];
     uint8_t *smem = reinterpret_cast<uint8_t *>(
         (reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~static_cast<uintptr_t>(1023));
-    __shared__ __align__(8) uint64_t full_bar[MAX_STAGES], empty_bar[MAX_STAGES], acc_bar;
+    __shared__ __align__(8) uint64_t full_bar[MAX_STAGES], empty_bar[MAX_STAGES];
+    __shared__ __align__(8) uint64_t accf_bar[2], acce_bar[2];
     __shared__ uint32_t tmem_holder;
-    __shared__ int8_t s_sid[BN1];
-    __shared__ float s_scale[BN1];
-    __shared__ float4 s_prm[8];
-    __shared__ float s_w[BM][8];
-    __shared__ float s_half[2][BM];
+    __shared__ float4 s_pt[BN1];          // per point of the tile: D_min, D_max, scale, -
+    __shared__ int32_t s_sid[BN1];
+    __shared__ float s_cl[8][BM], s_ch[8][BM];   // w/N * w_min, w/N * w_max per row
+    __shared__ float s_half[2][4][BM];
+    __shared__ float s_wmin[8], s_wmax[8];
+    __shared__ int32_t s_chunk[BN1 / 16];
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int n_rows = *ep.n_rows;
-    const int row0 = blockIdx.y * BM;
-    if (row0 >= n_rows) return;   // the whole CTA leaves before any barrier or TMEM use
-
-    int kb0 = 0, kb1 = job.kb_total;
-    if (job.kb_step > 0) {
-        kb0 = blockIdx.x * job.kb_step;
-        kb1 = min(kb0 + job.kb_step, job.kb_total);
-    }
-    const int b_row0 = blockIdx.x * job.b_row_step;
+    const int plan_tiles = (n_rows + BM - 1) / BM;
+    int kbps = job.kb_total, n_split = 1;
+    if (KIND == 2) split_plan(ep.sp, n_rows, &kbps, &n_split);
+    const int per_tile = KIND == 1 ? job.n_ptiles : n_split;
+    const int n_items = plan_tiles * per_tile;
+    if ((int)blockIdx.x >= n_items) return;   // no work: leave before any barrier or TMEM use
 
     if (threadIdx.x == 0) {
         for (int s = 0; s < job.n_stages; ++s) {
             mbar_init(smem_u32(&full_bar[s]), 1);
             mbar_init(smem_u32(&empty_bar[s]), 1);
         }
-        mbar_init(smem_u32(&acc_bar), 1);
+        for (int b = 0; b < job.n_bufs; ++b) {
+            mbar_init(smem_u32(&accf_bar[b]), 1);
+            mbar_init(smem_u32(&acce_bar[b]), EPI_WARPS);   // one arrival per epilogue warp
+        }
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
-    if (warp == 10) tmem_alloc(smem_u32(&tmem_holder), (uint32_t)job.tmem_cols);
-    if (KIND == 1 && threadIdx.x < 256) {
-        const int i = threadIdx.x;
-        const int64_t p = (int64_t)b_row0 + i;
-        s_sid[i] = p < ep.np_pad ? ep.sid[p] : (int8_t)-1;
-        s_scale[i] = p < ep.np_pad ? ep.scale[p] : 0.0f;
-        if (i < ep.n_struct) s_prm[i] = ep.sparams[i];
-        if (i < BM) {
-            const int row = row0 + i;
-            for (int s = 0; s < ep.n_struct; ++s)
-                s_w[i][s] = row < n_rows ? ep.Wc[(size_t)row * ep.n_struct + s] : 0.0f;
-        }
+    if (warp == W_TMEM) tmem_alloc(smem_u32(&tmem_holder), (uint32_t)job.tmem_cols);
+    if (KIND == 1 && threadIdx.x < ep.n_struct) {
+        s_wmin[threadIdx.x] = ep.sparams[threadIdx.x].x;
+        s_wmax[threadIdx.x] = ep.sparams[threadIdx.x].w;
     }
     fence_before();
     __syncthreads();
     fence_after();
     const uint32_t tmem = tmem_holder;
 
-    if (warp == 8) {
-        // ---------------- TMA producer
+    if (warp == W_TMA) {
+        // ---------------- TMA producer (one thread)
         if (lane == 0) {
             int it = 0;
             bool ok = true;
-            for (int gi = 0; gi < job.n_groups && ok; ++gi) {
-                const Group &g = job.g[gi];
-                for (int kb = kb0; kb < kb1; ++kb, ++it) {
-                    const int s = it % job.n_stages;
-                    const uint32_t ph = (uint32_t)(it / job.n_stages) & 1u;
-                    if (!mbar_wait(smem_u32(&empty_bar[s]), ph ^ 1u, ep.err, 1)) { ok = false; break; }
-                    uint8_t *st = smem + (size_t)s * job.stage_bytes;
-                    const uint32_t fb = smem_u32(&full_bar[s]);
-                    mbar_expect_tx(fb, (uint32_t)(job.b_bytes + g.n_a * A_TILE));
-                    for (int b = 0; b < job.b_boxes; ++b)
-                        tma_load_2d(smem_u32(st + b * job.b_box_rows * 128), &maps.m[g.b_map],
-                                    kb * BK, b_row0 + b * job.b_box_rows, fb);
-                    for (int t = 0; t < g.n_a; ++t)
-                        tma_load_2d(smem_u32(st + job.b_bytes + t * A_TILE), &maps.m[g.a_map[t]],
-                                    kb * BK, row0, fb);
+            for (int item = blockIdx.x; item < n_items && ok; item += gridDim.x) {
+                const int ptile = item / per_tile, sub = item - ptile * per_tile;
+                const int row0 = ptile * BM;
+                const int b_row0 = KIND == 1 ? sub * BN1 : 0;
+                const int kb0 = KIND == 1 ? 0 : sub * kbps;
+                const int kb1 = KIND == 1 ? job.kb_total : min(kb0 + kbps, job.kb_total);
+                for (int gi = 0; gi < job.n_groups && ok; ++gi) {
+                    const Group &g = job.g[gi];
+                    for (int kb = kb0; kb < kb1; ++kb, ++it) {
+                        const int s = it % job.n_stages;
+                        const uint32_t ph = (uint32_t)(it / job.n_stages) & 1u;
+                        if (!mbar_wait(smem_u32(&empty_bar[s]), ph ^ 1u, ep.err, 1)) { ok = false; break; }
+                        uint8_t *st = smem + (size_t)s * job.stage_bytes;
+                        const uint32_t fb = smem_u32(&full_bar[s]);
+                        mbar_expect_tx(fb, (uint32_t)(job.b_bytes + g.n_a * A_TILE));
+                        for (int b = 0; b < job.b_boxes; ++b)
+                            tma_load_2d(smem_u32(st + b * job.b_box_rows * 128), &maps.m[g.b_map],
+                                        kb * BK, b_row0 + b * job.b_box_rows, fb);
+                        for (int t = 0; t < g.n_a; ++t)
+                            tma_load_2d(smem_u32(st + job.b_bytes + t * A_TILE), &maps.m[g.a_map[t]],
+                                        kb * BK, row0, fb);
+                    }
                 }
             }
         }
-    } else if (warp == 9) {
+    } else if (warp == W_MMA) {
         // ---------------- MMA issuer (one thread)
         if (lane == 0) {
-            int it = 0;
-            bool started[2] = {false, false};
+            int it = 0, local = 0;
             bool ok = true;
-            for (int gi = 0; gi < job.n_groups && ok; ++gi) {
-                const Group &g = job.g[gi];
-                for (int kb = kb0; kb < kb1; ++kb, ++it) {
-                    const int s = it % job.n_stages;
-                    const uint32_t ph = (uint32_t)(it / job.n_stages) & 1u;
-                    if (!mbar_wait(smem_u32(&full_bar[s]), ph, ep.err, 2)) { ok = false; break; }
-                    fence_after();
-                    const uint32_t st = smem_u32(smem + (size_t)s * job.stage_bytes);
-                    const int k16n = KIND == 1 ? min(4, job.k16_total - kb * 4) : 4;
-                    for (int k16 = 0; k16 < k16n; ++k16) {
-                        for (int t = 0; t < g.n_a; ++t) {
-                            const uint64_t ad = sw128_desc(st + job.b_bytes + t * A_TILE + k16 * 32);
-                            const int acc = g.acc[t];
-                            const uint32_t accum = started[acc] ? 1u : 0u;
-                            mma_bf16(tmem + (uint32_t)(acc * job.acc_cols), ad,
-                                     sw128_desc(st + k16 * 32), idesc_bf16(job.n_part0), accum);
-                            if (job.n_mma > 1)
-                                mma_bf16(tmem + (uint32_t)(acc * job.acc_cols + job.n_part0), ad,
-                                         sw128_desc(st + job.n_part0 * 128 + k16 * 32),
-                                         idesc_bf16(job.n_part1), accum);
-                            started[acc] = true;
+            for (int item = blockIdx.x; item < n_items && ok; item += gridDim.x, ++local) {
+                const int ptile = item / per_tile, sub = item - ptile * per_tile;
+                const int kb0 = KIND == 1 ? 0 : sub * kbps;
+                const int kb1 = KIND == 1 ? job.kb_total : min(kb0 + kbps, job.kb_total);
+                const int buf = local % job.n_bufs;
+                const uint32_t use = (uint32_t)(local / job.n_bufs);
+                if (!mbar_wait(smem_u32(&acce_bar[buf]), (use & 1u) ^ 1u, ep.err, 4)) { ok = false; break; }
+                fence_after();
+                const uint32_t tbuf = tmem + (uint32_t)(buf * job.buf_cols);
+                uint32_t started = 0u;   // bit a: accumulator a already written in this item
+                const uint32_t id0 = idesc_bf16(job.n_part0), id1 = idesc_bf16(job.n_part1);
+                const uint32_t boff1 = (uint32_t)(job.n_part0 * 128);
+                for (int gi = 0; gi < job.n_groups && ok; ++gi) {
+                    const Group g = job.g[gi];
+                    for (int kb = kb0; kb < kb1; ++kb, ++it) {
+                        const int s = it % job.n_stages;
+                        const uint32_t ph = (uint32_t)(it / job.n_stages) & 1u;
+                        if (!mbar_wait(smem_u32(&full_bar[s]), ph, ep.err, 2)) { ok = false; break; }
+                        fence_after();
+                        const uint32_t st = smem_u32(smem + (size_t)s * job.stage_bytes);
+                        const uint32_t abase = st + (uint32_t)job.b_bytes;
+                        const int k16n = KIND == 1 ? min(4, job.k16_total - kb * 4) : 4;
+                        for (int k16 = 0; k16 < k16n; ++k16) {
+                            const uint64_t bd0 = sw128_desc(st + k16 * 32);
+                            const uint64_t bd1 = sw128_desc(st + boff1 + k16 * 32);
+#pragma unroll
+                            for (int t = 0; t < 4; ++t) {
+                                if (t < g.n_a) {
+                                    const uint64_t ad = sw128_desc(abase + t * A_TILE + k16 * 32);
+                                    const int acc = g.acc[t];
+                                    const uint32_t accum = (started >> acc) & 1u;
+                                    const uint32_t dcol = tbuf + (uint32_t)(acc * job.acc_cols);
+                                    mma_bf16(dcol, ad, bd0, id0, accum);
+                                    if (job.n_mma > 1) mma_bf16(dcol + (uint32_t)job.n_part0, ad, bd1, id1, accum);
+                                    started |= 1u << acc;
+                                }
+                            }
                         }
+                        mma_commit(smem_u32(&empty_bar[s]));   // stage free once these MMAs finish
                     }
-                    mma_commit(smem_u32(&empty_bar[s]));   // stage free once these MMAs finish
                 }
+                mma_commit(smem_u32(&accf_bar[buf]));       // accumulator ready for the epilogue
             }
-            mma_commit(smem_u32(&acc_bar));
         }
-    } else if (warp < 8) {
-        // ---------------- epilogue: TMEM lane quarter q, column half h
+    } else if (warp < EPI_WARPS) {
+        // ---------------- epilogue: TMEM lane quarter q, column quarter h
         const int q = warp & 3, h = warp >> 2;
         const int r = q * 32 + lane;
-        const int row = row0 + r;
-        const bool valid = row < n_rows;
-        const uint32_t lane_addr = tmem + ((uint32_t)(q * 32) << 16);
-        const bool ok = mbar_wait(smem_u32(&acc_bar), 0u, ep.err, 3);
-        fence_after();
-        if (KIND == 1) {
-            float fsum = 0.0f, dfsum = 0.0f;
-            if (ok) {
-                for (int c = h * (BN1 / 2); c < (h + 1) * (BN1 / 2); c += 16) {
-                    uint32_t dv[16], ddv[16];
-                    tmem_ld16(lane_addr + (uint32_t)c, dv);
-                    if (ep.has_dT) tmem_ld16(lane_addr + (uint32_t)(job.acc_cols + c), ddv);
-                    tmem_ld_wait();
-                    float out[16];
-#pragma unroll
-                    for (int i = 0; i < 16; ++i) {
-                        const int sv = s_sid[c + i];
-                        const float sc = s_scale[c + i];
-                        const float d = sc * __uint_as_float(dv[i]);
-                        out[i] = 0.0f;
-                        if (sv >= 0) {
-                            const float4 prm = s_prm[sv];
-                            const float cw = s_w[r][sv];
-                            float f, df;
-                            penalty(d, prm, cw, f, df);
-                            fsum += f;
-                            out[i] = ep.dose_out ? d : df * sc;
-                            if (ep.has_dT)
-                                dfsum += penalty_delta(d, sc * __uint_as_float(ddv[i]), prm, cw);
+        int local = 0;
+        for (int item = blockIdx.x; item < n_items; item += gridDim.x, ++local) {
+            const int ptile = item / per_tile, sub = item - ptile * per_tile;
+            const int row0 = ptile * BM;
+            const int row = row0 + r;
+            const bool valid = row < n_rows;
+            const int buf = local % job.n_bufs;
+            const uint32_t use = (uint32_t)(local / job.n_bufs);
+            const uint32_t lane_addr = tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)(buf * job.buf_cols);
+            if (KIND == 1) {
+                const int b_row0 = sub * BN1;
+                asm volatile("bar.sync 1, 512;" ::: "memory");   // previous item's readers done
+                {
+                    const int i = threadIdx.x;   // 0..511
+                    if (i < BN1) {
+                        const float4 v = ep.pt4[b_row0 + i];   // D_min, D_max, scale, id
+                        s_pt[i] = v;
+                        s_sid[i] = (int)v.w;
+                        if (i < BN1 / 16) s_chunk[i] = ep.chunk[b_row0 / 16 + i];
+                    } else if (i < 2 * BN1) {
+                        const int rr = i - BN1;   // 0..127: weights of row rr of this tile
+                        const int rw = row0 + rr;
+                        for (int s2 = 0; s2 < ep.n_struct; ++s2) {
+                            const float c = rw < n_rows ? ep.Wc[(size_t)rw * ep.n_struct + s2] : 0.0f;
+                            s_cl[s2][rr] = c * s_wmin[s2];
+                            s_ch[s2][rr] = c * s_wmax[s2];
                         }
                     }
-                    if (valid) {
-                        const size_t off = (size_t)row * ep.np_pad + b_row0 + c;
-                        if (ep.dose_out) {
-                            float4 *o = reinterpret_cast<float4 *>(ep.dose_out + off);
+                }
+                asm volatile("bar.sync 1, 512;" ::: "memory");
+                float fs0 = 0.0f, fs1 = 0.0f, dfs0 = 0.0f, dfs1 = 0.0f;
+                // warp-uniform: tcgen05.ld below is warp-collective; every named barrier of this
+                // loop is reached by all epilogue threads whatever the outcome
+                const bool ok = __all_sync(0xffffffffu, mbar_wait(smem_u32(&accf_bar[buf]), use & 1u, ep.err, 3));
+                fence_after();
+                if (ok) {
+                    const bool has_dT = ep.has_dT != 0;
+                    constexpr int CW = 8;                  // TMEM columns per load
+                    constexpr int NCH = BN1 / 4 / CW;      // chunks per warp and item
+#pragma unroll 1
+                    for (int chk = 0; chk < NCH; ++chk) {
+                        const int c = h * (BN1 / 4) + chk * CW;
+                        uint32_t dv[CW], ddv[CW];
 #pragma unroll
-                            for (int v = 0; v < 4; ++v)
-                                o[v] = make_float4(out[4 * v], out[4 * v + 1], out[4 * v + 2],
-                                                   out[4 * v + 3]);
-                        } else {
-                            for (int j = 0; j < ep.nG; ++j) {
-                                uint32_t pk[8];
+                        for (int i = 0; i < CW; ++i) ddv[i] = 0u;
+                        tmem_ld8(lane_addr + (uint32_t)c, dv);
+                        if (has_dT) tmem_ld8(lane_addr + (uint32_t)(job.acc_cols + c), ddv);
+                        tmem_ld_wait_regs8(dv, ddv);
+                        const int info = s_chunk[c / 16];
+                        const int mode = info & 7, sv0 = info >> 3;
+                        float out[CW];
+                        if (mode == 4) {            // padding points or a structure without bounds
 #pragma unroll
-                                for (int v = 0; v < 8; ++v) {
-                                    const __nv_bfloat16 a = __float2bfloat16_rn(out[2 * v]);
-                                    const __nv_bfloat16 b = __float2bfloat16_rn(out[2 * v + 1]);
-                                    pk[v] = pack_bf16(__bfloat162float(a), __bfloat162float(b));
-                                    out[2 * v] -= __bfloat162float(a);
-                                    out[2 * v + 1] -= __bfloat162float(b);
+                            for (int i = 0; i < CW; ++i) out[i] = 0.0f;
+                        } else if (mode == 1) {     // one structure, lower bound only
+                            const float lo = s_pt[c].x, cl = s_cl[sv0][r];
+#pragma unroll
+                            for (int i = 0; i < CW; ++i) {
+                                const float sc = s_pt[c + i].z;
+                                const float d = sc * __uint_as_float(dv[i]);
+                                const float u = fmaxf(lo - d, 0.0f);
+                                const float cu = cl * u;
+                                if (i & 1) fs1 = fmaf(cu, u, fs1); else fs0 = fmaf(cu, u, fs0);
+                                out[i] = ep.dose_out ? d : -2.0f * cu * sc;
+                                if (has_dT) {
+                                    const float dd = sc * __uint_as_float(ddv[i]);
+                                    const float ub = fmaxf(lo - (d - dd), 0.0f);
+                                    const float dl = (u > 0.0f && ub > 0.0f) ? -dd : u - ub;
+                                    if (i & 1) dfs1 = fmaf(cl * dl, u + ub, dfs1);
+                                    else dfs0 = fmaf(cl * dl, u + ub, dfs0);
                                 }
-                                uint4 *o = reinterpret_cast<uint4 *>(ep.G[j] + off);
-                                o[0] = make_uint4(pk[0], pk[1], pk[2], pk[3]);
-                                o[1] = make_uint4(pk[4], pk[5], pk[6], pk[7]);
+                            }
+                        } else if (mode == 2) {     // one structure, upper bound only
+                            const float hi = s_pt[c].y, ch = s_ch[sv0][r];
+#pragma unroll
+                            for (int i = 0; i < CW; ++i) {
+                                const float sc = s_pt[c + i].z;
+                                const float d = sc * __uint_as_float(dv[i]);
+                                const float o = fmaxf(d - hi, 0.0f);
+                                const float co = ch * o;
+                                if (i & 1) fs1 = fmaf(co, o, fs1); else fs0 = fmaf(co, o, fs0);
+                                out[i] = ep.dose_out ? d : 2.0f * co * sc;
+                                if (has_dT) {
+                                    const float dd = sc * __uint_as_float(ddv[i]);
+                                    const float ob = fmaxf((d - dd) - hi, 0.0f);
+                                    const float dh = (o > 0.0f && ob > 0.0f) ? dd : o - ob;
+                                    if (i & 1) dfs1 = fmaf(ch * dh, o + ob, dfs1);
+                                    else dfs0 = fmaf(ch * dh, o + ob, dfs0);
+                                }
+                            }
+                        } else {                    // mixed structures or two-sided bounds
+#pragma unroll
+                            for (int i = 0; i < CW; ++i) {
+                                const float4 pt = s_pt[c + i];
+                                const int sv = s_sid[c + i];
+                                const float cl = s_cl[sv][r], ch = s_ch[sv][r];
+                                const float d = pt.z * __uint_as_float(dv[i]);
+                                const float u = fmaxf(pt.x - d, 0.0f), o = fmaxf(d - pt.y, 0.0f);
+                                fs0 = fmaf(cl * u, u, fs0);
+                                fs1 = fmaf(ch * o, o, fs1);
+                                out[i] = ep.dose_out ? d : 2.0f * (ch * o - cl * u) * pt.z;
+                                if (has_dT) {
+                                    // f(d) - f(d - dd) without cancellation (see eval_simt.cu)
+                                    const float dd = pt.z * __uint_as_float(ddv[i]);
+                                    const float db = d - dd;
+                                    const float ub = fmaxf(pt.x - db, 0.0f), ob = fmaxf(db - pt.y, 0.0f);
+                                    const float dl = (u > 0.0f && ub > 0.0f) ? -dd : u - ub;
+                                    const float dh = (o > 0.0f && ob > 0.0f) ? dd : o - ob;
+                                    dfs0 = fmaf(cl * dl, u + ub, dfs0);
+                                    dfs1 = fmaf(ch * dh, o + ob, dfs1);
+                                }
+                            }
+                        }
+                        if (valid) {
+                            const size_t off = (size_t)row * ep.np_pad + b_row0 + c;
+                            if (ep.dose_out) {
+                                float4 *o4 = reinterpret_cast<float4 *>(ep.dose_out + off);
+                                o4[0] = make_float4(out[0], out[1], out[2], out[3]);
+                                o4[1] = make_float4(out[4], out[5], out[6], out[7]);
+                            } else {
+                                for (int j = 0; j < ep.nG; ++j) {
+                                    uint32_t pk[4];
+#pragma unroll
+                                    for (int v = 0; v < 4; ++v) {
+                                        const __nv_bfloat162 b2 = __floats2bfloat162_rn(out[2 * v], out[2 * v + 1]);
+                                        pk[v] = *reinterpret_cast<const uint32_t *>(&b2);
+                                        out[2 * v] -= __low2float(b2);
+                                        out[2 * v + 1] -= __high2float(b2);
+                                    }
+                                    *reinterpret_cast<uint4 *>(ep.G[j] + off) = make_uint4(pk[0], pk[1], pk[2], pk[3]);
+                                }
                             }
                         }
                     }
                 }
-            }
-            if (h == 1) {
-                s_half[0][r] = fsum;
-                s_half[1][r] = dfsum;
-            }
-            asm volatile("bar.sync 1, 256;" ::: "memory");
-            if (h == 0 && valid) {
-                ep.Fpart[(size_t)blockIdx.x * ep.cap + row] = fsum + s_half[0][r];
-                if (ep.dFpart) ep.dFpart[(size_t)blockIdx.x * ep.cap + row] = dfsum + s_half[1][r];
-            }
-        } else {
-            const int nch = ep.n_total / 16;
-            const int c_beg = h == 0 ? 0 : (nch + 1) / 2;
-            const int c_end = h == 0 ? (nch + 1) / 2 : nch;
-            float *out = ep.gpart + ((size_t)blockIdx.x * ep.cap + row) * ep.nd_pad;
-            if (ok) {
-                for (int ch = c_beg; ch < c_end; ++ch) {
-                    uint32_t v[16];
-                    tmem_ld16(lane_addr + (uint32_t)(ch * 16), v);
-                    tmem_ld_wait();
-                    if (valid) {
-                        float4 *o = reinterpret_cast<float4 *>(out + ch * 16);
+                fence_before();
+                __syncwarp();
+                if (lane == 0) asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(&acce_bar[buf])) : "memory");
+                s_half[0][h][r] = fs0 + fs1;
+                s_half[1][h][r] = dfs0 + dfs1;
+                asm volatile("bar.sync 1, 512;" ::: "memory");
+                if (h == 0 && valid) {   // fixed-order sum of the four column quarters
+                    ep.Fpart[(size_t)sub * ep.cap + row] =
+                        ((s_half[0][0][r] + s_half[0][1][r]) + s_half[0][2][r]) + s_half[0][3][r];
+                    if (ep.dFpart)
+                        ep.dFpart[(size_t)sub * ep.cap + row] =
+                            ((s_half[1][0][r] + s_half[1][1][r]) + s_half[1][2][r]) + s_half[1][3][r];
+                }
+            } else {
+                const int nch = ep.n_total / 16;
+                const int per = (nch + 3) / 4;
+                const int c_beg = min(h * per, nch);
+                const int c_end = min(c_beg + per, nch);
+                float *out = ep.gpart + ((size_t)sub * n_rows + row) * ep.nd_pad;
+                const bool ok = __all_sync(0xffffffffu, mbar_wait(smem_u32(&accf_bar[buf]), use & 1u, ep.err, 3));
+                fence_after();
+                if (ok) {
+                    for (int ch = c_beg; ch < c_end; ++ch) {
+                        uint32_t v[16];
+                        tmem_ld16(lane_addr + (uint32_t)(ch * 16), v);
+                        tmem_ld_wait();
+                        if (valid) {
+                            float4 *o4 = reinterpret_cast<float4 *>(out + ch * 16);
 #pragma unroll
-                        for (int k = 0; k < 4; ++k)
-                            o[k] = make_float4(__uint_as_float(v[4 * k]), __uint_as_float(v[4 * k + 1]),
-                                               __uint_as_float(v[4 * k + 2]),
-                                               __uint_as_float(v[4 * k + 3]));
+                            for (int k = 0; k < 4; ++k)
+                                o4[k] = make_float4(__uint_as_float(v[4 * k]), __uint_as_float(v[4 * k + 1]),
+                                                    __uint_as_float(v[4 * k + 2]),
+                                                    __uint_as_float(v[4 * k + 3]));
+                        }
                     }
                 }
+                fence_before();
+                __syncwarp();
+                if (lane == 0) asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(&acce_bar[buf])) : "memory");
+                if (h == 3 && valid)
+                    for (int c = ep.n_total; c < ep.nd_pad; ++c) out[c] = 0.0f;
+                if (!ok) break;
             }
-            if (h == 1 && valid)
-                for (int c = ep.n_total; c < ep.nd_pad; ++c) out[c] = 0.0f;
         }
     }
     fence_before();
     __syncthreads();
-    if (warp == 10) {
+    if (warp == W_TMEM) {
         fence_after();
         tmem_dealloc(tmem, (uint32_t)job.tmem_cols);
     }
@@ -483,6 +595,42 @@ __global__ void k_split_A(const float *__restrict__ A32, int64_t nd, int64_t nd_
             if (terms > 2) A3[o] = __float2bfloat16_rn(r1 - __bfloat162float(t2));
         }
     }
+}
+
+// Per-point epilogue data of the dose GEMM: (D_min, D_max, scale, structure id).
+__global__ void k_point_data(const int8_t *__restrict__ sid, const float4 *__restrict__ sparams,
+                             const float *__restrict__ scale, int64_t np_pad, float4 *__restrict__ out)
+{
+    const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i >= np_pad) return;
+    const int sv = sid[i];
+    float4 v = make_float4(-INFINITY, INFINITY, 0.0f, 0.0f);
+    if (sv >= 0) v = make_float4(sparams[sv].y, sparams[sv].z, scale[i], (float)sv);
+    out[i] = v;
+}
+
+// Epilogue mode of each run of 16 points: 4 = nothing to score (padding, or a structure with
+// both bounds infinite), 1 = one structure with a lower bound only, 2 = one structure with an
+// upper bound only, 3 = one structure with both bounds, 0 = several structures.
+__global__ void k_chunk_info(const int8_t *__restrict__ sid, const float4 *__restrict__ sparams,
+                             int64_t n_chunks, int32_t *__restrict__ out)
+{
+    const int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (c >= n_chunks) return;
+    const int s0 = sid[c * 16];
+    bool same = true;
+    for (int i = 1; i < 16; ++i) same = same && sid[c * 16 + i] == s0;
+    int info = 0;
+    if (same) {
+        if (s0 < 0) {
+            info = 4;
+        } else {
+            const bool lo = isfinite(sparams[s0].y), hi = isfinite(sparams[s0].z);
+            const int mode = lo && hi ? 3 : lo ? 1 : hi ? 2 : 4;
+            info = (s0 << 3) | mode;
+        }
+    }
+    out[c] = info;
 }
 
 __global__ void k_transpose_bf16(const __nv_bfloat16 *__restrict__ in, int64_t rows, int64_t cols,
@@ -536,6 +684,7 @@ __global__ void k_prep_tc(SolverState s, TcBuffers b, int32_t nT, int64_t kpad, 
     }
     if (threadIdx.x < s.n_struct)
         b.Wc[(size_t)i * s.n_struct + threadIdx.x] = s.Wn[(size_t)j * s.n_struct + threadIdx.x];
+    if (threadIdx.x == 0) s.slot_of[j] = i;
 }
 
 // ------------------------------------------------------------------ host helpers
@@ -619,8 +768,11 @@ Job make_dose_job(const DevProblem &pb, bool with_dT)
     job.n_mma = 1;
     job.n_part0 = BN1;
     job.n_part1 = 0;
-    job.acc_cols = BN1;
-    job.tmem_cols = with_dT ? 2 * BN1 : BN1;
+    job.acc_cols = BN1;                 // D at +0, dD at +BN1
+    job.buf_cols = 2 * BN1;
+    job.n_bufs = 2;
+    job.tmem_cols = 4 * BN1;
+    job.n_ptiles = (int32_t)(pb.np_pad / BN1);
     job.b_bytes = BN1 * 128;
     finish_stages(job, max_a);
     job.b_row_step = BN1;
@@ -654,11 +806,14 @@ Job make_grad_job(const DevProblem &pb, const TcBuffers &b)
     job.b_boxes = (int)ceil_div(n16, 256);
     job.b_box_rows = (int)round_up(ceil_div(n16, job.b_boxes), 8);
     job.acc_cols = 0;
-    job.tmem_cols = tmem_cols_for(n16);
+    job.n_bufs = n16 <= 256 ? 2 : 1;
+    job.buf_cols = n16 <= 256 ? 256 : n16;
+    job.tmem_cols = job.n_bufs == 2 ? 512 : tmem_cols_for(n16);
+    job.n_ptiles = 0;
     job.b_bytes = job.b_boxes * job.b_box_rows * 128;
     finish_stages(job, max_a);
     job.b_row_step = 0;
-    job.kb_step = b.kbps;
+    job.kb_step = 0;
     job.kb_total = (int32_t)(pb.np_pad / BK);
     job.k16_total = job.kb_total * 4;
     return job;
@@ -679,6 +834,17 @@ double tc_mma_units(const DevProblem &pb, bool with_dT, int which)
     return which == 1 ? pairs + (with_dT ? nA : 0) : pairs;
 }
 int32_t tc_max_split(const DevProblem &pb) { return (int32_t)std::min<int64_t>(148, pb.np_pad / BK); }
+
+SplitPlan tc_split_plan(const DevProblem &pb)
+{
+    SplitPlan p{};
+    p.rows_per_tile = BM;
+    p.other_tiles = 1;
+    p.kb_total = (int32_t)(pb.np_pad / BK);
+    p.target_ctas = 148;
+    p.max_split = tc_max_split(pb);
+    return p;
+}
 int64_t tc_launches_per_eval() { return 4; }
 
 cudaError_t tc_prepare_problem(DevProblem *pb, int precision, cudaStream_t st,
@@ -700,6 +866,16 @@ cudaError_t tc_prepare_problem(DevProblem *pb, int precision, cudaStream_t st,
                                                     pb->row_scale, pb->Ah[0], pb->Ah[1], pb->Ah[2]);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
+    e = alloc(reinterpret_cast<void **>(&pb->pt4), (size_t)pb->np_pad * sizeof(float4));
+    if (e != cudaSuccess) return e;
+    k_point_data<<<(unsigned)ceil_div(pb->np_pad, 256), 256, 0, st>>>(pb->sid, pb->sparams,
+                                                                      pb->row_scale, pb->np_pad, pb->pt4);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    e = alloc(reinterpret_cast<void **>(&pb->chunk), (size_t)(pb->np_pad / 16) * sizeof(int32_t));
+    if (e != cudaSuccess) return e;
+    k_chunk_info<<<(unsigned)ceil_div(pb->np_pad / 16, 256), 256, 0, st>>>(pb->sid, pb->sparams,
+                                                                          pb->np_pad / 16, pb->chunk);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
     for (int i = 0; i < terms; ++i) {
         dim3 grid((unsigned)ceil_div(pb->kpad, 32), (unsigned)ceil_div(pb->np_pad, 32));
         k_transpose_bf16<<<grid, dim3(32, 8), 0, st>>>(pb->Ah[i], pb->np_pad, pb->kpad, pb->AhT[i]);
@@ -733,12 +909,6 @@ cudaError_t tc_alloc(const DevProblem &pb, int32_t cap, TcBuffers *b, const Allo
         return e;
     if ((e = alloc(reinterpret_cast<void **>(&b->err), 4)) != cudaSuccess) return e;
     if ((e = cudaMemset(b->err, 0, 4)) != cudaSuccess) return e;
-    // point splits of the gradient GEMM: about one CTA per SM in total
-    const int64_t kb_total = pb.np_pad / BK;
-    const int64_t plan_tiles = ceil_div(cap, BM);
-    const int64_t target = std::max<int64_t>(1, 148 / plan_tiles);
-    b->kbps = (int32_t)ceil_div(kb_total, target);
-    b->n_split = (int32_t)ceil_div(kb_total, b->kbps);
     // tensor maps
     const int nA = pb.tc_terms;
     const int n16 = (int)round_up(pb.n_dwell, 16);
@@ -757,24 +927,18 @@ cudaError_t tc_alloc(const DevProblem &pb, int32_t cap, TcBuffers *b, const Allo
     return ok ? cudaSuccess : cudaErrorInvalidValue;
 }
 
-cudaError_t tc_launch_eval(const DevProblem &pb, const SolverState &s, const TcBuffers &b,
-                           float *Fpart, float *dFpart, float *gpart, int32_t cap, bool with_dT,
-                           float *dose_out, bool force_base, cudaStream_t st, int32_t *n_launches,
-                           cudaEvent_t *ev)
+cudaError_t tc_launch_gemms(const DevProblem &pb, const TcBuffers &b, const int32_t *n_rows,
+                            float *Fpart, float *dFpart, float *gpart, int32_t cap, bool with_dT,
+                            float *dose_out, cudaStream_t st, int32_t *n_launches, cudaEvent_t *ev)
 {
     int nl = 0;
-    if (ev) cudaEventRecord(ev[0], st);
-    k_prep_tc<<<cap, 128, 0, st>>>(s, b, n_t_terms(pb), pb.kpad, force_base ? 1 : 0);
-    cudaError_t e = cudaGetLastError();
-    if (e != cudaSuccess) return e;
-    ++nl;
-    if (ev) cudaEventRecord(ev[1], st);
+    cudaError_t e;
     EpiArgs ep{};
-    ep.n_rows = s.n_act;
+    ep.n_rows = n_rows;
     ep.cap = cap;
     ep.np_pad = pb.np_pad;
-    ep.sid = pb.sid;
-    ep.scale = pb.row_scale;
+    ep.pt4 = pb.pt4;
+    ep.chunk = pb.chunk;
     ep.sparams = pb.sparams;
     ep.n_struct = pb.n_struct;
     ep.Wc = b.Wc;
@@ -787,20 +951,50 @@ cudaError_t tc_launch_eval(const DevProblem &pb, const SolverState &s, const TcB
     ep.gpart = gpart;
     ep.nd_pad = (int32_t)pb.nd_pad;
     ep.n_total = (int32_t)round_up(pb.n_dwell, 16);
+    ep.sp = tc_split_plan(pb);
     ep.err = b.err;
     const Job j1 = make_dose_job(pb, with_dT);
-    dim3 g1((unsigned)(pb.np_pad / BN1), (unsigned)ceil_div(cap, BM));
-    k_tc<1><<<g1, NTHREADS, dyn_smem(j1), st>>>(b.maps1, j1, ep);
+    const int n_sm = 148;
+    const int64_t items1 = ceil_div(cap, BM) * (pb.np_pad / BN1);
+    k_tc<1><<<(unsigned)std::min<int64_t>(n_sm, items1), NTHREADS, dyn_smem(j1), st>>>(b.maps1, j1, ep);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
     ++nl;
     if (ev) cudaEventRecord(ev[2], st);
     if (!dose_out) {
         const Job j2 = make_grad_job(pb, b);
-        dim3 g2((unsigned)b.n_split, (unsigned)ceil_div(cap, BM));
-        k_tc<2><<<g2, NTHREADS, dyn_smem(j2), st>>>(b.maps2, j2, ep);
+        const int64_t items2 = ceil_div(cap, BM) * ep.sp.max_split;
+        k_tc<2><<<(unsigned)std::min<int64_t>(n_sm, items2), NTHREADS, dyn_smem(j2), st>>>(b.maps2, j2, ep);
         if ((e = cudaGetLastError()) != cudaSuccess) return e;
         ++nl;
     }
+    *n_launches = nl;
+    return cudaSuccess;
+}
+
+cudaError_t tc_launch_prep(const DevProblem &pb, const SolverState &s, const TcBuffers &b,
+                           int32_t cap, bool force_base, cudaStream_t st)
+{
+    k_prep_tc<<<cap, 128, 0, st>>>(s, b, n_t_terms(pb), pb.kpad, force_base ? 1 : 0);
+    return cudaGetLastError();
+}
+
+cudaError_t tc_launch_eval(const DevProblem &pb, const SolverState &s, const TcBuffers &b,
+                           float *Fpart, float *dFpart, float *gpart, int32_t cap, bool with_dT,
+                           float *dose_out, bool force_base, cudaStream_t st, int32_t *n_launches,
+                           cudaEvent_t *ev)
+{
+    int nl = 0;
+    if (ev) cudaEventRecord(ev[0], st);
+    k_prep_tc<<<cap, 128, 0, st>>>(s, b, n_t_terms(pb), pb.kpad, force_base ? 1 : 0);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    ++nl;
+    if (ev) cudaEventRecord(ev[1], st);
+    int32_t ng = 0;
+    if ((e = tc_launch_gemms(pb, b, s.n_act, Fpart, dFpart, gpart, cap, with_dT, dose_out, st, &ng,
+                             ev)) != cudaSuccess)
+        return e;
+    nl += ng;
     if (ev) cudaEventRecord(ev[3], st);
     EvalArgs fe{};
     fe.pb = pb;
@@ -809,7 +1003,7 @@ cudaError_t tc_launch_eval(const DevProblem &pb, const SolverState &s, const TcB
     fe.Fpart = Fpart;
     fe.dFpart = with_dT ? dFpart : nullptr;
     fe.gpart = dose_out ? nullptr : gpart;
-    fe.n_split = b.n_split;
+    fe.sp = tc_split_plan(pb);
     if ((e = launch_finish(s, fe, tc_n_ptiles(pb), st)) != cudaSuccess) return e;
     ++nl;
     if (ev) cudaEventRecord(ev[4], st);

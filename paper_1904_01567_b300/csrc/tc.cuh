@@ -23,13 +23,12 @@ struct TcBuffers {
     float *Wc = nullptr;                                 // cap x n_struct
     int32_t *err = nullptr;  // device flag: nonzero after a pipeline wait gave up
     int32_t cap = 0;
-    int32_t n_split = 1;   // point splits of the gradient GEMM
-    int32_t kbps = 1;      // 64-point K blocks per split
     TcMaps maps1{}, maps2{};   // dose GEMM (A terms, T terms, dT), gradient GEMM (A^T, G)
 };
 
 int32_t tc_n_ptiles(const DevProblem &pb);
 int32_t tc_max_split(const DevProblem &pb);
+SplitPlan tc_split_plan(const DevProblem &pb);
 int64_t tc_launches_per_eval();
 // MMA products per output element issued by the dose GEMM (which = 1) or gradient GEMM (2).
 double tc_mma_units(const DevProblem &pb, bool with_dT, int which);
@@ -46,5 +45,13 @@ cudaError_t tc_launch_eval(const DevProblem &pb, const SolverState &s, const TcB
                            float *Fpart, float *dFpart, float *gpart, int32_t cap, bool with_dT,
                            float *dose_out, bool force_base, cudaStream_t st,
                            int32_t *n_launches, cudaEvent_t *ev = nullptr);
+// The trial-row preparation alone (compact rows from s.list / s.n_act).
+cudaError_t tc_launch_prep(const DevProblem &pb, const SolverState &s, const TcBuffers &b,
+                           int32_t cap, bool force_base, cudaStream_t st);
+// The two GEMMs alone, over the compact rows counted by *n_rows (rows written elsewhere).
+cudaError_t tc_launch_gemms(const DevProblem &pb, const TcBuffers &b, const int32_t *n_rows,
+                            float *Fpart, float *dFpart, float *gpart, int32_t cap, bool with_dT,
+                            float *dose_out, cudaStream_t st, int32_t *n_launches,
+                            cudaEvent_t *ev = nullptr);
 
 }  // namespace gmco
