@@ -34,6 +34,7 @@ extern "C" {
 #endif
 
 typedef struct gmco_problem gmco_problem;
+typedef struct gmco_multi gmco_multi;
 
 typedef enum {
     GMCO_OK = 0,
@@ -83,6 +84,10 @@ typedef struct {
     int32_t steps_per_poll;/* device steps between host checks for completion, default 16 */
     int32_t stop_window;   /* a plan converges after this many consecutive accepted
                               iterations each with |F_prev - F| <= tol |F_prev|; default 1 */
+    int32_t grad_split_kb; /* tensor-core forms: points per split of the gradient GEMM, in
+                              blocks of 64 points (each split's partial sums are added in a
+                              fixed order); 0 (default) = chosen from the row count so that
+                              about one wave of splits covers the GPU */
 } gmco_options;
 
 /* Fills *opt with the defaults above. */
@@ -96,7 +101,7 @@ void gmco_default_options(gmco_options *opt);
  *                   finite and >= 0, D_min <= D_max, D_min may be -inf, D_max may be +inf
  *   opt             options, or NULL for the defaults
  * 1 <= n_dwell <= 1024, 1 <= n_pnt, 1 <= n_struct <= 16; the tensor-core precisions need
- * n_dwell <= 384 and n_struct <= 8 (GMCO_EUNSUPPORTED otherwise).  Returns GMCO_EINVAL on bad
+ * n_dwell <= 512 and n_struct <= 8 (GMCO_EUNSUPPORTED otherwise).  Returns GMCO_EINVAL on bad
  * arguments, GMCO_ENOMEM / GMCO_ECUDA on device failure; *out is NULL unless GMCO_OK. */
 gmco_status gmco_create_problem(const float *A, int64_t n_pnt, int64_t n_dwell,
                                 const int32_t *structure_ids, int32_t n_struct,
@@ -175,6 +180,54 @@ gmco_status gmco_dvh_from_dose(gmco_problem *prob, const float *dose, int64_t P,
  * Synchronous. */
 gmco_status gmco_profile_evaluate(gmco_problem *prob, const float *penalty_weights, int64_t P,
                                   const float *X, int32_t reps, double *ms, double *flops);
+
+/* ---- several patients in one launch (uneven batching) ----
+ * A gmco_multi groups 1..64 problems (patients with their own dwell and point counts) that
+ * share one tensor-core precision and the same m, c1, max_ls, stop_window and
+ * steps_per_poll options, on one device.  gmco_solve_multi solves every patient's batch of
+ * plans together: each solver step is one dose-GEMM launch, one gradient-GEMM launch and one
+ * update launch for all patients (persistent kernels that walk one list of work items:
+ * patient x plan tile x point tile, and patient x plan tile x point split), captured in CUDA
+ * graphs of steps_per_poll steps.  The paper solves one patient at a time; this is an
+ * extension of its batched solve (Sec. 2.3.2) to many patients.
+ * Results of patient p are bit for bit those of gmco_solve_batch on its own problem created
+ * with options.grad_split_kb equal to the multi object's split setting.
+ * The multi object keeps stacked copies of the problems' BF16 terms of A; the problems must
+ * outlive it and must not be used by another call while a multi call runs. */
+
+/* probs: n problem handles (host array).  GMCO_EINVAL for mixed precisions or options, an
+ * FP32-form problem (GMCO_EUNSUPPORTED), n outside 1..64 or problems on different devices. */
+gmco_status gmco_create_multi(gmco_problem *const *probs, int32_t n, gmco_multi **out);
+
+/* Releases the multi object (not its problems).  NULL is allowed. */
+void gmco_destroy_multi(gmco_multi *multi);
+
+/* Points per split of every patient's gradient GEMM, in blocks of 64 points (>= 1), or 0 for
+ * each problem's own automatic choice.  The default is set by gmco_multi_autotune, else 16. */
+gmco_status gmco_multi_set_split(gmco_multi *multi, int32_t split_kb);
+int32_t gmco_multi_get_split(const gmco_multi *multi);
+
+/* Solves every patient's plans.  All arrays have n entries (host arrays of pointers); entry p
+ * has the meaning and size of the same argument of gmco_solve_batch for patient p with P[p]
+ * plans (P[p] >= 1).  t0 may be NULL (uniform start for everyone) and so may any output
+ * array or any of its entries.  GMCO_ETIMEOUT as for gmco_solve_batch, when any patient hit
+ * the step budget. */
+gmco_status gmco_solve_multi(gmco_multi *multi, const float *const *penalty_weights,
+                             const int64_t *P, const float *const *t0, int32_t max_iters,
+                             double tol, float *const *T_out, double *const *objectives,
+                             float *const *dvh, int32_t *const *iters_out,
+                             int32_t *const *plan_status, void *cuda_stream);
+
+/* Autotuner of the multi-patient launch: for each candidate split length (as for
+ * gmco_multi_set_split) runs `steps` solver steps from the uniform start on the given
+ * weights, times them with CUDA events, writes the mean milliseconds per step to
+ * ms_per_step[i], selects the fastest and returns it in *best.  Synchronous. */
+gmco_status gmco_multi_autotune(gmco_multi *multi, const float *const *penalty_weights,
+                                const int64_t *P, int32_t steps, const int32_t *candidates,
+                                int32_t n_candidates, double *ms_per_step, int32_t *best);
+
+/* Kernel launches made by the most recent gmco_solve_multi call. */
+int64_t gmco_multi_last_launch_count(const gmco_multi *multi);
 
 /* Problem sizes as stored (after validation). */
 gmco_status gmco_problem_info(const gmco_problem *prob, int64_t *n_pnt, int64_t *n_dwell,

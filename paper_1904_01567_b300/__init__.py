@@ -5,6 +5,13 @@ include/gmco.h); this package only marshals arguments to it.
 """
 from .gmco import (  # noqa: F401
     Problem,
+    Multi,
+    OK,
+    EINVAL,
+    ENOMEM,
+    ECUDA,
+    ETIMEOUT,
+    EUNSUPPORTED,
     GmcoError,
     create_problem,
     destroy_problem,

@@ -117,6 +117,7 @@ struct gmco_problem {
     cudaGraphExec_t gexec[2] = {nullptr, nullptr};
 
     int64_t launches = 0;
+    int64_t ws_gen = 0;   // incremented whenever the workspace is re-created
 };
 
 namespace {
@@ -203,15 +204,16 @@ gmco_status ensure_workspace(gmco_problem *pr, int32_t P)
     CK(a.alloc(&pr->dFpart, (size_t)nparts * cap));
     int64_t grows = max_split_rows(simt_split_plan(pb), cap);
     if (pr->opt.precision != GMCO_PREC_FP32)
-        grows = std::max(grows, max_split_rows(tc_split_plan(pb), cap));
+        grows = std::max(grows, max_split_rows(tc_split_plan(pb, pr->opt.grad_split_kb), cap));
     CK(a.alloc(&pr->gpart, (size_t)grows * pb.nd_pad));
     if (pr->opt.precision != GMCO_PREC_FP32) {
-        cudaError_t e = tc_alloc(pb, cap, &pr->tcb, [&](void **p, size_t bytes) {
-            unsigned char *q = nullptr;
-            cudaError_t r = a.alloc(&q, bytes);
-            *p = q;
-            return r;
-        });
+        cudaError_t e = tc_alloc(pb, cap, pr->Fpart, pr->dFpart, pr->gpart, pr->G, s.cnt,
+                                 pr->opt.grad_split_kb, &pr->tcb, [&](void **p, size_t bytes) {
+                                     unsigned char *q = nullptr;
+                                     cudaError_t r = a.alloc(&q, bytes);
+                                     *p = q;
+                                     return r;
+                                 });
         CK(e);
     }
     CK(a.alloc(&pr->dW, (size_t)cap * S));
@@ -224,6 +226,7 @@ gmco_status ensure_workspace(gmco_problem *pr, int32_t P)
     pr->dDose = nullptr;
     pr->dose_cap = 0;
     pr->cap = cap;
+    pr->ws_gen++;
     return GMCO_OK;
 }
 
@@ -258,8 +261,7 @@ gmco_status launch_eval(gmco_problem *pr, SolverState s, int form, bool with_dT,
         pr->launches += 4;
     } else {
         int32_t nl = 0;
-        CK(tc_launch_eval(pb, s, pr->tcb, pr->Fpart, pr->dFpart, pr->gpart, pr->cap, with_dT,
-                          nullptr, false, st, &nl, ev));
+        CK(tc_launch_eval(pb, s, pr->tcb, pr->cap, with_dT, false, false, st, &nl, ev));
         pr->launches += nl;
     }
     return GMCO_OK;
@@ -267,9 +269,8 @@ gmco_status launch_eval(gmco_problem *pr, SolverState s, int form, bool with_dT,
 
 // Dose-mode FP32 evaluation of every plan at x: doses into pr->G (rows = plans in list
 // order), objectives into s.Ft.
-gmco_status launch_dose_eval(gmco_problem *pr, cudaStream_t st)
+gmco_status launch_dose_eval(gmco_problem *pr, const SolverState &s, cudaStream_t st)
 {
-    SolverState &s = pr->s;
     const DevProblem &pb = pr->pb;
     CK(launch_compact(s, 1, st));
     CK(launch_prep_fp32(s, pb, pr->Tc, nullptr, pr->Wc, true, st));
@@ -330,19 +331,20 @@ gmco_status record_steps(gmco_problem *pr, int form, int steps, const UpdatePara
             a.dTc = pr->dTc;
             a.Wc = pr->Wc;
         } else {
+            // the dose GEMM also clears the next step's counter
             int32_t nl = 0;
-            CK(tc_launch_gemms(pb, pr->tcb, cur, pr->Fpart, pr->dFpart, pr->gpart, pr->cap, true,
-                               nullptr, st, &nl));
+            CK(tc_launch_gemms(tc_single_set(pb, pr->tcb), k & 1, true, false, true, st, &nl));
             a.n_ptiles = tc_n_ptiles(pb);
-            a.sp = tc_split_plan(pb);
+            a.sp = pr->tcb.sp;
             a.fmt = 1;
             for (int j = 0; j < 3; ++j) a.Tb[j] = pr->tcb.T[j];
             a.dTb = pr->tcb.dT;
             a.nT = std::max(pb.tc_terms, 2);
             a.kpad = (int32_t)pb.kpad;
+            a.ldT = (int32_t)pb.kpad;
             a.Wc = pr->tcb.Wc;
         }
-        CK(cudaMemsetAsync(next, 0, sizeof(int32_t), st));
+        if (form == 0) CK(cudaMemsetAsync(next, 0, sizeof(int32_t), st));
         CK(launch_step(s, u, a, st));
     }
     return GMCO_OK;
@@ -360,7 +362,7 @@ gmco_status run_loop(gmco_problem *pr, int form, int32_t P, const UpdateParams &
         if (form == 0) {
             CK(launch_prep_fp32(s0, pr->pb, pr->Tc, pr->dTc, pr->Wc, false, pr->stream));
         } else {
-            CK(tc_launch_prep(pr->pb, s0, pr->tcb, pr->cap, false, pr->stream));
+            CK(tc_launch_prep(s0, tc_rows(pr->pb, pr->tcb), pr->cap, false, pr->stream));
         }
         pr->launches += 2;
     }
@@ -453,6 +455,346 @@ gmco_status end_call(gmco_problem *pr, void *user_stream)
 
 }  // namespace
 
+// ------------------------------------------------------------------ several patients
+struct gmco_multi {
+    int device = 0;
+    std::vector<gmco_problem *> probs;
+    int32_t n = 0;
+    int32_t tc_terms = 0;
+    int32_t split_kb = 16;
+    gmco_options opt{};
+    cudaStream_t stream = nullptr;
+    cudaEvent_t ev_in = nullptr, ev_out = nullptr;
+    int32_t *h_pinned = nullptr;
+    DevArena arena;   // stacked BF16 terms of A and A^T (for the life of the object)
+    DevArena ws;      // per-batch buffers, re-created when the batch shape changes
+    __nv_bfloat16 *Ah[3] = {nullptr, nullptr, nullptr}, *AhT[3] = {nullptr, nullptr, nullptr};
+    int64_t kpad_max = 0, np_max = 0, rows_A = 0, rows_AT = 0;
+    int32_t max_nd_pad = 0;
+    std::vector<int64_t> a_row, at_row;
+    int32_t *err = nullptr;
+    // workspace of the current batch shape
+    std::vector<int64_t> caps, gens;
+    int32_t ws_split = -1;
+    std::vector<int64_t> t_row;
+    std::vector<SolverState> st;   // each patient's state, P = its plans
+    __nv_bfloat16 *T[3] = {nullptr, nullptr, nullptr}, *dT = nullptr;
+    __nv_bfloat16 *G[3] = {nullptr, nullptr, nullptr};
+    float *Wc = nullptr;
+    std::vector<float *> Wc_p;
+    TcLaunchSet set;
+    StepDesc *d_step = nullptr;    // 2n: parity 0, then parity 1
+    int32_t *d_block_start = nullptr;
+    int32_t total_blocks = 0;
+    int32_t **d_cnt = nullptr;
+    int32_t *d_sum = nullptr;
+    // cached step graph
+    std::vector<int64_t> gkey_caps;
+    int32_t gkey_split = -1, gkey_steps = -1;
+    double gkey_tol = -1.0;
+    cudaGraphExec_t gexec = nullptr;
+    int64_t launches = 0;
+};
+
+namespace {
+
+void multi_destroy_graph(gmco_multi *m)
+{
+    if (m->gexec) cudaGraphExecDestroy(m->gexec);
+    m->gexec = nullptr;
+    m->gkey_caps.clear();
+}
+
+// Stacked per-batch buffers, descriptors and operand maps for P[p] plans per patient.
+gmco_status multi_workspace(gmco_multi *m, const std::vector<int64_t> &P)
+{
+    std::vector<int64_t> gens((size_t)m->n);
+    for (int p = 0; p < m->n; ++p) {
+        CKS(ensure_workspace(m->probs[p], (int32_t)P[p]));
+        gens[p] = m->probs[p]->ws_gen;
+    }
+    if (m->caps == P && m->gens == gens && m->ws_split == m->split_kb) return GMCO_OK;
+    CK(cudaStreamSynchronize(m->stream));
+    multi_destroy_graph(m);
+    m->ws.release();
+    m->caps.clear();
+    const int n = m->n;
+    const int nT = std::max(m->tc_terms, 2);
+    DevArena &a = m->ws;
+    m->t_row.assign((size_t)n, 0);
+    int64_t R = 0, wsum = 0;
+    for (int p = 0; p < n; ++p) {
+        m->t_row[p] = R;
+        R += P[p];
+        wsum += P[p] * m->probs[p]->pb.n_struct;
+    }
+    for (int j = 0; j < nT; ++j) {
+        CK(a.alloc(&m->T[j], (size_t)R * m->kpad_max));
+        CK(a.alloc(&m->G[j], (size_t)R * m->np_max));
+        CK(cudaMemset(m->T[j], 0, (size_t)R * m->kpad_max * 2));
+        CK(cudaMemset(m->G[j], 0, (size_t)R * m->np_max * 2));
+    }
+    CK(a.alloc(&m->dT, (size_t)R * m->kpad_max));
+    CK(cudaMemset(m->dT, 0, (size_t)R * m->kpad_max * 2));
+    CK(a.alloc(&m->Wc, (size_t)wsum));
+    bool ok = true;
+    TcLaunchSet &set = m->set;
+    set = TcLaunchSet{};
+    for (int i = 0; i < m->tc_terms; ++i) {
+        ok = ok && tc_encode_map(&set.maps1.m[i], m->Ah[i], m->kpad_max, m->rows_A, kTcBoxCols, kTcBoxRowsA);
+        ok = ok && tc_encode_map(&set.maps2.m[i], m->AhT[i], m->np_max, m->rows_AT, kTcBoxCols, kTcBoxRowsAT);
+    }
+    for (int j = 0; j < nT; ++j) {
+        ok = ok && tc_encode_map(&set.maps1.m[3 + j], m->T[j], m->kpad_max, R, kTcBoxCols, kTcBoxRowsT);
+        ok = ok && tc_encode_map(&set.maps2.m[3 + j], m->G[j], m->np_max, R, kTcBoxCols, kTcBoxRowsG);
+    }
+    ok = ok && tc_encode_map(&set.maps1.m[6], m->dT, m->kpad_max, R, kTcBoxCols, kTcBoxRowsT);
+    if (!ok) {
+        set_error_msg("gmco_solve_multi: cannot encode operand maps");
+        return GMCO_ECUDA;
+    }
+    std::vector<TcDoseProb> dp((size_t)n);
+    std::vector<TcGradProb> gp((size_t)n);
+    std::vector<StepDesc> sd((size_t)2 * n);
+    std::vector<int32_t> bstart((size_t)n + 1, 0);
+    std::vector<int32_t *> cntp((size_t)n);
+    m->st.assign((size_t)n, SolverState{});
+    m->Wc_p.assign((size_t)n, nullptr);
+    set.max_items1 = 0;
+    set.max_items2 = 0;
+    set.max_b_rows_grad = 0;
+    int64_t woff = 0;
+    int32_t blocks = 0;
+    for (int p = 0; p < n; ++p) {
+        gmco_problem *pr = m->probs[p];
+        const DevProblem &pb = pr->pb;
+        const int32_t cap = (int32_t)P[p];
+        SolverState s = pr->s;
+        s.P = cap;
+        m->st[p] = s;
+        float *Fpart = nullptr, *dFpart = nullptr, *gpart = nullptr;
+        const int32_t npt = tc_n_ptiles(pb);
+        CK(a.alloc(&Fpart, (size_t)npt * cap));
+        CK(a.alloc(&dFpart, (size_t)npt * cap));
+        const SplitPlan sp = tc_split_plan(pb, m->split_kb);
+        CK(a.alloc(&gpart, (size_t)max_split_rows(sp, cap) * pb.nd_pad));
+        float *Wc = m->Wc + woff;
+        woff += (int64_t)cap * pb.n_struct;
+        m->Wc_p[p] = Wc;
+        __nv_bfloat16 *Gp[3] = {nullptr, nullptr, nullptr};
+        for (int j = 0; j < nT; ++j) Gp[j] = m->G[j] + m->t_row[p] * m->np_max;
+        dp[p] = tc_dose_prob(pb, s.cnt, Wc, Gp, nullptr, Fpart, dFpart, (int32_t)m->a_row[p],
+                             (int32_t)m->t_row[p], cap, (int32_t)m->np_max);
+        gp[p] = tc_grad_prob(pb, s.cnt, gpart, sp, (int32_t)m->at_row[p], (int32_t)m->t_row[p]);
+        const int64_t ptiles = ceil_div(cap, 128);
+        set.max_items1 += ptiles * npt;
+        set.max_items2 += ptiles * sp.max_split;
+        set.max_b_rows_grad = std::max(set.max_b_rows_grad, tc_grad_b_rows(pb));
+        for (int par = 0; par < 2; ++par) {
+            StepDesc &d = sd[(size_t)par * n + p];
+            d.s = s;
+            StepArgs &ar = d.a;
+            ar = StepArgs{};
+            ar.Fpart = Fpart;
+            ar.dFpart = dFpart;
+            ar.gpart = gpart;
+            ar.n_ptiles = npt;
+            ar.cap = cap;
+            ar.sp = sp;
+            ar.rows_cur = s.cnt + par;
+            ar.rows_next = s.cnt + (par ^ 1);
+            ar.fmt = 1;
+            for (int j = 0; j < nT; ++j) ar.Tb[j] = m->T[j] + m->t_row[p] * m->kpad_max;
+            ar.dTb = m->dT + m->t_row[p] * m->kpad_max;
+            ar.nT = nT;
+            ar.kpad = (int32_t)pb.kpad;
+            ar.ldT = (int32_t)m->kpad_max;
+            ar.Wc = Wc;
+        }
+        bstart[p] = blocks;
+        blocks += (int32_t)ceil_div(cap, 8);
+        cntp[p] = s.cnt;
+    }
+    bstart[n] = blocks;
+    m->total_blocks = blocks;
+    TcDoseProb *d_dose = nullptr;
+    TcGradProb *d_grad = nullptr;
+    CK(a.alloc(&d_dose, (size_t)n));
+    CK(a.alloc(&d_grad, (size_t)n));
+    CK(a.alloc(&m->d_step, (size_t)2 * n));
+    CK(a.alloc(&m->d_block_start, (size_t)n + 1));
+    CK(a.alloc(&m->d_cnt, (size_t)n));
+    CK(a.alloc(&m->d_sum, 1));
+    CK(cudaMemcpy(d_dose, dp.data(), dp.size() * sizeof(TcDoseProb), cudaMemcpyHostToDevice));
+    CK(cudaMemcpy(d_grad, gp.data(), gp.size() * sizeof(TcGradProb), cudaMemcpyHostToDevice));
+    CK(cudaMemcpy(m->d_step, sd.data(), sd.size() * sizeof(StepDesc), cudaMemcpyHostToDevice));
+    CK(cudaMemcpy(m->d_block_start, bstart.data(), bstart.size() * sizeof(int32_t),
+                  cudaMemcpyHostToDevice));
+    CK(cudaMemcpy(m->d_cnt, cntp.data(), cntp.size() * sizeof(int32_t *), cudaMemcpyHostToDevice));
+    set.dose = d_dose;
+    set.grad = d_grad;
+    set.n = n;
+    set.tc_terms = m->tc_terms;
+    set.err = m->err;
+    m->caps = P;
+    m->gens = gens;
+    m->ws_split = m->split_kb;
+    return GMCO_OK;
+}
+
+TcRows multi_rows(const gmco_multi *m, int p)
+{
+    TcRows r{};
+    const int nT = std::max(m->tc_terms, 2);
+    for (int j = 0; j < nT; ++j) r.T[j] = m->T[j] + m->t_row[p] * m->kpad_max;
+    r.dT = m->dT + m->t_row[p] * m->kpad_max;
+    r.Wc = m->Wc_p[p];
+    r.ld = (int32_t)m->kpad_max;
+    r.kpad = (int32_t)m->probs[p]->pb.kpad;
+    r.nT = nT;
+    return r;
+}
+
+// Stages weights and start times, checks them, and puts every plan in INIT with its first
+// evaluation rows prepared.
+gmco_status multi_start(gmco_multi *m, const float *const *W, const float *const *t0,
+                        int32_t max_iters)
+{
+    for (int p = 0; p < m->n; ++p) {
+        gmco_problem *pr = m->probs[p];
+        const DevProblem &pb = pr->pb;
+        const int64_t P = m->caps[p];
+        CK(cudaMemcpyAsync(pr->dW, W[p], (size_t)P * pb.n_struct * sizeof(float), cudaMemcpyDefault,
+                           m->stream));
+        const bool has_t0 = t0 && t0[p];
+        if (has_t0)
+            CK(cudaMemcpyAsync(pr->dT0, t0[p], (size_t)P * pb.n_dwell * sizeof(float),
+                               cudaMemcpyDefault, m->stream));
+        CK(cudaMemsetAsync(pr->d_flag, 0, sizeof(int32_t), m->stream));
+        k_count_bad<<<(unsigned)std::min<int64_t>(ceil_div(P * pb.n_struct, 256), 1184), 256, 0,
+                      m->stream>>>(pr->dW, P * pb.n_struct, 0, pr->d_flag);
+        if (has_t0)
+            k_count_bad<<<(unsigned)std::min<int64_t>(ceil_div(P * pb.n_dwell, 256), 1184), 256, 0,
+                          m->stream>>>(pr->dT0, P * pb.n_dwell, 0, pr->d_flag);
+        CK(cudaGetLastError());
+        CK(cudaMemcpyAsync(m->h_pinned + 2 + p, pr->d_flag, sizeof(int32_t), cudaMemcpyDeviceToHost,
+                           m->stream));
+        m->launches += has_t0 ? 2 : 1;
+    }
+    CK(cudaStreamSynchronize(m->stream));
+    for (int p = 0; p < m->n; ++p)
+        if (m->h_pinned[2 + p]) {
+            char buf[160];
+            snprintf(buf, sizeof buf,
+                     "gmco_solve_multi: patient %d has negative or non-finite weights or start times", p);
+            set_error_msg(buf);
+            return GMCO_EINVAL;
+        }
+    for (int p = 0; p < m->n; ++p) {
+        gmco_problem *pr = m->probs[p];
+        const SolverState &s = m->st[p];
+        CK(launch_solver_init(s, pr->pb, pr->dW, (t0 && t0[p]) ? pr->dT0 : nullptr, max_iters,
+                              m->stream));
+        CK(launch_compact(s, 0, m->stream));
+        CK(tc_launch_prep(s, multi_rows(m, p), s.P, false, m->stream));
+        m->launches += 3;
+    }
+    return GMCO_OK;
+}
+
+// Graph of `steps` (even) steps of every patient: dose GEMM (which also clears the next
+// step's counters), gradient GEMM, fused update.
+gmco_status multi_graph(gmco_multi *m, int steps, double tol)
+{
+    if (m->gexec && m->gkey_caps == m->caps && m->gkey_split == m->split_kb &&
+        m->gkey_steps == steps && m->gkey_tol == tol)
+        return GMCO_OK;
+    multi_destroy_graph(m);
+    const UpdateParams u{m->opt.c1, tol, m->opt.max_ls, m->opt.stop_window};
+    cudaGraph_t g = nullptr;
+    CK(cudaStreamBeginCapture(m->stream, cudaStreamCaptureModeThreadLocal));
+    cudaError_t e = cudaSuccess;
+    for (int k = 0; k < steps && e == cudaSuccess; ++k) {
+        int32_t nl = 0;
+        e = tc_launch_gemms(m->set, k & 1, true, false, true, m->stream, &nl);
+        if (e == cudaSuccess)
+            e = launch_step_multi(m->d_step + (size_t)(k & 1) * m->n, m->d_block_start, m->n,
+                                  m->total_blocks, m->max_nd_pad, u, m->stream);
+    }
+    cudaError_t ee = cudaStreamEndCapture(m->stream, &g);
+    if (e != cudaSuccess) {
+        if (g) cudaGraphDestroy(g);
+        set_error("multi-patient step capture", e);
+        return GMCO_ECUDA;
+    }
+    CK(ee);
+    cudaError_t ei = cudaGraphInstantiate(&m->gexec, g, 0);
+    cudaGraphDestroy(g);
+    CK(ei);
+    m->gkey_caps = m->caps;
+    m->gkey_split = m->split_kb;
+    m->gkey_steps = steps;
+    m->gkey_tol = tol;
+    return GMCO_OK;
+}
+
+// Runs graphs until no patient has a plan left (or max_steps); counts launches.
+gmco_status multi_loop(gmco_multi *m, int steps, int64_t max_steps, int64_t *done_out)
+{
+    int64_t done = 0;
+    for (;;) {
+        CK(cudaGraphLaunch(m->gexec, m->stream));
+        m->launches += (int64_t)steps * 3;
+        done += steps;
+        CK(launch_sum_counters(m->d_cnt, m->n, m->d_sum, m->stream));
+        m->launches++;
+        CK(cudaMemcpyAsync(m->h_pinned, m->d_sum, sizeof(int32_t), cudaMemcpyDeviceToHost,
+                           m->stream));
+        CK(cudaStreamSynchronize(m->stream));
+        if (m->h_pinned[0] == 0) break;
+        if (done >= max_steps) {
+            *done_out = done;
+            return GMCO_ETIMEOUT;
+        }
+    }
+    *done_out = done;
+    return GMCO_OK;
+}
+
+gmco_status multi_check_err(gmco_multi *m)
+{
+    CK(cudaMemcpyAsync(m->h_pinned + 1, m->err, sizeof(int32_t), cudaMemcpyDeviceToHost, m->stream));
+    CK(cudaStreamSynchronize(m->stream));
+    if (m->h_pinned[1] != 0) {
+        char buf[128];
+        snprintf(buf, sizeof buf, "tensor-core pipeline wait timed out (code %d)", m->h_pinned[1]);
+        set_error_msg(buf);
+        cudaMemsetAsync(m->err, 0, sizeof(int32_t), m->stream);
+        return GMCO_ECUDA;
+    }
+    return GMCO_OK;
+}
+
+gmco_status multi_args(gmco_multi *m, const float *const *W, const int64_t *P,
+                       std::vector<int64_t> *Pv, const char *who)
+{
+    if (!m || !W || !P) {
+        set_error_msg((std::string(who) + ": null argument").c_str());
+        return GMCO_EINVAL;
+    }
+    Pv->assign((size_t)m->n, 0);
+    for (int p = 0; p < m->n; ++p) {
+        if (!W[p] || P[p] < 1 || P[p] > (1 << 20)) {
+            set_error_msg((std::string(who) + ": bad weights pointer or plan count").c_str());
+            return GMCO_EINVAL;
+        }
+        (*Pv)[p] = P[p];
+    }
+    return GMCO_OK;
+}
+
+}  // namespace
+
 extern "C" {
 
 void gmco_default_options(gmco_options *opt)
@@ -466,6 +808,7 @@ void gmco_default_options(gmco_options *opt)
     opt->refine_iters = 0;
     opt->steps_per_poll = 16;
     opt->stop_window = 1;
+    opt->grad_split_kb = 0;
 }
 
 const char *gmco_status_string(gmco_status s)
@@ -501,7 +844,7 @@ gmco_status gmco_create_problem(const float *A, int64_t n_pnt, int64_t n_dwell,
     if (o.precision < 0 || o.precision > 4 || o.m < 1 || o.m > kMaxHist || !(o.c1 > 0.0) ||
         !(o.c1 < 1.0) || o.max_ls < 1 || o.max_ls > 60 || !(o.rx_gy > 0.0) ||
         !isfinite(o.rx_gy) || o.refine_iters < 0 || o.steps_per_poll < 1 ||
-        o.steps_per_poll > 1024 || o.stop_window < 1) {
+        o.steps_per_poll > 1024 || o.stop_window < 1 || o.grad_split_kb < 0) {
         set_error_msg("gmco_create_problem: bad options");
         return GMCO_EINVAL;
     }
@@ -610,7 +953,7 @@ gmco_status gmco_create_problem(const float *A, int64_t n_pnt, int64_t n_dwell,
                                                return r;
                                            });
         if (e == cudaErrorNotSupported) {
-            set_error_msg("gmco_create_problem: tensor-core forms need n_dwell <= 384, n_struct <= 8");
+            set_error_msg("gmco_create_problem: tensor-core forms need n_dwell <= 512, n_struct <= 8");
             return fail(GMCO_EUNSUPPORTED);
         }
         if (!ck(e, "tensor-core problem setup")) return fail(GMCO_ECUDA);
@@ -704,7 +1047,7 @@ gmco_status gmco_solve_batch(gmco_problem *pr, const float *penalty_weights, int
     }
     CKS(check_tc_error(pr));
     // final FP32 evaluation at x: objectives and doses (for the DVH indices)
-    CKS(launch_dose_eval(pr, pr->stream));
+    CKS(launch_dose_eval(pr, s, pr->stream));
     if (dvh) {
         CK(launch_dvh(pb, pr->G, pb.np_pad, s.list, (int32_t)P, pr->opt.rx_gy, pr->dDvh,
                       pr->stream));
@@ -781,12 +1124,11 @@ gmco_status gmco_evaluate(gmco_problem *pr, const float *penalty_weights, int64_
     }
     if (dose || dvh) {
         if (form == 0) {
-            CKS(launch_dose_eval(pr, pr->stream));
+            CKS(launch_dose_eval(pr, s, pr->stream));
         } else {
             CK(launch_compact(s, 1, pr->stream));
             int32_t nl = 0;
-            CK(tc_launch_eval(pb, s, pr->tcb, pr->Fpart, pr->dFpart, pr->gpart, pr->cap, false,
-                              pr->G, true, pr->stream, &nl));
+            CK(tc_launch_eval(pb, s, pr->tcb, pr->cap, false, true, true, pr->stream, &nl));
             pr->launches += nl + 1;
         }
         if (dose)
@@ -942,6 +1284,252 @@ gmco_status gmco_dvh_from_dose(gmco_problem *pr, const float *dose, int64_t P, f
                        pr->stream));
     CKS(end_call(pr, cuda_stream));
     return GMCO_OK;
+}
+
+
+gmco_status gmco_create_multi(gmco_problem *const *probs, int32_t n, gmco_multi **out)
+{
+    if (!out) return GMCO_EINVAL;
+    *out = nullptr;
+    if (!probs || n < 1 || n > kMaxMulti) {
+        set_error_msg("gmco_create_multi: need 1..64 problems");
+        return GMCO_EINVAL;
+    }
+    for (int p = 0; p < n; ++p) {
+        if (!probs[p]) {
+            set_error_msg("gmco_create_multi: null problem");
+            return GMCO_EINVAL;
+        }
+        for (int q = 0; q < p; ++q)
+            if (probs[q] == probs[p]) {
+                set_error_msg("gmco_create_multi: a problem appears twice");
+                return GMCO_EINVAL;
+            }
+    }
+    const gmco_options &o = probs[0]->opt;
+    for (int p = 0; p < n; ++p) {
+        const gmco_problem *pr = probs[p];
+        if (pr->opt.precision == GMCO_PREC_FP32) {
+            set_error_msg("gmco_create_multi: the FP32 form has no multi-patient launch; use a "
+                          "tensor-core precision");
+            return GMCO_EUNSUPPORTED;
+        }
+        const gmco_options &q = pr->opt;
+        if (q.precision != o.precision || q.m != o.m || q.c1 != o.c1 || q.max_ls != o.max_ls ||
+            q.stop_window != o.stop_window || q.steps_per_poll != o.steps_per_poll ||
+            pr->device != probs[0]->device) {
+            set_error_msg("gmco_create_multi: problems differ in precision, solver options or device");
+            return GMCO_EINVAL;
+        }
+    }
+    gmco_multi *m = new gmco_multi();
+    m->device = probs[0]->device;
+    m->probs.assign(probs, probs + n);
+    m->n = n;
+    m->opt = o;
+    m->tc_terms = probs[0]->pb.tc_terms;
+    auto fail = [&](gmco_status st) {
+        gmco_destroy_multi(m);
+        return st;
+    };
+    auto ck = [&](cudaError_t e, const char *what) -> bool {
+        if (e != cudaSuccess) {
+            set_error(what, e);
+            return false;
+        }
+        return true;
+    };
+    if (!ck(cudaSetDevice(m->device), "device") ||
+        !ck(cudaStreamCreateWithFlags(&m->stream, cudaStreamNonBlocking), "stream") ||
+        !ck(cudaEventCreateWithFlags(&m->ev_in, cudaEventDisableTiming), "event") ||
+        !ck(cudaEventCreateWithFlags(&m->ev_out, cudaEventDisableTiming), "event") ||
+        !ck(cudaMallocHost(&m->h_pinned, 256 * sizeof(int32_t)), "pinned") ||
+        !ck(m->arena.alloc(&m->err, 1), "flag") || !ck(cudaMemset(m->err, 0, 4), "flag"))
+        return fail(GMCO_ECUDA);
+    m->a_row.assign((size_t)n, 0);
+    m->at_row.assign((size_t)n, 0);
+    for (int p = 0; p < n; ++p) {
+        const DevProblem &pb = probs[p]->pb;
+        m->a_row[p] = m->rows_A;
+        m->at_row[p] = m->rows_AT;
+        m->rows_A += pb.np_pad;
+        m->rows_AT += pb.kpad;
+        m->kpad_max = std::max(m->kpad_max, pb.kpad);
+        m->np_max = std::max(m->np_max, pb.np_pad);
+        m->max_nd_pad = std::max(m->max_nd_pad, (int32_t)pb.nd_pad);
+    }
+    for (int i = 0; i < m->tc_terms; ++i) {
+        const size_t na = (size_t)m->rows_A * m->kpad_max, nat = (size_t)m->rows_AT * m->np_max;
+        if (!ck(m->arena.alloc(&m->Ah[i], na), "alloc stacked A") ||
+            !ck(m->arena.alloc(&m->AhT[i], nat), "alloc stacked A^T"))
+            return fail(GMCO_ENOMEM);
+        if (!ck(cudaMemsetAsync(m->Ah[i], 0, na * 2, m->stream), "memset") ||
+            !ck(cudaMemsetAsync(m->AhT[i], 0, nat * 2, m->stream), "memset"))
+            return fail(GMCO_ECUDA);
+        for (int p = 0; p < n; ++p) {
+            const DevProblem &pb = probs[p]->pb;
+            if (!ck(cudaMemcpy2DAsync(m->Ah[i] + m->a_row[p] * m->kpad_max, m->kpad_max * 2, pb.Ah[i],
+                                      pb.kpad * 2, pb.kpad * 2, pb.np_pad, cudaMemcpyDeviceToDevice,
+                                      m->stream),
+                    "stack A") ||
+                !ck(cudaMemcpy2DAsync(m->AhT[i] + m->at_row[p] * m->np_max, m->np_max * 2, pb.AhT[i],
+                                      pb.np_pad * 2, pb.np_pad * 2, pb.kpad, cudaMemcpyDeviceToDevice,
+                                      m->stream),
+                    "stack A^T"))
+                return fail(GMCO_ECUDA);
+        }
+    }
+    if (!ck(cudaStreamSynchronize(m->stream), "sync")) return fail(GMCO_ECUDA);
+    *out = m;
+    return GMCO_OK;
+}
+
+void gmco_destroy_multi(gmco_multi *m)
+{
+    if (!m) return;
+    cudaSetDevice(m->device);
+    if (m->stream) cudaStreamSynchronize(m->stream);
+    multi_destroy_graph(m);
+    m->ws.release();
+    m->arena.release();
+    if (m->h_pinned) cudaFreeHost(m->h_pinned);
+    if (m->ev_in) cudaEventDestroy(m->ev_in);
+    if (m->ev_out) cudaEventDestroy(m->ev_out);
+    if (m->stream) cudaStreamDestroy(m->stream);
+    delete m;
+}
+
+gmco_status gmco_multi_set_split(gmco_multi *m, int32_t split_kb)
+{
+    if (!m || split_kb < 0) {
+        set_error_msg("gmco_multi_set_split: bad arguments");
+        return GMCO_EINVAL;
+    }
+    m->split_kb = split_kb;
+    return GMCO_OK;
+}
+
+int32_t gmco_multi_get_split(const gmco_multi *m) { return m ? m->split_kb : -1; }
+
+int64_t gmco_multi_last_launch_count(const gmco_multi *m) { return m ? m->launches : -1; }
+
+gmco_status gmco_solve_multi(gmco_multi *m, const float *const *penalty_weights,
+                             const int64_t *P, const float *const *t0, int32_t max_iters,
+                             double tol, float *const *T_out, double *const *objectives,
+                             float *const *dvh, int32_t *const *iters_out,
+                             int32_t *const *plan_status, void *cuda_stream)
+{
+    std::vector<int64_t> Pv;
+    CKS(multi_args(m, penalty_weights, P, &Pv, "gmco_solve_multi"));
+    if (max_iters < 0 || !(tol >= 0.0) || !isfinite(tol)) {
+        set_error_msg("gmco_solve_multi: bad arguments");
+        return GMCO_EINVAL;
+    }
+    m->launches = 0;
+    CK(cudaSetDevice(m->device));
+    CK(cudaEventRecord(m->ev_in, (cudaStream_t)cuda_stream));
+    CK(cudaStreamWaitEvent(m->stream, m->ev_in, 0));
+    CKS(multi_workspace(m, Pv));
+    CKS(multi_start(m, penalty_weights, t0, max_iters));
+    const int steps = (int)round_up(std::max(2, m->opt.steps_per_poll), 2);
+    CKS(multi_graph(m, steps, tol));
+    const int64_t budget = ((int64_t)max_iters + 1) * (m->opt.max_ls + 1) + 4;
+    int64_t done = 0;
+    gmco_status rs = multi_loop(m, steps, budget, &done);
+    if (rs != GMCO_OK && rs != GMCO_ETIMEOUT) return rs;
+    CKS(multi_check_err(m));
+    for (int p = 0; p < m->n; ++p) {
+        gmco_problem *pr = m->probs[p];
+        const DevProblem &pb = pr->pb;
+        const SolverState &s = m->st[p];
+        const int64_t Pp = Pv[p];
+        // final FP32 evaluation at x: objectives and doses (for the DVH indices)
+        CKS(launch_dose_eval(pr, s, m->stream));
+        m->launches += 4;
+        if (dvh && dvh[p]) {
+            CK(launch_dvh(pb, pr->G, pb.np_pad, s.list, (int32_t)Pp, m->opt.rx_gy, pr->dDvh,
+                          m->stream));
+            m->launches++;
+            CK(cudaMemcpyAsync(dvh[p], pr->dDvh, (size_t)Pp * GMCO_DVH_K * sizeof(float),
+                               cudaMemcpyDefault, m->stream));
+        }
+        if (T_out && T_out[p]) {
+            CK(launch_square(s.x, pr->dTout, Pp, pb.n_dwell, pb.nd_pad, m->stream));
+            m->launches++;
+            CK(cudaMemcpyAsync(T_out[p], pr->dTout, (size_t)Pp * pb.n_dwell * sizeof(float),
+                               cudaMemcpyDefault, m->stream));
+        }
+        if (objectives && objectives[p])
+            CK(cudaMemcpyAsync(objectives[p], s.Ft, (size_t)Pp * sizeof(double), cudaMemcpyDefault,
+                               m->stream));
+        if (iters_out && iters_out[p])
+            CK(cudaMemcpyAsync(iters_out[p], s.iters, (size_t)Pp * sizeof(int32_t),
+                               cudaMemcpyDefault, m->stream));
+        if (plan_status && plan_status[p])
+            CK(cudaMemcpyAsync(plan_status[p], s.status, (size_t)Pp * sizeof(int32_t),
+                               cudaMemcpyDefault, m->stream));
+    }
+    CK(cudaEventRecord(m->ev_out, m->stream));
+    CK(cudaStreamWaitEvent((cudaStream_t)cuda_stream, m->ev_out, 0));
+    CK(cudaStreamSynchronize(m->stream));
+    return rs;
+}
+
+gmco_status gmco_multi_autotune(gmco_multi *m, const float *const *penalty_weights,
+                                const int64_t *P, int32_t steps, const int32_t *candidates,
+                                int32_t n_candidates, double *ms_per_step, int32_t *best)
+{
+    std::vector<int64_t> Pv;
+    CKS(multi_args(m, penalty_weights, P, &Pv, "gmco_multi_autotune"));
+    if (!candidates || n_candidates < 1 || n_candidates > 64 || steps < 2 || steps > 1024) {
+        set_error_msg("gmco_multi_autotune: bad arguments");
+        return GMCO_EINVAL;
+    }
+    for (int c = 0; c < n_candidates; ++c)
+        if (candidates[c] < 0) {
+            set_error_msg("gmco_multi_autotune: negative candidate");
+            return GMCO_EINVAL;
+        }
+    CK(cudaSetDevice(m->device));
+    const int st = (int)round_up(steps, 2);
+    const int32_t saved = m->split_kb;
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    CK(cudaEventCreate(&e0));
+    CK(cudaEventCreate(&e1));
+    gmco_status rs = GMCO_OK;
+    double best_ms = INFINITY;
+    int32_t best_c = saved;
+    for (int c = 0; c < n_candidates && rs == GMCO_OK; ++c) {
+        m->split_kb = candidates[c];
+        if ((rs = multi_workspace(m, Pv)) != GMCO_OK) break;
+        if ((rs = multi_graph(m, st, 0.0)) != GMCO_OK) break;
+        float ms = 0.0f;
+        for (int rep = 0; rep < 2 && rs == GMCO_OK; ++rep) {   // warm-up, then timed
+            if ((rs = multi_start(m, penalty_weights, nullptr, 1 << 30)) != GMCO_OK) break;
+            if (cudaEventRecord(e0, m->stream) != cudaSuccess ||
+                cudaGraphLaunch(m->gexec, m->stream) != cudaSuccess ||
+                cudaEventRecord(e1, m->stream) != cudaSuccess ||
+                cudaStreamSynchronize(m->stream) != cudaSuccess) {
+                set_error("gmco_multi_autotune: timed run", cudaGetLastError());
+                rs = GMCO_ECUDA;
+                break;
+            }
+            cudaEventElapsedTime(&ms, e0, e1);
+        }
+        if (rs != GMCO_OK) break;
+        if ((rs = multi_check_err(m)) != GMCO_OK) break;
+        const double per = (double)ms / st;
+        if (ms_per_step) ms_per_step[c] = per;
+        if (per < best_ms) {
+            best_ms = per;
+            best_c = candidates[c];
+        }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    m->split_kb = rs == GMCO_OK ? best_c : saved;
+    if (rs == GMCO_OK && best) *best = best_c;
+    return rs;
 }
 
 }  // extern "C"

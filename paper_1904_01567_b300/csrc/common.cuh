@@ -109,8 +109,15 @@ struct StepArgs {
     float *Tc, *dTc;
     __nv_bfloat16 *Tb[3];
     __nv_bfloat16 *dTb;
-    int32_t nT, kpad;
+    int32_t nT, kpad;                // BF16 terms of t; row length written (columns >= nd_pad zero)
+    int32_t ldT;                     // row stride of Tb / dTb (elements)
     float *Wc;
+};
+
+// A problem's part of a multi-problem solver step: its state and its step arguments.
+struct StepDesc {
+    SolverState s;
+    StepArgs a;
 };
 
 struct UpdateParams {
@@ -129,6 +136,13 @@ cudaError_t launch_finish(const SolverState &s, const EvalArgs &e, int32_t n_pti
                           cudaStream_t st);
 cudaError_t launch_step(const SolverState &s, const UpdateParams &u, const StepArgs &a,
                         cudaStream_t st);
+// The step of every plan of n problems: blocks [block_start[p], block_start[p+1]) take the
+// plans of problem p (8 per block); d[p] holds its state and step arguments.
+cudaError_t launch_step_multi(const StepDesc *d, const int32_t *block_start, int32_t n,
+                              int32_t total_blocks, int32_t max_nd_pad, const UpdateParams &u,
+                              cudaStream_t st);
+// *sum = sum over p < n of *counters[p].
+cudaError_t launch_sum_counters(int32_t *const *counters, int32_t n, int32_t *sum, cudaStream_t st);
 cudaError_t launch_count_live(const SolverState &s, cudaStream_t st);
 cudaError_t launch_reopen(const SolverState &s, int32_t extra_iters, cudaStream_t st);
 cudaError_t launch_profile_setup(const SolverState &s, cudaStream_t st);

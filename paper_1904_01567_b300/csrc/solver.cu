@@ -215,7 +215,7 @@ __device__ __forceinline__ void write_trial_row(const SolverState &s, const Step
             a.Tc[(size_t)slot * nd + l] = t;
             a.dTc[(size_t)slot * nd + l] = dt;
         } else {
-            const size_t o = (size_t)slot * a.kpad + l;
+            const size_t o = (size_t)slot * a.ldT + l;
             const __nv_bfloat16 t1 = __float2bfloat16_rn(t);
             a.Tb[0][o] = t1;
             const float r1 = t - __bfloat162float(t1);
@@ -229,7 +229,7 @@ __device__ __forceinline__ void write_trial_row(const SolverState &s, const Step
     }
     if (a.fmt != 0) {   // BF16 rows are kpad long: keep the columns past nd_pad at zero
         for (int l = nd + lane; l < a.kpad; l += 32) {
-            const size_t o = (size_t)slot * a.kpad + l;
+            const size_t o = (size_t)slot * a.ldT + l;
             for (int k = 0; k < a.nT; ++k) a.Tb[k][o] = __float2bfloat16_rn(0.0f);
             a.dTb[o] = __float2bfloat16_rn(0.0f);
         }
@@ -244,11 +244,9 @@ __device__ __forceinline__ void write_trial_row(const SolverState &s, const Step
 //   new direction by the two-loop recursion; then, if the plan still runs, claim a slot of the
 //   next step's compact rows and write its next trial point there.
 template <int EPL>
-__global__ void __launch_bounds__(256) k_step(SolverState s, UpdateParams u, StepArgs a)
+__device__ __forceinline__ void step_plan(const SolverState &s, const UpdateParams &u,
+                                          const StepArgs &a, const int j, const int lane)
 {
-    const int j = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-    const int lane = threadIdx.x & 31;
-    if (j >= s.P) return;
     const int st = s.state[j];
     if (st != ST_INIT && st != ST_TRIAL) return;
     const int nd = s.nd_pad, epl = nd >> 5, m = s.m;
@@ -534,6 +532,54 @@ __global__ void __launch_bounds__(256) k_step(SolverState s, UpdateParams u, Ste
     }
 }
 
+template <int EPL>
+__global__ void __launch_bounds__(256) k_step(SolverState s, UpdateParams u, StepArgs a)
+{
+    const int j = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    if (j >= s.P) return;
+    step_plan<EPL>(s, u, a, j, threadIdx.x & 31);
+}
+
+// The same step for the plans of several problems; each block's problem descriptor is
+// staged in shared memory.
+template <int EPL>
+__global__ void __launch_bounds__(256) k_step_multi(const StepDesc *__restrict__ d,
+                                                    const int32_t *__restrict__ block_start,
+                                                    int32_t n, UpdateParams u)
+{
+    __shared__ __align__(16) StepDesc sd;
+    __shared__ int32_t s_p;
+    const int b = blockIdx.x;
+    if (threadIdx.x == 0) {
+        int lo = 0, hi = n - 1;   // last p with block_start[p] <= b
+        while (lo < hi) {
+            const int mid = (lo + hi + 1) >> 1;
+            if (block_start[mid] <= b) lo = mid; else hi = mid - 1;
+        }
+        s_p = lo;
+    }
+    __syncthreads();
+    const int p = s_p;
+    {
+        static_assert(sizeof(StepDesc) % 4 == 0, "descriptor size");
+        const uint32_t *src = reinterpret_cast<const uint32_t *>(d + p);
+        uint32_t *dst = reinterpret_cast<uint32_t *>(&sd);
+        for (int i = threadIdx.x; i < (int)(sizeof(StepDesc) / 4); i += blockDim.x) dst[i] = src[i];
+    }
+    __syncthreads();
+    const int j = (b - block_start[p]) * (blockDim.x >> 5) + (threadIdx.x >> 5);
+    if (j >= sd.s.P) return;
+    step_plan<EPL>(sd.s, u, sd.a, j, threadIdx.x & 31);
+}
+
+__global__ void k_sum_counters(int32_t *const *__restrict__ c, int32_t n, int32_t *__restrict__ sum)
+{
+    int v = 0;
+    for (int p = threadIdx.x; p < n; p += 32) v += *c[p];
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(kFull, v, o);
+    if (threadIdx.x == 0) *sum = v;
+}
+
 // Measurement set-up: every plan in a line-search trial at x + 0.01 x (t_trial != t).
 __global__ void k_profile_setup(SolverState s)
 {
@@ -612,6 +658,25 @@ cudaError_t launch_step(const SolverState &s, const UpdateParams &u, const StepA
     else if (epl <= 12) k_step<12><<<blocks, 256, 0, st>>>(s, u, a);
     else if (epl <= 16) k_step<16><<<blocks, 256, 0, st>>>(s, u, a);
     else k_step<32><<<blocks, 256, 0, st>>>(s, u, a);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_step_multi(const StepDesc *d, const int32_t *block_start, int32_t n,
+                              int32_t total_blocks, int32_t max_nd_pad, const UpdateParams &u,
+                              cudaStream_t st)
+{
+    const int epl = max_nd_pad / 32;
+    if (epl <= 4) k_step_multi<4><<<total_blocks, 256, 0, st>>>(d, block_start, n, u);
+    else if (epl <= 8) k_step_multi<8><<<total_blocks, 256, 0, st>>>(d, block_start, n, u);
+    else if (epl <= 12) k_step_multi<12><<<total_blocks, 256, 0, st>>>(d, block_start, n, u);
+    else if (epl <= 16) k_step_multi<16><<<total_blocks, 256, 0, st>>>(d, block_start, n, u);
+    else return cudaErrorInvalidValue;   // multi-problem launches serve n_dwell <= 512
+    return cudaGetLastError();
+}
+
+cudaError_t launch_sum_counters(int32_t *const *counters, int32_t n, int32_t *sum, cudaStream_t st)
+{
+    k_sum_counters<<<1, 32, 0, st>>>(counters, n, sum);
     return cudaGetLastError();
 }
 

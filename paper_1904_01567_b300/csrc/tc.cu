@@ -37,49 +37,10 @@ constexpr int EPI_WARPS = 16;           // 4 per TMEM lane quarter
 constexpr int W_TMA = EPI_WARPS, W_MMA = EPI_WARPS + 1, W_TMEM = EPI_WARPS + 2;
 constexpr int NTHREADS = (EPI_WARPS + 3) * 32;   // epilogue, TMA, MMA, TMEM owner
 constexpr int MAX_STAGES = 4;
-constexpr int SMEM_BUDGET = 208 * 1024;   // dynamic ring; static shared memory adds ~7 KB
+constexpr int SMEM_BUDGET = 200 * 1024;   // dynamic ring; static shared memory adds ~25 KB
+constexpr int TMEM_COLS = 512;          // two accumulator buffers
+constexpr int BUF_COLS = 256;
 constexpr long long kSpinCycles = 2000000000LL;   // about 1 s at 2 GHz
-
-struct Group {
-    int32_t b_map, n_a;
-    int32_t a_map[4], acc[4];
-};
-
-struct Job {
-    int32_t n_groups;
-    Group g[3];
-    int32_t b_boxes, b_box_rows;
-    int32_t n_mma, n_part0, n_part1;
-    int32_t acc_cols, tmem_cols;
-    int32_t n_bufs, buf_cols;        // TMEM accumulator buffers and their column stride
-    int32_t n_ptiles;                // dose GEMM: point tiles
-    int32_t n_stages, stage_bytes, b_bytes;
-    int32_t b_row_step;
-    int32_t kb_step, kb_total;
-    int32_t k16_total;
-};
-
-struct EpiArgs {
-    const int32_t *n_rows;
-    int32_t cap;
-    int64_t np_pad;
-    // dose GEMM
-    const float4 *pt4;       // per point: D_min, D_max, scale, structure id (padding: -inf, inf, 0, 0)
-    const int32_t *chunk;    // per 16 points: (structure id << 3) | mode, see k_chunk_info
-    const float4 *sparams;
-    int32_t n_struct;
-    const float *Wc;
-    __nv_bfloat16 *G[3];
-    int32_t nG;
-    float *dose_out;
-    float *Fpart, *dFpart;
-    int32_t has_dT;
-    // gradient GEMM
-    float *gpart;
-    int32_t nd_pad, n_total;
-    SplitPlan sp;            // gradient GEMM: point splits from the row count
-    int32_t *err;
-};
 
 // ------------------------------------------------------------------ PTX wrappers
 __device__ __forceinline__ uint32_t smem_u32(const void *p)
@@ -207,6 +168,8 @@ __device__ __forceinline__ void tmem_ld8(uint32_t taddr, uint32_t (&r)[8])
                  : "r"(taddr));
 }
 
+// Waits for outstanding tcgen05.ld and tells the compiler that the given registers are only
+// valid from here on (an asynchronous load's destinations must not be read or copied earlier).
 __device__ __forceinline__ void tmem_ld_wait_regs8(uint32_t (&a)[8], uint32_t (&b)[8])
 {
     asm volatile("tcgen05.wait::ld.sync.aligned;"
@@ -217,69 +180,119 @@ __device__ __forceinline__ void tmem_ld_wait_regs8(uint32_t (&a)[8], uint32_t (&
                  : "memory");
 }
 
-// Waits for outstanding tcgen05.ld and tells the compiler that the given registers are only
-// valid from here on (an asynchronous load's destinations must not be read or copied earlier).
-__device__ __forceinline__ void tmem_ld_wait_regs(uint32_t (&a)[16], uint32_t (&b)[16])
+// ------------------------------------------------------------------ the GEMM kernel
+struct Group {
+    int32_t b_map, n_a;
+    int32_t a_map[4], acc[4];
+};
+
+// Launch parameters common to every problem of the list.
+struct KParams {
+    TcMaps maps;
+    const void *probs;        // TcDoseProb[n_probs] (dose GEMM) or TcGradProb[n_probs]
+    int32_t n_probs, parity;
+    int32_t has_dT, write_dose, zero_next;
+    int32_t nG;               // BF16 terms of G written by the dose epilogue
+    int32_t n_groups;
+    Group g[3];
+    int32_t n_stages, stage_bytes, b_bytes;   // ring stage size and its B-operand slot
+    int32_t *err;
+};
+
+template <int KIND>
+struct ProbOf;
+template <>
+struct ProbOf<1> { using type = TcDoseProb; };
+template <>
+struct ProbOf<2> { using type = TcGradProb; };
+
+__device__ __forceinline__ int find_prob(const int32_t *start, int p, int item)
 {
-    asm volatile("tcgen05.wait::ld.sync.aligned;"
-                 : "+r"(a[0]), "+r"(a[1]), "+r"(a[2]), "+r"(a[3]), "+r"(a[4]), "+r"(a[5]),
-                   "+r"(a[6]), "+r"(a[7]), "+r"(a[8]), "+r"(a[9]), "+r"(a[10]), "+r"(a[11]),
-                   "+r"(a[12]), "+r"(a[13]), "+r"(a[14]), "+r"(a[15]), "+r"(b[0]), "+r"(b[1]),
-                   "+r"(b[2]), "+r"(b[3]), "+r"(b[4]), "+r"(b[5]), "+r"(b[6]), "+r"(b[7]),
-                   "+r"(b[8]), "+r"(b[9]), "+r"(b[10]), "+r"(b[11]), "+r"(b[12]), "+r"(b[13]),
-                   "+r"(b[14]), "+r"(b[15])
-                 :
-                 : "memory");
+    while (item >= start[p + 1]) ++p;   // items are visited in increasing order
+    return p;
 }
 
-// ------------------------------------------------------------------ the GEMM kernel
-// Persistent: the grid is one CTA per SM, and each CTA walks work items derived from the
-// number of compact rows at run time (dose GEMM: plan tile x point tile; gradient GEMM: plan
-// tile x point split).  The TMA ring continues across items; accumulators live in n_bufs TMEM
-// buffers handed between the MMA thread and the epilogue warps through acc_full / acc_empty
-// barriers, so the epilogue of one item overlaps the MMAs of the next.
+// Persistent: the grid is at most one CTA per SM, and each CTA walks the work items of all
+// problems of the launch (dose GEMM: problem x plan tile x point tile; gradient GEMM:
+// problem x plan tile x point split), derived from each problem's compact-row count at run
+// time.  The problems' descriptors are staged in shared memory.  The TMA ring continues
+// across items; accumulators live in two TMEM buffers of 256 columns handed between the MMA
+// thread and the epilogue warps through acc_full / acc_empty barriers, so the epilogue of
+// one item overlaps the MMAs of the next.  A gradient item wider than 256 dwells takes both
+// buffers.
 template <int KIND>   // 1: dose GEMM with penalty epilogue, 2: gradient GEMM
-__global__ void __launch_bounds__(NTHREADS, 1)
-    k_tc(const __grid_constant__ TcMaps maps, const Job job, const EpiArgs ep)
+__global__ void __launch_bounds__(NTHREADS, 1) k_tc(const __grid_constant__ KParams kp)
 {
+    using Prob = typename ProbOf<KIND>::type;
     extern __shared__ uint8_t smem_raw[];
     uint8_t *smem = reinterpret_cast<uint8_t *>(
         (reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~static_cast<uintptr_t>(1023));
     __shared__ __align__(8) uint64_t full_bar[MAX_STAGES], empty_bar[MAX_STAGES];
     __shared__ __align__(8) uint64_t accf_bar[2], acce_bar[2];
     __shared__ uint32_t tmem_holder;
+    __shared__ __align__(16) Prob s_prob[kMaxMulti];
+    __shared__ int32_t s_start[kMaxMulti + 1];   // first work item of each problem
+    __shared__ int32_t s_rows[kMaxMulti];        // compact rows of each problem
+    __shared__ int32_t s_per[kMaxMulti];         // work items per plan tile
+    __shared__ int32_t s_kbps[kMaxMulti];        // gradient GEMM: K blocks per split
+    __shared__ int32_t s_fail;
     __shared__ float4 s_pt[BN1];          // per point of the tile: D_min, D_max, scale, -
     __shared__ int32_t s_sid[BN1];
     __shared__ float s_cl[8][BM], s_ch[8][BM];   // w/N * w_min, w/N * w_max per row
     __shared__ float s_half[2][4][BM];
-    __shared__ float s_wmin[8], s_wmax[8];
     __shared__ int32_t s_chunk[BN1 / 16];
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int n_rows = *ep.n_rows;
-    const int plan_tiles = (n_rows + BM - 1) / BM;
-    int kbps = job.kb_total, n_split = 1;
-    if (KIND == 2) split_plan(ep.sp, n_rows, &kbps, &n_split);
-    const int per_tile = KIND == 1 ? job.n_ptiles : n_split;
-    const int n_items = plan_tiles * per_tile;
+    const int np = kp.n_probs;
+    const Prob *gprob = static_cast<const Prob *>(kp.probs);
+    {
+        static_assert(sizeof(Prob) % 4 == 0, "descriptor size");
+        const uint32_t *src = reinterpret_cast<const uint32_t *>(gprob);
+        uint32_t *dst = reinterpret_cast<uint32_t *>(s_prob);
+        const int words = np * (int)(sizeof(Prob) / 4);
+        for (int i = threadIdx.x; i < words; i += blockDim.x) dst[i] = src[i];
+    }
+    if ((int)threadIdx.x < np) {
+        const int p = threadIdx.x;
+        const Prob &d = gprob[p];
+        const int rows = *d.n_rows[kp.parity];
+        int per = 1, kbps = 0;
+        if constexpr (KIND == 1) {
+            per = d.n_ptiles;
+            if (kp.zero_next && blockIdx.x == 0) *const_cast<int32_t *>(d.n_rows[kp.parity ^ 1]) = 0;
+        } else {
+            split_plan(d.sp, rows, &kbps, &per);
+        }
+        s_rows[p] = rows;
+        s_per[p] = per;
+        s_kbps[p] = kbps;
+    }
+    if (threadIdx.x == 0) s_fail = 0;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        int acc = 0;
+        for (int p = 0; p < np; ++p) {
+            s_start[p] = acc;
+            acc += ((s_rows[p] + BM - 1) / BM) * s_per[p];
+        }
+        s_start[np] = acc;
+    }
+    __syncthreads();
+    const int n_items = s_start[np];
     if ((int)blockIdx.x >= n_items) return;   // no work: leave before any barrier or TMEM use
 
     if (threadIdx.x == 0) {
-        for (int s = 0; s < job.n_stages; ++s) {
+        for (int s = 0; s < kp.n_stages; ++s) {
             mbar_init(smem_u32(&full_bar[s]), 1);
             mbar_init(smem_u32(&empty_bar[s]), 1);
         }
-        for (int b = 0; b < job.n_bufs; ++b) {
+        for (int b = 0; b < 2; ++b) {
             mbar_init(smem_u32(&accf_bar[b]), 1);
             mbar_init(smem_u32(&acce_bar[b]), EPI_WARPS);   // one arrival per epilogue warp
         }
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
-    if (warp == W_TMEM) tmem_alloc(smem_u32(&tmem_holder), (uint32_t)job.tmem_cols);
-    if (KIND == 1 && threadIdx.x < ep.n_struct) {
-        s_wmin[threadIdx.x] = ep.sparams[threadIdx.x].x;
-        s_wmax[threadIdx.x] = ep.sparams[threadIdx.x].w;
-    }
+    if (warp == W_TMEM) tmem_alloc(smem_u32(&tmem_holder), (uint32_t)TMEM_COLS);
     fence_before();
     __syncthreads();
     fence_after();
@@ -288,28 +301,44 @@ __global__ void __launch_bounds__(NTHREADS, 1)
     if (warp == W_TMA) {
         // ---------------- TMA producer (one thread)
         if (lane == 0) {
-            int it = 0;
+            int it = 0, p = 0;
             bool ok = true;
             for (int item = blockIdx.x; item < n_items && ok; item += gridDim.x) {
-                const int ptile = item / per_tile, sub = item - ptile * per_tile;
-                const int row0 = ptile * BM;
-                const int b_row0 = KIND == 1 ? sub * BN1 : 0;
-                const int kb0 = KIND == 1 ? 0 : sub * kbps;
-                const int kb1 = KIND == 1 ? job.kb_total : min(kb0 + kbps, job.kb_total);
-                for (int gi = 0; gi < job.n_groups && ok; ++gi) {
-                    const Group &g = job.g[gi];
+                p = find_prob(s_start, p, item);
+                const Prob &d = s_prob[p];
+                const int local = item - s_start[p];
+                const int ptile = local / s_per[p], sub = local - ptile * s_per[p];
+                int row0, brow0, kb0, kb1, nbox, box_rows;
+                if constexpr (KIND == 1) {
+                    row0 = d.t_row + ptile * BM;
+                    brow0 = d.a_row + sub * BN1;
+                    kb0 = 0;
+                    kb1 = d.kb;
+                    box_rows = BN1;
+                    nbox = 1;
+                } else {
+                    row0 = d.g_row + ptile * BM;
+                    brow0 = d.at_row;
+                    kb0 = sub * s_kbps[p];
+                    kb1 = min(kb0 + s_kbps[p], d.kb);
+                    box_rows = kTcBoxRowsAT;
+                    nbox = (d.n16 + box_rows - 1) / box_rows;
+                }
+                const uint32_t bbytes = (uint32_t)(nbox * box_rows * 128);
+                for (int gi = 0; gi < kp.n_groups && ok; ++gi) {
+                    const Group &g = kp.g[gi];
                     for (int kb = kb0; kb < kb1; ++kb, ++it) {
-                        const int s = it % job.n_stages;
-                        const uint32_t ph = (uint32_t)(it / job.n_stages) & 1u;
-                        if (!mbar_wait(smem_u32(&empty_bar[s]), ph ^ 1u, ep.err, 1)) { ok = false; break; }
-                        uint8_t *st = smem + (size_t)s * job.stage_bytes;
+                        const int s = it % kp.n_stages;
+                        const uint32_t ph = (uint32_t)(it / kp.n_stages) & 1u;
+                        if (!mbar_wait(smem_u32(&empty_bar[s]), ph ^ 1u, kp.err, 1)) { ok = false; break; }
+                        uint8_t *st = smem + (size_t)s * kp.stage_bytes;
                         const uint32_t fb = smem_u32(&full_bar[s]);
-                        mbar_expect_tx(fb, (uint32_t)(job.b_bytes + g.n_a * A_TILE));
-                        for (int b = 0; b < job.b_boxes; ++b)
-                            tma_load_2d(smem_u32(st + b * job.b_box_rows * 128), &maps.m[g.b_map],
-                                        kb * BK, b_row0 + b * job.b_box_rows, fb);
+                        mbar_expect_tx(fb, bbytes + (uint32_t)(g.n_a * A_TILE));
+                        for (int b = 0; b < nbox; ++b)
+                            tma_load_2d(smem_u32(st + b * box_rows * 128), &kp.maps.m[g.b_map],
+                                        kb * BK, brow0 + b * box_rows, fb);
                         for (int t = 0; t < g.n_a; ++t)
-                            tma_load_2d(smem_u32(st + job.b_bytes + t * A_TILE), &maps.m[g.a_map[t]],
+                            tma_load_2d(smem_u32(st + kp.b_bytes + t * A_TILE), &kp.maps.m[g.a_map[t]],
                                         kb * BK, row0, fb);
                     }
                 }
@@ -318,30 +347,53 @@ __global__ void __launch_bounds__(NTHREADS, 1)
     } else if (warp == W_MMA) {
         // ---------------- MMA issuer (one thread)
         if (lane == 0) {
-            int it = 0, local = 0;
+            int it = 0, p = 0, nb = 0;
+            uint32_t use0 = 0u, use1 = 0u;   // completed uses of each accumulator buffer
             bool ok = true;
-            for (int item = blockIdx.x; item < n_items && ok; item += gridDim.x, ++local) {
-                const int ptile = item / per_tile, sub = item - ptile * per_tile;
-                const int kb0 = KIND == 1 ? 0 : sub * kbps;
-                const int kb1 = KIND == 1 ? job.kb_total : min(kb0 + kbps, job.kb_total);
-                const int buf = local % job.n_bufs;
-                const uint32_t use = (uint32_t)(local / job.n_bufs);
-                if (!mbar_wait(smem_u32(&acce_bar[buf]), (use & 1u) ^ 1u, ep.err, 4)) { ok = false; break; }
+            for (int item = blockIdx.x; item < n_items && ok; item += gridDim.x) {
+                p = find_prob(s_start, p, item);
+                const Prob &d = s_prob[p];
+                const int local = item - s_start[p];
+                const int ptile = local / s_per[p], sub = local - ptile * s_per[p];
+                (void)ptile;
+                int kb0, kb1, k16_total, n0, n1;
+                bool dbl;
+                if constexpr (KIND == 1) {
+                    kb0 = 0;
+                    kb1 = d.kb;
+                    k16_total = d.k16;
+                    n0 = BN1;
+                    n1 = 0;
+                    dbl = false;
+                } else {
+                    kb0 = sub * s_kbps[p];
+                    kb1 = min(kb0 + s_kbps[p], d.kb);
+                    k16_total = 1 << 30;
+                    n0 = d.n_part0;
+                    n1 = d.n_part1;
+                    dbl = d.n16 > 256;
+                }
+                const int buf = dbl ? 0 : nb;
+                if (dbl || buf == 0)
+                    ok = mbar_wait(smem_u32(&acce_bar[0]), (use0 & 1u) ^ 1u, kp.err, 4);
+                if (ok && (dbl || buf == 1))
+                    ok = mbar_wait(smem_u32(&acce_bar[1]), (use1 & 1u) ^ 1u, kp.err, 4);
+                if (!ok) break;
                 fence_after();
-                const uint32_t tbuf = tmem + (uint32_t)(buf * job.buf_cols);
+                const uint32_t tbuf = tmem + (uint32_t)(buf * BUF_COLS);
                 uint32_t started = 0u;   // bit a: accumulator a already written in this item
-                const uint32_t id0 = idesc_bf16(job.n_part0), id1 = idesc_bf16(job.n_part1);
-                const uint32_t boff1 = (uint32_t)(job.n_part0 * 128);
-                for (int gi = 0; gi < job.n_groups && ok; ++gi) {
-                    const Group g = job.g[gi];
+                const uint32_t id0 = idesc_bf16(n0), id1 = idesc_bf16(n1 > 0 ? n1 : 16);
+                const uint32_t boff1 = (uint32_t)(n0 * 128);
+                for (int gi = 0; gi < kp.n_groups && ok; ++gi) {
+                    const Group g = kp.g[gi];
                     for (int kb = kb0; kb < kb1; ++kb, ++it) {
-                        const int s = it % job.n_stages;
-                        const uint32_t ph = (uint32_t)(it / job.n_stages) & 1u;
-                        if (!mbar_wait(smem_u32(&full_bar[s]), ph, ep.err, 2)) { ok = false; break; }
+                        const int s = it % kp.n_stages;
+                        const uint32_t ph = (uint32_t)(it / kp.n_stages) & 1u;
+                        if (!mbar_wait(smem_u32(&full_bar[s]), ph, kp.err, 2)) { ok = false; break; }
                         fence_after();
-                        const uint32_t st = smem_u32(smem + (size_t)s * job.stage_bytes);
-                        const uint32_t abase = st + (uint32_t)job.b_bytes;
-                        const int k16n = KIND == 1 ? min(4, job.k16_total - kb * 4) : 4;
+                        const uint32_t st = smem_u32(smem + (size_t)s * kp.stage_bytes);
+                        const uint32_t abase = st + (uint32_t)kp.b_bytes;
+                        const int k16n = min(4, k16_total - kb * 4);
                         for (int k16 = 0; k16 < k16n; ++k16) {
                             const uint64_t bd0 = sw128_desc(st + k16 * 32);
                             const uint64_t bd1 = sw128_desc(st + boff1 + k16 * 32);
@@ -351,9 +403,9 @@ __global__ void __launch_bounds__(NTHREADS, 1)
                                     const uint64_t ad = sw128_desc(abase + t * A_TILE + k16 * 32);
                                     const int acc = g.acc[t];
                                     const uint32_t accum = (started >> acc) & 1u;
-                                    const uint32_t dcol = tbuf + (uint32_t)(acc * job.acc_cols);
+                                    const uint32_t dcol = tbuf + (uint32_t)(acc * BN1);
                                     mma_bf16(dcol, ad, bd0, id0, accum);
-                                    if (job.n_mma > 1) mma_bf16(dcol + (uint32_t)job.n_part0, ad, bd1, id1, accum);
+                                    if (n1 > 0) mma_bf16(dcol + (uint32_t)n0, ad, bd1, id1, accum);
                                     started |= 1u << acc;
                                 }
                             }
@@ -361,39 +413,52 @@ __global__ void __launch_bounds__(NTHREADS, 1)
                         mma_commit(smem_u32(&empty_bar[s]));   // stage free once these MMAs finish
                     }
                 }
-                mma_commit(smem_u32(&accf_bar[buf]));       // accumulator ready for the epilogue
+                if (!ok) break;
+                // accumulator(s) ready for the epilogue
+                if (dbl || buf == 0) mma_commit(smem_u32(&accf_bar[0]));
+                if (dbl || buf == 1) mma_commit(smem_u32(&accf_bar[1]));
+                if (dbl || buf == 0) ++use0;
+                if (dbl || buf == 1) ++use1;
+                nb = dbl ? 0 : buf ^ 1;
             }
         }
     } else if (warp < EPI_WARPS) {
         // ---------------- epilogue: TMEM lane quarter q, column quarter h
         const int q = warp & 3, h = warp >> 2;
         const int r = q * 32 + lane;
-        int local = 0;
-        for (int item = blockIdx.x; item < n_items; item += gridDim.x, ++local) {
-            const int ptile = item / per_tile, sub = item - ptile * per_tile;
-            const int row0 = ptile * BM;
-            const int row = row0 + r;
+        int p = 0, nb = 0;
+        uint32_t use0 = 0u, use1 = 0u;
+        for (int item = blockIdx.x; item < n_items; item += gridDim.x) {
+            p = find_prob(s_start, p, item);
+            const Prob &d = s_prob[p];
+            const int local = item - s_start[p];
+            const int ptile = local / s_per[p], sub = local - ptile * s_per[p];
+            const int n_rows = s_rows[p];
+            const int row = ptile * BM + r;   // compact row within the problem
             const bool valid = row < n_rows;
-            const int buf = local % job.n_bufs;
-            const uint32_t use = (uint32_t)(local / job.n_bufs);
-            const uint32_t lane_addr = tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)(buf * job.buf_cols);
-            if (KIND == 1) {
-                const int b_row0 = sub * BN1;
+            bool dbl = false;
+            if constexpr (KIND == 2) dbl = d.n16 > 256;
+            const int buf = dbl ? 0 : nb;
+            const uint32_t lane_addr = tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)(buf * BUF_COLS);
+            bool ok = true;
+            if constexpr (KIND == 1) {
+                const int b_col0 = sub * BN1;
                 asm volatile("bar.sync 1, 512;" ::: "memory");   // previous item's readers done
                 {
                     const int i = threadIdx.x;   // 0..511
                     if (i < BN1) {
-                        const float4 v = ep.pt4[b_row0 + i];   // D_min, D_max, scale, id
+                        const float4 v = d.pt4[b_col0 + i];   // D_min, D_max, scale, id
                         s_pt[i] = v;
                         s_sid[i] = (int)v.w;
-                        if (i < BN1 / 16) s_chunk[i] = ep.chunk[b_row0 / 16 + i];
+                        if (i < BN1 / 16) s_chunk[i] = d.chunk[b_col0 / 16 + i];
                     } else if (i < 2 * BN1) {
                         const int rr = i - BN1;   // 0..127: weights of row rr of this tile
-                        const int rw = row0 + rr;
-                        for (int s2 = 0; s2 < ep.n_struct; ++s2) {
-                            const float c = rw < n_rows ? ep.Wc[(size_t)rw * ep.n_struct + s2] : 0.0f;
-                            s_cl[s2][rr] = c * s_wmin[s2];
-                            s_ch[s2][rr] = c * s_wmax[s2];
+                        const int rw = ptile * BM + rr;
+                        for (int s2 = 0; s2 < d.n_struct; ++s2) {
+                            const float c = rw < n_rows ? d.Wc[(size_t)rw * d.n_struct + s2] : 0.0f;
+                            const float4 sp = d.sparams[s2];
+                            s_cl[s2][rr] = c * sp.x;
+                            s_ch[s2][rr] = c * sp.w;
                         }
                     }
                 }
@@ -401,10 +466,12 @@ __global__ void __launch_bounds__(NTHREADS, 1)
                 float fs0 = 0.0f, fs1 = 0.0f, dfs0 = 0.0f, dfs1 = 0.0f;
                 // warp-uniform: tcgen05.ld below is warp-collective; every named barrier of this
                 // loop is reached by all epilogue threads whatever the outcome
-                const bool ok = __all_sync(0xffffffffu, mbar_wait(smem_u32(&accf_bar[buf]), use & 1u, ep.err, 3));
+                ok = __all_sync(0xffffffffu,
+                                mbar_wait(smem_u32(&accf_bar[buf]), ((buf ? use1 : use0) & 1u), kp.err, 3));
                 fence_after();
                 if (ok) {
-                    const bool has_dT = ep.has_dT != 0;
+                    const bool has_dT = kp.has_dT != 0;
+                    const bool wdose = kp.write_dose != 0;
                     constexpr int CW = 8;                  // TMEM columns per load
                     constexpr int NCH = BN1 / 4 / CW;      // chunks per warp and item
 #pragma unroll 1
@@ -414,27 +481,27 @@ __global__ void __launch_bounds__(NTHREADS, 1)
 #pragma unroll
                         for (int i = 0; i < CW; ++i) ddv[i] = 0u;
                         tmem_ld8(lane_addr + (uint32_t)c, dv);
-                        if (has_dT) tmem_ld8(lane_addr + (uint32_t)(job.acc_cols + c), ddv);
+                        if (has_dT) tmem_ld8(lane_addr + (uint32_t)(BN1 + c), ddv);
                         tmem_ld_wait_regs8(dv, ddv);
                         const int info = s_chunk[c / 16];
                         const int mode = info & 7, sv0 = info >> 3;
                         float out[CW];
                         if (mode == 4) {            // padding points or a structure without bounds
 #pragma unroll
-                            for (int i = 0; i < CW; ++i) out[i] = 0.0f;
+                            for (int i = 0; i < CW; ++i) out[i] = wdose ? s_pt[c + i].z * __uint_as_float(dv[i]) : 0.0f;
                         } else if (mode == 1) {     // one structure, lower bound only
                             const float lo = s_pt[c].x, cl = s_cl[sv0][r];
 #pragma unroll
                             for (int i = 0; i < CW; ++i) {
                                 const float sc = s_pt[c + i].z;
-                                const float d = sc * __uint_as_float(dv[i]);
-                                const float u = fmaxf(lo - d, 0.0f);
+                                const float dd0 = sc * __uint_as_float(dv[i]);
+                                const float u = fmaxf(lo - dd0, 0.0f);
                                 const float cu = cl * u;
                                 if (i & 1) fs1 = fmaf(cu, u, fs1); else fs0 = fmaf(cu, u, fs0);
-                                out[i] = ep.dose_out ? d : -2.0f * cu * sc;
+                                out[i] = wdose ? dd0 : -2.0f * cu * sc;
                                 if (has_dT) {
                                     const float dd = sc * __uint_as_float(ddv[i]);
-                                    const float ub = fmaxf(lo - (d - dd), 0.0f);
+                                    const float ub = fmaxf(lo - (dd0 - dd), 0.0f);
                                     const float dl = (u > 0.0f && ub > 0.0f) ? -dd : u - ub;
                                     if (i & 1) dfs1 = fmaf(cl * dl, u + ub, dfs1);
                                     else dfs0 = fmaf(cl * dl, u + ub, dfs0);
@@ -445,14 +512,14 @@ __global__ void __launch_bounds__(NTHREADS, 1)
 #pragma unroll
                             for (int i = 0; i < CW; ++i) {
                                 const float sc = s_pt[c + i].z;
-                                const float d = sc * __uint_as_float(dv[i]);
-                                const float o = fmaxf(d - hi, 0.0f);
+                                const float dd0 = sc * __uint_as_float(dv[i]);
+                                const float o = fmaxf(dd0 - hi, 0.0f);
                                 const float co = ch * o;
                                 if (i & 1) fs1 = fmaf(co, o, fs1); else fs0 = fmaf(co, o, fs0);
-                                out[i] = ep.dose_out ? d : 2.0f * co * sc;
+                                out[i] = wdose ? dd0 : 2.0f * co * sc;
                                 if (has_dT) {
                                     const float dd = sc * __uint_as_float(ddv[i]);
-                                    const float ob = fmaxf((d - dd) - hi, 0.0f);
+                                    const float ob = fmaxf((dd0 - dd) - hi, 0.0f);
                                     const float dh = (o > 0.0f && ob > 0.0f) ? dd : o - ob;
                                     if (i & 1) dfs1 = fmaf(ch * dh, o + ob, dfs1);
                                     else dfs0 = fmaf(ch * dh, o + ob, dfs0);
@@ -464,15 +531,15 @@ __global__ void __launch_bounds__(NTHREADS, 1)
                                 const float4 pt = s_pt[c + i];
                                 const int sv = s_sid[c + i];
                                 const float cl = s_cl[sv][r], ch = s_ch[sv][r];
-                                const float d = pt.z * __uint_as_float(dv[i]);
-                                const float u = fmaxf(pt.x - d, 0.0f), o = fmaxf(d - pt.y, 0.0f);
+                                const float dd0 = pt.z * __uint_as_float(dv[i]);
+                                const float u = fmaxf(pt.x - dd0, 0.0f), o = fmaxf(dd0 - pt.y, 0.0f);
                                 fs0 = fmaf(cl * u, u, fs0);
                                 fs1 = fmaf(ch * o, o, fs1);
-                                out[i] = ep.dose_out ? d : 2.0f * (ch * o - cl * u) * pt.z;
+                                out[i] = wdose ? dd0 : 2.0f * (ch * o - cl * u) * pt.z;
                                 if (has_dT) {
                                     // f(d) - f(d - dd) without cancellation (see eval_simt.cu)
                                     const float dd = pt.z * __uint_as_float(ddv[i]);
-                                    const float db = d - dd;
+                                    const float db = dd0 - dd;
                                     const float ub = fmaxf(pt.x - db, 0.0f), ob = fmaxf(db - pt.y, 0.0f);
                                     const float dl = (u > 0.0f && ub > 0.0f) ? -dd : u - ub;
                                     const float dh = (o > 0.0f && ob > 0.0f) ? dd : o - ob;
@@ -482,13 +549,13 @@ __global__ void __launch_bounds__(NTHREADS, 1)
                             }
                         }
                         if (valid) {
-                            const size_t off = (size_t)row * ep.np_pad + b_row0 + c;
-                            if (ep.dose_out) {
-                                float4 *o4 = reinterpret_cast<float4 *>(ep.dose_out + off);
+                            const size_t off = (size_t)row * d.ld_g + b_col0 + c;
+                            if (wdose) {
+                                float4 *o4 = reinterpret_cast<float4 *>(d.dose_out + off);
                                 o4[0] = make_float4(out[0], out[1], out[2], out[3]);
                                 o4[1] = make_float4(out[4], out[5], out[6], out[7]);
                             } else {
-                                for (int j = 0; j < ep.nG; ++j) {
+                                for (int j = 0; j < kp.nG; ++j) {
                                     uint32_t pk[4];
 #pragma unroll
                                     for (int v = 0; v < 4; ++v) {
@@ -497,7 +564,7 @@ __global__ void __launch_bounds__(NTHREADS, 1)
                                         out[2 * v] -= __low2float(b2);
                                         out[2 * v + 1] -= __high2float(b2);
                                     }
-                                    *reinterpret_cast<uint4 *>(ep.G[j] + off) = make_uint4(pk[0], pk[1], pk[2], pk[3]);
+                                    *reinterpret_cast<uint4 *>(d.G[j] + off) = make_uint4(pk[0], pk[1], pk[2], pk[3]);
                                 }
                             }
                         }
@@ -508,21 +575,26 @@ __global__ void __launch_bounds__(NTHREADS, 1)
                 if (lane == 0) asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(&acce_bar[buf])) : "memory");
                 s_half[0][h][r] = fs0 + fs1;
                 s_half[1][h][r] = dfs0 + dfs1;
+                if (!ok && lane == 0) s_fail = 1;
                 asm volatile("bar.sync 1, 512;" ::: "memory");
-                if (h == 0 && valid) {   // fixed-order sum of the four column quarters
-                    ep.Fpart[(size_t)sub * ep.cap + row] =
+                if (h == 0 && valid && ok) {   // fixed-order sum of the four column quarters
+                    d.Fpart[(size_t)sub * d.cap + row] =
                         ((s_half[0][0][r] + s_half[0][1][r]) + s_half[0][2][r]) + s_half[0][3][r];
-                    if (ep.dFpart)
-                        ep.dFpart[(size_t)sub * ep.cap + row] =
+                    if (kp.has_dT)
+                        d.dFpart[(size_t)sub * d.cap + row] =
                             ((s_half[1][0][r] + s_half[1][1][r]) + s_half[1][2][r]) + s_half[1][3][r];
                 }
+                ok = s_fail == 0;   // uniform over the epilogue warps (read after the barrier)
             } else {
-                const int nch = ep.n_total / 16;
+                const int nch = d.n16 / 16;
                 const int per = (nch + 3) / 4;
                 const int c_beg = min(h * per, nch);
                 const int c_end = min(c_beg + per, nch);
-                float *out = ep.gpart + ((size_t)sub * n_rows + row) * ep.nd_pad;
-                const bool ok = __all_sync(0xffffffffu, mbar_wait(smem_u32(&accf_bar[buf]), use & 1u, ep.err, 3));
+                float *out = d.gpart + ((size_t)sub * n_rows + row) * d.nd_pad;
+                bool w = true;
+                if (dbl || buf == 0) w = mbar_wait(smem_u32(&accf_bar[0]), use0 & 1u, kp.err, 3);
+                if (w && (dbl || buf == 1)) w = mbar_wait(smem_u32(&accf_bar[1]), use1 & 1u, kp.err, 3);
+                ok = __all_sync(0xffffffffu, w);
                 fence_after();
                 if (ok) {
                     for (int ch = c_beg; ch < c_end; ++ch) {
@@ -541,18 +613,24 @@ __global__ void __launch_bounds__(NTHREADS, 1)
                 }
                 fence_before();
                 __syncwarp();
-                if (lane == 0) asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(&acce_bar[buf])) : "memory");
+                if (lane == 0) {
+                    if (dbl || buf == 0) asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(&acce_bar[0])) : "memory");
+                    if (dbl || buf == 1) asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(&acce_bar[1])) : "memory");
+                }
                 if (h == 3 && valid)
-                    for (int c = ep.n_total; c < ep.nd_pad; ++c) out[c] = 0.0f;
-                if (!ok) break;
+                    for (int c = d.n16; c < d.nd_pad; ++c) out[c] = 0.0f;
             }
+            if (dbl || buf == 0) ++use0;
+            if (dbl || buf == 1) ++use1;
+            nb = dbl ? 0 : buf ^ 1;
+            if (!ok) break;
         }
     }
     fence_before();
     __syncthreads();
     if (warp == W_TMEM) {
         fence_after();
-        tmem_dealloc(tmem, (uint32_t)job.tmem_cols);
+        tmem_dealloc(tmem, (uint32_t)TMEM_COLS);
     }
 }
 
@@ -651,15 +729,15 @@ __global__ void k_transpose_bf16(const __nv_bfloat16 *__restrict__ in, int64_t r
 
 // Trial point of each compact row, as in k_prep_fp32, written as BF16 split terms of t and
 // one BF16 term of dT.
-__global__ void k_prep_tc(SolverState s, TcBuffers b, int32_t nT, int64_t kpad, int32_t force_base)
+__global__ void k_prep_tc(SolverState s, TcRows r, int32_t force_base)
 {
     const int i = blockIdx.x;
     if (i >= *s.n_act) return;
     const int j = s.list[i];
     const bool trial = !force_base && s.state[j] == ST_TRIAL;
     const float a = trial ? (float)s.alpha[j] : 0.0f;
-    const size_t pb = (size_t)j * s.nd_pad, cb = (size_t)i * kpad;
-    for (int64_t l = threadIdx.x; l < kpad; l += blockDim.x) {
+    const size_t pb = (size_t)j * s.nd_pad, cb = (size_t)i * r.ld;
+    for (int64_t l = threadIdx.x; l < r.kpad; l += blockDim.x) {
         float t = 0.0f, dt = 0.0f;
         if (l < s.nd_pad) {
             const float xv = s.x[pb + l];
@@ -673,17 +751,17 @@ __global__ void k_prep_tc(SolverState s, TcBuffers b, int32_t nT, int64_t kpad, 
             t = xt * xt;
         }
         const __nv_bfloat16 t1 = __float2bfloat16_rn(t);
-        b.T[0][cb + l] = t1;
+        r.T[0][cb + l] = t1;
         const float r1 = t - __bfloat162float(t1);
-        if (nT > 1) {
+        if (r.nT > 1) {
             const __nv_bfloat16 t2 = __float2bfloat16_rn(r1);
-            b.T[1][cb + l] = t2;
-            if (nT > 2) b.T[2][cb + l] = __float2bfloat16_rn(r1 - __bfloat162float(t2));
+            r.T[1][cb + l] = t2;
+            if (r.nT > 2) r.T[2][cb + l] = __float2bfloat16_rn(r1 - __bfloat162float(t2));
         }
-        b.dT[cb + l] = __float2bfloat16_rn(dt);
+        r.dT[cb + l] = __float2bfloat16_rn(dt);
     }
     if (threadIdx.x < s.n_struct)
-        b.Wc[(size_t)i * s.n_struct + threadIdx.x] = s.Wn[(size_t)j * s.n_struct + threadIdx.x];
+        r.Wc[(size_t)i * s.n_struct + threadIdx.x] = s.Wn[(size_t)j * s.n_struct + threadIdx.x];
     if (threadIdx.x == 0) s.slot_of[j] = i;
 }
 
@@ -709,47 +787,28 @@ EncodeTiledFn encode_fn()
     return fn;
 }
 
-bool encode_map(CUtensorMap *m, const void *ptr, uint64_t cols, uint64_t rows,
-                uint32_t box_cols, uint32_t box_rows)
-{
-    cuuint64_t dims[2] = {cols, rows};
-    cuuint64_t strides[1] = {cols * 2};
-    cuuint32_t box[2] = {box_cols, box_rows};
-    cuuint32_t es[2] = {1, 1};
-    EncodeTiledFn enc = encode_fn();
-    if (!enc) return false;
-    return enc(m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<void *>(ptr),
-                                  dims, strides, box, es, CU_TENSOR_MAP_INTERLEAVE_NONE,
-                                  CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
-                                  CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
-}
-
-int n_t_terms(const DevProblem &pb) { return std::max(pb.tc_terms, 2); }
+int n_t_terms(int tc_terms) { return std::max(tc_terms, 2); }
 
 // pairs (i, j) of split terms kept in a product: i + j <= max(nA, nB) + 1 (1-based)
 bool keep_pair(int i, int j, int nA, int nB) { return (i + 1) + (j + 1) <= std::max(nA, nB) + 1; }
 
-int tmem_cols_for(int cols)
+KParams make_params(const TcLaunchSet &set, int kind, int parity, bool with_dT, bool write_dose,
+                    bool zero_next)
 {
-    int c = 32;
-    while (c < cols) c <<= 1;
-    return c;
-}
-
-void finish_stages(Job &job, int max_a)
-{
-    job.stage_bytes = job.b_bytes + max_a * A_TILE;
-    job.n_stages = std::max(1, std::min(MAX_STAGES, SMEM_BUDGET / job.stage_bytes));
-}
-
-Job make_dose_job(const DevProblem &pb, bool with_dT)
-{
-    Job job{};
-    const int nA = pb.tc_terms, nT = n_t_terms(pb);
+    KParams k{};
+    k.maps = kind == 1 ? set.maps1 : set.maps2;
+    k.probs = kind == 1 ? static_cast<const void *>(set.dose) : static_cast<const void *>(set.grad);
+    k.n_probs = set.n;
+    k.parity = parity;
+    k.has_dT = with_dT ? 1 : 0;
+    k.write_dose = write_dose ? 1 : 0;
+    k.zero_next = zero_next ? 1 : 0;
+    const int nA = set.tc_terms, nT = n_t_terms(nA);
+    k.nG = nT;
+    k.n_groups = nA;
     int max_a = 0;
-    job.n_groups = nA;
     for (int i = 0; i < nA; ++i) {
-        Group &g = job.g[i];
+        Group &g = k.g[i];
         g.b_map = i;
         g.n_a = 0;
         for (int j = 0; j < nT; ++j)
@@ -757,77 +816,57 @@ Job make_dose_job(const DevProblem &pb, bool with_dT)
                 g.a_map[g.n_a] = 3 + j;
                 g.acc[g.n_a++] = 0;
             }
-        if (with_dT) {
+        if (kind == 1 && with_dT) {
             g.a_map[g.n_a] = 6;
             g.acc[g.n_a++] = 1;
         }
         max_a = std::max(max_a, g.n_a);
     }
-    job.b_boxes = 1;
-    job.b_box_rows = BN1;
-    job.n_mma = 1;
-    job.n_part0 = BN1;
-    job.n_part1 = 0;
-    job.acc_cols = BN1;                 // D at +0, dD at +BN1
-    job.buf_cols = 2 * BN1;
-    job.n_bufs = 2;
-    job.tmem_cols = 4 * BN1;
-    job.n_ptiles = (int32_t)(pb.np_pad / BN1);
-    job.b_bytes = BN1 * 128;
-    finish_stages(job, max_a);
-    job.b_row_step = BN1;
-    job.kb_step = 0;
-    job.kb_total = (int32_t)(pb.kpad / BK);
-    job.k16_total = (int32_t)(round_up(pb.n_dwell, 16) / 16);
-    return job;
+    k.b_bytes = kind == 1 ? BN1 * 128 : set.max_b_rows_grad * 128;
+    k.stage_bytes = k.b_bytes + max_a * A_TILE;
+    k.n_stages = std::max(1, std::min(MAX_STAGES, SMEM_BUDGET / k.stage_bytes));
+    k.err = set.err;
+    return k;
 }
 
-Job make_grad_job(const DevProblem &pb, const TcBuffers &b)
+size_t dyn_smem(const KParams &k) { return (size_t)k.n_stages * k.stage_bytes + 1024; }
+
+cudaError_t ensure_attrs()
 {
-    Job job{};
-    const int nA = pb.tc_terms, nG = n_t_terms(pb);
-    int max_a = 0;
-    job.n_groups = nA;
-    for (int i = 0; i < nA; ++i) {
-        Group &g = job.g[i];
-        g.b_map = i;
-        g.n_a = 0;
-        for (int j = 0; j < nG; ++j)
-            if (keep_pair(i, j, nA, nG)) {
-                g.a_map[g.n_a] = 3 + j;
-                g.acc[g.n_a++] = 0;
-            }
-        max_a = std::max(max_a, g.n_a);
-    }
-    const int n16 = (int)round_up(pb.n_dwell, 16);
-    job.n_mma = n16 > 256 ? 2 : 1;
-    job.n_part0 = job.n_mma == 1 ? n16 : (int)round_up(ceil_div(n16, 2), 16);
-    job.n_part1 = n16 - job.n_part0;
-    job.b_boxes = (int)ceil_div(n16, 256);
-    job.b_box_rows = (int)round_up(ceil_div(n16, job.b_boxes), 8);
-    job.acc_cols = 0;
-    job.n_bufs = n16 <= 256 ? 2 : 1;
-    job.buf_cols = n16 <= 256 ? 256 : n16;
-    job.tmem_cols = job.n_bufs == 2 ? 512 : tmem_cols_for(n16);
-    job.n_ptiles = 0;
-    job.b_bytes = job.b_boxes * job.b_box_rows * 128;
-    finish_stages(job, max_a);
-    job.b_row_step = 0;
-    job.kb_step = 0;
-    job.kb_total = (int32_t)(pb.np_pad / BK);
-    job.k16_total = job.kb_total * 4;
-    return job;
+    static bool done = false;
+    if (done) return cudaSuccess;
+    cudaError_t e = cudaFuncSetAttribute(k_tc<1>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         SMEM_BUDGET + 1024);
+    if (e != cudaSuccess) return e;
+    e = cudaFuncSetAttribute(k_tc<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_BUDGET + 1024);
+    if (e != cudaSuccess) return e;
+    done = true;
+    return cudaSuccess;
 }
 
-size_t dyn_smem(const Job &job) { return (size_t)job.n_stages * job.stage_bytes + 1024; }
+int n16_of(const DevProblem &pb) { return (int)round_up(pb.n_dwell, 16); }
 
 }  // namespace
+
+bool tc_encode_map(CUtensorMap *m, const void *ptr, uint64_t cols, uint64_t rows,
+                   uint32_t box_cols, uint32_t box_rows)
+{
+    cuuint64_t dims[2] = {cols, rows};
+    cuuint64_t strides[1] = {cols * 2};
+    cuuint32_t box[2] = {box_cols, box_rows};
+    cuuint32_t es[2] = {1, 1};
+    EncodeTiledFn enc = encode_fn();
+    if (!enc) return false;
+    return enc(m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<void *>(ptr), dims, strides, box,
+               es, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+               CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
 
 int32_t tc_n_ptiles(const DevProblem &pb) { return (int32_t)(pb.np_pad / BN1); }
 
 double tc_mma_units(const DevProblem &pb, bool with_dT, int which)
 {
-    const int nA = pb.tc_terms, nT = n_t_terms(pb);
+    const int nA = pb.tc_terms, nT = n_t_terms(pb.tc_terms);
     int pairs = 0;
     for (int i = 0; i < nA; ++i)
         for (int j = 0; j < nT; ++j) pairs += keep_pair(i, j, nA, nT);
@@ -835,22 +874,30 @@ double tc_mma_units(const DevProblem &pb, bool with_dT, int which)
 }
 int32_t tc_max_split(const DevProblem &pb) { return (int32_t)std::min<int64_t>(148, pb.np_pad / BK); }
 
-SplitPlan tc_split_plan(const DevProblem &pb)
+SplitPlan tc_split_plan(const DevProblem &pb, int32_t kb_per_split)
 {
     SplitPlan p{};
     p.rows_per_tile = BM;
     p.other_tiles = 1;
     p.kb_total = (int32_t)(pb.np_pad / BK);
-    p.target_ctas = 148;
-    p.max_split = tc_max_split(pb);
+    if (kb_per_split > 0) {   // fixed split length: as many splits as that takes
+        p.target_ctas = 1 << 30;
+        p.max_split = (int32_t)ceil_div(p.kb_total, kb_per_split);
+    } else {
+        p.target_ctas = 148;
+        p.max_split = tc_max_split(pb);
+    }
     return p;
 }
+
+int32_t tc_grad_b_rows(const DevProblem &pb) { return (int32_t)round_up(n16_of(pb), kTcBoxRowsAT); }
+
 int64_t tc_launches_per_eval() { return 4; }
 
 cudaError_t tc_prepare_problem(DevProblem *pb, int precision, cudaStream_t st,
                                const AllocFn &alloc)
 {
-    if (pb->n_dwell > 384 || pb->n_struct > 8) return cudaErrorNotSupported;
+    if (pb->n_dwell > 512 || pb->n_struct > 8) return cudaErrorNotSupported;
     const int terms = precision == GMCO_PREC_BF16X3 ? 3 : precision == GMCO_PREC_BF16X2 ? 2 : 1;
     pb->tc_terms = terms;
     pb->kpad = round_up(pb->n_dwell, 64);
@@ -882,22 +929,61 @@ cudaError_t tc_prepare_problem(DevProblem *pb, int precision, cudaStream_t st,
         e = cudaGetLastError();
         if (e != cudaSuccess) return e;
     }
-    static bool attr_set = false;
-    if (!attr_set) {
-        e = cudaFuncSetAttribute(k_tc<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_BUDGET + 1024);
-        if (e != cudaSuccess) return e;
-        e = cudaFuncSetAttribute(k_tc<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_BUDGET + 1024);
-        if (e != cudaSuccess) return e;
-        attr_set = true;
-    }
-    return cudaSuccess;
+    return ensure_attrs();
 }
 
-cudaError_t tc_alloc(const DevProblem &pb, int32_t cap, TcBuffers *b, const AllocFn &alloc)
+TcDoseProb tc_dose_prob(const DevProblem &pb, const int32_t *cnt, const float *Wc,
+                        __nv_bfloat16 *const *G, float *dose_out, float *Fpart, float *dFpart,
+                        int32_t a_row, int32_t t_row, int32_t cap, int32_t ld_g)
+{
+    TcDoseProb d{};
+    d.n_rows[0] = cnt;
+    d.n_rows[1] = cnt + 1;
+    d.pt4 = pb.pt4;
+    d.chunk = pb.chunk;
+    d.sparams = pb.sparams;
+    d.Wc = Wc;
+    for (int j = 0; j < 3; ++j) d.G[j] = j < n_t_terms(pb.tc_terms) ? G[j] : nullptr;
+    d.dose_out = dose_out;
+    d.Fpart = Fpart;
+    d.dFpart = dFpart;
+    d.a_row = a_row;
+    d.t_row = t_row;
+    d.kb = (int32_t)(pb.kpad / BK);
+    d.k16 = n16_of(pb) / 16;
+    d.n_ptiles = tc_n_ptiles(pb);
+    d.n_struct = pb.n_struct;
+    d.cap = cap;
+    d.ld_g = ld_g;
+    return d;
+}
+
+TcGradProb tc_grad_prob(const DevProblem &pb, const int32_t *cnt, float *gpart, SplitPlan sp,
+                        int32_t at_row, int32_t g_row)
+{
+    TcGradProb d{};
+    d.n_rows[0] = cnt;
+    d.n_rows[1] = cnt + 1;
+    d.gpart = gpart;
+    d.sp = sp;
+    d.at_row = at_row;
+    d.g_row = g_row;
+    d.kb = (int32_t)(pb.np_pad / BK);
+    const int n16 = n16_of(pb);
+    d.n16 = n16;
+    d.n_part0 = n16 <= 256 ? n16 : (int)round_up(ceil_div(n16, 2), 16);
+    d.n_part1 = n16 - d.n_part0;
+    d.nd_pad = (int32_t)pb.nd_pad;
+    return d;
+}
+
+cudaError_t tc_alloc(const DevProblem &pb, int32_t cap, float *Fpart, float *dFpart,
+                     float *gpart, float *dose_out, const int32_t *cnt, int32_t split_kb,
+                     TcBuffers *b, const AllocFn &alloc)
 {
     *b = TcBuffers{};
     b->cap = cap;
-    const int nT = n_t_terms(pb);
+    const int nT = n_t_terms(pb.tc_terms);
     const size_t tn = (size_t)cap * pb.kpad, gn = (size_t)cap * pb.np_pad;
     cudaError_t e;
     for (int j = 0; j < nT; ++j) {
@@ -909,61 +995,82 @@ cudaError_t tc_alloc(const DevProblem &pb, int32_t cap, TcBuffers *b, const Allo
         return e;
     if ((e = alloc(reinterpret_cast<void **>(&b->err), 4)) != cudaSuccess) return e;
     if ((e = cudaMemset(b->err, 0, 4)) != cudaSuccess) return e;
-    // tensor maps
-    const int nA = pb.tc_terms;
-    const int n16 = (int)round_up(pb.n_dwell, 16);
-    const int boxes = (int)ceil_div(n16, 256);
-    const uint32_t box_rows2 = (uint32_t)round_up(ceil_div(n16, boxes), 8);
+    // operand maps
     bool ok = true;
-    for (int i = 0; i < nA; ++i) {
-        ok = ok && encode_map(&b->maps1.m[i], pb.Ah[i], pb.kpad, pb.np_pad, BK, BN1);
-        ok = ok && encode_map(&b->maps2.m[i], pb.AhT[i], pb.np_pad, pb.kpad, BK, box_rows2);
+    for (int i = 0; i < pb.tc_terms; ++i) {
+        ok = ok && tc_encode_map(&b->maps1.m[i], pb.Ah[i], pb.kpad, pb.np_pad, kTcBoxCols, kTcBoxRowsA);
+        ok = ok && tc_encode_map(&b->maps2.m[i], pb.AhT[i], pb.np_pad, pb.kpad, kTcBoxCols, kTcBoxRowsAT);
     }
     for (int j = 0; j < nT; ++j) {
-        ok = ok && encode_map(&b->maps1.m[3 + j], b->T[j], pb.kpad, cap, BK, BM);
-        ok = ok && encode_map(&b->maps2.m[3 + j], b->G[j], pb.np_pad, cap, BK, BM);
+        ok = ok && tc_encode_map(&b->maps1.m[3 + j], b->T[j], pb.kpad, cap, kTcBoxCols, kTcBoxRowsT);
+        ok = ok && tc_encode_map(&b->maps2.m[3 + j], b->G[j], pb.np_pad, cap, kTcBoxCols, kTcBoxRowsG);
     }
-    ok = ok && encode_map(&b->maps1.m[6], b->dT, pb.kpad, cap, BK, BM);
-    return ok ? cudaSuccess : cudaErrorInvalidValue;
+    ok = ok && tc_encode_map(&b->maps1.m[6], b->dT, pb.kpad, cap, kTcBoxCols, kTcBoxRowsT);
+    if (!ok) return cudaErrorInvalidValue;
+    // descriptors of this problem alone
+    b->Fpart = Fpart;
+    b->dFpart = dFpart;
+    b->gpart = gpart;
+    b->dose_out = dose_out;
+    b->sp = tc_split_plan(pb, split_kb);
+    const TcDoseProb dp = tc_dose_prob(pb, cnt, b->Wc, b->G, dose_out, Fpart, dFpart, 0, 0, cap,
+                                       (int32_t)pb.np_pad);
+    const TcGradProb gp = tc_grad_prob(pb, cnt, gpart, b->sp, 0, 0);
+    if ((e = alloc(reinterpret_cast<void **>(&b->d_dose), sizeof(TcDoseProb))) != cudaSuccess) return e;
+    if ((e = alloc(reinterpret_cast<void **>(&b->d_grad), sizeof(TcGradProb))) != cudaSuccess) return e;
+    if ((e = cudaMemcpy(b->d_dose, &dp, sizeof dp, cudaMemcpyHostToDevice)) != cudaSuccess) return e;
+    if ((e = cudaMemcpy(b->d_grad, &gp, sizeof gp, cudaMemcpyHostToDevice)) != cudaSuccess) return e;
+    return cudaSuccess;
 }
 
-cudaError_t tc_launch_gemms(const DevProblem &pb, const TcBuffers &b, const int32_t *n_rows,
-                            float *Fpart, float *dFpart, float *gpart, int32_t cap, bool with_dT,
-                            float *dose_out, cudaStream_t st, int32_t *n_launches, cudaEvent_t *ev)
+TcLaunchSet tc_single_set(const DevProblem &pb, const TcBuffers &b)
+{
+    TcLaunchSet set;
+    set.maps1 = b.maps1;
+    set.maps2 = b.maps2;
+    set.dose = b.d_dose;
+    set.grad = b.d_grad;
+    set.n = 1;
+    set.tc_terms = pb.tc_terms;
+    set.max_b_rows_grad = tc_grad_b_rows(pb);
+    set.err = b.err;
+    const int64_t ptiles = ceil_div(b.cap, BM);
+    set.max_items1 = ptiles * tc_n_ptiles(pb);
+    set.max_items2 = ptiles * b.sp.max_split;
+    return set;
+}
+
+TcRows tc_rows(const DevProblem &pb, const TcBuffers &b)
+{
+    TcRows r{};
+    for (int j = 0; j < 3; ++j) r.T[j] = b.T[j];
+    r.dT = b.dT;
+    r.Wc = b.Wc;
+    r.ld = (int32_t)pb.kpad;
+    r.kpad = (int32_t)pb.kpad;
+    r.nT = n_t_terms(pb.tc_terms);
+    return r;
+}
+
+cudaError_t tc_launch_gemms(const TcLaunchSet &set, int32_t parity, bool with_dT,
+                            bool write_dose, bool zero_next, cudaStream_t st,
+                            int32_t *n_launches, cudaEvent_t *ev)
 {
     int nl = 0;
-    cudaError_t e;
-    EpiArgs ep{};
-    ep.n_rows = n_rows;
-    ep.cap = cap;
-    ep.np_pad = pb.np_pad;
-    ep.pt4 = pb.pt4;
-    ep.chunk = pb.chunk;
-    ep.sparams = pb.sparams;
-    ep.n_struct = pb.n_struct;
-    ep.Wc = b.Wc;
-    for (int j = 0; j < 3; ++j) ep.G[j] = b.G[j];
-    ep.nG = n_t_terms(pb);
-    ep.dose_out = dose_out;
-    ep.Fpart = Fpart;
-    ep.dFpart = with_dT ? dFpart : nullptr;
-    ep.has_dT = with_dT ? 1 : 0;
-    ep.gpart = gpart;
-    ep.nd_pad = (int32_t)pb.nd_pad;
-    ep.n_total = (int32_t)round_up(pb.n_dwell, 16);
-    ep.sp = tc_split_plan(pb);
-    ep.err = b.err;
-    const Job j1 = make_dose_job(pb, with_dT);
+    cudaError_t e = ensure_attrs();
+    if (e != cudaSuccess) return e;
+    if (set.n < 1 || set.n > kMaxMulti) return cudaErrorInvalidValue;
     const int n_sm = 148;
-    const int64_t items1 = ceil_div(cap, BM) * (pb.np_pad / BN1);
-    k_tc<1><<<(unsigned)std::min<int64_t>(n_sm, items1), NTHREADS, dyn_smem(j1), st>>>(b.maps1, j1, ep);
+    const KParams k1 = make_params(set, 1, parity, with_dT, write_dose, zero_next);
+    k_tc<1><<<(unsigned)std::max<int64_t>(1, std::min<int64_t>(n_sm, set.max_items1)), NTHREADS,
+              dyn_smem(k1), st>>>(k1);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
     ++nl;
     if (ev) cudaEventRecord(ev[2], st);
-    if (!dose_out) {
-        const Job j2 = make_grad_job(pb, b);
-        const int64_t items2 = ceil_div(cap, BM) * ep.sp.max_split;
-        k_tc<2><<<(unsigned)std::min<int64_t>(n_sm, items2), NTHREADS, dyn_smem(j2), st>>>(b.maps2, j2, ep);
+    if (!write_dose) {
+        const KParams k2 = make_params(set, 2, parity, false, false, false);
+        k_tc<2><<<(unsigned)std::max<int64_t>(1, std::min<int64_t>(n_sm, set.max_items2)), NTHREADS,
+                  dyn_smem(k2), st>>>(k2);
         if ((e = cudaGetLastError()) != cudaSuccess) return e;
         ++nl;
     }
@@ -971,28 +1078,26 @@ cudaError_t tc_launch_gemms(const DevProblem &pb, const TcBuffers &b, const int3
     return cudaSuccess;
 }
 
-cudaError_t tc_launch_prep(const DevProblem &pb, const SolverState &s, const TcBuffers &b,
-                           int32_t cap, bool force_base, cudaStream_t st)
+cudaError_t tc_launch_prep(const SolverState &s, const TcRows &r, int32_t cap, bool force_base,
+                           cudaStream_t st)
 {
-    k_prep_tc<<<cap, 128, 0, st>>>(s, b, n_t_terms(pb), pb.kpad, force_base ? 1 : 0);
+    k_prep_tc<<<cap, 128, 0, st>>>(s, r, force_base ? 1 : 0);
     return cudaGetLastError();
 }
 
 cudaError_t tc_launch_eval(const DevProblem &pb, const SolverState &s, const TcBuffers &b,
-                           float *Fpart, float *dFpart, float *gpart, int32_t cap, bool with_dT,
-                           float *dose_out, bool force_base, cudaStream_t st, int32_t *n_launches,
-                           cudaEvent_t *ev)
+                           int32_t cap, bool with_dT, bool write_dose, bool force_base,
+                           cudaStream_t st, int32_t *n_launches, cudaEvent_t *ev)
 {
     int nl = 0;
     if (ev) cudaEventRecord(ev[0], st);
-    k_prep_tc<<<cap, 128, 0, st>>>(s, b, n_t_terms(pb), pb.kpad, force_base ? 1 : 0);
-    cudaError_t e = cudaGetLastError();
+    cudaError_t e = tc_launch_prep(s, tc_rows(pb, b), cap, force_base, st);
     if (e != cudaSuccess) return e;
     ++nl;
     if (ev) cudaEventRecord(ev[1], st);
     int32_t ng = 0;
-    if ((e = tc_launch_gemms(pb, b, s.n_act, Fpart, dFpart, gpart, cap, with_dT, dose_out, st, &ng,
-                             ev)) != cudaSuccess)
+    if ((e = tc_launch_gemms(tc_single_set(pb, b), 0, with_dT, write_dose, false, st, &ng, ev)) !=
+        cudaSuccess)
         return e;
     nl += ng;
     if (ev) cudaEventRecord(ev[3], st);
@@ -1000,10 +1105,10 @@ cudaError_t tc_launch_eval(const DevProblem &pb, const SolverState &s, const TcB
     fe.pb = pb;
     fe.n_rows = s.n_act;
     fe.cap = cap;
-    fe.Fpart = Fpart;
-    fe.dFpart = with_dT ? dFpart : nullptr;
-    fe.gpart = dose_out ? nullptr : gpart;
-    fe.sp = tc_split_plan(pb);
+    fe.Fpart = b.Fpart;
+    fe.dFpart = with_dT ? b.dFpart : nullptr;
+    fe.gpart = write_dose ? nullptr : b.gpart;
+    fe.sp = b.sp;
     if ((e = launch_finish(s, fe, tc_n_ptiles(pb), st)) != cudaSuccess) return e;
     ++nl;
     if (ev) cudaEventRecord(ev[4], st);

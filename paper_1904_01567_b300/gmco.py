@@ -34,7 +34,7 @@ class _Options(ctypes.Structure):
     _fields_ = [("precision", ctypes.c_int32), ("m", ctypes.c_int32), ("c1", ctypes.c_double),
                 ("max_ls", ctypes.c_int32), ("rx_gy", ctypes.c_double),
                 ("refine_iters", ctypes.c_int32), ("steps_per_poll", ctypes.c_int32),
-                ("stop_window", ctypes.c_int32)]
+                ("stop_window", ctypes.c_int32), ("grad_split_kb", ctypes.c_int32)]
 
 
 _lib = None
@@ -77,6 +77,21 @@ def load():
         lib.gmco_status_string.restype = ctypes.c_char_p
         lib.gmco_last_error.argtypes = []
         lib.gmco_last_error.restype = ctypes.c_char_p
+        lib.gmco_create_multi.argtypes = [_vp, _i32, ctypes.POINTER(_vp)]
+        lib.gmco_create_multi.restype = ctypes.c_int
+        lib.gmco_destroy_multi.argtypes = [_vp]
+        lib.gmco_destroy_multi.restype = None
+        lib.gmco_multi_set_split.argtypes = [_vp, _i32]
+        lib.gmco_multi_set_split.restype = ctypes.c_int
+        lib.gmco_multi_get_split.argtypes = [_vp]
+        lib.gmco_multi_get_split.restype = _i32
+        lib.gmco_multi_last_launch_count.argtypes = [_vp]
+        lib.gmco_multi_last_launch_count.restype = _i64
+        lib.gmco_solve_multi.argtypes = [_vp, _vp, _vp, _vp, _i32, ctypes.c_double, _vp, _vp, _vp,
+                                         _vp, _vp, _vp]
+        lib.gmco_solve_multi.restype = ctypes.c_int
+        lib.gmco_multi_autotune.argtypes = [_vp, _vp, _vp, _i32, _vp, _i32, _vp, _vp]
+        lib.gmco_multi_autotune.restype = ctypes.c_int
         _lib = lib
     return _lib
 
@@ -297,6 +312,127 @@ class Problem:
     def close(self):
         if self.handle:
             destroy_problem(self.handle)
+            self.handle = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+# ---------------------------------------------------------------- several patients
+def _ptr_array(ptrs):
+    arr = (_vp * len(ptrs))()
+    for i, p in enumerate(ptrs):
+        arr[i] = p
+    return arr
+
+
+class Multi:
+    """Owning wrapper of gmco_multi: several problems (patients) solved in one launch per
+    step.  `problems` are Problem objects that must outlive this object."""
+
+    def __init__(self, problems):
+        self.problems = list(problems)
+        hs = _ptr_array([pr.handle for pr in self.problems])
+        h = _vp()
+        _check(load().gmco_create_multi(ctypes.cast(hs, _vp), len(self.problems), ctypes.byref(h)),
+               "gmco_create_multi")
+        self.handle = h.value
+
+    @property
+    def split(self) -> int:
+        return int(load().gmco_multi_get_split(self.handle))
+
+    @split.setter
+    def split(self, kb: int):
+        _check(load().gmco_multi_set_split(self.handle, int(kb)), "gmco_multi_set_split")
+
+    def last_launch_count(self) -> int:
+        return int(load().gmco_multi_last_launch_count(self.handle))
+
+    def _weights(self, weights):
+        keeps, ptrs, cuda = [], [], False
+        for w in weights:
+            k, ptr, c = _prep(w, np.float32, "float32")
+            keeps.append(k)
+            ptrs.append(ptr)
+            cuda = cuda or c
+        P = (_i64 * len(keeps))(*[int(k.shape[0]) for k in keeps])
+        return keeps, ptrs, P, cuda
+
+    def solve(self, weights, t0=None, max_iters=500, tol=1e-6, stream=None,
+              want=("T", "objectives", "dvh", "iters", "status"), allow_timeout=False):
+        """gmco_solve_multi.  weights: one P_p x n_struct array per patient.  Returns a list
+        (one dict per patient) with the requested outputs."""
+        assert len(weights) == len(self.problems)
+        keeps, wptrs, P, cuda = self._weights(weights)
+        t_keeps, t_ptrs = [], []
+        if t0 is not None:
+            for t in t0:
+                k, ptr, _ = _prep(t, np.float32, "float32")
+                t_keeps.append(k)
+                t_ptrs.append(ptr)
+        outs = [dict() for _ in self.problems]
+        arrays = {}
+        for k in ("T", "objectives", "dvh", "iters", "status"):
+            if k not in want:
+                arrays[k] = None
+                continue
+            ptrs = []
+            for i, pr in enumerate(self.problems):
+                n = int(P[i])
+                shape, nd_, td_ = dict(T=((n, pr.info["n_dwell"]), np.float32, "float32"),
+                                       objectives=((n,), np.float64, "float64"),
+                                       dvh=((n, DVH_K), np.float32, "float32"),
+                                       iters=((n,), np.int32, "int32"),
+                                       status=((n,), np.int32, "int32"))[k]
+                outs[i][k], ptr = _alloc(shape, nd_, td_, cuda)
+                ptrs.append(ptr)
+            arrays[k] = _ptr_array(ptrs)
+        wa = _ptr_array(wptrs)
+        ta = _ptr_array(t_ptrs) if t0 is not None else None
+
+        def cp(a):
+            return ctypes.cast(a, _vp) if a is not None else None
+        st = load().gmco_solve_multi(self.handle, cp(wa), ctypes.cast(P, _vp), cp(ta),
+                                     int(max_iters), float(tol), cp(arrays["T"]),
+                                     cp(arrays["objectives"]), cp(arrays["dvh"]),
+                                     cp(arrays["iters"]), cp(arrays["status"]),
+                                     _stream_ptr(stream, cuda))
+        if st == ETIMEOUT and allow_timeout:
+            for o in outs:
+                o["timeout"] = True
+        else:
+            _check(st, "gmco_solve_multi")
+        del keeps, t_keeps
+        return outs
+
+    def autotune(self, weights, steps=8, candidates=(0, 4, 8, 16, 32, 64)):
+        """gmco_multi_autotune: times `steps` solver steps per candidate split length and
+        keeps the fastest.  Returns (best, {candidate: ms per step})."""
+        keeps, wptrs, P, _ = self._weights(weights)
+        cand = (_i32 * len(candidates))(*[int(c) for c in candidates])
+        ms = np.zeros(len(candidates))
+        best = _i32()
+        wa = _ptr_array(wptrs)
+        _check(load().gmco_multi_autotune(self.handle, ctypes.cast(wa, _vp), ctypes.cast(P, _vp),
+                                          int(steps), ctypes.cast(cand, _vp), len(candidates),
+                                          ms.ctypes.data, ctypes.byref(best)),
+               "gmco_multi_autotune")
+        del keeps
+        return int(best.value), {int(c): float(v) for c, v in zip(candidates, ms)}
+
+    def close(self):
+        if self.handle:
+            load().gmco_destroy_multi(self.handle)
             self.handle = None
 
     def __enter__(self):

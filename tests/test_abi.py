@@ -52,3 +52,21 @@ def test_no_cpu_fallback_without_device(gmco_mod):
         gmco_mod.create_problem(np.ones((4, 3), np.float32), np.zeros(4, np.int32),
                                 np.array([[1.0, 15.0, np.inf, 1.0]]))
     assert e.value.status == 3   # GMCO_ECUDA: the library never computes on the host
+
+
+def test_multi_host_validation(gmco_mod):
+    lib = gmco_mod.load()
+    h = ctypes.c_void_p()
+    assert lib.gmco_create_multi(None, 0, ctypes.byref(h)) == gmco_mod.EINVAL
+    assert h.value is None
+    arr = (ctypes.c_void_p * 1)(None)
+    assert lib.gmco_create_multi(ctypes.cast(arr, ctypes.c_void_p), 1, ctypes.byref(h)) == gmco_mod.EINVAL
+    assert lib.gmco_create_multi(ctypes.cast(arr, ctypes.c_void_p), 65, ctypes.byref(h)) == gmco_mod.EINVAL
+    assert lib.gmco_multi_set_split(None, 4) == gmco_mod.EINVAL
+    assert lib.gmco_multi_get_split(None) == -1
+    assert lib.gmco_multi_last_launch_count(None) == -1
+    lib.gmco_destroy_multi(None)
+    assert lib.gmco_solve_multi(None, None, None, None, 1, 0.0, None, None, None, None, None,
+                                None) == gmco_mod.EINVAL
+    o = gmco_mod.default_options()
+    assert o.grad_split_kb == 0 and o.stop_window == 1
