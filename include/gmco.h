@@ -229,6 +229,65 @@ gmco_status gmco_multi_autotune(gmco_multi *multi, const float *const *penalty_w
 /* Kernel launches made by the most recent gmco_solve_multi call. */
 int64_t gmco_multi_last_launch_count(const gmco_multi *multi);
 
+/* ---- learned warm start ----
+ * A per-dwell-position multilayer perceptron predicts each plan's dwell times from 10
+ * geometric features of the dwell position and the plan's 4 penalty weights; the solver then
+ * starts from the prediction.  The paper has no learned part (it starts from uniform times,
+ * Sec. 2.3.2); this is an extension.  Network:
+ *     x0  = [f_1 .. f_10, log10 max(w_1, 1e-3) .. log10 max(w_4, 1e-3)]        (14 inputs)
+ *     h_l = GELU(h_{l-1} W_l + b_l), l = 1..3, width 128, GELU(z) = z (1 + erf(z / sqrt 2)) / 2
+ *     t   = softplus(h_3 . w_4 + b_4)      (seconds)
+ * Parameters are one FP32 array of GMCO_MLP_NPARAM values in this order, matrices
+ * row-major with the input index first: W_1 [14][128], b_1 [128], W_2 [128][128], b_2,
+ * W_3 [128][128], b_3, w_4 [128], b_4 [1].  Products use BF16 weights and activations with
+ * FP32 accumulation; FP32 master weights are updated by Adam (beta 0.9, 0.999, eps 1e-8).
+ * Loss: mean over the batch rows of (t - t_target)^2.  The 10 features are the caller's
+ * (computed from its contours); the library treats them as numbers. */
+#define GMCO_MLP_NPARAM 35073
+typedef struct gmco_mlp gmco_mlp;
+
+/* Creates a network from initial parameters (host or device; finite). */
+gmco_status gmco_mlp_create(const float *params, gmco_mlp **out);
+void gmco_mlp_destroy(gmco_mlp *mlp);
+/* Current FP32 master parameters. */
+gmco_status gmco_mlp_get_params(gmco_mlp *mlp, float *params);
+
+/* Predicted dwell times of P plans of one patient: t_out[p][l] for features[l] (n_dwell x
+ * 10) and penalty_weights[p] (P x 4), each at least t_floor. */
+gmco_status gmco_mlp_predict(gmco_mlp *mlp, const float *features, int64_t n_dwell,
+                             const float *penalty_weights, int64_t P, float t_floor,
+                             float *t_out, void *cuda_stream);
+
+/* Loss and gradient (GMCO_MLP_NPARAM values, the parameter layout) at the current weights
+ * over R training rows: row r has features[pairs[r][0]] (n_feat x 10 table), penalty
+ * weights penalty_weights[pairs[r][1]] (n_w x 4 table) and target dwell time target[r]. */
+gmco_status gmco_mlp_gradient(gmco_mlp *mlp, const float *features, int64_t n_feat,
+                              const float *penalty_weights, int64_t n_w, const int32_t *pairs,
+                              const float *target, int64_t R, float *loss, float *grad,
+                              void *cuda_stream);
+
+/* One Adam step with learning rate lr on the gradient of those rows; *loss (may be NULL) is
+ * the loss before the step. */
+gmco_status gmco_mlp_train_step(gmco_mlp *mlp, const float *features, int64_t n_feat,
+                                const float *penalty_weights, int64_t n_w, const int32_t *pairs,
+                                const float *target, int64_t R, float lr, float *loss,
+                                void *cuda_stream);
+
+/* Kernel launches of the most recent call on this network. */
+int64_t gmco_mlp_last_launch_count(const gmco_mlp *mlp);
+
+/* Text of the most recent network error on the calling host thread. */
+const char *gmco_mlp_last_error(void);
+
+/* Warm start with fallback: predicts t for each of the P plans, evaluates the objective of
+ * the prediction and of the uniform start (1 s) with the problem's precision, and writes to
+ * t0_out (P x n_dwell) the prediction where its objective is not larger, else the uniform
+ * start.  from_model[p] (may be NULL) is 1 where the prediction was kept.  t0_out then goes
+ * to gmco_solve_batch. */
+gmco_status gmco_warm_start(gmco_problem *prob, gmco_mlp *mlp, const float *features,
+                            const float *penalty_weights, int64_t P, float t_floor,
+                            float *t0_out, int32_t *from_model, void *cuda_stream);
+
 /* Problem sizes as stored (after validation). */
 gmco_status gmco_problem_info(const gmco_problem *prob, int64_t *n_pnt, int64_t *n_dwell,
                               int32_t *n_struct, int32_t *precision);

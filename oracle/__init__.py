@@ -20,3 +20,4 @@ from .oracle import (  # noqa: F401
     NONFINITE,
 )
 from .optimum import fstar, objective_t, kkt_residual  # noqa: F401,E402
+from . import mlp  # noqa: F401,E402

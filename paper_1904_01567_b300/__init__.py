@@ -6,6 +6,10 @@ include/gmco.h); this package only marshals arguments to it.
 from .gmco import (  # noqa: F401
     Problem,
     Multi,
+    Mlp,
+    warm_start,
+    MLP_NPARAM,
+    MLP_NFEAT,
     OK,
     EINVAL,
     ENOMEM,

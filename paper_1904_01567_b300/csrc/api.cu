@@ -453,6 +453,19 @@ gmco_status end_call(gmco_problem *pr, void *user_stream)
     return GMCO_OK;
 }
 
+
+// Start of each plan: the model's prediction where its objective is not larger than the
+// uniform start's (a NaN objective selects the uniform start), else t = 1 s.
+__global__ void k_choose_start(const double *__restrict__ F_pred, const double *__restrict__ F_unif,
+                               const float *__restrict__ t_pred, int64_t nd, float *__restrict__ t0,
+                               int32_t *__restrict__ flag)
+{
+    const int64_t p = blockIdx.x;
+    const bool use = F_pred[p] <= F_unif[p];
+    for (int64_t l = threadIdx.x; l < nd; l += blockDim.x) t0[p * nd + l] = use ? t_pred[p * nd + l] : 1.0f;
+    if (threadIdx.x == 0) flag[p] = use ? 1 : 0;
+}
+
 }  // namespace
 
 // ------------------------------------------------------------------ several patients
@@ -1530,6 +1543,63 @@ gmco_status gmco_multi_autotune(gmco_multi *m, const float *const *penalty_weigh
     m->split_kb = rs == GMCO_OK ? best_c : saved;
     if (rs == GMCO_OK && best) *best = best_c;
     return rs;
+}
+
+gmco_status gmco_warm_start(gmco_problem *pr, gmco_mlp *mlp, const float *features,
+                            const float *penalty_weights, int64_t P, float t_floor,
+                            float *t0_out, int32_t *from_model, void *cuda_stream)
+{
+    if (!pr || !mlp || !features || !penalty_weights || !t0_out || P < 1 || P > (1 << 20) ||
+        !(t_floor >= 0.0f) || !isfinite(t_floor)) {
+        set_error_msg("gmco_warm_start: bad arguments");
+        return GMCO_EINVAL;
+    }
+    if (pr->pb.n_struct != 4) {
+        set_error_msg("gmco_warm_start: the network takes 4 penalty weights per plan");
+        return GMCO_EUNSUPPORTED;
+    }
+    pr->launches = 0;
+    CKS(begin_call(pr, cuda_stream));
+    CKS(ensure_workspace(pr, (int32_t)P));
+    const DevProblem &pb = pr->pb;
+    CKS(stage_in(pr, penalty_weights, pr->dW, (size_t)P * pb.n_struct * sizeof(float)));
+    int32_t bad = 0;
+    CKS(count_bad(pr, pr->dW, P * pb.n_struct, false, &bad));
+    if (bad) {
+        set_error_msg("gmco_warm_start: negative or non-finite weights");
+        return GMCO_EINVAL;
+    }
+    const gmco_status ms = gmco_mlp_predict(mlp, features, pb.n_dwell, pr->dW, P, t_floor, pr->dT0,
+                                            pr->stream);
+    if (ms != GMCO_OK) {
+        set_error_msg((std::string("gmco_warm_start: ") + gmco_mlp_last_error()).c_str());
+        return ms;
+    }
+    pr->launches += gmco_mlp_last_launch_count(mlp);
+    SolverState s = pr->s;
+    s.P = (int32_t)P;
+    const int form = pr->opt.precision == GMCO_PREC_FP32 ? 0 : 1;
+    // objective of the prediction, then of the uniform start
+    CK(launch_solver_init(s, pb, pr->dW, pr->dT0, 0, pr->stream));
+    CK(launch_compact(s, 0, pr->stream));
+    CKS(launch_eval(pr, s, form, false, pr->stream));
+    CK(cudaMemcpyAsync(pr->dObj, s.Ft, (size_t)P * sizeof(double), cudaMemcpyDeviceToDevice, pr->stream));
+    CK(launch_solver_init(s, pb, pr->dW, nullptr, 0, pr->stream));
+    CK(launch_compact(s, 0, pr->stream));
+    CKS(launch_eval(pr, s, form, false, pr->stream));
+    pr->launches += 4;
+    k_choose_start<<<(unsigned)P, 128, 0, pr->stream>>>(pr->dObj, s.Ft, pr->dT0, pb.n_dwell, pr->dTout,
+                                                        pr->dIters);
+    CK(cudaGetLastError());
+    pr->launches++;
+    CK(cudaMemcpyAsync(t0_out, pr->dTout, (size_t)P * pb.n_dwell * sizeof(float), cudaMemcpyDefault,
+                       pr->stream));
+    if (from_model)
+        CK(cudaMemcpyAsync(from_model, pr->dIters, (size_t)P * sizeof(int32_t), cudaMemcpyDefault,
+                           pr->stream));
+    CKS(check_tc_error(pr));
+    CKS(end_call(pr, cuda_stream));
+    return GMCO_OK;
 }
 
 }  // extern "C"

@@ -92,6 +92,25 @@ def load():
         lib.gmco_solve_multi.restype = ctypes.c_int
         lib.gmco_multi_autotune.argtypes = [_vp, _vp, _vp, _i32, _vp, _i32, _vp, _vp]
         lib.gmco_multi_autotune.restype = ctypes.c_int
+        lib.gmco_mlp_create.argtypes = [_vp, ctypes.POINTER(_vp)]
+        lib.gmco_mlp_create.restype = ctypes.c_int
+        lib.gmco_mlp_destroy.argtypes = [_vp]
+        lib.gmco_mlp_destroy.restype = None
+        lib.gmco_mlp_get_params.argtypes = [_vp, _vp]
+        lib.gmco_mlp_get_params.restype = ctypes.c_int
+        lib.gmco_mlp_predict.argtypes = [_vp, _vp, _i64, _vp, _i64, ctypes.c_float, _vp, _vp]
+        lib.gmco_mlp_predict.restype = ctypes.c_int
+        lib.gmco_mlp_gradient.argtypes = [_vp, _vp, _i64, _vp, _i64, _vp, _vp, _i64, _vp, _vp, _vp]
+        lib.gmco_mlp_gradient.restype = ctypes.c_int
+        lib.gmco_mlp_train_step.argtypes = [_vp, _vp, _i64, _vp, _i64, _vp, _vp, _i64,
+                                            ctypes.c_float, _vp, _vp]
+        lib.gmco_mlp_train_step.restype = ctypes.c_int
+        lib.gmco_mlp_last_launch_count.argtypes = [_vp]
+        lib.gmco_mlp_last_launch_count.restype = _i64
+        lib.gmco_mlp_last_error.argtypes = []
+        lib.gmco_mlp_last_error.restype = ctypes.c_char_p
+        lib.gmco_warm_start.argtypes = [_vp, _vp, _vp, _vp, _i64, ctypes.c_float, _vp, _vp, _vp]
+        lib.gmco_warm_start.restype = ctypes.c_int
         _lib = lib
     return _lib
 
@@ -446,3 +465,103 @@ class Multi:
             self.close()
         except Exception:
             pass
+
+
+# ---------------------------------------------------------------- learned warm start
+MLP_NPARAM = 35073
+MLP_NFEAT = 10
+
+
+def _check_mlp(status, where):
+    if status != OK:
+        raise GmcoError(status, where, load().gmco_mlp_last_error().decode())
+
+
+class Mlp:
+    """Owning wrapper of gmco_mlp (per-dwell warm-start network).  `params`: the
+    GMCO_MLP_NPARAM initial parameters (see include/gmco.h for the layout)."""
+
+    def __init__(self, params):
+        keep, ptr, _ = _prep(params, np.float32, "float32")
+        assert int(np.prod(keep.shape)) == MLP_NPARAM
+        h = _vp()
+        _check_mlp(load().gmco_mlp_create(ptr, ctypes.byref(h)), "gmco_mlp_create")
+        self.handle = h.value
+
+    def params(self):
+        out = np.empty(MLP_NPARAM, np.float32)
+        _check_mlp(load().gmco_mlp_get_params(self.handle, out.ctypes.data), "gmco_mlp_get_params")
+        return out
+
+    def last_launch_count(self) -> int:
+        return int(load().gmco_mlp_last_launch_count(self.handle))
+
+    def predict(self, features, penalty_weights, t_floor=0.0, stream=None):
+        f_keep, f_ptr, cuda = _prep(features, np.float32, "float32")
+        w_keep, w_ptr, c2 = _prep(penalty_weights, np.float32, "float32")
+        cuda = cuda or c2
+        nd, P = int(f_keep.shape[0]), int(w_keep.shape[0])
+        out, optr = _alloc((P, nd), np.float32, "float32", cuda)
+        _check_mlp(load().gmco_mlp_predict(self.handle, f_ptr, nd, w_ptr, P, float(t_floor), optr,
+                                           _stream_ptr(stream, cuda)), "gmco_mlp_predict")
+        del f_keep, w_keep
+        return out
+
+    def _batch(self, features, penalty_weights, pairs, target):
+        f = _prep(features, np.float32, "float32")
+        w = _prep(penalty_weights, np.float32, "float32")
+        pr = _prep(pairs, np.int32, "int32")
+        tg = _prep(target, np.float32, "float32")
+        cuda = f[2] or w[2] or pr[2] or tg[2]
+        return (f, w, pr, tg), cuda
+
+    def gradient(self, features, penalty_weights, pairs, target, stream=None):
+        (f, w, pr, tg), cuda = self._batch(features, penalty_weights, pairs, target)
+        grad = np.empty(MLP_NPARAM, np.float32)
+        loss = ctypes.c_float()
+        _check_mlp(load().gmco_mlp_gradient(self.handle, f[1], int(f[0].shape[0]), w[1],
+                                            int(w[0].shape[0]), pr[1], tg[1], int(tg[0].shape[0]),
+                                            ctypes.byref(loss), grad.ctypes.data,
+                                            _stream_ptr(stream, cuda)), "gmco_mlp_gradient")
+        return float(loss.value), grad
+
+    def train_step(self, features, penalty_weights, pairs, target, lr=1e-3, stream=None):
+        (f, w, pr, tg), cuda = self._batch(features, penalty_weights, pairs, target)
+        loss = ctypes.c_float()
+        _check_mlp(load().gmco_mlp_train_step(self.handle, f[1], int(f[0].shape[0]), w[1],
+                                              int(w[0].shape[0]), pr[1], tg[1],
+                                              int(tg[0].shape[0]), float(lr), ctypes.byref(loss),
+                                              _stream_ptr(stream, cuda)), "gmco_mlp_train_step")
+        return float(loss.value)
+
+    def close(self):
+        if self.handle:
+            load().gmco_mlp_destroy(self.handle)
+            self.handle = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def warm_start(problem, mlp, features, penalty_weights, t_floor=0.3, stream=None):
+    """gmco_warm_start: per-plan start times (model prediction, or uniform where the
+    prediction's objective is larger) and the per-plan choice (1 = model)."""
+    f_keep, f_ptr, c1 = _prep(features, np.float32, "float32")
+    w_keep, w_ptr, c2 = _prep(penalty_weights, np.float32, "float32")
+    cuda = c1 or c2
+    P = int(w_keep.shape[0])
+    t0, tptr = _alloc((P, problem.info["n_dwell"]), np.float32, "float32", cuda)
+    flag, fptr = _alloc((P,), np.int32, "int32", cuda)
+    _check(load().gmco_warm_start(problem.handle, mlp.handle, f_ptr, w_ptr, P, float(t_floor), tptr,
+                                  fptr, _stream_ptr(stream, cuda)), "gmco_warm_start")
+    del f_keep, w_keep
+    return t0, flag

@@ -17,4 +17,6 @@ from .patient import (  # noqa: F401
     weights_dirichlet,
     workload,
     multi_patient_specs,
+    dwell_features,
+    mlp_init_params,
 )

@@ -278,3 +278,46 @@ def multi_patient_specs(n_patients: int = 64, seed: int = BASE_SEED + 3):
         specs.append(dict(seed=seed * 1000 + k, n_catheters=n_cat, dwell_step=0.2,
                           n_points=(n_p, n_u, n_r, n_b), scale=f))
     return specs
+
+
+def dwell_features(pat: Patient) -> np.ndarray:
+    """The 10 per-dwell input features of the warm-start network, (n_dwell, 10) float32:
+    signed distances (cm, negative inside) to the prostate surface, the urethra, the rectum
+    and the bladder; depth along the catheter (0 at its first dwell, 1 at its last); x, y, z
+    (cm); the prostate's size (cube root of a b c, cm); and the dwell density (dwell
+    positions per cm^3 of prostate).  The prostate distance is the radial one, exact for a
+    sphere."""
+    g = pat.geometry
+    p = pat.dwells
+    x, y, z = p[:, 0], p[:, 1], p[:, 2]
+    r = np.sqrt(x * x + y * y + z * z)
+    s = np.sqrt((x / g.a) ** 2 + (y / g.b) ** 2 + (z / g.c) ** 2)
+    d_pro = np.where(s > 1e-9, (s - 1.0) * r / np.maximum(s, 1e-9), -min(g.a, g.b, g.c))
+    d_ure = np.sqrt(x * x + y * y) - g.urethra_r
+    d_rec = np.sqrt(x * x + (y - g.rectum_y) ** 2) - g.rectum_r
+    d_bla = np.sqrt(x * x + y * y + (z - g.bladder_z) ** 2) - g.bladder_r
+    depth = np.zeros(len(p))
+    for c in np.unique(pat.catheter):
+        m = pat.catheter == c
+        zc = z[m]
+        span = zc.max() - zc.min()
+        depth[m] = (zc - zc.min()) / span if span > 0 else 0.0
+    size = np.full(len(p), (g.a * g.b * g.c) ** (1.0 / 3.0))
+    density = np.full(len(p), len(p) / (4.0 / 3.0 * np.pi * g.a * g.b * g.c))
+    return np.stack([d_pro, d_ure, d_rec, d_bla, depth, x, y, z, size, density], axis=1).astype(np.float32)
+
+
+def mlp_init_params(seed: int) -> np.ndarray:
+    """Seeded initial parameters of the warm-start network in the C ABI's layout (W_1 [14][128],
+    b_1, W_2 [128][128], b_2, W_3, b_3, w_4 [128], b_4): weights uniform in +-sqrt(6 / fan_in)
+    / 2, hidden biases 0, output weights uniform in +-1 / sqrt(128), output bias such that
+    softplus(b_4) = 1 s."""
+    rng = np.random.default_rng(np.random.SeedSequence([seed, 5]))
+    parts = []
+    for fan_in, fan_out in ((14, 128), (128, 128), (128, 128)):
+        lim = 0.5 * np.sqrt(6.0 / fan_in)
+        parts.append(rng.uniform(-lim, lim, fan_in * fan_out))
+        parts.append(np.zeros(fan_out))
+    parts.append(rng.uniform(-1.0, 1.0, 128) / np.sqrt(128.0))
+    parts.append(np.array([np.log(np.expm1(1.0))]))
+    return np.concatenate(parts).astype(np.float32)
