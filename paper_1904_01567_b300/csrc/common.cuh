@@ -48,6 +48,7 @@ struct SplitPlan {
     int32_t kb_total;        // K blocks (of points) in total
     int32_t target_ctas;     // CTAs to aim for
     int32_t max_split;       // grid extent along the split dimension
+    int32_t min_kb;          // fewest K blocks per split: bounds the partial sums a reader adds
 };
 
 __host__ __device__ inline void split_plan(const SplitPlan &p, int32_t n_rows, int32_t *kbps,
@@ -57,7 +58,8 @@ __host__ __device__ inline void split_plan(const SplitPlan &p, int32_t n_rows, i
     tiles = (tiles < 1 ? 1 : tiles) * (p.other_tiles < 1 ? 1 : p.other_tiles);
     int32_t target = p.target_ctas / tiles;
     target = target < 1 ? 1 : (target > p.max_split ? p.max_split : target);
-    const int32_t k = (p.kb_total + target - 1) / target;
+    int32_t k = (p.kb_total + target - 1) / target;
+    k = k < p.min_kb ? p.min_kb : k;
     *kbps = k;
     *n_split = (p.kb_total + k - 1) / k;
 }

@@ -294,6 +294,7 @@ SplitPlan simt_split_plan(const DevProblem &pb)
     p.kb_total = (int32_t)(pb.np_pad / BK);
     p.target_ctas = 148 * 2 * 2;     // two CTAs per SM, two waves
     p.max_split = (int32_t)std::min<int64_t>(148, p.kb_total);
+    p.min_kb = 32;                   // splits of at least 512 points (see tc_split_plan)
     return p;
 }
 

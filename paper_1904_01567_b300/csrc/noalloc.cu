@@ -140,6 +140,7 @@ cudaError_t noalloc_evaluate(const DevProblem &pb, const float *W, int64_t P, co
     ea.sp = simt_split_plan(pb);
     ea.sp.target_ctas = 1 << 30;     // always exactly kSplit point splits
     ea.sp.max_split = kSplit;
+    ea.sp.min_kb = 1;
     k_na_prep<<<(unsigned)P, 128, 0, st>>>(X, W, pb.inv_count, (int32_t)P, (int32_t)pb.n_dwell,
                                            (int32_t)pb.nd_pad, pb.n_struct, Tc, Wc, n_rows);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;

@@ -157,10 +157,23 @@ __global__ void k_finish(SolverState s, EvalArgs e, int32_t n_ptiles)
         const int R = *e.n_rows;
         int kbps, n_split;
         split_plan(e.sp, R, &kbps, &n_split);
-        for (int l = threadIdx.x; l < nd; l += blockDim.x) {
-            float acc = 0.0f;
-            for (int q = 0; q < n_split; ++q) acc += e.gpart[((size_t)q * R + i) * nd + l];
-            s.gt[(size_t)j * nd + l] = 2.0f * s.xt[(size_t)j * nd + l] * acc;
+        // split order per element, as in the fused step; up to 8 elements per thread
+        // (nd <= 1024 = 8 x 128 threads) loaded independently within each split
+        float acc[8];
+#pragma unroll
+        for (int k = 0; k < 8; ++k) acc[k] = 0.0f;
+        for (int q = 0; q < n_split; ++q) {
+            const float *gq = e.gpart + ((size_t)q * R + i) * nd;
+#pragma unroll
+            for (int k = 0; k < 8; ++k) {
+                const int l = threadIdx.x + k * 128;
+                if (l < nd) acc[k] += gq[l];
+            }
+        }
+#pragma unroll
+        for (int k = 0; k < 8; ++k) {
+            const int l = threadIdx.x + k * 128;
+            if (l < nd) s.gt[(size_t)j * nd + l] = 2.0f * s.xt[(size_t)j * nd + l] * acc[k];
         }
     }
     __shared__ double red[2][128];
@@ -266,17 +279,35 @@ __device__ __forceinline__ void step_plan(const SolverState &s, const UpdatePara
     const double dF = warp_sum_d(dfsum);
     int kbps, n_split;
     split_plan(a.sp, R, &kbps, &n_split);
+    // sum over the splits in split order; each split's EPL loads are independent, so the
+    // latency chain is one load per split rather than one per element and split
     float gtv[EPL];
 #pragma unroll
-    for (int e = 0; e < EPL; ++e) {
-        gtv[e] = 0.0f;
-        if (e < epl) {
-            const int l = lane + 32 * e;
-            float acc = 0.0f;
-            for (int q = 0; q < n_split; ++q) acc += a.gpart[((size_t)q * R + slot) * nd + l];
-            gtv[e] = 2.0f * xt[l] * acc;
+    for (int e = 0; e < EPL; ++e) gtv[e] = 0.0f;
+    int q = 0;
+    for (; q + 4 <= n_split; q += 4) {   // four splits' loads in flight, added in split order
+        float v[4][EPL];
+#pragma unroll
+        for (int r = 0; r < 4; ++r) {
+            const float *gq = a.gpart + ((size_t)(q + r) * R + slot) * nd + lane;
+#pragma unroll
+            for (int e = 0; e < EPL; ++e) v[r][e] = e < epl ? gq[32 * e] : 0.0f;
         }
+#pragma unroll
+        for (int r = 0; r < 4; ++r)
+#pragma unroll
+            for (int e = 0; e < EPL; ++e)
+                if (e < epl) gtv[e] += v[r][e];
     }
+    for (; q < n_split; ++q) {
+        const float *gq = a.gpart + ((size_t)q * R + slot) * nd + lane;
+#pragma unroll
+        for (int e = 0; e < EPL; ++e)
+            if (e < epl) gtv[e] += gq[32 * e];
+    }
+#pragma unroll
+    for (int e = 0; e < EPL; ++e)
+        if (e < epl) gtv[e] *= 2.0f * xt[lane + 32 * e];
 
     float gv[EPL];
     float gmax = 0.0f;

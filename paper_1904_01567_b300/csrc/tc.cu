@@ -883,9 +883,13 @@ SplitPlan tc_split_plan(const DevProblem &pb, int32_t kb_per_split)
     if (kb_per_split > 0) {   // fixed split length: as many splits as that takes
         p.target_ctas = 1 << 30;
         p.max_split = (int32_t)ceil_div(p.kb_total, kb_per_split);
+        p.min_kb = 1;
     } else {
+        // about one wave of CTAs, but splits of at least 512 points: a few plan rows would
+        // otherwise get ~150 splits whose partial sums the step kernel adds one by one
         p.target_ctas = 148;
         p.max_split = tc_max_split(pb);
+        p.min_kb = 8;
     }
     return p;
 }
