@@ -45,9 +45,13 @@ def parse_args():
     ap.add_argument("--precision", default="bf16x2",
                     choices=["fp32", "bf16", "fp8", "bf16x2", "bf16x3"])
     ap.add_argument("--tol", type=float, default=1e-10)
-    ap.add_argument("--max-iters", type=int, default=20000)
+    ap.add_argument("--max-iters", type=int, default=3000)
     ap.add_argument("--steps-per-poll", type=int, default=32)
     ap.add_argument("--stop-window", type=int, default=1)
+    ap.add_argument("--grad-split-kb", type=int, default=0,
+                    help="tensor-core forms: 64-point blocks per gradient split (0: automatic)")
+    ap.add_argument("--refine-iters", type=int, default=0,
+                    help="tensor-core forms: further iterations with the FP32 evaluation")
     ap.add_argument("--profile-reps", type=int, default=20)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
@@ -199,6 +203,7 @@ def workload_config(args, pat, P):
     return {"workload": args.workload, "n_pnt": int(pat.n_pnt), "n_dwell": int(pat.n_dwell),
             "n_struct": 4, "plans_per_gpu": int(P), "m": 10, "tol": args.tol,
             "max_iters": args.max_iters, "stop_window": args.stop_window,
+            "refine_iters_fp32": args.refine_iters, "grad_split_kb": args.grad_split_kb,
             "start": "uniform t = 1 s",
             "quality": f"F <= F*(1+{QUALITY:g}), F* = exact FP64 optimum per plan",
             "l2": "flushed between timed steps (256 MB write)" if not args.no_flush else "not flushed",
@@ -434,7 +439,8 @@ def run_ours(args):
     P = W.shape[0]
     fstar = read_fstar(args.workload)[:P]
     prob = g.Problem(pat.A, pat.sid, pat.params, precision=args.precision,
-                     steps_per_poll=args.steps_per_poll, stop_window=args.stop_window)
+                     steps_per_poll=args.steps_per_poll, stop_window=args.stop_window,
+                     refine_iters=args.refine_iters, grad_split_kb=args.grad_split_kb)
     Wd = torch.from_numpy(W).cuda()
     stream = torch.cuda.current_stream()
     flush = None if args.no_flush else torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32,

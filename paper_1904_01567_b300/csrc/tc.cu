@@ -115,12 +115,12 @@ __device__ __forceinline__ void fence_before() { asm volatile("tcgen05.fence::be
 __device__ __forceinline__ void fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
 
 // Shared-memory matrix descriptor: K-major operand, 128-byte swizzle, 8-row atoms of
-// 1024 bytes (stride-dimension byte offset 1024), descriptor version 1.
-__device__ __forceinline__ uint64_t sw128_desc(uint32_t saddr)
-{
-    return (uint64_t)((saddr & 0x3FFFFu) >> 4) | ((uint64_t)1 << 16) |
-           ((uint64_t)(1024 >> 4) << 32) | ((uint64_t)1 << 46) | ((uint64_t)2 << 61);
-}
+// 1024 bytes (stride-dimension byte offset 1024), descriptor version 1.  Only the start
+// address field (bits 0-13, address / 16) varies; the rest is DESC_FIXED.
+constexpr uint64_t DESC_FIXED = ((uint64_t)1 << 16) | ((uint64_t)(1024 >> 4) << 32) |
+                                ((uint64_t)1 << 46) | ((uint64_t)2 << 61);
+__device__ __forceinline__ uint32_t desc_lo(uint32_t saddr) { return (saddr & 0x3FFFFu) >> 4; }
+__device__ __forceinline__ uint64_t sw128_desc(uint32_t saddr) { return DESC_FIXED | desc_lo(saddr); }
 
 // Instruction descriptor, kind::f16: FP32 accumulator, BF16 A and B, both K-major, M = 128.
 __device__ __forceinline__ uint32_t idesc_bf16(int n)
@@ -181,9 +181,14 @@ __device__ __forceinline__ void tmem_ld_wait_regs8(uint32_t (&a)[8], uint32_t (&
 }
 
 // ------------------------------------------------------------------ the GEMM kernel
+// One kind of ring stage: the B tiles (b_map) and A tiles (a_map) loaded for one K block, and
+// the products issued on them: pair q multiplies A tile pair_a[q] by B tile pair_b[q] into
+// accumulator pair_acc[q].
+constexpr int MAX_B = 3, MAX_A = 4, MAX_PAIRS = 8;
 struct Group {
-    int32_t b_map, n_a;
-    int32_t a_map[4], acc[4];
+    int32_t n_b, n_a, n_pair;
+    int32_t b_map[MAX_B], a_map[MAX_A];
+    int32_t pair_b[MAX_PAIRS], pair_a[MAX_PAIRS], pair_acc[MAX_PAIRS];
 };
 
 // Launch parameters common to every problem of the list.
@@ -195,7 +200,8 @@ struct KParams {
     int32_t nG;               // BF16 terms of G written by the dose epilogue
     int32_t n_groups;
     Group g[3];
-    int32_t n_stages, stage_bytes, b_bytes;   // ring stage size and its B-operand slot
+    int32_t n_stages, stage_bytes, b_bytes;   // ring stage size and the size of one B slot
+    int32_t a_off;                            // offset of the A tiles in a stage
     int32_t *err;
 };
 
@@ -333,12 +339,13 @@ __global__ void __launch_bounds__(NTHREADS, 1) k_tc(const __grid_constant__ KPar
                         if (!mbar_wait(smem_u32(&empty_bar[s]), ph ^ 1u, kp.err, 1)) { ok = false; break; }
                         uint8_t *st = smem + (size_t)s * kp.stage_bytes;
                         const uint32_t fb = smem_u32(&full_bar[s]);
-                        mbar_expect_tx(fb, bbytes + (uint32_t)(g.n_a * A_TILE));
-                        for (int b = 0; b < nbox; ++b)
-                            tma_load_2d(smem_u32(st + b * box_rows * 128), &kp.maps.m[g.b_map],
-                                        kb * BK, brow0 + b * box_rows, fb);
+                        mbar_expect_tx(fb, (uint32_t)g.n_b * bbytes + (uint32_t)(g.n_a * A_TILE));
+                        for (int bi = 0; bi < g.n_b; ++bi)
+                            for (int b = 0; b < nbox; ++b)
+                                tma_load_2d(smem_u32(st + bi * kp.b_bytes + b * box_rows * 128),
+                                            &kp.maps.m[g.b_map[bi]], kb * BK, brow0 + b * box_rows, fb);
                         for (int t = 0; t < g.n_a; ++t)
-                            tma_load_2d(smem_u32(st + kp.b_bytes + t * A_TILE), &kp.maps.m[g.a_map[t]],
+                            tma_load_2d(smem_u32(st + kp.a_off + t * A_TILE), &kp.maps.m[g.a_map[t]],
                                         kb * BK, row0, fb);
                     }
                 }
@@ -381,32 +388,52 @@ __global__ void __launch_bounds__(NTHREADS, 1) k_tc(const __grid_constant__ KPar
                 if (!ok) break;
                 fence_after();
                 const uint32_t tbuf = tmem + (uint32_t)(buf * BUF_COLS);
-                uint32_t started = 0u;   // bit a: accumulator a already written in this item
                 const uint32_t id0 = idesc_bf16(n0), id1 = idesc_bf16(n1 > 0 ? n1 : 16);
                 const uint32_t boff1 = (uint32_t)(n0 * 128);
+                // Per product q of a group: descriptor address fields (16-byte units) of its
+                // A and B tiles relative to the stage, its accumulator column, and whether it
+                // is the first product into that accumulator (which starts the sum).  In the
+                // loop a descriptor is DESC_FIXED | (stage + offset + 2 per 32-byte K step).
+                const uint32_t s_lo0 = desc_lo(smem_u32(smem));
+                const uint32_t stage_lo = (uint32_t)kp.stage_bytes >> 4;
+                const uint32_t b1_lo = boff1 >> 4;
                 for (int gi = 0; gi < kp.n_groups && ok; ++gi) {
-                    const Group g = kp.g[gi];
+                    const int np = kp.g[gi].n_pair;
+                    uint32_t bq[MAX_PAIRS], aq[MAX_PAIRS], dq[MAX_PAIRS], fq[MAX_PAIRS];
+#pragma unroll
+                    for (int q = 0; q < MAX_PAIRS; ++q) {
+                        const int qq = q < np ? q : 0;
+                        const int acc = kp.g[gi].pair_acc[qq];
+                        bq[q] = (uint32_t)(kp.g[gi].pair_b[qq] * kp.b_bytes) >> 4;
+                        aq[q] = (uint32_t)(kp.a_off + kp.g[gi].pair_a[qq] * A_TILE) >> 4;
+                        dq[q] = tbuf + (uint32_t)(acc * BN1);
+                        bool first = gi == 0;
+#pragma unroll
+                        for (int r = 0; r < MAX_PAIRS; ++r)
+                            if (r < q && kp.g[gi].pair_acc[r] == acc) first = false;
+                        fq[q] = first ? 1u : 0u;
+                    }
                     for (int kb = kb0; kb < kb1; ++kb, ++it) {
                         const int s = it % kp.n_stages;
                         const uint32_t ph = (uint32_t)(it / kp.n_stages) & 1u;
                         if (!mbar_wait(smem_u32(&full_bar[s]), ph, kp.err, 2)) { ok = false; break; }
                         fence_after();
-                        const uint32_t st = smem_u32(smem + (size_t)s * kp.stage_bytes);
-                        const uint32_t abase = st + (uint32_t)kp.b_bytes;
+                        const uint32_t st_lo = s_lo0 + (uint32_t)s * stage_lo;
+                        const uint32_t fresh = kb == kb0 ? 1u : 0u;
                         const int k16n = min(4, k16_total - kb * 4);
-                        for (int k16 = 0; k16 < k16n; ++k16) {
-                            const uint64_t bd0 = sw128_desc(st + k16 * 32);
-                            const uint64_t bd1 = sw128_desc(st + boff1 + k16 * 32);
 #pragma unroll
-                            for (int t = 0; t < 4; ++t) {
-                                if (t < g.n_a) {
-                                    const uint64_t ad = sw128_desc(abase + t * A_TILE + k16 * 32);
-                                    const int acc = g.acc[t];
-                                    const uint32_t accum = (started >> acc) & 1u;
-                                    const uint32_t dcol = tbuf + (uint32_t)(acc * BN1);
-                                    mma_bf16(dcol, ad, bd0, id0, accum);
-                                    if (n1 > 0) mma_bf16(dcol + (uint32_t)n0, ad, bd1, id1, accum);
-                                    started |= 1u << acc;
+                        for (int k16 = 0; k16 < 4; ++k16) {
+                            if (k16 < k16n) {
+                                const uint32_t kk = st_lo + 2u * (uint32_t)k16;
+#pragma unroll
+                                for (int q = 0; q < MAX_PAIRS; ++q) {
+                                    if (q < np) {
+                                        const uint64_t ad = DESC_FIXED | (kk + aq[q]);
+                                        const uint32_t accum = (k16 == 0 && (fresh & fq[q])) ? 0u : 1u;
+                                        mma_bf16(dq[q], ad, DESC_FIXED | (kk + bq[q]), id0, accum);
+                                        if (n1 > 0)
+                                            mma_bf16(dq[q] + (uint32_t)n0, ad, DESC_FIXED | (kk + bq[q] + b1_lo), id1, accum);
+                                    }
                                 }
                             }
                         }
@@ -805,25 +832,62 @@ KParams make_params(const TcLaunchSet &set, int kind, int parity, bool with_dT, 
     k.zero_next = zero_next ? 1 : 0;
     const int nA = set.tc_terms, nT = n_t_terms(nA);
     k.nG = nT;
-    k.n_groups = nA;
-    int max_a = 0;
-    for (int i = 0; i < nA; ++i) {
-        Group &g = k.g[i];
-        g.b_map = i;
-        g.n_a = 0;
-        for (int j = 0; j < nT; ++j)
-            if (keep_pair(i, j, nA, nT)) {
-                g.a_map[g.n_a] = 3 + j;
-                g.acc[g.n_a++] = 0;
-            }
-        if (kind == 1 && with_dT) {
-            g.a_map[g.n_a] = 6;
-            g.acc[g.n_a++] = 1;
-        }
-        max_a = std::max(max_a, g.n_a);
-    }
     k.b_bytes = kind == 1 ? BN1 * 128 : set.max_b_rows_grad * 128;
-    k.stage_bytes = k.b_bytes + max_a * A_TILE;
+    auto add_pair = [](Group &g, int b, int a, int acc) {
+        g.pair_b[g.n_pair] = b;
+        g.pair_a[g.n_pair] = a;
+        g.pair_acc[g.n_pair++] = acc;
+    };
+    // dose GEMM: every B term and every A operand of a K block in one stage (each tile loaded
+    // once per K block) when two such stages fit; otherwise one stage kind per B term
+    const int na_all = nT + ((kind == 1 && with_dT) ? 1 : 0);
+    const bool merged = kind == 1 && nA * k.b_bytes + na_all * A_TILE <= SMEM_BUDGET / 2 &&
+                        nA * nT + nA <= MAX_PAIRS;
+    int max_b = 1, max_a = 0;
+    if (merged) {
+        k.n_groups = 1;
+        Group &g = k.g[0];
+        g = Group{};
+        g.n_b = nA;
+        for (int i = 0; i < nA; ++i) g.b_map[i] = i;
+        g.n_a = na_all;
+        for (int j = 0; j < nT; ++j) g.a_map[j] = 3 + j;
+        if (with_dT) g.a_map[nT] = 6;
+        // products into the dose (0) and dose-change (1) accumulators alternate where they
+        // can, so consecutive MMAs do not wait on the same accumulator
+        int d_i[MAX_PAIRS], d_j[MAX_PAIRS], nd = 0, c_i[MAX_PAIRS], nc = 0;
+        for (int i = 0; i < nA; ++i) {
+            for (int j = 0; j < nT; ++j)
+                if (keep_pair(i, j, nA, nT)) { d_i[nd] = i; d_j[nd++] = j; }
+            if (with_dT) c_i[nc++] = i;
+        }
+        for (int q = 0; q < std::max(nd, nc); ++q) {
+            if (q < nd) add_pair(g, d_i[q], d_j[q], 0);
+            if (q < nc) add_pair(g, c_i[q], nT, 1);
+        }
+        max_b = nA;
+        max_a = na_all;
+    } else {
+        k.n_groups = nA;
+        for (int i = 0; i < nA; ++i) {
+            Group &g = k.g[i];
+            g = Group{};
+            g.n_b = 1;
+            g.b_map[0] = i;
+            for (int j = 0; j < nT; ++j)
+                if (keep_pair(i, j, nA, nT)) {
+                    g.a_map[g.n_a] = 3 + j;
+                    add_pair(g, 0, g.n_a++, 0);
+                }
+            if (kind == 1 && with_dT) {
+                g.a_map[g.n_a] = 6;
+                add_pair(g, 0, g.n_a++, 1);
+            }
+            max_a = std::max(max_a, g.n_a);
+        }
+    }
+    k.a_off = max_b * k.b_bytes;
+    k.stage_bytes = k.a_off + max_a * A_TILE;
     k.n_stages = std::max(1, std::min(MAX_STAGES, SMEM_BUDGET / k.stage_bytes));
     k.err = set.err;
     return k;
@@ -885,11 +949,11 @@ SplitPlan tc_split_plan(const DevProblem &pb, int32_t kb_per_split)
         p.max_split = (int32_t)ceil_div(p.kb_total, kb_per_split);
         p.min_kb = 1;
     } else {
-        // about one wave of CTAs, but splits of at least 512 points: a few plan rows would
-        // otherwise get ~150 splits whose partial sums the step kernel adds one by one
+        // about one wave of CTAs, but splits of at least 128 points: a few plan rows would
+        // otherwise get up to 148 splits whose partial sums the step kernel adds
         p.target_ctas = 148;
         p.max_split = tc_max_split(pb);
-        p.min_kb = 8;
+        p.min_kb = 2;
     }
     return p;
 }
