@@ -266,6 +266,16 @@ __device__ __forceinline__ void step_plan(const SolverState &s, const UpdatePara
     const size_t vb = (size_t)j * nd;
     float *x = s.x + vb, *g = s.g + vb, *p = s.p + vb;
     const float *xt = s.xt + vb;
+    // the plan's scalars, read by every lane before lane 0 writes any of them
+    int it = s.iters[j];
+    int cnt = s.hcount[j];
+    int nw = s.hnewest[j];
+    const double F_old = s.F[j];
+    const int nsmall_old = s.nsmall[j];
+    const double alpha_old = s.alpha[j], gtp_old = s.gtp[j];
+    const int ls_old = s.ls[j];
+    const int maxit = s.maxit[j];
+    __syncwarp();
 
     // ---- results of this step's evaluation (fixed summation order)
     const int slot = s.slot_of[j];
@@ -311,9 +321,6 @@ __device__ __forceinline__ void step_plan(const SolverState &s, const UpdatePara
 
     float gv[EPL];
     float gmax = 0.0f;
-    int it = s.iters[j];
-    int cnt = s.hcount[j];
-    int nw = s.hnewest[j];
     bool need_dir = false;
     bool retry = false;          // line search continues with a halved step
     double alpha_next = 0.0;
@@ -340,7 +347,7 @@ __device__ __forceinline__ void step_plan(const SolverState &s, const UpdatePara
         if (Ft == 0.0 || gmax == 0.0f) { plan_done(s, j, GMCO_PLAN_CONVERGED, lane); return; }
         need_dir = true;
     } else {
-        const double alpha = s.alpha[j], gtp = s.gtp[j];
+        const double alpha = alpha_old, gtp = gtp_old;
         const bool ok = isfinite(dF) && isfinite(Ft) && dF <= u.c1 * alpha * gtp;
         if (ok) {
             float sv[EPL], yv[EPL];
@@ -384,8 +391,9 @@ __device__ __forceinline__ void step_plan(const SolverState &s, const UpdatePara
                     s.rho[(size_t)j * m + nw] = 1.0 / sy;
                     s.gamma[j] = sy / yy;
                 }
+                __syncwarp();   // read back by every lane in the two-loop below
             }
-            const double Fprev = s.F[j];
+            const double Fprev = F_old;
             ++it;
             if (lane == 0) {
                 s.F[j] = Fprev + dF;
@@ -395,7 +403,7 @@ __device__ __forceinline__ void step_plan(const SolverState &s, const UpdatePara
                 s.hnewest[j] = nw;
             }
             if (!fin) { plan_done(s, j, GMCO_PLAN_NONFINITE, lane); return; }
-            const int nsm = fabs(dF) <= u.tol * fmax(fabs(Fprev), 1e-300) ? s.nsmall[j] + 1 : 0;
+            const int nsm = fabs(dF) <= u.tol * fmax(fabs(Fprev), 1e-300) ? nsmall_old + 1 : 0;
             if (lane == 0) s.nsmall[j] = nsm;
             if (Ft == 0.0 || gmax == 0.0f || nsm >= u.stop_window) {
                 plan_done(s, j, GMCO_PLAN_CONVERGED, lane);
@@ -403,7 +411,7 @@ __device__ __forceinline__ void step_plan(const SolverState &s, const UpdatePara
             }
             need_dir = true;
         } else {
-            const int lsn = s.ls[j] + 1;
+            const int lsn = ls_old + 1;
             if (lsn >= u.max_ls) {
                 if (cnt > 0) {   // retry once along steepest descent with a fresh history
                     cnt = 0;
@@ -434,7 +442,7 @@ __device__ __forceinline__ void step_plan(const SolverState &s, const UpdatePara
     }
 
     if (need_dir) {
-        if (it >= s.maxit[j]) { plan_done(s, j, GMCO_PLAN_MAXITER, lane); return; }
+        if (it >= maxit) { plan_done(s, j, GMCO_PLAN_MAXITER, lane); return; }
 
         // two-loop recursion, q in registers (FP32 vectors and dot products); the next
         // history pair is loaded while the current dot product is reduced

@@ -120,7 +120,6 @@ __device__ __forceinline__ void fence_after() { asm volatile("tcgen05.fence::aft
 constexpr uint64_t DESC_FIXED = ((uint64_t)1 << 16) | ((uint64_t)(1024 >> 4) << 32) |
                                 ((uint64_t)1 << 46) | ((uint64_t)2 << 61);
 __device__ __forceinline__ uint32_t desc_lo(uint32_t saddr) { return (saddr & 0x3FFFFu) >> 4; }
-__device__ __forceinline__ uint64_t sw128_desc(uint32_t saddr) { return DESC_FIXED | desc_lo(saddr); }
 
 // Instruction descriptor, kind::f16: FP32 accumulator, BF16 A and B, both K-major, M = 128.
 __device__ __forceinline__ uint32_t idesc_bf16(int n)
@@ -184,10 +183,10 @@ __device__ __forceinline__ void tmem_ld_wait_regs8(uint32_t (&a)[8], uint32_t (&
 // One kind of ring stage: the B tiles (b_map) and A tiles (a_map) loaded for one K block, and
 // the products issued on them: pair q multiplies A tile pair_a[q] by B tile pair_b[q] into
 // accumulator pair_acc[q].
-constexpr int MAX_B = 3, MAX_A = 4, MAX_PAIRS = 8;
+constexpr int MAX_A = 4, MAX_PAIRS = 8;
 struct Group {
     int32_t n_b, n_a, n_pair;
-    int32_t b_map[MAX_B], a_map[MAX_A];
+    int32_t b_map[MAX_A], a_map[MAX_A];
     int32_t pair_b[MAX_PAIRS], pair_a[MAX_PAIRS], pair_acc[MAX_PAIRS];
 };
 
