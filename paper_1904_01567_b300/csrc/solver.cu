@@ -256,9 +256,20 @@ __device__ __forceinline__ void write_trial_row(const SolverState &s, const Step
 //   INIT: take F, g; TRIAL: Armijo test on dF (FP64), curvature pair (FP64 s'y, y'y), stop test;
 //   new direction by the two-loop recursion; then, if the plan still runs, claim a slot of the
 //   next step's compact rows and write its next trial point there.
+__device__ __forceinline__ void cp_async16(void *smem, const void *gmem)
+{
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 16;" ::"r"((uint32_t)__cvta_generic_to_shared(smem)),
+                 "l"(gmem)
+                 : "memory");
+}
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;" ::: "memory"); }
+
+// hS / hY: this plan's history rows in shared memory (m x nd each, the same slots as s.S / s.Y),
+// or null to read them from global memory
 template <int EPL>
 __device__ __forceinline__ void step_plan(const SolverState &s, const UpdateParams &u,
-                                          const StepArgs &a, const int j, const int lane)
+                                          const StepArgs &a, const int j, const int lane,
+                                          float *hS = nullptr, float *hY = nullptr)
 {
     const int st = s.state[j];
     if (st != ST_INIT && st != ST_TRIAL) return;
@@ -276,6 +287,21 @@ __device__ __forceinline__ void step_plan(const SolverState &s, const UpdatePara
     const int ls_old = s.ls[j];
     const int maxit = s.maxit[j];
     __syncwarp();
+    // the history rows the two-loop will read, copied asynchronously while the partial sums
+    // below are added (16-byte copies; rows are nd_pad floats, a multiple of 32)
+    const float *HS = s.S + (size_t)j * m * nd, *HY = s.Y + (size_t)j * m * nd;
+    if (hS) {
+        const int q4 = nd >> 2;   // 16-byte chunks per row
+        for (int k = 0; k < cnt; ++k) {
+            const int i = (nw - k + m) % m;
+            for (int c = lane; c < q4; c += 32) {
+                cp_async16(hS + (size_t)i * nd + 4 * c, HS + (size_t)i * nd + 4 * c);
+                cp_async16(hY + (size_t)i * nd + 4 * c, HY + (size_t)i * nd + 4 * c);
+            }
+        }
+        HS = hS;
+        HY = hY;
+    }
 
     // ---- results of this step's evaluation (fixed summation order)
     const int slot = s.slot_of[j];
@@ -380,11 +406,19 @@ __device__ __forceinline__ void step_plan(const SolverState &s, const UpdatePara
                 nw = (nw + 1) % m;
                 float *Sd = s.S + ((size_t)j * m + nw) * nd;
                 float *Yd = s.Y + ((size_t)j * m + nw) * nd;
+                if (hS) {   // every lane's copy of the slot being replaced has landed
+                    cp_async_wait_all();
+                    __syncwarp();
+                }
 #pragma unroll
                 for (int e = 0; e < EPL; ++e)
                     if (e < epl) {
                         Sd[lane + 32 * e] = sv[e];
                         Yd[lane + 32 * e] = yv[e];
+                        if (hS) {
+                            hS[(size_t)nw * nd + lane + 32 * e] = sv[e];
+                            hY[(size_t)nw * nd + lane + 32 * e] = yv[e];
+                        }
                     }
                 cnt = min(cnt + 1, m);
                 if (lane == 0) {
@@ -449,13 +483,17 @@ __device__ __forceinline__ void step_plan(const SolverState &s, const UpdatePara
         float q[EPL];
 #pragma unroll
         for (int e = 0; e < EPL; ++e) q[e] = gv[e];
+        if (hS) {
+            cp_async_wait_all();
+            __syncwarp();
+        }
         if (cnt > 0) {
             float al[kMaxHist];
             float sc[EPL], yc[EPL];
             {
                 const int i0 = nw;
-                const float *Si = s.S + ((size_t)j * m + i0) * nd;
-                const float *Yi = s.Y + ((size_t)j * m + i0) * nd;
+                const float *Si = HS + (size_t)i0 * nd;
+                const float *Yi = HY + (size_t)i0 * nd;
 #pragma unroll
                 for (int e = 0; e < EPL; ++e) {
                     sc[e] = e < epl ? Si[lane + 32 * e] : 0.0f;
@@ -470,8 +508,8 @@ __device__ __forceinline__ void step_plan(const SolverState &s, const UpdatePara
                     float sn[EPL], yn[EPL];
                     const bool more = k + 1 < cnt;
                     const int i1 = (nw - k - 1 + m) % m;
-                    const float *Sn = s.S + ((size_t)j * m + i1) * nd;
-                    const float *Yn = s.Y + ((size_t)j * m + i1) * nd;
+                    const float *Sn = HS + (size_t)i1 * nd;
+                    const float *Yn = HY + (size_t)i1 * nd;
 #pragma unroll
                     for (int e = 0; e < EPL; ++e) {
                         sn[e] = (more && e < epl) ? Sn[lane + 32 * e] : 0.0f;
@@ -495,8 +533,8 @@ __device__ __forceinline__ void step_plan(const SolverState &s, const UpdatePara
             for (int e = 0; e < EPL; ++e) q[e] *= gam;
             {
                 const int io = (nw - (cnt - 1) + m) % m;   // oldest pair first
-                const float *Si = s.S + ((size_t)j * m + io) * nd;
-                const float *Yi = s.Y + ((size_t)j * m + io) * nd;
+                const float *Si = HS + (size_t)io * nd;
+                const float *Yi = HY + (size_t)io * nd;
 #pragma unroll
                 for (int e = 0; e < EPL; ++e) {
                     sc[e] = e < epl ? Si[lane + 32 * e] : 0.0f;
@@ -510,8 +548,8 @@ __device__ __forceinline__ void step_plan(const SolverState &s, const UpdatePara
                     float sn[EPL], yn[EPL];
                     const bool more = k > 0;
                     const int i1 = (nw - k + 1 + m) % m;
-                    const float *Sn = s.S + ((size_t)j * m + i1) * nd;
-                    const float *Yn = s.Y + ((size_t)j * m + i1) * nd;
+                    const float *Sn = HS + (size_t)i1 * nd;
+                    const float *Yn = HY + (size_t)i1 * nd;
 #pragma unroll
                     for (int e = 0; e < EPL; ++e) {
                         sn[e] = (more && e < epl) ? Sn[lane + 32 * e] : 0.0f;
@@ -571,12 +609,22 @@ __device__ __forceinline__ void step_plan(const SolverState &s, const UpdatePara
     }
 }
 
+// use_smem: each warp's plan keeps its history rows in dynamic shared memory (2 m nd_pad
+// floats per warp)
 template <int EPL>
-__global__ void __launch_bounds__(256) k_step(SolverState s, UpdateParams u, StepArgs a)
+__global__ void __launch_bounds__(256) k_step(SolverState s, UpdateParams u, StepArgs a,
+                                              int32_t use_smem)
 {
+    extern __shared__ __align__(16) float hist[];
     const int j = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     if (j >= s.P) return;
-    step_plan<EPL>(s, u, a, j, threadIdx.x & 31);
+    float *hS = nullptr, *hY = nullptr;
+    if (use_smem) {
+        hS = hist + (size_t)(threadIdx.x >> 5) * 2 * s.m * s.nd_pad;
+        hY = hS + (size_t)s.m * s.nd_pad;
+    }
+    step_plan<EPL>(s, u, a, j, threadIdx.x & 31, hS, hY);
+    if (use_smem) cp_async_wait_all();   // nothing in flight into shared memory at exit
 }
 
 // The same step for the plans of several problems; each block's problem descriptor is
@@ -687,16 +735,41 @@ cudaError_t launch_finish(const SolverState &s, const EvalArgs &e, int32_t n_pti
     return cudaGetLastError();
 }
 
+constexpr int kStepSmem = 96 * 1024;
+
+cudaError_t step_attrs()
+{
+    static bool done = false;
+    if (done) return cudaSuccess;
+    cudaError_t e;
+    if ((e = cudaFuncSetAttribute(k_step<4>, cudaFuncAttributeMaxDynamicSharedMemorySize, kStepSmem)) != cudaSuccess) return e;
+    if ((e = cudaFuncSetAttribute(k_step<8>, cudaFuncAttributeMaxDynamicSharedMemorySize, kStepSmem)) != cudaSuccess) return e;
+    if ((e = cudaFuncSetAttribute(k_step<12>, cudaFuncAttributeMaxDynamicSharedMemorySize, kStepSmem)) != cudaSuccess) return e;
+    if ((e = cudaFuncSetAttribute(k_step<16>, cudaFuncAttributeMaxDynamicSharedMemorySize, kStepSmem)) != cudaSuccess) return e;
+    if ((e = cudaFuncSetAttribute(k_step<32>, cudaFuncAttributeMaxDynamicSharedMemorySize, kStepSmem)) != cudaSuccess) return e;
+    done = true;
+    return cudaSuccess;
+}
+
 cudaError_t launch_step(const SolverState &s, const UpdateParams &u, const StepArgs &a,
                         cudaStream_t st)
 {
+    // One plan per block with its history rows staged in shared memory when they fit (up to
+    // kStepSmem bytes; several blocks share an SM), else two plans per block reading the
+    // history from global memory.
     const int epl = s.nd_pad / 32;
-    const int blocks = (int)ceil_div((int64_t)s.P * 32, 256);
-    if (epl <= 4) k_step<4><<<blocks, 256, 0, st>>>(s, u, a);
-    else if (epl <= 8) k_step<8><<<blocks, 256, 0, st>>>(s, u, a);
-    else if (epl <= 12) k_step<12><<<blocks, 256, 0, st>>>(s, u, a);
-    else if (epl <= 16) k_step<16><<<blocks, 256, 0, st>>>(s, u, a);
-    else k_step<32><<<blocks, 256, 0, st>>>(s, u, a);
+    const size_t hist = (size_t)2 * s.m * s.nd_pad * sizeof(float);
+    const int use = hist <= (size_t)kStepSmem ? 1 : 0;
+    const int tpb = use ? 32 : 64;
+    const size_t smem = use ? hist : 0;
+    const int blocks = (int)ceil_div((int64_t)s.P * 32, tpb);
+    cudaError_t e = step_attrs();
+    if (e != cudaSuccess) return e;
+    if (epl <= 4) k_step<4><<<blocks, tpb, smem, st>>>(s, u, a, use);
+    else if (epl <= 8) k_step<8><<<blocks, tpb, smem, st>>>(s, u, a, use);
+    else if (epl <= 12) k_step<12><<<blocks, tpb, smem, st>>>(s, u, a, use);
+    else if (epl <= 16) k_step<16><<<blocks, tpb, smem, st>>>(s, u, a, use);
+    else k_step<32><<<blocks, tpb, smem, st>>>(s, u, a, use);
     return cudaGetLastError();
 }
 
