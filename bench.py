@@ -221,9 +221,7 @@ def run_reference(args):
     cores, model = cpu_info()
     n = args.cpu_sample or max(8, min(2 * cores, 64))
     n = min(n, W.shape[0])
-    for _ in range(max(args.warmup, 0) and 1):
-        pass   # the oracle has no warm-up state; one untimed tiny call loads its library
-    import oracle
+    import oracle   # the oracle keeps no state between calls: nothing to warm up
     oracle.build()
     times, oks = [], []
     for _ in range(args.steps):
