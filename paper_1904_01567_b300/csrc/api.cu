@@ -338,7 +338,8 @@ gmco_status record_steps(gmco_problem *pr, int form, int steps, const UpdatePara
             a.sp = pr->tcb.sp;
             a.fmt = 1;
             for (int j = 0; j < 3; ++j) a.Tb[j] = pr->tcb.T[j];
-            a.dTb = pr->tcb.dT;
+            a.dTb[0] = pr->tcb.dT[0];
+            a.dTb[1] = pr->tcb.dT[1];
             a.nT = std::max(pb.tc_terms, 2);
             a.kpad = (int32_t)pb.kpad;
             a.ldT = (int32_t)pb.kpad;
@@ -491,7 +492,7 @@ struct gmco_multi {
     int32_t ws_split = -1;
     std::vector<int64_t> t_row;
     std::vector<SolverState> st;   // each patient's state, P = its plans
-    __nv_bfloat16 *T[3] = {nullptr, nullptr, nullptr}, *dT = nullptr;
+    __nv_bfloat16 *T[3] = {nullptr, nullptr, nullptr}, *dT[2] = {nullptr, nullptr};
     __nv_bfloat16 *G[3] = {nullptr, nullptr, nullptr};
     float *Wc = nullptr;
     std::vector<float *> Wc_p;
@@ -547,8 +548,10 @@ gmco_status multi_workspace(gmco_multi *m, const std::vector<int64_t> &P)
         CK(cudaMemset(m->T[j], 0, (size_t)R * m->kpad_max * 2));
         CK(cudaMemset(m->G[j], 0, (size_t)R * m->np_max * 2));
     }
-    CK(a.alloc(&m->dT, (size_t)R * m->kpad_max));
-    CK(cudaMemset(m->dT, 0, (size_t)R * m->kpad_max * 2));
+    for (int j = 0; j < 2; ++j) {
+        CK(a.alloc(&m->dT[j], (size_t)R * m->kpad_max));
+        CK(cudaMemset(m->dT[j], 0, (size_t)R * m->kpad_max * 2));
+    }
     CK(a.alloc(&m->Wc, (size_t)wsum));
     bool ok = true;
     TcLaunchSet &set = m->set;
@@ -561,7 +564,8 @@ gmco_status multi_workspace(gmco_multi *m, const std::vector<int64_t> &P)
         ok = ok && tc_encode_map(&set.maps1.m[3 + j], m->T[j], m->kpad_max, R, kTcBoxCols, kTcBoxRowsT);
         ok = ok && tc_encode_map(&set.maps2.m[3 + j], m->G[j], m->np_max, R, kTcBoxCols, kTcBoxRowsG);
     }
-    ok = ok && tc_encode_map(&set.maps1.m[6], m->dT, m->kpad_max, R, kTcBoxCols, kTcBoxRowsT);
+    for (int j = 0; j < 2; ++j)
+        ok = ok && tc_encode_map(&set.maps1.m[6 + j], m->dT[j], m->kpad_max, R, kTcBoxCols, kTcBoxRowsT);
     if (!ok) {
         set_error_msg("gmco_solve_multi: cannot encode operand maps");
         return GMCO_ECUDA;
@@ -618,7 +622,7 @@ gmco_status multi_workspace(gmco_multi *m, const std::vector<int64_t> &P)
             ar.rows_next = s.cnt + (par ^ 1);
             ar.fmt = 1;
             for (int j = 0; j < nT; ++j) ar.Tb[j] = m->T[j] + m->t_row[p] * m->kpad_max;
-            ar.dTb = m->dT + m->t_row[p] * m->kpad_max;
+            for (int j = 0; j < 2; ++j) ar.dTb[j] = m->dT[j] + m->t_row[p] * m->kpad_max;
             ar.nT = nT;
             ar.kpad = (int32_t)pb.kpad;
             ar.ldT = (int32_t)m->kpad_max;
@@ -660,7 +664,7 @@ TcRows multi_rows(const gmco_multi *m, int p)
     TcRows r{};
     const int nT = std::max(m->tc_terms, 2);
     for (int j = 0; j < nT; ++j) r.T[j] = m->T[j] + m->t_row[p] * m->kpad_max;
-    r.dT = m->dT + m->t_row[p] * m->kpad_max;
+    for (int j = 0; j < 2; ++j) r.dT[j] = m->dT[j] + m->t_row[p] * m->kpad_max;
     r.Wc = m->Wc_p[p];
     r.ld = (int32_t)m->kpad_max;
     r.kpad = (int32_t)m->probs[p]->pb.kpad;

@@ -110,7 +110,7 @@ struct StepArgs {
     int32_t fmt;                     // 0: FP32 rows (Tc, dTc), 1: BF16 split rows (Tb, dTb)
     float *Tc, *dTc;
     __nv_bfloat16 *Tb[3];
-    __nv_bfloat16 *dTb;
+    __nv_bfloat16 *dTb[2];
     int32_t nT, kpad;                // BF16 terms of t; row length written (columns >= nd_pad zero)
     int32_t ldT;                     // row stride of Tb / dTb (elements)
     float *Wc;

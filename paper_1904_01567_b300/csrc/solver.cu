@@ -237,14 +237,17 @@ __device__ __forceinline__ void write_trial_row(const SolverState &s, const Step
                 a.Tb[1][o] = t2;
                 if (a.nT > 2) a.Tb[2][o] = __float2bfloat16_rn(r1 - __bfloat162float(t2));
             }
-            a.dTb[o] = __float2bfloat16_rn(dt);
+            const __nv_bfloat16 d1 = __float2bfloat16_rn(dt);
+            a.dTb[0][o] = d1;
+            a.dTb[1][o] = __float2bfloat16_rn(dt - __bfloat162float(d1));
         }
     }
     if (a.fmt != 0) {   // BF16 rows are kpad long: keep the columns past nd_pad at zero
         for (int l = nd + lane; l < a.kpad; l += 32) {
             const size_t o = (size_t)slot * a.ldT + l;
             for (int k = 0; k < a.nT; ++k) a.Tb[k][o] = __float2bfloat16_rn(0.0f);
-            a.dTb[o] = __float2bfloat16_rn(0.0f);
+            a.dTb[0][o] = __float2bfloat16_rn(0.0f);
+            a.dTb[1][o] = __float2bfloat16_rn(0.0f);
         }
     }
     if (lane < s.n_struct)

@@ -10,7 +10,10 @@
 //
 // Dose GEMM (rows = plans, columns = points, K = dwells):
 //   acc0 = sum_{i,j} T_j A_i^T            -> d = s * acc0
-//   acc1 = sum_i dT A_i^T                 -> dd = s * acc1, the dose change of the step
+//   acc1 = sum_i dT1 A_i^T + dT2 A_1^T    -> dd = s * acc1, the dose change of the step
+//   (dT = dT1 + dT2 in two BF16 terms: the objective change sums f(d) - f(d - dd) over points
+//   whose first-order parts nearly cancel near the optimum, so a 2^-9 relative error in dd
+//   would swamp the Armijo and stop tests there)
 //   epilogue: Eq. (1) penalty, per-plan partial of F and of F(t) - F(t - dT) (factored, see
 //   eval_simt.cu), and G = s * dF/dd split into BF16 terms for the gradient GEMM.
 // Gradient GEMM (rows = plans, columns = dwells, K = points, split over point ranges):
@@ -183,7 +186,7 @@ __device__ __forceinline__ void tmem_ld_wait_regs8(uint32_t (&a)[8], uint32_t (&
 // One kind of ring stage: the B tiles (b_map) and A tiles (a_map) loaded for one K block, and
 // the products issued on them: pair q multiplies A tile pair_a[q] by B tile pair_b[q] into
 // accumulator pair_acc[q].
-constexpr int MAX_A = 4, MAX_PAIRS = 8;
+constexpr int MAX_A = 5, MAX_PAIRS = 8;
 struct Group {
     int32_t n_b, n_a, n_pair;
     int32_t b_map[MAX_A], a_map[MAX_A];
@@ -754,7 +757,7 @@ __global__ void k_transpose_bf16(const __nv_bfloat16 *__restrict__ in, int64_t r
 }
 
 // Trial point of each compact row, as in k_prep_fp32, written as BF16 split terms of t and
-// one BF16 term of dT.
+// two BF16 terms of dT.
 __global__ void k_prep_tc(SolverState s, TcRows r, int32_t force_base)
 {
     const int i = blockIdx.x;
@@ -784,7 +787,9 @@ __global__ void k_prep_tc(SolverState s, TcRows r, int32_t force_base)
             r.T[1][cb + l] = t2;
             if (r.nT > 2) r.T[2][cb + l] = __float2bfloat16_rn(r1 - __bfloat162float(t2));
         }
-        r.dT[cb + l] = __float2bfloat16_rn(dt);
+        const __nv_bfloat16 d1 = __float2bfloat16_rn(dt);
+        r.dT[0][cb + l] = d1;
+        r.dT[1][cb + l] = __float2bfloat16_rn(dt - __bfloat162float(d1));
     }
     if (threadIdx.x < s.n_struct)
         r.Wc[(size_t)i * s.n_struct + threadIdx.x] = s.Wn[(size_t)j * s.n_struct + threadIdx.x];
@@ -839,9 +844,9 @@ KParams make_params(const TcLaunchSet &set, int kind, int parity, bool with_dT, 
     };
     // dose GEMM: every B term and every A operand of a K block in one stage (each tile loaded
     // once per K block) when two such stages fit; otherwise one stage kind per B term
-    const int na_all = nT + ((kind == 1 && with_dT) ? 1 : 0);
+    const int na_all = nT + ((kind == 1 && with_dT) ? 2 : 0);
     const bool merged = kind == 1 && nA * k.b_bytes + na_all * A_TILE <= SMEM_BUDGET / 2 &&
-                        nA * nT + nA <= MAX_PAIRS;
+                        nA * nT + nA + 1 <= MAX_PAIRS;
     int max_b = 1, max_a = 0;
     if (merged) {
         k.n_groups = 1;
@@ -851,7 +856,10 @@ KParams make_params(const TcLaunchSet &set, int kind, int parity, bool with_dT, 
         for (int i = 0; i < nA; ++i) g.b_map[i] = i;
         g.n_a = na_all;
         for (int j = 0; j < nT; ++j) g.a_map[j] = 3 + j;
-        if (with_dT) g.a_map[nT] = 6;
+        if (with_dT) {
+            g.a_map[nT] = 6;
+            g.a_map[nT + 1] = 7;
+        }
         // products into the dose (0) and dose-change (1) accumulators alternate where they
         // can, so consecutive MMAs do not wait on the same accumulator
         int d_i[MAX_PAIRS], d_j[MAX_PAIRS], nd = 0, c_i[MAX_PAIRS], nc = 0;
@@ -864,6 +872,7 @@ KParams make_params(const TcLaunchSet &set, int kind, int parity, bool with_dT, 
             if (q < nd) add_pair(g, d_i[q], d_j[q], 0);
             if (q < nc) add_pair(g, c_i[q], nT, 1);
         }
+        if (with_dT) add_pair(g, 0, nT + 1, 1);   // dT2 A_1
         max_b = nA;
         max_a = na_all;
     } else {
@@ -881,6 +890,10 @@ KParams make_params(const TcLaunchSet &set, int kind, int parity, bool with_dT, 
             if (kind == 1 && with_dT) {
                 g.a_map[g.n_a] = 6;
                 add_pair(g, 0, g.n_a++, 1);
+                if (i == 0) {   // dT2 A_1
+                    g.a_map[g.n_a] = 7;
+                    add_pair(g, 0, g.n_a++, 1);
+                }
             }
             max_a = std::max(max_a, g.n_a);
         }
@@ -933,7 +946,7 @@ double tc_mma_units(const DevProblem &pb, bool with_dT, int which)
     int pairs = 0;
     for (int i = 0; i < nA; ++i)
         for (int j = 0; j < nT; ++j) pairs += keep_pair(i, j, nA, nT);
-    return which == 1 ? pairs + (with_dT ? nA : 0) : pairs;
+    return which == 1 ? pairs + (with_dT ? nA + 1 : 0) : pairs;
 }
 int32_t tc_max_split(const DevProblem &pb) { return (int32_t)std::min<int64_t>(148, pb.np_pad / BK); }
 
@@ -1057,7 +1070,10 @@ cudaError_t tc_alloc(const DevProblem &pb, int32_t cap, float *Fpart, float *dFp
         if ((e = alloc(reinterpret_cast<void **>(&b->T[j]), tn * 2)) != cudaSuccess) return e;
         if ((e = alloc(reinterpret_cast<void **>(&b->G[j]), gn * 2)) != cudaSuccess) return e;
     }
-    if ((e = alloc(reinterpret_cast<void **>(&b->dT), tn * 2)) != cudaSuccess) return e;
+    for (int j = 0; j < 2; ++j) {
+        if ((e = alloc(reinterpret_cast<void **>(&b->dT[j]), tn * 2)) != cudaSuccess) return e;
+        if ((e = cudaMemset(b->dT[j], 0, tn * 2)) != cudaSuccess) return e;
+    }
     if ((e = alloc(reinterpret_cast<void **>(&b->Wc), (size_t)cap * pb.n_struct * 4)) != cudaSuccess)
         return e;
     if ((e = alloc(reinterpret_cast<void **>(&b->err), 4)) != cudaSuccess) return e;
@@ -1072,7 +1088,8 @@ cudaError_t tc_alloc(const DevProblem &pb, int32_t cap, float *Fpart, float *dFp
         ok = ok && tc_encode_map(&b->maps1.m[3 + j], b->T[j], pb.kpad, cap, kTcBoxCols, kTcBoxRowsT);
         ok = ok && tc_encode_map(&b->maps2.m[3 + j], b->G[j], pb.np_pad, cap, kTcBoxCols, kTcBoxRowsG);
     }
-    ok = ok && tc_encode_map(&b->maps1.m[6], b->dT, pb.kpad, cap, kTcBoxCols, kTcBoxRowsT);
+    for (int j = 0; j < 2; ++j)
+        ok = ok && tc_encode_map(&b->maps1.m[6 + j], b->dT[j], pb.kpad, cap, kTcBoxCols, kTcBoxRowsT);
     if (!ok) return cudaErrorInvalidValue;
     // descriptors of this problem alone
     b->Fpart = Fpart;
@@ -1111,7 +1128,8 @@ TcRows tc_rows(const DevProblem &pb, const TcBuffers &b)
 {
     TcRows r{};
     for (int j = 0; j < 3; ++j) r.T[j] = b.T[j];
-    r.dT = b.dT;
+    r.dT[0] = b.dT[0];
+    r.dT[1] = b.dT[1];
     r.Wc = b.Wc;
     r.ld = (int32_t)pb.kpad;
     r.kpad = (int32_t)pb.kpad;

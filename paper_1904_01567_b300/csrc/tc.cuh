@@ -18,7 +18,7 @@ using AllocFn = std::function<cudaError_t(void **, size_t)>;
 constexpr int kMaxMulti = 64;    // problems in one GEMM launch (descriptors in shared memory)
 
 // Operand maps.  Dose GEMM: m[0..2] A terms (rows = points, columns = dwells), m[3..5] T terms
-// (rows = plans, columns = dwells), m[6] dT.  Gradient GEMM: m[0..2] A^T terms (rows = dwells,
+// (rows = plans, columns = dwells), m[6], m[7] the two terms of dT.  Gradient GEMM: m[0..2] A^T terms (rows = dwells,
 // columns = points), m[3..5] G terms (rows = plans, columns = points).  Problems are stacked
 // along the rows of each map.
 constexpr int kTcMaps = 8;
@@ -63,7 +63,7 @@ struct TcGradProb {
 // Compact per-evaluation operands of one problem (cap plan rows) and its operand maps.
 struct TcBuffers {
     __nv_bfloat16 *T[3] = {nullptr, nullptr, nullptr};   // cap x kpad, split terms of t
-    __nv_bfloat16 *dT = nullptr;                         // cap x kpad, t_trial - t (BF16)
+    __nv_bfloat16 *dT[2] = {nullptr, nullptr};           // cap x kpad, t_trial - t (two terms)
     __nv_bfloat16 *G[3] = {nullptr, nullptr, nullptr};   // cap x np_pad, split terms of dF/dd
     float *Wc = nullptr;                                 // cap x n_struct
     int32_t *err = nullptr;  // device flag: nonzero after a pipeline wait gave up
@@ -78,7 +78,7 @@ struct TcBuffers {
 // Where the trial rows of a problem's compact plans go (tensor-core operand layout).
 struct TcRows {
     __nv_bfloat16 *T[3];
-    __nv_bfloat16 *dT;
+    __nv_bfloat16 *dT[2];
     float *Wc;
     int32_t ld;      // row stride of T and dT (elements)
     int32_t kpad;    // row length written (columns past nd_pad are zero)
