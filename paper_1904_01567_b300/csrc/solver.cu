@@ -207,10 +207,12 @@ __device__ __forceinline__ void plan_done(const SolverState &s, int j, int statu
 }
 
 // Next trial row of plan j in compact slot `slot`: x_t = x + alpha p, t = x_t^2 and
-// dT = alpha p (2 x + alpha p), written in the evaluation form's operand layout.
+// dT = alpha p (2 x + alpha p), written in the evaluation form's operand layout.  x and p are
+// this lane's elements (lane + 32 e), already in registers.
 template <int EPL>
 __device__ __forceinline__ void write_trial_row(const SolverState &s, const StepArgs &a, int j,
-                                                int slot, float alpha, int lane)
+                                                int slot, float alpha, int lane,
+                                                const float (&xv)[EPL], const float (&pv)[EPL])
 {
     const int nd = s.nd_pad, epl = nd >> 5;
     const size_t vb = (size_t)j * nd;
@@ -218,10 +220,9 @@ __device__ __forceinline__ void write_trial_row(const SolverState &s, const Step
     for (int e = 0; e < EPL; ++e) {
         if (e >= epl) continue;
         const int l = lane + 32 * e;
-        const float xv = s.x[vb + l];
-        const float ap = alpha * s.p[vb + l];
-        const float xn = xv + ap;
-        const float dt = ap * (2.0f * xv + ap);
+        const float ap = alpha * pv[e];
+        const float xn = xv[e] + ap;
+        const float dt = ap * (2.0f * xv[e] + ap);
         s.xt[vb + l] = xn;
         const float t = xn * xn;
         if (a.fmt == 0) {
@@ -259,6 +260,9 @@ __device__ __forceinline__ void write_trial_row(const SolverState &s, const Step
 //   INIT: take F, g; TRIAL: Armijo test on dF (FP64), curvature pair (FP64 s'y, y'y), stop test;
 //   new direction by the two-loop recursion; then, if the plan still runs, claim a slot of the
 //   next step's compact rows and write its next trial point there.
+// The step is one warp's dependent chain, so its global loads are issued together at the start
+// (the plan's scalars, rho of every history slot on the lanes, x, p, g, x_t) and the vectors
+// stay in registers until the next trial row is written.
 __device__ __forceinline__ void cp_async16(void *smem, const void *gmem)
 {
     asm volatile("cp.async.ca.shared.global [%0], [%1], 16;" ::"r"((uint32_t)__cvta_generic_to_shared(smem)),
@@ -274,13 +278,10 @@ __device__ __forceinline__ void step_plan(const SolverState &s, const UpdatePara
                                           const StepArgs &a, const int j, const int lane,
                                           float *hS = nullptr, float *hY = nullptr)
 {
-    const int st = s.state[j];
-    if (st != ST_INIT && st != ST_TRIAL) return;
     const int nd = s.nd_pad, epl = nd >> 5, m = s.m;
     const size_t vb = (size_t)j * nd;
-    float *x = s.x + vb, *g = s.g + vb, *p = s.p + vb;
-    const float *xt = s.xt + vb;
     // the plan's scalars, read by every lane before lane 0 writes any of them
+    const int st = s.state[j];
     int it = s.iters[j];
     int cnt = s.hcount[j];
     int nw = s.hnewest[j];
@@ -289,7 +290,23 @@ __device__ __forceinline__ void step_plan(const SolverState &s, const UpdatePara
     const double alpha_old = s.alpha[j], gtp_old = s.gtp[j];
     const int ls_old = s.ls[j];
     const int maxit = s.maxit[j];
+    const int slot = s.slot_of[j];
+    const int R = *a.rows_cur;
+    double rho_l = lane < m ? s.rho[(size_t)j * m + lane] : 0.0;   // lane i: rho of slot i
+    double gam = s.gamma[j];
     __syncwarp();
+    if (st != ST_INIT && st != ST_TRIAL) return;
+    float *x = s.x + vb, *g = s.g + vb, *p = s.p + vb;
+    const float *xt = s.xt + vb;
+    float xv[EPL], pv[EPL], gov[EPL], xtv[EPL];
+#pragma unroll
+    for (int e = 0; e < EPL; ++e) {
+        const int l = lane + 32 * e;
+        xv[e] = e < epl ? x[l] : 0.0f;
+        pv[e] = e < epl ? p[l] : 0.0f;
+        gov[e] = e < epl ? g[l] : 0.0f;
+        xtv[e] = e < epl ? xt[l] : 0.0f;
+    }
     // the history rows the two-loop will read, copied asynchronously while the partial sums
     // below are added (16-byte copies; rows are nd_pad floats, a multiple of 32)
     const float *HS = s.S + (size_t)j * m * nd, *HY = s.Y + (size_t)j * m * nd;
@@ -307,9 +324,8 @@ __device__ __forceinline__ void step_plan(const SolverState &s, const UpdatePara
     }
 
     // ---- results of this step's evaluation (fixed summation order)
-    const int slot = s.slot_of[j];
-    const int R = *a.rows_cur;
     double fsum = 0.0, dfsum = 0.0;
+#pragma unroll 4
     for (int t = lane; t < a.n_ptiles; t += 32) {
         fsum += (double)a.Fpart[(size_t)t * a.cap + slot];
         if (st == ST_TRIAL) dfsum += (double)a.dFpart[(size_t)t * a.cap + slot];
@@ -319,21 +335,22 @@ __device__ __forceinline__ void step_plan(const SolverState &s, const UpdatePara
     int kbps, n_split;
     split_plan(a.sp, R, &kbps, &n_split);
     // sum over the splits in split order; each split's EPL loads are independent, so the
-    // latency chain is one load per split rather than one per element and split
+    // latency chain is one load per batch of splits rather than one per element and split
     float gtv[EPL];
 #pragma unroll
     for (int e = 0; e < EPL; ++e) gtv[e] = 0.0f;
+    constexpr int QB = EPL <= 12 ? 8 : 4;   // splits in flight (registers: QB x EPL)
     int q = 0;
-    for (; q + 4 <= n_split; q += 4) {   // four splits' loads in flight, added in split order
-        float v[4][EPL];
+    for (; q + QB <= n_split; q += QB) {
+        float v[QB][EPL];
 #pragma unroll
-        for (int r = 0; r < 4; ++r) {
+        for (int r = 0; r < QB; ++r) {
             const float *gq = a.gpart + ((size_t)(q + r) * R + slot) * nd + lane;
 #pragma unroll
             for (int e = 0; e < EPL; ++e) v[r][e] = e < epl ? gq[32 * e] : 0.0f;
         }
 #pragma unroll
-        for (int r = 0; r < 4; ++r)
+        for (int r = 0; r < QB; ++r)
 #pragma unroll
             for (int e = 0; e < EPL; ++e)
                 if (e < epl) gtv[e] += v[r][e];
@@ -346,12 +363,11 @@ __device__ __forceinline__ void step_plan(const SolverState &s, const UpdatePara
     }
 #pragma unroll
     for (int e = 0; e < EPL; ++e)
-        if (e < epl) gtv[e] *= 2.0f * xt[lane + 32 * e];
+        if (e < epl) gtv[e] *= 2.0f * xtv[e];
 
     float gv[EPL];
     float gmax = 0.0f;
     bool need_dir = false;
-    bool retry = false;          // line search continues with a halved step
     double alpha_next = 0.0;
 
     if (st == ST_INIT) {
@@ -389,15 +405,16 @@ __device__ __forceinline__ void step_plan(const SolverState &s, const UpdatePara
                 gv[e] = 0.0f;
                 if (e < epl) {
                     const int l = lane + 32 * e;
-                    const float xo = x[l], xn = xt[l], go = g[l], gn = gtv[e];
-                    sv[e] = xn - xo;
-                    yv[e] = gn - go;
+                    const float xn = xtv[e], gn = gtv[e];
+                    sv[e] = xn - xv[e];
+                    yv[e] = gn - gov[e];
                     sy += (double)sv[e] * (double)yv[e];
                     yy += (double)yv[e] * (double)yv[e];
                     fin = fin && isfinite(gn);
                     gmax = fmaxf(gmax, fabsf(gn));
                     x[l] = xn;
                     g[l] = gn;
+                    xv[e] = xn;
                     gv[e] = gn;
                 }
             }
@@ -424,11 +441,14 @@ __device__ __forceinline__ void step_plan(const SolverState &s, const UpdatePara
                         }
                     }
                 cnt = min(cnt + 1, m);
+                const double rho_new = 1.0 / sy;
+                gam = sy / yy;
+                if (lane == nw) rho_l = rho_new;
                 if (lane == 0) {
-                    s.rho[(size_t)j * m + nw] = 1.0 / sy;
-                    s.gamma[j] = sy / yy;
+                    s.rho[(size_t)j * m + nw] = rho_new;
+                    s.gamma[j] = gam;
                 }
-                __syncwarp();   // read back by every lane in the two-loop below
+                if (hS) __syncwarp();   // the new pair is read back by every lane below
             }
             const double Fprev = F_old;
             ++it;
@@ -457,7 +477,7 @@ __device__ __forceinline__ void step_plan(const SolverState &s, const UpdatePara
                     for (int e = 0; e < EPL; ++e) {
                         gv[e] = 0.0f;
                         if (e < epl) {
-                            gv[e] = g[lane + 32 * e];
+                            gv[e] = gov[e];
                             gmax = fmaxf(gmax, fabsf(gv[e]));
                         }
                     }
@@ -468,7 +488,6 @@ __device__ __forceinline__ void step_plan(const SolverState &s, const UpdatePara
                     return;
                 }
             } else {
-                retry = true;
                 alpha_next = alpha * 0.5;
                 if (lane == 0) {
                     s.alpha[j] = alpha_next;
@@ -477,10 +496,14 @@ __device__ __forceinline__ void step_plan(const SolverState &s, const UpdatePara
             }
         }
     }
+    if (need_dir && it >= maxit) { plan_done(s, j, GMCO_PLAN_MAXITER, lane); return; }
+
+    // the plan runs on: claim its row of the next step now, so that the atomic's round trip
+    // overlaps the two-loop below
+    int ns = 0;
+    if (lane == 0) ns = atomicAdd(a.rows_next, 1);
 
     if (need_dir) {
-        if (it >= maxit) { plan_done(s, j, GMCO_PLAN_MAXITER, lane); return; }
-
         // two-loop recursion, q in registers (FP32 vectors and dot products); the next
         // history pair is loaded while the current dot product is reduced
         float q[EPL];
@@ -491,7 +514,10 @@ __device__ __forceinline__ void step_plan(const SolverState &s, const UpdatePara
             __syncwarp();
         }
         if (cnt > 0) {
-            float al[kMaxHist];
+            // The history loops stay rolled (their bodies are reused from the instruction
+            // cache; fully unrolled, one warp's pass over straight-line code is fetch-bound)
+            // and alpha_k of the first loop is kept on lane k for the second.
+            float al_l = 0.0f;
             float sc[EPL], yc[EPL];
             {
                 const int i0 = nw;
@@ -503,37 +529,35 @@ __device__ __forceinline__ void step_plan(const SolverState &s, const UpdatePara
                     yc[e] = e < epl ? Yi[lane + 32 * e] : 0.0f;
                 }
             }
+#pragma unroll 1
+            for (int k = 0; k < cnt; ++k) {
+                const int i = (nw - k + m) % m;
+                float sn[EPL], yn[EPL];
+                const bool more = k + 1 < cnt;
+                const int i1 = (nw - k - 1 + m) % m;
+                const float *Sn = HS + (size_t)i1 * nd;
+                const float *Yn = HY + (size_t)i1 * nd;
 #pragma unroll
-            for (int k = 0; k < kMaxHist; ++k) {
-                al[k] = 0.0f;
-                if (k < cnt) {
-                    const int i = (nw - k + m) % m;
-                    float sn[EPL], yn[EPL];
-                    const bool more = k + 1 < cnt;
-                    const int i1 = (nw - k - 1 + m) % m;
-                    const float *Sn = HS + (size_t)i1 * nd;
-                    const float *Yn = HY + (size_t)i1 * nd;
+                for (int e = 0; e < EPL; ++e) {
+                    sn[e] = (more && e < epl) ? Sn[lane + 32 * e] : 0.0f;
+                    yn[e] = (more && e < epl) ? Yn[lane + 32 * e] : 0.0f;
+                }
+                const float rho = (float)__shfl_sync(kFull, rho_l, i);
+                float d = 0.0f;
 #pragma unroll
-                    for (int e = 0; e < EPL; ++e) {
-                        sn[e] = (more && e < epl) ? Sn[lane + 32 * e] : 0.0f;
-                        yn[e] = (more && e < epl) ? Yn[lane + 32 * e] : 0.0f;
-                    }
-                    float d = 0.0f;
+                for (int e = 0; e < EPL; ++e) d += sc[e] * q[e];
+                const float av = rho * warp_sum_f(d);
+                if (lane == k) al_l = av;
 #pragma unroll
-                    for (int e = 0; e < EPL; ++e) d += sc[e] * q[e];
-                    const float av = (float)s.rho[(size_t)j * m + i] * warp_sum_f(d);
-                    al[k] = av;
-#pragma unroll
-                    for (int e = 0; e < EPL; ++e) {
-                        q[e] -= av * yc[e];
-                        sc[e] = sn[e];
-                        yc[e] = yn[e];
-                    }
+                for (int e = 0; e < EPL; ++e) {
+                    q[e] -= av * yc[e];
+                    sc[e] = sn[e];
+                    yc[e] = yn[e];
                 }
             }
-            const float gam = (float)s.gamma[j];
+            const float gamf = (float)gam;
 #pragma unroll
-            for (int e = 0; e < EPL; ++e) q[e] *= gam;
+            for (int e = 0; e < EPL; ++e) q[e] *= gamf;
             {
                 const int io = (nw - (cnt - 1) + m) % m;   // oldest pair first
                 const float *Si = HS + (size_t)io * nd;
@@ -544,30 +568,30 @@ __device__ __forceinline__ void step_plan(const SolverState &s, const UpdatePara
                     yc[e] = e < epl ? Yi[lane + 32 * e] : 0.0f;
                 }
             }
+#pragma unroll 1
+            for (int k = cnt - 1; k >= 0; --k) {
+                const int i = (nw - k + m) % m;
+                float sn[EPL], yn[EPL];
+                const bool more = k > 0;
+                const int i1 = (nw - k + 1 + m) % m;
+                const float *Sn = HS + (size_t)i1 * nd;
+                const float *Yn = HY + (size_t)i1 * nd;
 #pragma unroll
-            for (int k = kMaxHist - 1; k >= 0; --k) {
-                if (k < cnt) {
-                    const int i = (nw - k + m) % m;
-                    float sn[EPL], yn[EPL];
-                    const bool more = k > 0;
-                    const int i1 = (nw - k + 1 + m) % m;
-                    const float *Sn = HS + (size_t)i1 * nd;
-                    const float *Yn = HY + (size_t)i1 * nd;
+                for (int e = 0; e < EPL; ++e) {
+                    sn[e] = (more && e < epl) ? Sn[lane + 32 * e] : 0.0f;
+                    yn[e] = (more && e < epl) ? Yn[lane + 32 * e] : 0.0f;
+                }
+                const float rho = (float)__shfl_sync(kFull, rho_l, i);
+                const float alk = __shfl_sync(kFull, al_l, k);
+                float d = 0.0f;
 #pragma unroll
-                    for (int e = 0; e < EPL; ++e) {
-                        sn[e] = (more && e < epl) ? Sn[lane + 32 * e] : 0.0f;
-                        yn[e] = (more && e < epl) ? Yn[lane + 32 * e] : 0.0f;
-                    }
-                    float d = 0.0f;
+                for (int e = 0; e < EPL; ++e) d += yc[e] * q[e];
+                const float b = rho * warp_sum_f(d);
 #pragma unroll
-                    for (int e = 0; e < EPL; ++e) d += yc[e] * q[e];
-                    const float b = (float)s.rho[(size_t)j * m + i] * warp_sum_f(d);
-#pragma unroll
-                    for (int e = 0; e < EPL; ++e) {
-                        q[e] += sc[e] * (al[k] - b);
-                        sc[e] = sn[e];
-                        yc[e] = yn[e];
-                    }
+                for (int e = 0; e < EPL; ++e) {
+                    q[e] += sc[e] * (alk - b);
+                    sc[e] = sn[e];
+                    yc[e] = yn[e];
                 }
             }
         }
@@ -589,8 +613,10 @@ __device__ __forceinline__ void step_plan(const SolverState &s, const UpdatePara
             alpha0 = fmin(1.0, 1.0 / (double)gmax);
         }
 #pragma unroll
-        for (int e = 0; e < EPL; ++e)
-            if (e < epl) p[lane + 32 * e] = -q[e];
+        for (int e = 0; e < EPL; ++e) {
+            pv[e] = -q[e];
+            if (e < epl) p[lane + 32 * e] = pv[e];
+        }
         if (lane == 0) {
             s.gtp[j] = gtp;
             s.alpha[j] = alpha0;
@@ -599,17 +625,12 @@ __device__ __forceinline__ void step_plan(const SolverState &s, const UpdatePara
             s.state[j] = ST_TRIAL;
         }
         alpha_next = alpha0;
-        retry = true;
     }
 
-    if (retry) {   // still running: next trial point into a slot of the next step's rows
-        int ns = 0;
-        if (lane == 0) ns = atomicAdd(a.rows_next, 1);
-        ns = __shfl_sync(kFull, ns, 0);
-        if (lane == 0) s.slot_of[j] = ns;
-        __syncwarp();
-        write_trial_row<EPL>(s, a, j, ns, (float)alpha_next, lane);
-    }
+    // next trial point into the claimed slot of the next step's rows
+    ns = __shfl_sync(kFull, ns, 0);
+    if (lane == 0) s.slot_of[j] = ns;
+    write_trial_row<EPL>(s, a, j, ns, (float)alpha_next, lane, xv, pv);
 }
 
 // use_smem: each warp's plan keeps its history rows in dynamic shared memory (2 m nd_pad
