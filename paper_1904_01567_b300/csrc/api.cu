@@ -579,7 +579,6 @@ gmco_status multi_workspace(gmco_multi *m, const std::vector<int64_t> &P)
     m->Wc_p.assign((size_t)n, nullptr);
     set.max_items1 = 0;
     set.max_items2 = 0;
-    set.max_b_rows_grad = 0;
     int64_t woff = 0;
     int32_t blocks = 0;
     for (int p = 0; p < n; ++p) {
@@ -603,10 +602,8 @@ gmco_status multi_workspace(gmco_multi *m, const std::vector<int64_t> &P)
         dp[p] = tc_dose_prob(pb, s.cnt, Wc, Gp, nullptr, Fpart, dFpart, (int32_t)m->a_row[p],
                              (int32_t)m->t_row[p], cap, (int32_t)m->np_max);
         gp[p] = tc_grad_prob(pb, s.cnt, gpart, sp, (int32_t)m->at_row[p], (int32_t)m->t_row[p]);
-        const int64_t ptiles = ceil_div(cap, 128);
-        set.max_items1 += ptiles * npt;
-        set.max_items2 += ptiles * sp.max_split;
-        set.max_b_rows_grad = std::max(set.max_b_rows_grad, tc_grad_b_rows(pb));
+        set.max_items1 += ceil_div(cap, 128) * npt;
+        set.max_items2 += ceil_div(cap, grad_bn(pb.tc_terms)) * tc_n_dtiles(pb) * sp.max_split;
         for (int par = 0; par < 2; ++par) {
             StepDesc &d = sd[(size_t)par * n + p];
             d.s = s;

@@ -32,10 +32,8 @@ namespace gmco {
 
 namespace {
 
-constexpr int BM = 128;                 // plan rows per tile (TMEM lanes)
+constexpr int BM = 128;                 // M rows per tile (TMEM lanes): points or dwells
 constexpr int BK = 64;                  // K elements per stage: 128 bytes of BF16
-constexpr int A_TILE = BM * BK * 2;     // bytes of one A-operand tile
-constexpr int BN1 = 128;                // points per dose-GEMM tile
 constexpr int EPI_WARPS = 16;           // 4 per TMEM lane quarter
 constexpr int W_TMA = EPI_WARPS, W_MMA = EPI_WARPS + 1, W_TMEM = EPI_WARPS + 2;
 constexpr int NTHREADS = (EPI_WARPS + 3) * 32;   // epilogue, TMA, MMA, TMEM owner
@@ -183,14 +181,22 @@ __device__ __forceinline__ void tmem_ld_wait_regs8(uint32_t (&a)[8], uint32_t (&
 }
 
 // ------------------------------------------------------------------ the GEMM kernel
-// One kind of ring stage: the B tiles (b_map) and A tiles (a_map) loaded for one K block, and
-// the products issued on them: pair q multiplies A tile pair_a[q] by B tile pair_b[q] into
-// accumulator pair_acc[q].
-constexpr int MAX_A = 5, MAX_PAIRS = 8;
+// One kind of ring stage: the M-side tiles (a_map, 128 rows each) and the N-side slots loaded
+// for one K block, and the products issued on them.  A slot holds one or two boxes of 128
+// rows stacked in shared memory (b_map[slot][0], b_map[slot][1]; -1 = none; b_roff = row
+// offset of a box), so that one MMA of N = 256 multiplies an M-side tile by both: in the dose
+// GEMM a slot is [T_j | dT_j], and one product gives A_i T_j and A_i dT_j side by side; in the
+// gradient GEMM it is a 256-plan tile of G_j in two halves.  Product q multiplies tile
+// pair_a[q] by slot pair_b[q] with N = pair_n[q].  Fewer, wider MMAs matter here: the single
+// issuing thread shares the SM with the epilogue warps, and its issue rate, not the tensor
+// pipe, bounds a stream of N = 128 MMAs (measured).
+constexpr int MAX_A = 3, MAX_B = 3, MAX_PAIRS = 8;
+constexpr int BOX = BM * BK * 2;        // bytes of one 128-row box of a K block
 struct Group {
-    int32_t n_b, n_a, n_pair;
-    int32_t b_map[MAX_A], a_map[MAX_A];
-    int32_t pair_b[MAX_PAIRS], pair_a[MAX_PAIRS], pair_acc[MAX_PAIRS];
+    int32_t n_a, n_b, n_pair;
+    int32_t a_map[MAX_A];
+    int32_t b_map[MAX_B][2], b_roff[MAX_B][2];
+    int32_t pair_a[MAX_PAIRS], pair_b[MAX_PAIRS], pair_n[MAX_PAIRS];
 };
 
 // Launch parameters common to every problem of the list.
@@ -200,10 +206,11 @@ struct KParams {
     int32_t n_probs, parity;
     int32_t has_dT, write_dose, zero_next;
     int32_t nG;               // BF16 terms of G written by the dose epilogue
+    int32_t bn;               // plans per tile: 128 (dose GEMM), 256 or 128 (gradient GEMM)
     int32_t n_groups;
     Group g[3];
-    int32_t n_stages, stage_bytes, b_bytes;   // ring stage size and the size of one B slot
-    int32_t a_off;                            // offset of the A tiles in a stage
+    int32_t n_stages, stage_bytes, slot_bytes;   // ring stage size, size of one N-side slot
+    int32_t b_off;                               // offset of the N-side slots in a stage
     int32_t *err;
 };
 
@@ -220,14 +227,96 @@ __device__ __forceinline__ int find_prob(const int32_t *start, int p, int item)
     return p;
 }
 
+// A work item decoded: plan tile, point tile (dose GEMM) or dwell tile and point split
+// (gradient GEMM), and whether a gradient plan tile of 256 holds at most 128 valid rows (its
+// products then run with N = 128 on the first half).
+struct Item {
+    int p, ptile, sub, dt;
+    bool half;
+};
+
+template <int KIND>
+__device__ __forceinline__ Item decode_item(const int32_t *s_start, const int32_t *s_per,
+                                            const int32_t *s_nsplit, const int32_t *s_rows, int bn,
+                                            int p, int item)
+{
+    Item it;
+    it.p = find_prob(s_start, p, item);
+    const int local = item - s_start[it.p];
+    it.ptile = local / s_per[it.p];
+    const int r = local - it.ptile * s_per[it.p];
+    if constexpr (KIND == 1) {
+        it.sub = r;
+        it.dt = 0;
+        it.half = false;
+    } else {
+        it.dt = r / s_nsplit[it.p];
+        it.sub = r - it.dt * s_nsplit[it.p];
+        it.half = bn > 128 && s_rows[it.p] - it.ptile * bn <= 128;
+    }
+    return it;
+}
+
+// Column sums over a warp of 8 values per lane, in a fixed order: afterwards every lane holds
+// the sum over all 32 lanes of column (lane >> 2) & 7.  Three halving exchanges leave each
+// lane one column summed over 8 lanes; two more add the 4 lanes that share it.
+__device__ __forceinline__ float warp_col_sum8(const float (&v)[8], int lane)
+{
+    constexpr unsigned kAll = 0xffffffffu;
+    const bool b4 = lane & 16, b3 = lane & 8, b2 = lane & 4;
+    float w[4];
+#pragma unroll
+    for (int t = 0; t < 4; ++t) {
+        const float keep = b4 ? v[t + 4] : v[t], give = b4 ? v[t] : v[t + 4];
+        w[t] = keep + __shfl_xor_sync(kAll, give, 16);
+    }
+    float y[2];
+#pragma unroll
+    for (int t = 0; t < 2; ++t) {
+        const float keep = b3 ? w[t + 2] : w[t], give = b3 ? w[t] : w[t + 2];
+        y[t] = keep + __shfl_xor_sync(kAll, give, 8);
+    }
+    float z = (b2 ? y[1] : y[0]) + __shfl_xor_sync(kAll, b2 ? y[0] : y[1], 4);
+    z += __shfl_xor_sync(kAll, z, 2);
+    z += __shfl_xor_sync(kAll, z, 1);
+    return z;
+}
+
+// 8 x 8 transpose within each group of 8 lanes: lane r of a group holds row r (v[i] = M[r][i])
+// before and column r (v[j] = M[j][r]) after.  Three butterfly stages; the one at distance s
+// swaps the elements whose row and column differ in bit s.
+__device__ __forceinline__ void transpose8(uint32_t (&v)[8], int lane)
+{
+#pragma unroll
+    for (int s = 4; s >= 1; s >>= 1) {
+        const bool up = lane & s;
+#pragma unroll
+        for (int i = 0; i < 8; ++i) {
+            if (i & s) continue;
+            const uint32_t send = up ? v[i] : v[i | s];
+            const uint32_t recv = __shfl_xor_sync(0xffffffffu, send, s);
+            if (up) v[i] = recv;
+            else v[i | s] = recv;
+        }
+    }
+}
+
+__device__ __forceinline__ uint4 pick16(const uint32_t (&v)[8], uint32_t sel)
+{
+    return make_uint4(__byte_perm(v[0], v[1], sel), __byte_perm(v[2], v[3], sel),
+                      __byte_perm(v[4], v[5], sel), __byte_perm(v[6], v[7], sel));
+}
+
+constexpr int kClStride = 132;   // row stride of the per-plan weight tables (bank spread)
+
 // Persistent: the grid is at most one CTA per SM, and each CTA walks the work items of all
 // problems of the launch (dose GEMM: problem x plan tile x point tile; gradient GEMM:
-// problem x plan tile x point split), derived from each problem's compact-row count at run
-// time.  The problems' descriptors are staged in shared memory.  The TMA ring continues
-// across items; accumulators live in two TMEM buffers of 256 columns handed between the MMA
-// thread and the epilogue warps through acc_full / acc_empty barriers, so the epilogue of
-// one item overlaps the MMAs of the next.  A gradient item wider than 256 dwells takes both
-// buffers.
+// problem x plan tile x dwell tile x point split), derived from each problem's compact-row
+// count at run time.  The problems' descriptors are staged in shared memory.  The TMA ring
+// continues across items; accumulators live in two TMEM buffers of 256 columns handed
+// between the MMA thread and the epilogue warps through acc_full / acc_empty barriers, so the
+// epilogue of one item overlaps the MMAs of the next.  TMEM lanes are points (dose GEMM) or
+// dwells (gradient GEMM); columns are plans.
 template <int KIND>   // 1: dose GEMM with penalty epilogue, 2: gradient GEMM
 __global__ void __launch_bounds__(NTHREADS, 1) k_tc(const __grid_constant__ KParams kp)
 {
@@ -243,12 +332,10 @@ __global__ void __launch_bounds__(NTHREADS, 1) k_tc(const __grid_constant__ KPar
     __shared__ int32_t s_rows[kMaxMulti];        // compact rows of each problem
     __shared__ int32_t s_per[kMaxMulti];         // work items per plan tile
     __shared__ int32_t s_kbps[kMaxMulti];        // gradient GEMM: K blocks per split
+    __shared__ int32_t s_nsplit[kMaxMulti];      // gradient GEMM: splits
     __shared__ int32_t s_fail;
-    __shared__ float4 s_pt[BN1];          // per point of the tile: D_min, D_max, scale, -
-    __shared__ int32_t s_sid[BN1];
-    __shared__ float s_cl[8][BM], s_ch[8][BM];   // w/N * w_min, w/N * w_max per row
-    __shared__ float s_half[2][4][BM];
-    __shared__ int32_t s_chunk[BN1 / 16];
+    __shared__ __align__(16) float s_cl[8][kClStride], s_ch[8][kClStride];   // w/N w_min, w/N w_max per plan
+    __shared__ float s_part[2][4][BM];           // per lane quarter and plan: partial F, dF
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int np = kp.n_probs;
@@ -264,16 +351,18 @@ __global__ void __launch_bounds__(NTHREADS, 1) k_tc(const __grid_constant__ KPar
         const int p = threadIdx.x;
         const Prob &d = gprob[p];
         const int rows = *d.n_rows[kp.parity];
-        int per = 1, kbps = 0;
+        int per = 1, kbps = 0, nsplit = 1;
         if constexpr (KIND == 1) {
             per = d.n_ptiles;
             if (kp.zero_next && blockIdx.x == 0) *const_cast<int32_t *>(d.n_rows[kp.parity ^ 1]) = 0;
         } else {
-            split_plan(d.sp, rows, &kbps, &per);
+            split_plan(d.sp, rows, &kbps, &nsplit);
+            per = d.n_dt * nsplit;
         }
         s_rows[p] = rows;
         s_per[p] = per;
         s_kbps[p] = kbps;
+        s_nsplit[p] = nsplit;
     }
     if (threadIdx.x == 0) s_fail = 0;
     __syncthreads();
@@ -281,7 +370,7 @@ __global__ void __launch_bounds__(NTHREADS, 1) k_tc(const __grid_constant__ KPar
         int acc = 0;
         for (int p = 0; p < np; ++p) {
             s_start[p] = acc;
-            acc += ((s_rows[p] + BM - 1) / BM) * s_per[p];
+            acc += ((s_rows[p] + kp.bn - 1) / kp.bn) * s_per[p];
         }
         s_start[np] = acc;
     }
@@ -312,43 +401,43 @@ __global__ void __launch_bounds__(NTHREADS, 1) k_tc(const __grid_constant__ KPar
             int it = 0, p = 0;
             bool ok = true;
             for (int item = blockIdx.x; item < n_items && ok; item += gridDim.x) {
-                p = find_prob(s_start, p, item);
+                const Item w = decode_item<KIND>(s_start, s_per, s_nsplit, s_rows, kp.bn, p, item);
+                p = w.p;
                 const Prob &d = s_prob[p];
-                const int local = item - s_start[p];
-                const int ptile = local / s_per[p], sub = local - ptile * s_per[p];
-                int row0, brow0, kb0, kb1, nbox, box_rows;
+                int arow, brow, kb0, kb1;
                 if constexpr (KIND == 1) {
-                    row0 = d.t_row + ptile * BM;
-                    brow0 = d.a_row + sub * BN1;
+                    arow = d.a_row + w.sub * BM;
+                    brow = d.t_row + w.ptile * kp.bn;
                     kb0 = 0;
                     kb1 = d.kb;
-                    box_rows = BN1;
-                    nbox = 1;
                 } else {
-                    row0 = d.g_row + ptile * BM;
-                    brow0 = d.at_row;
-                    kb0 = sub * s_kbps[p];
+                    arow = d.at_row + w.dt * BM;
+                    brow = d.g_row + w.ptile * kp.bn;
+                    kb0 = w.sub * s_kbps[p];
                     kb1 = min(kb0 + s_kbps[p], d.kb);
-                    box_rows = kTcBoxRowsAT;
-                    nbox = (d.n16 + box_rows - 1) / box_rows;
                 }
-                const uint32_t bbytes = (uint32_t)(nbox * box_rows * 128);
                 for (int gi = 0; gi < kp.n_groups && ok; ++gi) {
                     const Group &g = kp.g[gi];
+                    uint32_t bytes = (uint32_t)(g.n_a * BOX);
+                    for (int b = 0; b < g.n_b; ++b)
+                        bytes += (uint32_t)BOX * ((g.b_map[b][1] >= 0 && !w.half) ? 2u : 1u);
                     for (int kb = kb0; kb < kb1; ++kb, ++it) {
                         const int s = it % kp.n_stages;
                         const uint32_t ph = (uint32_t)(it / kp.n_stages) & 1u;
                         if (!mbar_wait(smem_u32(&empty_bar[s]), ph ^ 1u, kp.err, 1)) { ok = false; break; }
                         uint8_t *st = smem + (size_t)s * kp.stage_bytes;
                         const uint32_t fb = smem_u32(&full_bar[s]);
-                        mbar_expect_tx(fb, (uint32_t)g.n_b * bbytes + (uint32_t)(g.n_a * A_TILE));
-                        for (int bi = 0; bi < g.n_b; ++bi)
-                            for (int b = 0; b < nbox; ++b)
-                                tma_load_2d(smem_u32(st + bi * kp.b_bytes + b * box_rows * 128),
-                                            &kp.maps.m[g.b_map[bi]], kb * BK, brow0 + b * box_rows, fb);
+                        mbar_expect_tx(fb, bytes);
                         for (int t = 0; t < g.n_a; ++t)
-                            tma_load_2d(smem_u32(st + kp.a_off + t * A_TILE), &kp.maps.m[g.a_map[t]],
-                                        kb * BK, row0, fb);
+                            tma_load_2d(smem_u32(st + t * BOX), &kp.maps.m[g.a_map[t]], kb * BK, arow, fb);
+                        for (int b = 0; b < g.n_b; ++b) {
+                            uint8_t *slot = st + kp.b_off + b * kp.slot_bytes;
+                            tma_load_2d(smem_u32(slot), &kp.maps.m[g.b_map[b][0]], kb * BK,
+                                        brow + g.b_roff[b][0], fb);
+                            if (g.b_map[b][1] >= 0 && !w.half)
+                                tma_load_2d(smem_u32(slot + BOX), &kp.maps.m[g.b_map[b][1]], kb * BK,
+                                            brow + g.b_roff[b][1], fb);
+                        }
                     }
                 }
             }
@@ -357,63 +446,41 @@ __global__ void __launch_bounds__(NTHREADS, 1) k_tc(const __grid_constant__ KPar
         // ---------------- MMA issuer (one thread)
         if (lane == 0) {
             int it = 0, p = 0, nb = 0;
-            uint32_t use0 = 0u, use1 = 0u;   // completed uses of each accumulator buffer
+            uint32_t use[2] = {0u, 0u};   // completed uses of each accumulator buffer
             bool ok = true;
+            const uint32_t s_lo0 = desc_lo(smem_u32(smem));
+            const uint32_t stage_lo = (uint32_t)kp.stage_bytes >> 4;
             for (int item = blockIdx.x; item < n_items && ok; item += gridDim.x) {
-                p = find_prob(s_start, p, item);
+                const Item w = decode_item<KIND>(s_start, s_per, s_nsplit, s_rows, kp.bn, p, item);
+                p = w.p;
                 const Prob &d = s_prob[p];
-                const int local = item - s_start[p];
-                const int ptile = local / s_per[p], sub = local - ptile * s_per[p];
-                (void)ptile;
-                int kb0, kb1, k16_total, n0, n1;
-                bool dbl;
+                int kb0, kb1, k16_total;
                 if constexpr (KIND == 1) {
                     kb0 = 0;
                     kb1 = d.kb;
                     k16_total = d.k16;
-                    n0 = BN1;
-                    n1 = 0;
-                    dbl = false;
                 } else {
-                    kb0 = sub * s_kbps[p];
+                    kb0 = w.sub * s_kbps[p];
                     kb1 = min(kb0 + s_kbps[p], d.kb);
                     k16_total = 1 << 30;
-                    n0 = d.n_part0;
-                    n1 = d.n_part1;
-                    dbl = d.n16 > 256;
                 }
-                const int buf = dbl ? 0 : nb;
-                if (dbl || buf == 0)
-                    ok = mbar_wait(smem_u32(&acce_bar[0]), (use0 & 1u) ^ 1u, kp.err, 4);
-                if (ok && (dbl || buf == 1))
-                    ok = mbar_wait(smem_u32(&acce_bar[1]), (use1 & 1u) ^ 1u, kp.err, 4);
-                if (!ok) break;
+                const int buf = nb;
+                if (!mbar_wait(smem_u32(&acce_bar[buf]), (use[buf] & 1u) ^ 1u, kp.err, 4)) break;
                 fence_after();
                 const uint32_t tbuf = tmem + (uint32_t)(buf * BUF_COLS);
-                const uint32_t id0 = idesc_bf16(n0), id1 = idesc_bf16(n1 > 0 ? n1 : 16);
-                const uint32_t boff1 = (uint32_t)(n0 * 128);
-                // Per product q of a group: descriptor address fields (16-byte units) of its
-                // A and B tiles relative to the stage, its accumulator column, and whether it
-                // is the first product into that accumulator (which starts the sum).  In the
-                // loop a descriptor is DESC_FIXED | (stage + offset + 2 per 32-byte K step).
-                const uint32_t s_lo0 = desc_lo(smem_u32(smem));
-                const uint32_t stage_lo = (uint32_t)kp.stage_bytes >> 4;
-                const uint32_t b1_lo = boff1 >> 4;
                 for (int gi = 0; gi < kp.n_groups && ok; ++gi) {
-                    const int np = kp.g[gi].n_pair;
-                    uint32_t bq[MAX_PAIRS], aq[MAX_PAIRS], dq[MAX_PAIRS], fq[MAX_PAIRS];
+                    const Group &g = kp.g[gi];
+                    const int npair = g.n_pair;
+                    // per product: descriptor address fields (16-byte units) of its tiles
+                    // relative to the stage, and its instruction descriptor; in the loop a
+                    // descriptor is DESC_FIXED | (stage + offset + 2 per 32-byte K step)
+                    uint32_t aq[MAX_PAIRS], bq[MAX_PAIRS], iq[MAX_PAIRS];
 #pragma unroll
                     for (int q = 0; q < MAX_PAIRS; ++q) {
-                        const int qq = q < np ? q : 0;
-                        const int acc = kp.g[gi].pair_acc[qq];
-                        bq[q] = (uint32_t)(kp.g[gi].pair_b[qq] * kp.b_bytes) >> 4;
-                        aq[q] = (uint32_t)(kp.a_off + kp.g[gi].pair_a[qq] * A_TILE) >> 4;
-                        dq[q] = tbuf + (uint32_t)(acc * BN1);
-                        bool first = gi == 0;
-#pragma unroll
-                        for (int r = 0; r < MAX_PAIRS; ++r)
-                            if (r < q && kp.g[gi].pair_acc[r] == acc) first = false;
-                        fq[q] = first ? 1u : 0u;
+                        const int qq = q < npair ? q : 0;
+                        aq[q] = (uint32_t)(g.pair_a[qq] * BOX) >> 4;
+                        bq[q] = (uint32_t)(kp.b_off + g.pair_b[qq] * kp.slot_bytes) >> 4;
+                        iq[q] = idesc_bf16(w.half ? 128 : g.pair_n[qq]);
                     }
                     for (int kb = kb0; kb < kb1; ++kb, ++it) {
                         const int s = it % kp.n_stages;
@@ -421,7 +488,9 @@ __global__ void __launch_bounds__(NTHREADS, 1) k_tc(const __grid_constant__ KPar
                         if (!mbar_wait(smem_u32(&full_bar[s]), ph, kp.err, 2)) { ok = false; break; }
                         fence_after();
                         const uint32_t st_lo = s_lo0 + (uint32_t)s * stage_lo;
-                        const uint32_t fresh = kb == kb0 ? 1u : 0u;
+                        // the first product of the item (an N = 256 one whenever any is)
+                        // starts the accumulator
+                        const bool fresh = gi == 0 && kb == kb0;
                         const int k16n = min(4, k16_total - kb * 4);
 #pragma unroll
                         for (int k16 = 0; k16 < 4; ++k16) {
@@ -429,12 +498,10 @@ __global__ void __launch_bounds__(NTHREADS, 1) k_tc(const __grid_constant__ KPar
                                 const uint32_t kk = st_lo + 2u * (uint32_t)k16;
 #pragma unroll
                                 for (int q = 0; q < MAX_PAIRS; ++q) {
-                                    if (q < np) {
-                                        const uint64_t ad = DESC_FIXED | (kk + aq[q]);
-                                        const uint32_t accum = (k16 == 0 && (fresh & fq[q])) ? 0u : 1u;
-                                        mma_bf16(dq[q], ad, DESC_FIXED | (kk + bq[q]), id0, accum);
-                                        if (n1 > 0)
-                                            mma_bf16(dq[q] + (uint32_t)n0, ad, DESC_FIXED | (kk + bq[q] + b1_lo), id1, accum);
+                                    if (q < npair) {
+                                        const uint32_t accum = (fresh && k16 == 0 && q == 0) ? 0u : 1u;
+                                        mma_bf16(tbuf, DESC_FIXED | (kk + aq[q]), DESC_FIXED | (kk + bq[q]),
+                                                 iq[q], accum);
                                     }
                                 }
                             }
@@ -443,158 +510,149 @@ __global__ void __launch_bounds__(NTHREADS, 1) k_tc(const __grid_constant__ KPar
                     }
                 }
                 if (!ok) break;
-                // accumulator(s) ready for the epilogue
-                if (dbl || buf == 0) mma_commit(smem_u32(&accf_bar[0]));
-                if (dbl || buf == 1) mma_commit(smem_u32(&accf_bar[1]));
-                if (dbl || buf == 0) ++use0;
-                if (dbl || buf == 1) ++use1;
-                nb = dbl ? 0 : buf ^ 1;
+                mma_commit(smem_u32(&accf_bar[buf]));   // accumulator ready for the epilogue
+                ++use[buf];
+                nb = buf ^ 1;
             }
         }
     } else if (warp < EPI_WARPS) {
         // ---------------- epilogue: TMEM lane quarter q, column quarter h
         const int q = warp & 3, h = warp >> 2;
-        const int r = q * 32 + lane;
         int p = 0, nb = 0;
-        uint32_t use0 = 0u, use1 = 0u;
+        uint32_t use[2] = {0u, 0u};
         for (int item = blockIdx.x; item < n_items; item += gridDim.x) {
-            p = find_prob(s_start, p, item);
+            const Item w = decode_item<KIND>(s_start, s_per, s_nsplit, s_rows, kp.bn, p, item);
+            p = w.p;
             const Prob &d = s_prob[p];
-            const int local = item - s_start[p];
-            const int ptile = local / s_per[p], sub = local - ptile * s_per[p];
             const int n_rows = s_rows[p];
-            const int row = ptile * BM + r;   // compact row within the problem
-            const bool valid = row < n_rows;
-            bool dbl = false;
-            if constexpr (KIND == 2) dbl = d.n16 > 256;
-            const int buf = dbl ? 0 : nb;
+            const int buf = nb;
             const uint32_t lane_addr = tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)(buf * BUF_COLS);
             bool ok = true;
             if constexpr (KIND == 1) {
-                const int b_col0 = sub * BN1;
+                const int pt_i = w.sub * BM + q * 32 + lane;   // this thread's point (in the problem)
+                const float4 pt = d.pt4[pt_i];                // D_min, D_max, scale, structure
+                const int sv_own = (int)pt.w;
+                // 32 points of one structure and bound pattern take that branch warp-uniformly
+                const int c16 = (w.sub * BM + q * 32) / 16;
+                const int i0 = d.chunk[c16], i1 = d.chunk[c16 + 1];
+                const int mode = i0 == i1 ? (i0 & 7) : 0;
+                const int sv = mode != 0 ? (i0 >> 3) : sv_own;
                 asm volatile("bar.sync 1, 512;" ::: "memory");   // previous item's readers done
-                {
-                    const int i = threadIdx.x;   // 0..511
-                    if (i < BN1) {
-                        const float4 v = d.pt4[b_col0 + i];   // D_min, D_max, scale, id
-                        s_pt[i] = v;
-                        s_sid[i] = (int)v.w;
-                        if (i < BN1 / 16) s_chunk[i] = d.chunk[b_col0 / 16 + i];
-                    } else if (i < 2 * BN1) {
-                        const int rr = i - BN1;   // 0..127: weights of row rr of this tile
-                        const int rw = ptile * BM + rr;
-                        for (int s2 = 0; s2 < d.n_struct; ++s2) {
-                            const float c = rw < n_rows ? d.Wc[(size_t)rw * d.n_struct + s2] : 0.0f;
-                            const float4 sp = d.sparams[s2];
-                            s_cl[s2][rr] = c * sp.x;
-                            s_ch[s2][rr] = c * sp.w;
-                        }
+                if (threadIdx.x < BM) {
+                    const int rr = threadIdx.x, rw = w.ptile * BM + rr;   // plan row of the tile
+                    for (int s2 = 0; s2 < d.n_struct; ++s2) {
+                        const float c = rw < n_rows ? d.Wc[(size_t)rw * d.n_struct + s2] : 0.0f;
+                        const float4 sp = d.sparams[s2];
+                        s_cl[s2][rr] = c * sp.x;
+                        s_ch[s2][rr] = c * sp.w;
                     }
                 }
                 asm volatile("bar.sync 1, 512;" ::: "memory");
-                float fs0 = 0.0f, fs1 = 0.0f, dfs0 = 0.0f, dfs1 = 0.0f;
                 // warp-uniform: tcgen05.ld below is warp-collective; every named barrier of this
                 // loop is reached by all epilogue threads whatever the outcome
                 ok = __all_sync(0xffffffffu,
-                                mbar_wait(smem_u32(&accf_bar[buf]), ((buf ? use1 : use0) & 1u), kp.err, 3));
+                                mbar_wait(smem_u32(&accf_bar[buf]), use[buf] & 1u, kp.err, 3));
                 fence_after();
                 if (ok) {
                     const bool has_dT = kp.has_dT != 0;
                     const bool wdose = kp.write_dose != 0;
-                    constexpr int CW = 8;                  // TMEM columns per load
-                    constexpr int NCH = BN1 / 4 / CW;      // chunks per warp and item
+                    const float lo = pt.x, hi = pt.y, sc = pt.z;
+                    const float *clr = s_cl[sv < 0 ? 0 : sv], *chr = s_ch[sv < 0 ? 0 : sv];
+                    constexpr int CW = 8;                  // plan columns per TMEM load
 #pragma unroll 1
-                    for (int chk = 0; chk < NCH; ++chk) {
-                        const int c = h * (BN1 / 4) + chk * CW;
+                    for (int chk = 0; chk < BM / 4 / CW; ++chk) {
+                        const int c = h * (BM / 4) + chk * CW;   // first plan column
                         uint32_t dv[CW], ddv[CW];
 #pragma unroll
                         for (int i = 0; i < CW; ++i) ddv[i] = 0u;
                         tmem_ld8(lane_addr + (uint32_t)c, dv);
-                        if (has_dT) tmem_ld8(lane_addr + (uint32_t)(BN1 + c), ddv);
+                        if (has_dT) tmem_ld8(lane_addr + (uint32_t)(BM + c), ddv);
                         tmem_ld_wait_regs8(dv, ddv);
-                        const int info = s_chunk[c / 16];
-                        const int mode = info & 7, sv0 = info >> 3;
-                        float out[CW];
-                        if (mode == 4) {            // padding points or a structure without bounds
+                        float out[CW], fv[CW], dfv[CW];
 #pragma unroll
-                            for (int i = 0; i < CW; ++i) out[i] = wdose ? s_pt[c + i].z * __uint_as_float(dv[i]) : 0.0f;
-                        } else if (mode == 1) {     // one structure, lower bound only
-                            const float lo = s_pt[c].x, cl = s_cl[sv0][r];
-#pragma unroll
-                            for (int i = 0; i < CW; ++i) {
-                                const float sc = s_pt[c + i].z;
-                                const float dd0 = sc * __uint_as_float(dv[i]);
+                        for (int i = 0; i < CW; ++i) {
+                            const float dd0 = sc * __uint_as_float(dv[i]);
+                            const float dd = sc * __uint_as_float(ddv[i]);
+                            float f = 0.0f, df = 0.0f, gval = 0.0f;
+                            if (mode == 1) {            // lower bound only
+                                const float cl = clr[c + i];
                                 const float u = fmaxf(lo - dd0, 0.0f);
-                                const float cu = cl * u;
-                                if (i & 1) fs1 = fmaf(cu, u, fs1); else fs0 = fmaf(cu, u, fs0);
-                                out[i] = wdose ? dd0 : -2.0f * cu * sc;
-                                if (has_dT) {
-                                    const float dd = sc * __uint_as_float(ddv[i]);
-                                    const float ub = fmaxf(lo - (dd0 - dd), 0.0f);
-                                    const float dl = (u > 0.0f && ub > 0.0f) ? -dd : u - ub;
-                                    if (i & 1) dfs1 = fmaf(cl * dl, u + ub, dfs1);
-                                    else dfs0 = fmaf(cl * dl, u + ub, dfs0);
-                                }
-                            }
-                        } else if (mode == 2) {     // one structure, upper bound only
-                            const float hi = s_pt[c].y, ch = s_ch[sv0][r];
-#pragma unroll
-                            for (int i = 0; i < CW; ++i) {
-                                const float sc = s_pt[c + i].z;
-                                const float dd0 = sc * __uint_as_float(dv[i]);
-                                const float o = fmaxf(dd0 - hi, 0.0f);
-                                const float co = ch * o;
-                                if (i & 1) fs1 = fmaf(co, o, fs1); else fs0 = fmaf(co, o, fs0);
-                                out[i] = wdose ? dd0 : 2.0f * co * sc;
-                                if (has_dT) {
-                                    const float dd = sc * __uint_as_float(ddv[i]);
-                                    const float ob = fmaxf((dd0 - dd) - hi, 0.0f);
-                                    const float dh = (o > 0.0f && ob > 0.0f) ? dd : o - ob;
-                                    if (i & 1) dfs1 = fmaf(ch * dh, o + ob, dfs1);
-                                    else dfs0 = fmaf(ch * dh, o + ob, dfs0);
-                                }
-                            }
-                        } else {                    // mixed structures or two-sided bounds
-#pragma unroll
-                            for (int i = 0; i < CW; ++i) {
-                                const float4 pt = s_pt[c + i];
-                                const int sv = s_sid[c + i];
-                                const float cl = s_cl[sv][r], ch = s_ch[sv][r];
-                                const float dd0 = pt.z * __uint_as_float(dv[i]);
-                                const float u = fmaxf(pt.x - dd0, 0.0f), o = fmaxf(dd0 - pt.y, 0.0f);
-                                fs0 = fmaf(cl * u, u, fs0);
-                                fs1 = fmaf(ch * o, o, fs1);
-                                out[i] = wdose ? dd0 : 2.0f * (ch * o - cl * u) * pt.z;
+                                f = cl * u * u;
+                                gval = -2.0f * cl * u * sc;
                                 if (has_dT) {
                                     // f(d) - f(d - dd) without cancellation (see eval_simt.cu)
-                                    const float dd = pt.z * __uint_as_float(ddv[i]);
+                                    const float ub = fmaxf(lo - (dd0 - dd), 0.0f);
+                                    const float dl = (u > 0.0f && ub > 0.0f) ? -dd : u - ub;
+                                    df = cl * dl * (u + ub);
+                                }
+                            } else if (mode == 2) {     // upper bound only
+                                const float ch = chr[c + i];
+                                const float o = fmaxf(dd0 - hi, 0.0f);
+                                f = ch * o * o;
+                                gval = 2.0f * ch * o * sc;
+                                if (has_dT) {
+                                    const float ob = fmaxf((dd0 - dd) - hi, 0.0f);
+                                    const float dh = (o > 0.0f && ob > 0.0f) ? dd : o - ob;
+                                    df = ch * dh * (o + ob);
+                                }
+                            } else if (mode != 4 && sv >= 0) {   // both bounds, or mixed points
+                                const float cl = clr[c + i], ch = chr[c + i];
+                                const float u = fmaxf(lo - dd0, 0.0f), o = fmaxf(dd0 - hi, 0.0f);
+                                f = cl * u * u + ch * o * o;
+                                gval = 2.0f * (ch * o - cl * u) * sc;
+                                if (has_dT) {
                                     const float db = dd0 - dd;
-                                    const float ub = fmaxf(pt.x - db, 0.0f), ob = fmaxf(db - pt.y, 0.0f);
+                                    const float ub = fmaxf(lo - db, 0.0f), ob = fmaxf(db - hi, 0.0f);
                                     const float dl = (u > 0.0f && ub > 0.0f) ? -dd : u - ub;
                                     const float dh = (o > 0.0f && ob > 0.0f) ? dd : o - ob;
-                                    dfs0 = fmaf(cl * dl, u + ub, dfs0);
-                                    dfs1 = fmaf(ch * dh, o + ob, dfs1);
+                                    df = cl * dl * (u + ub) + ch * dh * (o + ob);
                                 }
                             }
+                            fv[i] = f;
+                            dfv[i] = df;
+                            out[i] = wdose ? dd0 : gval;
                         }
-                        if (valid) {
-                            const size_t off = (size_t)row * d.ld_g + b_col0 + c;
+                        // per plan column: sum over this warp's 32 points, then over the lane
+                        // quarters below (fixed order)
+                        const float fsum = warp_col_sum8(fv, lane);
+                        const float dfsum = has_dT ? warp_col_sum8(dfv, lane) : 0.0f;
+                        if ((lane & 3) == 0) {
+                            s_part[0][q][c + ((lane >> 2) & 7)] = fsum;
+                            s_part[1][q][c + ((lane >> 2) & 7)] = dfsum;
+                        }
+                        // rows of G (or of the dose) run over points: the 8 x 8 blocks of (plan,
+                        // point) values are transposed within each group of 8 lanes, so that a
+                        // lane writes 8 consecutive points of one plan, 16 bytes per term
+                        uint32_t wv[CW], wv3[CW];   // BF16 terms 1 | 2 (or the FP32 dose), term 3
+#pragma unroll
+                        for (int i = 0; i < CW; ++i) {
+                            if (wdose) {
+                                wv[i] = __float_as_uint(out[i]);
+                                wv3[i] = 0u;
+                            } else {
+                                const __nv_bfloat16 b1 = __float2bfloat16_rn(out[i]);
+                                const float r1 = out[i] - __bfloat162float(b1);
+                                const __nv_bfloat16 b2 = __float2bfloat16_rn(r1);
+                                const __nv_bfloat16 b3 = __float2bfloat16_rn(r1 - __bfloat162float(b2));
+                                wv[i] = (uint32_t)__bfloat16_as_ushort(b1) | ((uint32_t)__bfloat16_as_ushort(b2) << 16);
+                                wv3[i] = (uint32_t)__bfloat16_as_ushort(b3);
+                            }
+                        }
+                        transpose8(wv, lane);
+                        if (kp.nG > 2 && !wdose) transpose8(wv3, lane);
+                        const int row = w.ptile * BM + c + (lane & 7);   // compact row of this lane's plan
+                        if (row < n_rows) {
+                            const size_t off = (size_t)row * d.ld_g + w.sub * BM + q * 32 + (lane >> 3) * 8;
                             if (wdose) {
                                 float4 *o4 = reinterpret_cast<float4 *>(d.dose_out + off);
-                                o4[0] = make_float4(out[0], out[1], out[2], out[3]);
-                                o4[1] = make_float4(out[4], out[5], out[6], out[7]);
+                                o4[0] = make_float4(__uint_as_float(wv[0]), __uint_as_float(wv[1]),
+                                                    __uint_as_float(wv[2]), __uint_as_float(wv[3]));
+                                o4[1] = make_float4(__uint_as_float(wv[4]), __uint_as_float(wv[5]),
+                                                    __uint_as_float(wv[6]), __uint_as_float(wv[7]));
                             } else {
-                                for (int j = 0; j < kp.nG; ++j) {
-                                    uint32_t pk[4];
-#pragma unroll
-                                    for (int v = 0; v < 4; ++v) {
-                                        const __nv_bfloat162 b2 = __floats2bfloat162_rn(out[2 * v], out[2 * v + 1]);
-                                        pk[v] = *reinterpret_cast<const uint32_t *>(&b2);
-                                        out[2 * v] -= __low2float(b2);
-                                        out[2 * v + 1] -= __high2float(b2);
-                                    }
-                                    *reinterpret_cast<uint4 *>(d.G[j] + off) = make_uint4(pk[0], pk[1], pk[2], pk[3]);
-                                }
+                                *reinterpret_cast<uint4 *>(d.G[0] + off) = pick16(wv, 0x5410u);
+                                *reinterpret_cast<uint4 *>(d.G[1] + off) = pick16(wv, 0x7632u);
+                                if (kp.nG > 2) *reinterpret_cast<uint4 *>(d.G[2] + off) = pick16(wv3, 0x5410u);
                             }
                         }
                     }
@@ -602,56 +660,45 @@ __global__ void __launch_bounds__(NTHREADS, 1) k_tc(const __grid_constant__ KPar
                 fence_before();
                 __syncwarp();
                 if (lane == 0) asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(&acce_bar[buf])) : "memory");
-                s_half[0][h][r] = fs0 + fs1;
-                s_half[1][h][r] = dfs0 + dfs1;
                 if (!ok && lane == 0) s_fail = 1;
                 asm volatile("bar.sync 1, 512;" ::: "memory");
-                if (h == 0 && valid && ok) {   // fixed-order sum of the four column quarters
-                    d.Fpart[(size_t)sub * d.cap + row] =
-                        ((s_half[0][0][r] + s_half[0][1][r]) + s_half[0][2][r]) + s_half[0][3][r];
-                    if (kp.has_dT)
-                        d.dFpart[(size_t)sub * d.cap + row] =
-                            ((s_half[1][0][r] + s_half[1][1][r]) + s_half[1][2][r]) + s_half[1][3][r];
-                }
                 ok = s_fail == 0;   // uniform over the epilogue warps (read after the barrier)
+                if (threadIdx.x < BM && ok) {   // fixed-order sum of the four lane quarters
+                    const int rr = threadIdx.x, row = w.ptile * BM + rr;
+                    if (row < n_rows) {
+                        d.Fpart[(size_t)w.sub * d.cap + row] =
+                            ((s_part[0][0][rr] + s_part[0][1][rr]) + s_part[0][2][rr]) + s_part[0][3][rr];
+                        if (kp.has_dT)
+                            d.dFpart[(size_t)w.sub * d.cap + row] =
+                                ((s_part[1][0][rr] + s_part[1][1][rr]) + s_part[1][2][rr]) + s_part[1][3][rr];
+                    }
+                }
             } else {
-                const int nch = d.n16 / 16;
-                const int per = (nch + 3) / 4;
-                const int c_beg = min(h * per, nch);
-                const int c_end = min(c_beg + per, nch);
-                float *out = d.gpart + ((size_t)sub * n_rows + row) * d.nd_pad;
-                bool w = true;
-                if (dbl || buf == 0) w = mbar_wait(smem_u32(&accf_bar[0]), use0 & 1u, kp.err, 3);
-                if (w && (dbl || buf == 1)) w = mbar_wait(smem_u32(&accf_bar[1]), use1 & 1u, kp.err, 3);
-                ok = __all_sync(0xffffffffu, w);
+                const int dw = w.dt * BM + q * 32 + lane;   // this thread's dwell
+                const bool dw_ok = dw < d.nd_pad;
+                const int ncols = w.half ? 128 : kp.bn;
+                const int cw = ncols / 4;                   // plan columns of this warp
+                ok = __all_sync(0xffffffffu,
+                                mbar_wait(smem_u32(&accf_bar[buf]), use[buf] & 1u, kp.err, 3));
                 fence_after();
                 if (ok) {
-                    for (int ch = c_beg; ch < c_end; ++ch) {
+                    float *out = d.gpart + (size_t)w.sub * n_rows * d.nd_pad + dw;
+                    for (int c0 = h * cw; c0 < (h + 1) * cw; c0 += 16) {
                         uint32_t v[16];
-                        tmem_ld16(lane_addr + (uint32_t)(ch * 16), v);
+                        tmem_ld16(lane_addr + (uint32_t)c0, v);
                         tmem_ld_wait();
-                        if (valid) {
-                            float4 *o4 = reinterpret_cast<float4 *>(out + ch * 16);
+                        const int row0 = w.ptile * kp.bn + c0;
 #pragma unroll
-                            for (int k = 0; k < 4; ++k)
-                                o4[k] = make_float4(__uint_as_float(v[4 * k]), __uint_as_float(v[4 * k + 1]),
-                                                    __uint_as_float(v[4 * k + 2]),
-                                                    __uint_as_float(v[4 * k + 3]));
-                        }
+                        for (int k = 0; k < 16; ++k)
+                            if (dw_ok && row0 + k < n_rows) out[(size_t)(row0 + k) * d.nd_pad] = __uint_as_float(v[k]);
                     }
                 }
                 fence_before();
                 __syncwarp();
-                if (lane == 0) {
-                    if (dbl || buf == 0) asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(&acce_bar[0])) : "memory");
-                    if (dbl || buf == 1) asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(&acce_bar[1])) : "memory");
-                }
-                if (h == 3 && valid)
-                    for (int c = d.n16; c < d.nd_pad; ++c) out[c] = 0.0f;
+                if (lane == 0) asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(&acce_bar[buf])) : "memory");
             }
-            if (dbl || buf == 0) ++use0;
-            if (dbl || buf == 1) ++use1;
-            nb = dbl ? 0 : buf ^ 1;
+            ++use[buf];
+            nb = buf ^ 1;
             if (!ok) break;
         }
     }
@@ -831,75 +878,75 @@ KParams make_params(const TcLaunchSet &set, int kind, int parity, bool with_dT, 
     k.probs = kind == 1 ? static_cast<const void *>(set.dose) : static_cast<const void *>(set.grad);
     k.n_probs = set.n;
     k.parity = parity;
-    k.has_dT = with_dT ? 1 : 0;
+    k.has_dT = kind == 1 && with_dT ? 1 : 0;
     k.write_dose = write_dose ? 1 : 0;
     k.zero_next = zero_next ? 1 : 0;
     const int nA = set.tc_terms, nT = n_t_terms(nA);
     k.nG = nT;
-    k.b_bytes = kind == 1 ? BN1 * 128 : set.max_b_rows_grad * 128;
-    auto add_pair = [](Group &g, int b, int a, int acc) {
-        g.pair_b[g.n_pair] = b;
-        g.pair_a[g.n_pair] = a;
-        g.pair_acc[g.n_pair++] = acc;
+    k.bn = kind == 1 ? BM : grad_bn(nA);
+    // N-side slot j: dose GEMM T_j, with dT_j stacked behind it for the two terms of dT;
+    // gradient GEMM G_j, both 128-row halves of a 256-plan tile
+    auto slot_maps = [&](Group &g, int j) {
+        const int b = g.n_b++;
+        g.b_map[b][0] = 3 + j;
+        g.b_roff[b][0] = 0;
+        g.b_map[b][1] = -1;
+        g.b_roff[b][1] = 0;
+        if (kind == 1 && k.has_dT && j < 2) {
+            g.b_map[b][1] = 6 + j;
+        } else if (kind == 2 && k.bn == 256) {
+            g.b_map[b][1] = 3 + j;
+            g.b_roff[b][1] = 128;
+        }
+        return b;
     };
-    // dose GEMM: every B term and every A operand of a K block in one stage (each tile loaded
-    // once per K block) when two such stages fit; otherwise one stage kind per B term
-    const int na_all = nT + ((kind == 1 && with_dT) ? 2 : 0);
-    const bool merged = kind == 1 && nA * k.b_bytes + na_all * A_TILE <= SMEM_BUDGET / 2 &&
-                        nA * nT + nA + 1 <= MAX_PAIRS;
-    int max_b = 1, max_a = 0;
+    auto slot_n = [&](int j) { return kind == 1 ? ((k.has_dT && j < 2) ? 256 : 128) : k.bn; };
+    auto add_pair = [](Group &g, int a, int b, int n) {
+        g.pair_a[g.n_pair] = a;
+        g.pair_b[g.n_pair] = b;
+        g.pair_n[g.n_pair++] = n;
+    };
+    const bool stacked = (kind == 1 && k.has_dT) || (kind == 2 && k.bn == 256);
+    k.slot_bytes = stacked ? 2 * BOX : BOX;
+    int npairs = 0;
+    for (int i = 0; i < nA; ++i)
+        for (int j = 0; j < nT; ++j) npairs += keep_pair(i, j, nA, nT);
+    const bool merged = nA * BOX + nT * k.slot_bytes <= SMEM_BUDGET / 2 && npairs <= MAX_PAIRS;
+    int max_a = 0, max_b = 0;
     if (merged) {
+        // every term of a K block in one stage, each tile loaded once per K block; the
+        // N = 256 products first (the first product starts the accumulator)
         k.n_groups = 1;
         Group &g = k.g[0];
         g = Group{};
-        g.n_b = nA;
-        for (int i = 0; i < nA; ++i) g.b_map[i] = i;
-        g.n_a = na_all;
-        for (int j = 0; j < nT; ++j) g.a_map[j] = 3 + j;
-        if (with_dT) {
-            g.a_map[nT] = 6;
-            g.a_map[nT + 1] = 7;
-        }
-        // products into the dose (0) and dose-change (1) accumulators alternate where they
-        // can, so consecutive MMAs do not wait on the same accumulator
-        int d_i[MAX_PAIRS], d_j[MAX_PAIRS], nd = 0, c_i[MAX_PAIRS], nc = 0;
-        for (int i = 0; i < nA; ++i) {
+        g.n_a = nA;
+        for (int i = 0; i < nA; ++i) g.a_map[i] = i;
+        for (int j = 0; j < nT; ++j) slot_maps(g, j);
+        for (int wide = 1; wide >= 0; --wide)
             for (int j = 0; j < nT; ++j)
-                if (keep_pair(i, j, nA, nT)) { d_i[nd] = i; d_j[nd++] = j; }
-            if (with_dT) c_i[nc++] = i;
-        }
-        for (int q = 0; q < std::max(nd, nc); ++q) {
-            if (q < nd) add_pair(g, d_i[q], d_j[q], 0);
-            if (q < nc) add_pair(g, c_i[q], nT, 1);
-        }
-        if (with_dT) add_pair(g, 0, nT + 1, 1);   // dT2 A_1
-        max_b = nA;
-        max_a = na_all;
+                for (int i = 0; i < nA; ++i)
+                    if (keep_pair(i, j, nA, nT) && (slot_n(j) == 256) == (wide == 1))
+                        add_pair(g, i, j, slot_n(j));
+        max_a = nA;
+        max_b = nT;
     } else {
-        k.n_groups = nA;
-        for (int i = 0; i < nA; ++i) {
-            Group &g = k.g[i];
+        // one stage kind per N-side term j, with the M-side terms it pairs with
+        k.n_groups = nT;
+        for (int j = 0; j < nT; ++j) {
+            Group &g = k.g[j];
             g = Group{};
-            g.n_b = 1;
-            g.b_map[0] = i;
-            for (int j = 0; j < nT; ++j)
+            slot_maps(g, j);
+            for (int i = 0; i < nA; ++i)
                 if (keep_pair(i, j, nA, nT)) {
-                    g.a_map[g.n_a] = 3 + j;
-                    add_pair(g, 0, g.n_a++, 0);
+                    g.a_map[g.n_a] = i;
+                    add_pair(g, g.n_a++, 0, slot_n(j));
                 }
-            if (kind == 1 && with_dT) {
-                g.a_map[g.n_a] = 6;
-                add_pair(g, 0, g.n_a++, 1);
-                if (i == 0) {   // dT2 A_1
-                    g.a_map[g.n_a] = 7;
-                    add_pair(g, 0, g.n_a++, 1);
-                }
-            }
             max_a = std::max(max_a, g.n_a);
         }
+        max_b = 1;
     }
-    k.a_off = max_b * k.b_bytes;
-    k.stage_bytes = k.a_off + max_a * A_TILE;
+    k.b_off = max_a * BOX;
+    k.stage_bytes = k.b_off + max_b * k.slot_bytes;
     k.n_stages = std::max(1, std::min(MAX_STAGES, SMEM_BUDGET / k.stage_bytes));
     k.err = set.err;
     return k;
@@ -924,6 +971,14 @@ int n16_of(const DevProblem &pb) { return (int)round_up(pb.n_dwell, 16); }
 
 }  // namespace
 
+// Plans per tile of the gradient GEMM: 256 when a merged stage of all terms fits twice in
+// the ring (one MMA of N = 256 per product), else 128.
+int grad_bn(int tc_terms)
+{
+    const int nA = tc_terms, nT = n_t_terms(tc_terms);
+    return (nA + 2 * nT) * BOX <= SMEM_BUDGET / 2 ? 256 : 128;
+}
+
 bool tc_encode_map(CUtensorMap *m, const void *ptr, uint64_t cols, uint64_t rows,
                    uint32_t box_cols, uint32_t box_rows)
 {
@@ -938,23 +993,29 @@ bool tc_encode_map(CUtensorMap *m, const void *ptr, uint64_t cols, uint64_t rows
                CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
 
-int32_t tc_n_ptiles(const DevProblem &pb) { return (int32_t)(pb.np_pad / BN1); }
+int32_t tc_n_ptiles(const DevProblem &pb) { return (int32_t)(pb.np_pad / BM); }
+
+int32_t tc_n_dtiles(const DevProblem &pb) { return (int32_t)ceil_div(pb.nd_pad, BM); }
 
 double tc_mma_units(const DevProblem &pb, bool with_dT, int which)
 {
     const int nA = pb.tc_terms, nT = n_t_terms(pb.tc_terms);
-    int pairs = 0;
+    int pairs = 0, with_dt_term = 0;
     for (int i = 0; i < nA; ++i)
-        for (int j = 0; j < nT; ++j) pairs += keep_pair(i, j, nA, nT);
-    return which == 1 ? pairs + (with_dT ? nA + 1 : 0) : pairs;
+        for (int j = 0; j < nT; ++j)
+            if (keep_pair(i, j, nA, nT)) {
+                ++pairs;
+                with_dt_term += j < 2;   // these products also give A_i dT_j
+            }
+    return which == 1 ? pairs + (with_dT ? with_dt_term : 0) : pairs;
 }
 int32_t tc_max_split(const DevProblem &pb) { return (int32_t)std::min<int64_t>(148, pb.np_pad / BK); }
 
 SplitPlan tc_split_plan(const DevProblem &pb, int32_t kb_per_split)
 {
     SplitPlan p{};
-    p.rows_per_tile = BM;
-    p.other_tiles = 1;
+    p.rows_per_tile = grad_bn(pb.tc_terms);
+    p.other_tiles = tc_n_dtiles(pb);
     p.kb_total = (int32_t)(pb.np_pad / BK);
     if (kb_per_split > 0) {   // fixed split length: as many splits as that takes
         p.target_ctas = 1 << 30;
@@ -970,8 +1031,6 @@ SplitPlan tc_split_plan(const DevProblem &pb, int32_t kb_per_split)
     return p;
 }
 
-int32_t tc_grad_b_rows(const DevProblem &pb) { return (int32_t)round_up(n16_of(pb), kTcBoxRowsAT); }
-
 int64_t tc_launches_per_eval() { return 4; }
 
 cudaError_t tc_prepare_problem(DevProblem *pb, int precision, cudaStream_t st,
@@ -980,7 +1039,7 @@ cudaError_t tc_prepare_problem(DevProblem *pb, int precision, cudaStream_t st,
     if (pb->n_dwell > 512 || pb->n_struct > 8) return cudaErrorNotSupported;
     const int terms = precision == GMCO_PREC_BF16X3 ? 3 : precision == GMCO_PREC_BF16X2 ? 2 : 1;
     pb->tc_terms = terms;
-    pb->kpad = round_up(pb->n_dwell, 64);
+    pb->kpad = round_up(pb->n_dwell, BM);   // whole dwell tiles of the gradient GEMM
     const size_t n = (size_t)pb->np_pad * pb->kpad;
     for (int i = 0; i < terms; ++i) {
         cudaError_t e = alloc(reinterpret_cast<void **>(&pb->Ah[i]), n * sizeof(__nv_bfloat16));
@@ -1049,10 +1108,7 @@ TcGradProb tc_grad_prob(const DevProblem &pb, const int32_t *cnt, float *gpart, 
     d.at_row = at_row;
     d.g_row = g_row;
     d.kb = (int32_t)(pb.np_pad / BK);
-    const int n16 = n16_of(pb);
-    d.n16 = n16;
-    d.n_part0 = n16 <= 256 ? n16 : (int)round_up(ceil_div(n16, 2), 16);
-    d.n_part1 = n16 - d.n_part0;
+    d.n_dt = tc_n_dtiles(pb);
     d.nd_pad = (int32_t)pb.nd_pad;
     return d;
 }
@@ -1116,11 +1172,9 @@ TcLaunchSet tc_single_set(const DevProblem &pb, const TcBuffers &b)
     set.grad = b.d_grad;
     set.n = 1;
     set.tc_terms = pb.tc_terms;
-    set.max_b_rows_grad = tc_grad_b_rows(pb);
     set.err = b.err;
-    const int64_t ptiles = ceil_div(b.cap, BM);
-    set.max_items1 = ptiles * tc_n_ptiles(pb);
-    set.max_items2 = ptiles * b.sp.max_split;
+    set.max_items1 = ceil_div(b.cap, BM) * tc_n_ptiles(pb);
+    set.max_items2 = ceil_div(b.cap, grad_bn(pb.tc_terms)) * tc_n_dtiles(pb) * b.sp.max_split;
     return set;
 }
 

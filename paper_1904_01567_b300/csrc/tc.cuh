@@ -54,10 +54,8 @@ struct TcGradProb {
     int32_t at_row;             // first row of this problem's dwells in the A^T maps
     int32_t g_row;              // first row of its plans in the G maps
     int32_t kb;                 // K blocks of 64 points
-    int32_t n16;                // dwells rounded up to 16 (accumulator columns)
-    int32_t n_part0, n_part1;   // MMA widths: columns [0, n_part0) and [n_part0, n16)
+    int32_t n_dt;               // dwell tiles of 128 (TMEM lanes)
     int32_t nd_pad;
-    int32_t pad_;
 };
 
 // Compact per-evaluation operands of one problem (cap plan rows) and its operand maps.
@@ -92,7 +90,6 @@ struct TcLaunchSet {
     const TcGradProb *grad = nullptr;   // device array of n
     int32_t n = 0;
     int32_t tc_terms = 0;               // BF16 terms of A (all problems alike)
-    int32_t max_b_rows_grad = 0;        // largest n16 rounded to 32
     int64_t max_items1 = 1, max_items2 = 1;   // work items at full capacity (grid bound)
     int32_t *err = nullptr;
 };
@@ -102,7 +99,9 @@ int32_t tc_max_split(const DevProblem &pb);
 // Default split plan of a problem's gradient GEMM; kb_per_split > 0 fixes the number of
 // 64-point blocks per split instead.
 SplitPlan tc_split_plan(const DevProblem &pb, int32_t kb_per_split = 0);
-int32_t tc_grad_b_rows(const DevProblem &pb);
+int32_t tc_n_dtiles(const DevProblem &pb);
+// Plans per tile of the gradient GEMM (256, or 128 where a stage of 256 does not fit).
+int grad_bn(int tc_terms);
 int64_t tc_launches_per_eval();
 // MMA products per output element issued by the dose GEMM (which = 1) or gradient GEMM (2).
 double tc_mma_units(const DevProblem &pb, bool with_dT, int which);
@@ -128,7 +127,7 @@ TcRows tc_rows(const DevProblem &pb, const TcBuffers &b);
 // Operand maps over stacked buffers (rows of all problems one after another).
 bool tc_encode_map(CUtensorMap *m, const void *ptr, uint64_t cols, uint64_t rows,
                    uint32_t box_cols, uint32_t box_rows);
-constexpr int kTcBoxRowsA = 128, kTcBoxRowsT = 128, kTcBoxRowsAT = 32, kTcBoxRowsG = 128;
+constexpr int kTcBoxRowsA = 128, kTcBoxRowsT = 128, kTcBoxRowsAT = 128, kTcBoxRowsG = 128;
 constexpr int kTcBoxCols = 64;
 
 // One evaluation of the compact rows (s.list, s.n_act): prep, dose GEMM + penalty epilogue,
