@@ -147,6 +147,30 @@ __device__ __forceinline__ void mma_commit(uint32_t bar)
         : "memory");
 }
 
+// The same two, issued by one lane that elect.sync picks from the whole (converged) warp: the
+// warp computes the operands together, so they stay warp-uniform, and one lane issues.  The
+// commit elects the same lane as the MMAs it tracks (the choice depends only on the mask).
+__device__ __forceinline__ void mma_bf16_elect(uint32_t d, uint64_t a, uint64_t b, uint32_t idesc,
+                                               uint32_t accum)
+{
+    asm volatile(
+        "{\n\t.reg .pred p, e;\n\t"
+        "setp.ne.b32 p, %4, 0;\n\t"
+        "elect.sync _|e, 0xffffffff;\n\t"
+        "@e tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(d),
+        "l"(a), "l"(b), "r"(idesc), "r"(accum)
+        : "memory");
+}
+
+__device__ __forceinline__ void mma_commit_elect(uint32_t bar)
+{
+    asm volatile(
+        "{\n\t.reg .pred e;\n\t"
+        "elect.sync _|e, 0xffffffff;\n\t"
+        "@e tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];\n\t}" ::"r"(bar)
+        : "memory");
+}
+
 __device__ __forceinline__ void tmem_ld16(uint32_t taddr, uint32_t (&r)[16])
 {
     asm volatile(
@@ -443,8 +467,8 @@ __global__ void __launch_bounds__(NTHREADS, 1) k_tc(const __grid_constant__ KPar
             }
         }
     } else if (warp == W_MMA) {
-        // ---------------- MMA issuer (one thread)
-        if (lane == 0) {
+        // ---------------- MMA issuer (the whole warp walks the items; one elected lane issues)
+        {
             int it = 0, p = 0, nb = 0;
             uint32_t use[2] = {0u, 0u};   // completed uses of each accumulator buffer
             bool ok = true;
@@ -465,7 +489,8 @@ __global__ void __launch_bounds__(NTHREADS, 1) k_tc(const __grid_constant__ KPar
                     k16_total = 1 << 30;
                 }
                 const int buf = nb;
-                if (!mbar_wait(smem_u32(&acce_bar[buf]), (use[buf] & 1u) ^ 1u, kp.err, 4)) break;
+                if (!__all_sync(0xffffffffu, mbar_wait(smem_u32(&acce_bar[buf]), (use[buf] & 1u) ^ 1u, kp.err, 4)))
+                    break;
                 fence_after();
                 const uint32_t tbuf = tmem + (uint32_t)(buf * BUF_COLS);
                 for (int gi = 0; gi < kp.n_groups && ok; ++gi) {
@@ -485,7 +510,10 @@ __global__ void __launch_bounds__(NTHREADS, 1) k_tc(const __grid_constant__ KPar
                     for (int kb = kb0; kb < kb1; ++kb, ++it) {
                         const int s = it % kp.n_stages;
                         const uint32_t ph = (uint32_t)(it / kp.n_stages) & 1u;
-                        if (!mbar_wait(smem_u32(&full_bar[s]), ph, kp.err, 2)) { ok = false; break; }
+                        if (!__all_sync(0xffffffffu, mbar_wait(smem_u32(&full_bar[s]), ph, kp.err, 2))) {
+                            ok = false;   // warp-uniform
+                            break;
+                        }
                         fence_after();
                         const uint32_t st_lo = s_lo0 + (uint32_t)s * stage_lo;
                         // the first product of the item (an N = 256 one whenever any is)
@@ -500,17 +528,17 @@ __global__ void __launch_bounds__(NTHREADS, 1) k_tc(const __grid_constant__ KPar
                                 for (int q = 0; q < MAX_PAIRS; ++q) {
                                     if (q < npair) {
                                         const uint32_t accum = (fresh && k16 == 0 && q == 0) ? 0u : 1u;
-                                        mma_bf16(tbuf, DESC_FIXED | (kk + aq[q]), DESC_FIXED | (kk + bq[q]),
-                                                 iq[q], accum);
+                                        mma_bf16_elect(tbuf, DESC_FIXED | (kk + aq[q]), DESC_FIXED | (kk + bq[q]),
+                                                       iq[q], accum);
                                     }
                                 }
                             }
                         }
-                        mma_commit(smem_u32(&empty_bar[s]));   // stage free once these MMAs finish
+                        mma_commit_elect(smem_u32(&empty_bar[s]));   // stage free once these MMAs finish
                     }
                 }
                 if (!ok) break;
-                mma_commit(smem_u32(&accf_bar[buf]));   // accumulator ready for the epilogue
+                mma_commit_elect(smem_u32(&accf_bar[buf]));   // accumulator ready for the epilogue
                 ++use[buf];
                 nb = buf ^ 1;
             }
@@ -629,13 +657,13 @@ __global__ void __launch_bounds__(NTHREADS, 1) k_tc(const __grid_constant__ KPar
                             if (wdose) {
                                 wv[i] = __float_as_uint(out[i]);
                                 wv3[i] = 0u;
-                            } else {
-                                const __nv_bfloat16 b1 = __float2bfloat16_rn(out[i]);
-                                const float r1 = out[i] - __bfloat162float(b1);
-                                const __nv_bfloat16 b2 = __float2bfloat16_rn(r1);
-                                const __nv_bfloat16 b3 = __float2bfloat16_rn(r1 - __bfloat162float(b2));
-                                wv[i] = (uint32_t)__bfloat16_as_ushort(b1) | ((uint32_t)__bfloat16_as_ushort(b2) << 16);
-                                wv3[i] = (uint32_t)__bfloat16_as_ushort(b3);
+                            } else {   // terms 1 and 2 packed by one conversion; term 3 for bf16x3
+                                const float r1 = out[i] - __bfloat162float(__float2bfloat16_rn(out[i]));
+                                const __nv_bfloat162 b12 = __floats2bfloat162_rn(out[i], r1);
+                                wv[i] = *reinterpret_cast<const uint32_t *>(&b12);
+                                wv3[i] = kp.nG > 2 ? (uint32_t)__bfloat16_as_ushort(__float2bfloat16_rn(
+                                                         r1 - __bfloat162float(b12.y)))
+                                                   : 0u;
                             }
                         }
                         transpose8(wv, lane);
