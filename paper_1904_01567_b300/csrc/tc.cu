@@ -35,6 +35,7 @@ namespace {
 constexpr int BM = 128;                 // M rows per tile (TMEM lanes): points or dwells
 constexpr int BK = 64;                  // K elements per stage: 128 bytes of BF16
 constexpr int EPI_WARPS = 16;           // 4 per TMEM lane quarter
+constexpr int EPI_GROUPS = EPI_WARPS / 4;   // column groups of the epilogue
 constexpr int W_TMA = EPI_WARPS, W_MMA = EPI_WARPS + 1, W_TMEM = EPI_WARPS + 2;
 constexpr int NTHREADS = (EPI_WARPS + 3) * 32;   // epilogue, TMA, MMA, TMEM owner
 constexpr int MAX_STAGES = 4;
@@ -129,27 +130,10 @@ __device__ __forceinline__ uint32_t idesc_bf16(int n)
            ((uint32_t)(BM >> 4) << 24);
 }
 
-__device__ __forceinline__ void mma_bf16(uint32_t d, uint64_t a, uint64_t b, uint32_t idesc,
-                                         uint32_t accum)
-{
-    asm volatile(
-        "{\n\t.reg .pred p;\n\t"
-        "setp.ne.b32 p, %4, 0;\n\t"
-        "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(d),
-        "l"(a), "l"(b), "r"(idesc), "r"(accum)
-        : "memory");
-}
-
-__device__ __forceinline__ void mma_commit(uint32_t bar)
-{
-    asm volatile(
-        "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar)
-        : "memory");
-}
-
-// The same two, issued by one lane that elect.sync picks from the whole (converged) warp: the
-// warp computes the operands together, so they stay warp-uniform, and one lane issues.  The
-// commit elects the same lane as the MMAs it tracks (the choice depends only on the mask).
+// An MMA (D = A B, or D += A B when accum) and a commit of the MMAs before it to an mbarrier,
+// issued by one lane that elect.sync picks from the whole (converged) warp: the warp computes
+// the operands together, so they stay warp-uniform, and one lane issues.  The commit elects the
+// same lane as the MMAs it tracks (the choice depends only on the mask).
 __device__ __forceinline__ void mma_bf16_elect(uint32_t d, uint64_t a, uint64_t b, uint32_t idesc,
                                                uint32_t accum)
 {
@@ -565,17 +549,24 @@ __global__ void __launch_bounds__(NTHREADS, 1) k_tc(const __grid_constant__ KPar
                 const int i0 = d.chunk[c16], i1 = d.chunk[c16 + 1];
                 const int mode = i0 == i1 ? (i0 & 7) : 0;
                 const int sv = mode != 0 ? (i0 >> 3) : sv_own;
-                asm volatile("bar.sync 1, 512;" ::: "memory");   // previous item's readers done
-                if (threadIdx.x < BM) {
+                asm volatile("bar.sync 1, %0;" ::"n"(EPI_WARPS * 32) : "memory");   // previous item's readers done
+                if (threadIdx.x < BM) {   // all loads first (one round trip), then the stores
                     const int rr = threadIdx.x, rw = w.ptile * BM + rr;   // plan row of the tile
-                    for (int s2 = 0; s2 < d.n_struct; ++s2) {
-                        const float c = rw < n_rows ? d.Wc[(size_t)rw * d.n_struct + s2] : 0.0f;
-                        const float4 sp = d.sparams[s2];
-                        s_cl[s2][rr] = c * sp.x;
-                        s_ch[s2][rr] = c * sp.w;
+                    float c[8];
+                    float4 sp[8];
+#pragma unroll
+                    for (int s2 = 0; s2 < 8; ++s2) {
+                        const bool on = s2 < d.n_struct;
+                        c[s2] = on && rw < n_rows ? d.Wc[(size_t)rw * d.n_struct + s2] : 0.0f;
+                        sp[s2] = on ? d.sparams[s2] : make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+                    }
+#pragma unroll
+                    for (int s2 = 0; s2 < 8; ++s2) {
+                        s_cl[s2][rr] = c[s2] * sp[s2].x;
+                        s_ch[s2][rr] = c[s2] * sp[s2].w;
                     }
                 }
-                asm volatile("bar.sync 1, 512;" ::: "memory");
+                asm volatile("bar.sync 1, %0;" ::"n"(EPI_WARPS * 32) : "memory");
                 // warp-uniform: tcgen05.ld below is warp-collective; every named barrier of this
                 // loop is reached by all epilogue threads whatever the outcome
                 ok = __all_sync(0xffffffffu,
@@ -588,8 +579,8 @@ __global__ void __launch_bounds__(NTHREADS, 1) k_tc(const __grid_constant__ KPar
                     const float *clr = s_cl[sv < 0 ? 0 : sv], *chr = s_ch[sv < 0 ? 0 : sv];
                     constexpr int CW = 8;                  // plan columns per TMEM load
 #pragma unroll 1
-                    for (int chk = 0; chk < BM / 4 / CW; ++chk) {
-                        const int c = h * (BM / 4) + chk * CW;   // first plan column
+                    for (int chk = 0; chk < BM / EPI_GROUPS / CW; ++chk) {
+                        const int c = h * (BM / EPI_GROUPS) + chk * CW;   // first plan column
                         uint32_t dv[CW], ddv[CW];
 #pragma unroll
                         for (int i = 0; i < CW; ++i) ddv[i] = 0u;
@@ -689,7 +680,7 @@ __global__ void __launch_bounds__(NTHREADS, 1) k_tc(const __grid_constant__ KPar
                 __syncwarp();
                 if (lane == 0) asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(&acce_bar[buf])) : "memory");
                 if (!ok && lane == 0) s_fail = 1;
-                asm volatile("bar.sync 1, 512;" ::: "memory");
+                asm volatile("bar.sync 1, %0;" ::"n"(EPI_WARPS * 32) : "memory");
                 ok = s_fail == 0;   // uniform over the epilogue warps (read after the barrier)
                 if (threadIdx.x < BM && ok) {   // fixed-order sum of the four lane quarters
                     const int rr = threadIdx.x, row = w.ptile * BM + rr;
@@ -705,7 +696,7 @@ __global__ void __launch_bounds__(NTHREADS, 1) k_tc(const __grid_constant__ KPar
                 const int dw = w.dt * BM + q * 32 + lane;   // this thread's dwell
                 const bool dw_ok = dw < d.nd_pad;
                 const int ncols = w.half ? 128 : kp.bn;
-                const int cw = ncols / 4;                   // plan columns of this warp
+                const int cw = ncols / EPI_GROUPS;          // plan columns of this warp
                 ok = __all_sync(0xffffffffu,
                                 mbar_wait(smem_u32(&accf_bar[buf]), use[buf] & 1u, kp.err, 3));
                 fence_after();
