@@ -581,6 +581,7 @@ __global__ void __launch_bounds__(NTHREADS, 1) k_tc(const __grid_constant__ KPar
 #pragma unroll 1
                     for (int chk = 0; chk < BM / EPI_GROUPS / CW; ++chk) {
                         const int c = h * (BM / EPI_GROUPS) + chk * CW;   // first plan column
+                        if (w.ptile * BM + c >= n_rows) break;   // no live plan left in this warp's columns
                         uint32_t dv[CW], ddv[CW];
 #pragma unroll
                         for (int i = 0; i < CW; ++i) ddv[i] = 0u;
