@@ -88,6 +88,11 @@ typedef struct {
                               blocks of 64 points (each split's partial sums are added in a
                               fixed order); 0 (default) = chosen from the row count so that
                               about one wave of splits covers the GPU */
+    int32_t max_evals;     /* objective evaluations per plan (the first one and every
+                              line-search trial), >= 0; a plan that would exceed it stops at
+                              its last accepted point with GMCO_PLAN_MAXITER.  Every batched
+                              step evaluates each running plan once, so this bounds the
+                              steps of a solve.  0 (default) = no limit */
 } gmco_options;
 
 /* Fills *opt with the defaults above. */

@@ -142,11 +142,11 @@ void oracle_two_loop(int64_t n, int32_t m, int32_t count, int32_t newest, const 
 int oracle_lbfgs(const double *A, int64_t n_pnt, int64_t n_dwell, const int32_t *sid,
                  int32_t n_struct, const double *params, const double *w, const double *t0,
                  int32_t max_iters, double tol, int32_t m, double c1, int32_t max_ls,
-                 int32_t stop_window, double *t_out, double *F_out, int32_t *iters_out,
-                 int32_t *status_out, double *trace, int64_t *n_evals)
+                 int32_t stop_window, int32_t max_evals, double *t_out, double *F_out,
+                 int32_t *iters_out, int32_t *status_out, double *trace, int64_t *n_evals)
 {
-    if (m < 1 || m > 64 || max_ls < 1 || max_iters < 0 || stop_window < 1 || !t_out || !F_out ||
-        !iters_out || !status_out)
+    if (m < 1 || m > 64 || max_ls < 1 || max_iters < 0 || stop_window < 1 || max_evals < 0 ||
+        !t_out || !F_out || !iters_out || !status_out)
         return -1;
     const int64_t n = n_dwell;
     const size_t vb = (size_t)(n > 0 ? n : 1) * sizeof(double);
@@ -187,13 +187,17 @@ int oracle_lbfgs(const double *A, int64_t n_pnt, int64_t n_dwell, const int32_t 
         /* backtracking Armijo line search: F(x + a p) <= F + c1 a g'p, a <- a / 2 */
         double alpha = alpha0, Ft = 0.0;
         int accepted = 0;
+        int out_of_evals = 0;
         for (int32_t ls = 0; ls < max_ls; ++ls) {
+            /* evaluation budget (first evaluation and every trial), 0 = none: stop at x */
+            if (max_evals > 0 && evals >= max_evals) { out_of_evals = 1; break; }
             for (int64_t l = 0; l < n; ++l) xt[l] = x[l] + alpha * p[l];
             oracle_objective(A, n_pnt, n_dwell, sid, n_struct, params, w, xt, &Ft, gt, NULL, NULL);
             evals++;
             if (isfinite(Ft) && Ft <= F + c1 * alpha * gtp) { accepted = 1; break; }
             alpha *= 0.5;
         }
+        if (out_of_evals) { status = ORACLE_MAXITER; break; }
         if (!accepted) {
             if (count > 0) { count = 0; continue; } /* retry once with steepest descent */
             status = ORACLE_LSFAIL;
@@ -244,8 +248,8 @@ done:
 int oracle_lbfgs_batch(const double *A, int64_t n_pnt, int64_t n_dwell, const int32_t *sid,
                        int32_t n_struct, const double *params, const double *W, int64_t P,
                        const double *T0, int32_t max_iters, double tol, int32_t m, double c1,
-                       int32_t max_ls, int32_t stop_window, double *T_out, double *F_out,
-                       int32_t *iters_out, int32_t *status_out, int64_t *n_evals,
+                       int32_t max_ls, int32_t stop_window, int32_t max_evals, double *T_out,
+                       double *F_out, int32_t *iters_out, int32_t *status_out, int64_t *n_evals,
                        int32_t n_threads)
 {
     int bad = 0;
@@ -257,8 +261,8 @@ int oracle_lbfgs_batch(const double *A, int64_t n_pnt, int64_t n_dwell, const in
         int64_t ev = 0;
         int r = oracle_lbfgs(A, n_pnt, n_dwell, sid, n_struct, params, W + j * n_struct,
                              T0 ? T0 + j * n_dwell : NULL, max_iters, tol, m, c1, max_ls,
-                             stop_window, T_out + j * n_dwell, F_out + j, iters_out + j, status_out + j,
-                             NULL, &ev);
+                             stop_window, max_evals, T_out + j * n_dwell, F_out + j, iters_out + j,
+                             status_out + j, NULL, &ev);
         if (n_evals) n_evals[j] = ev;
         bad |= (r != 0);
     }

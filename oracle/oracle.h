@@ -59,20 +59,23 @@ void oracle_two_loop(int64_t n, int32_t m, int32_t count, int32_t newest, const 
  * (stop_window = 1: the single-iteration rule).
  * trace (optional, 3 x (max_iters + 1) doubles): for each accepted iteration k the
  * objective F_k, the accepted step alpha_k and the directional derivative g'p; row 0 holds
- * F_0.  n_evals counts objective evaluations.  Returns 0 or -1 on invalid arguments. */
+ * F_0.  n_evals counts objective evaluations (the first one and every line-search trial);
+ * max_evals > 0 caps them: the plan stops at its last accepted point, with the max-iteration
+ * status, where a further evaluation would exceed the cap (0 = no cap).  Returns 0 or -1 on
+ * invalid arguments. */
 int oracle_lbfgs(const double *A, int64_t n_pnt, int64_t n_dwell, const int32_t *sid,
                  int32_t n_struct, const double *params, const double *w, const double *t0,
                  int32_t max_iters, double tol, int32_t m, double c1, int32_t max_ls,
-                 int32_t stop_window, double *t_out, double *F_out, int32_t *iters_out,
-                 int32_t *status_out, double *trace, int64_t *n_evals);
+                 int32_t stop_window, int32_t max_evals, double *t_out, double *F_out,
+                 int32_t *iters_out, int32_t *status_out, double *trace, int64_t *n_evals);
 
 /* P independent plans (rows of W and T0), one plan per OpenMP thread.  T0 may be NULL.
  * n_threads <= 0 uses the OpenMP default.  Returns 0 or -1. */
 int oracle_lbfgs_batch(const double *A, int64_t n_pnt, int64_t n_dwell, const int32_t *sid,
                        int32_t n_struct, const double *params, const double *W, int64_t P,
                        const double *T0, int32_t max_iters, double tol, int32_t m, double c1,
-                       int32_t max_ls, int32_t stop_window, double *T_out, double *F_out,
-                       int32_t *iters_out, int32_t *status_out, int64_t *n_evals,
+                       int32_t max_ls, int32_t stop_window, int32_t max_evals, double *T_out,
+                       double *F_out, int32_t *iters_out, int32_t *status_out, int64_t *n_evals,
                        int32_t n_threads);
 
 /* DVH indices of one dose vector (Sec. 2.3.1 definitions), rx = prescription (Gy):

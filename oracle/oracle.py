@@ -51,11 +51,11 @@ def load():
         lib.oracle_two_loop.argtypes = [_i64, _i32, _i32, _i32, _dp, _dp, _dp, _dp, _dp]
         lib.oracle_two_loop.restype = None
         lib.oracle_lbfgs.argtypes = [_dp, _i64, _i64, _ip, _i32, _dp, _dp, _dp, _i32, _f64, _i32,
-                                     _f64, _i32, _i32, _dp, _dp, _ip, _ip, _dp, _lp]
+                                     _f64, _i32, _i32, _i32, _dp, _dp, _ip, _ip, _dp, _lp]
         lib.oracle_lbfgs.restype = ctypes.c_int
         lib.oracle_lbfgs_batch.argtypes = [_dp, _i64, _i64, _ip, _i32, _dp, _dp, _i64, _dp, _i32,
-                                           _f64, _i32, _f64, _i32, _i32, _dp, _dp, _ip, _ip, _lp,
-                                           _i32]
+                                           _f64, _i32, _f64, _i32, _i32, _i32, _dp, _dp, _ip, _ip,
+                                           _lp, _i32]
         lib.oracle_lbfgs_batch.restype = ctypes.c_int
         lib.oracle_dvh.argtypes = [_dp, _ip, _i64, _i32, _f64, _dp]
         lib.oracle_dvh.restype = None
@@ -114,8 +114,9 @@ def two_loop(S, Y, rho, count, newest, g):
 
 
 def lbfgs(A, sid, params, w, t0=None, max_iters=200, tol=1e-6, m=10, c1=1e-4, max_ls=30,
-          trace=False, stop_window=1):
-    """One plan.  Returns dict(t, F, iters, status, evals[, trace])."""
+          trace=False, stop_window=1, max_evals=0):
+    """One plan.  Returns dict(t, F, iters, status, evals[, trace]).  max_evals > 0 caps the
+    objective evaluations (the first one and every line-search trial)."""
     A = _d(A); sid = _i(sid); params = _d(params); w = _d(w)
     t0 = None if t0 is None else _d(t0)
     n = A.shape[1]
@@ -123,8 +124,8 @@ def lbfgs(A, sid, params, w, t0=None, max_iters=200, tol=1e-6, m=10, c1=1e-4, ma
     ev = np.zeros(1, np.int64)
     tr = np.full(3 * (max_iters + 1), np.nan) if trace else None
     rc = load().oracle_lbfgs(_p(A), A.shape[0], n, _p(sid, _ip), params.shape[0], _p(params),
-                             _p(w), _p(t0), max_iters, tol, m, c1, max_ls, stop_window, _p(t), _p(F),
-                             _p(it, _ip), _p(st, _ip), _p(tr), _p(ev, _lp))
+                             _p(w), _p(t0), max_iters, tol, m, c1, max_ls, stop_window, int(max_evals),
+                             _p(t), _p(F), _p(it, _ip), _p(st, _ip), _p(tr), _p(ev, _lp))
     if rc != 0:
         raise ValueError("oracle_lbfgs: invalid arguments")
     out = dict(t=t, F=float(F[0]), iters=int(it[0]), status=int(st[0]), evals=int(ev[0]))
@@ -135,7 +136,7 @@ def lbfgs(A, sid, params, w, t0=None, max_iters=200, tol=1e-6, m=10, c1=1e-4, ma
 
 
 def lbfgs_batch(A, sid, params, W, T0=None, max_iters=200, tol=1e-6, m=10, c1=1e-4, max_ls=30,
-                n_threads=0, stop_window=1):
+                n_threads=0, stop_window=1, max_evals=0):
     """P plans, one per OpenMP thread.  Returns dict(T, F, iters, status, evals)."""
     A = _d(A); sid = _i(sid); params = _d(params); W = _d(W)
     P = W.shape[0]
@@ -145,8 +146,8 @@ def lbfgs_batch(A, sid, params, W, T0=None, max_iters=200, tol=1e-6, m=10, c1=1e
     ev = np.empty(P, np.int64)
     rc = load().oracle_lbfgs_batch(_p(A), A.shape[0], n, _p(sid, _ip), params.shape[0],
                                    _p(params), _p(W), P, _p(T0), max_iters, tol, m, c1, max_ls,
-                                   stop_window, _p(T), _p(F), _p(it, _ip), _p(st, _ip), _p(ev, _lp),
-                                   int(n_threads))
+                                   stop_window, int(max_evals), _p(T), _p(F), _p(it, _ip), _p(st, _ip),
+                                   _p(ev, _lp), int(n_threads))
     if rc != 0:
         raise ValueError("oracle_lbfgs_batch: invalid arguments")
     return dict(T=T, F=F, iters=it, status=st, evals=ev)

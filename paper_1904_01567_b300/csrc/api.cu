@@ -105,12 +105,12 @@ struct gmco_problem {
 
     // cached step graphs, one per evaluation form
     struct GraphKey {
-        int32_t P = -1, form = -1, max_ls = -1, steps = -1, window = -1;
+        int32_t P = -1, form = -1, max_ls = -1, steps = -1, window = -1, max_evals = -1;
         double tol = -1, c1 = -1;
         bool operator==(const GraphKey &o) const
         {
             return P == o.P && form == o.form && max_ls == o.max_ls && steps == o.steps &&
-                   window == o.window && tol == o.tol && c1 == o.c1;
+                   window == o.window && max_evals == o.max_evals && tol == o.tol && c1 == o.c1;
         }
     };
     GraphKey gkey[2];
@@ -189,6 +189,7 @@ gmco_status ensure_workspace(gmco_problem *pr, int32_t P)
     CK(a.alloc(&s.iters, (size_t)cap)); CK(a.alloc(&s.maxit, (size_t)cap));
     CK(a.alloc(&s.ls, (size_t)cap)); CK(a.alloc(&s.hcount, (size_t)cap));
     CK(a.alloc(&s.hnewest, (size_t)cap)); CK(a.alloc(&s.nsmall, (size_t)cap));
+    CK(a.alloc(&s.nevals, (size_t)cap));
     CK(a.alloc(&s.slot_of, (size_t)cap)); CK(a.alloc(&s.cnt, 2));
     CK(a.alloc(&s.Wn, (size_t)cap * S));
     CK(a.alloc(&s.list, (size_t)cap)); CK(a.alloc(&s.n_live, 1));
@@ -373,6 +374,7 @@ gmco_status run_loop(gmco_problem *pr, int form, int32_t P, const UpdateParams &
     key.max_ls = u.max_ls;
     key.steps = steps;
     key.window = u.stop_window;
+    key.max_evals = u.max_evals;
     key.tol = u.tol;
     key.c1 = u.c1;
     if (!(pr->gkey[form] == key) || !pr->gexec[form]) {
@@ -724,7 +726,7 @@ gmco_status multi_graph(gmco_multi *m, int steps, double tol)
         m->gkey_steps == steps && m->gkey_tol == tol)
         return GMCO_OK;
     multi_destroy_graph(m);
-    const UpdateParams u{m->opt.c1, tol, m->opt.max_ls, m->opt.stop_window};
+    const UpdateParams u{m->opt.c1, tol, m->opt.max_ls, m->opt.stop_window, m->opt.max_evals};
     cudaGraph_t g = nullptr;
     CK(cudaStreamBeginCapture(m->stream, cudaStreamCaptureModeThreadLocal));
     cudaError_t e = cudaSuccess;
@@ -822,6 +824,7 @@ void gmco_default_options(gmco_options *opt)
     opt->refine_iters = 0;
     opt->steps_per_poll = 16;
     opt->stop_window = 1;
+    opt->max_evals = 0;
     opt->grad_split_kb = 0;
 }
 
@@ -858,7 +861,7 @@ gmco_status gmco_create_problem(const float *A, int64_t n_pnt, int64_t n_dwell,
     if (o.precision < 0 || o.precision > 4 || o.m < 1 || o.m > kMaxHist || !(o.c1 > 0.0) ||
         !(o.c1 < 1.0) || o.max_ls < 1 || o.max_ls > 60 || !(o.rx_gy > 0.0) ||
         !isfinite(o.rx_gy) || o.refine_iters < 0 || o.steps_per_poll < 1 ||
-        o.steps_per_poll > 1024 || o.stop_window < 1 || o.grad_split_kb < 0) {
+        o.steps_per_poll > 1024 || o.stop_window < 1 || o.grad_split_kb < 0 || o.max_evals < 0) {
         set_error_msg("gmco_create_problem: bad options");
         return GMCO_EINVAL;
     }
@@ -1046,7 +1049,7 @@ gmco_status gmco_solve_batch(gmco_problem *pr, const float *penalty_weights, int
 
     CK(launch_solver_init(s, pb, pr->dW, t0 ? pr->dT0 : nullptr, max_iters, pr->stream));
     pr->launches++;
-    UpdateParams u{pr->opt.c1, tol, pr->opt.max_ls, pr->opt.stop_window};
+    UpdateParams u{pr->opt.c1, tol, pr->opt.max_ls, pr->opt.stop_window, pr->opt.max_evals};
     const int form = pr->opt.precision == GMCO_PREC_FP32 ? 0 : 1;
     const int64_t budget = ((int64_t)max_iters + pr->opt.refine_iters + 1) * (pr->opt.max_ls + 1) + 4;
     int64_t steps = 0;
@@ -1330,7 +1333,8 @@ gmco_status gmco_create_multi(gmco_problem *const *probs, int32_t n, gmco_multi 
         }
         const gmco_options &q = pr->opt;
         if (q.precision != o.precision || q.m != o.m || q.c1 != o.c1 || q.max_ls != o.max_ls ||
-            q.stop_window != o.stop_window || q.steps_per_poll != o.steps_per_poll ||
+            q.stop_window != o.stop_window || q.max_evals != o.max_evals ||
+            q.steps_per_poll != o.steps_per_poll ||
             pr->device != probs[0]->device) {
             set_error_msg("gmco_create_multi: problems differ in precision, solver options or device");
             return GMCO_EINVAL;

@@ -90,6 +90,7 @@ struct SolverState {
     int32_t *state = nullptr, *status = nullptr, *iters = nullptr, *maxit = nullptr;
     int32_t *ls = nullptr, *hcount = nullptr, *hnewest = nullptr;
     int32_t *nsmall = nullptr;          // consecutive iterations below the stop tolerance
+    int32_t *nevals = nullptr;          // objective evaluations so far
     int32_t *slot_of = nullptr;         // compact row of each plan in the current evaluation
     int32_t *cnt = nullptr;             // 2 counters: rows of even and odd steps
     float *Wn = nullptr;                // P x n_struct, w / N_s
@@ -126,6 +127,7 @@ struct UpdateParams {
     double c1, tol;
     int32_t max_ls;
     int32_t stop_window;
+    int32_t max_evals;               // evaluations per plan, 0 = no limit
 };
 
 // ---- launchers (return cudaError_t of the launch) ----

@@ -69,6 +69,7 @@ __global__ void k_solver_init(SolverState s, const float *__restrict__ W,
         s.hcount[j] = 0;
         s.hnewest[j] = s.m - 1;
         s.nsmall[j] = 0;
+        s.nevals[j] = 0;
         s.F[j] = 0.0;
         s.Ft[j] = 0.0;
         s.dFt[j] = 0.0;
@@ -290,12 +291,14 @@ __device__ __forceinline__ void step_plan(const SolverState &s, const UpdatePara
     const double alpha_old = s.alpha[j], gtp_old = s.gtp[j];
     const int ls_old = s.ls[j];
     const int maxit = s.maxit[j];
+    const int ne = s.nevals[j] + 1;   // this evaluation included
     const int slot = s.slot_of[j];
     const int R = *a.rows_cur;
     double rho_l = lane < m ? s.rho[(size_t)j * m + lane] : 0.0;   // lane i: rho of slot i
     double gam = s.gamma[j];
     __syncwarp();
     if (st != ST_INIT && st != ST_TRIAL) return;
+    if (lane == 0) s.nevals[j] = ne;
     float *x = s.x + vb, *g = s.g + vb, *p = s.p + vb;
     const float *xt = s.xt + vb;
     float xv[EPL], pv[EPL], gov[EPL], xtv[EPL];
@@ -496,7 +499,11 @@ __device__ __forceinline__ void step_plan(const SolverState &s, const UpdatePara
             }
         }
     }
-    if (need_dir && it >= maxit) { plan_done(s, j, GMCO_PLAN_MAXITER, lane); return; }
+    // iteration cap, or the evaluation budget (the next trial would exceed it): stop at x
+    if ((need_dir && it >= maxit) || (u.max_evals > 0 && ne >= u.max_evals)) {
+        plan_done(s, j, GMCO_PLAN_MAXITER, lane);
+        return;
+    }
 
     // the plan runs on: claim its row of the next step now, so that the atomic's round trip
     // overlaps the two-loop below
@@ -714,6 +721,7 @@ __global__ void k_reopen(SolverState s, int32_t extra)
         s.status[j] = GMCO_PLAN_MAXITER;
         s.maxit[j] = s.iters[j] + extra;
         s.nsmall[j] = 0;
+        s.nevals[j] = 0;   // the refinement has its own evaluation budget
     }
 }
 

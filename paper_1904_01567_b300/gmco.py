@@ -34,7 +34,8 @@ class _Options(ctypes.Structure):
     _fields_ = [("precision", ctypes.c_int32), ("m", ctypes.c_int32), ("c1", ctypes.c_double),
                 ("max_ls", ctypes.c_int32), ("rx_gy", ctypes.c_double),
                 ("refine_iters", ctypes.c_int32), ("steps_per_poll", ctypes.c_int32),
-                ("stop_window", ctypes.c_int32), ("grad_split_kb", ctypes.c_int32)]
+                ("stop_window", ctypes.c_int32), ("grad_split_kb", ctypes.c_int32),
+                ("max_evals", ctypes.c_int32)]
 
 
 _lib = None

@@ -105,6 +105,22 @@ def test_first_iterations_follow_oracle(gmco_mod, oracle_mod, small, prob_fp32):
             assert np.allclose(out["T"][j], r["t"], rtol=1e-4, atol=1e-6)
 
 
+
+def test_evaluation_budget_follows_oracle(gmco_mod, oracle_mod, small):
+    """max_evals: every plan stops after the same evaluations and iterations as the oracle with
+    the same budget, at the same point."""
+    p, W = small
+    for cap in (1, 5):
+        with gmco_mod.Problem(p.A, p.sid, p.params, precision="fp32", max_evals=cap) as pr:
+            out = pr.solve_batch(W, max_iters=100, tol=0.0)
+        for j in range(8):
+            r = oracle_mod.lbfgs(p.A, p.sid, p.params, W[j], None, max_iters=100, tol=0.0,
+                                 max_evals=cap)
+            assert out["status"][j] == r["status"] == oracle_mod.MAXITER
+            assert out["iters"][j] == r["iters"]
+            assert abs(out["objectives"][j] / r["F"] - 1.0) <= 1e-5
+            assert np.allclose(out["T"][j], r["t"], rtol=1e-4, atol=1e-6)
+
 def test_zero_objective_start(gmco_mod, small):
     p, W = small
     d0 = p.A.astype(np.float64) @ np.ones(p.n_dwell)

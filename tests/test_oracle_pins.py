@@ -272,6 +272,25 @@ def test_max_iters_zero_and_status(oracle_mod):
     assert r["status"] == oracle_mod.NONFINITE
 
 
+
+def test_evaluation_budget_stops_on_the_same_path(oracle_mod):
+    """max_evals bounds the objective evaluations (the first one and every line-search trial):
+    the capped run takes exactly the uncapped run's path and stops at its last accepted point
+    once the next trial would exceed the budget."""
+    p, W, _ = workload("prostate-2k-8plans")
+    runs = [oracle_mod.lbfgs(p.A, p.sid, p.params, W[j], None, max_iters=150, tol=0.0, trace=True)
+            for j in range(8)]
+    j = int(np.argmax([r["evals"] - r["iters"] for r in runs]))
+    full = runs[j]
+    assert full["evals"] > full["iters"] + 1          # this path has rejected trials
+    for cap in (1, 2, 9, 40, full["evals"] - 1, full["evals"]):
+        r = oracle_mod.lbfgs(p.A, p.sid, p.params, W[j], None, max_iters=150, tol=0.0, max_evals=cap)
+        assert r["evals"] == cap and r["status"] == oracle_mod.MAXITER
+        assert r["F"] == full["trace"][r["iters"], 0]
+        assert r["iters"] <= cap - 1
+    r = oracle_mod.lbfgs(p.A, p.sid, p.params, W[j], None, max_iters=150, tol=0.0, max_evals=0)
+    assert r["evals"] == full["evals"] and r["F"] == full["F"]
+
 # ---------------------------------------------------------------- DVH indices
 def test_dvh_hand_made(oracle_mod):
     pro = np.arange(2.0, 21.0, 2.0)            # 2, 4, ..., 20 (N = 10)
