@@ -589,6 +589,46 @@ __global__ void __launch_bounds__(NTHREADS, 1) k_tc(const __grid_constant__ KPar
                         if (has_dT) tmem_ld8(lane_addr + (uint32_t)(BM + c), ddv);
                         tmem_ld_wait_regs8(dv, ddv);
                         float out[CW], fv[CW], dfv[CW];
+                        if ((mode == 1 || mode == 2) && !wdose) {
+                            // one structure with one bound (warp-uniform): pairs of plan columns in
+                            // packed FP32x2 arithmetic.  With s = +1 (lower bound) or -1 (upper):
+                            // v = max(s (bound - d), 0), f = c v^2, dF/dd = -2 s c v, and the
+                            // dose change's part f(d) - f(d - dd) = c dv (v + v_b), where dv is
+                            // -s dd when both v, v_b > 0 and v - v_b otherwise (no cancellation)
+                            const float sg = mode == 1 ? 1.0f : -1.0f;
+                            const float bnd = mode == 1 ? lo : hi;
+                            const float2 a2 = make_float2(-sg * sc, -sg * sc), b2 = make_float2(sg * bnd, sg * bnd);
+                            const float2 s2 = make_float2(sg * sc, sg * sc), g2 = make_float2(-2.0f * sg * sc, -2.0f * sg * sc);
+                            const float *wrow = mode == 1 ? clr : chr;
+#pragma unroll
+                            for (int i = 0; i < CW; i += 2) {
+                                const float2 acc = make_float2(__uint_as_float(dv[i]), __uint_as_float(dv[i + 1]));
+                                const float2 cw = *reinterpret_cast<const float2 *>(wrow + c + i);
+                                const float2 t = __ffma2_rn(a2, acc, b2);   // s (bound - d)
+                                const float2 v = make_float2(fmaxf(t.x, 0.0f), fmaxf(t.y, 0.0f));
+                                const float2 cv = __fmul2_rn(cw, v);
+                                const float2 fq = __fmul2_rn(cv, v);
+                                const float2 gq = __fmul2_rn(g2, cv);
+                                fv[i] = fq.x;
+                                fv[i + 1] = fq.y;
+                                out[i] = gq.x;
+                                out[i + 1] = gq.y;
+                                dfv[i] = 0.0f;
+                                dfv[i + 1] = 0.0f;
+                                if (has_dT) {
+                                    const float2 dacc = make_float2(__uint_as_float(ddv[i]), __uint_as_float(ddv[i + 1]));
+                                    const float2 tb = __ffma2_rn(s2, dacc, t);   // s (bound - (d - dd))
+                                    const float2 vb = make_float2(fmaxf(tb.x, 0.0f), fmaxf(tb.y, 0.0f));
+                                    const float2 sdd = __fmul2_rn(s2, dacc);     // s dd
+                                    const float2 dif = __fadd2_rn(v, make_float2(-vb.x, -vb.y));
+                                    const float2 dl = make_float2((v.x > 0.0f && vb.x > 0.0f) ? -sdd.x : dif.x,
+                                                                  (v.y > 0.0f && vb.y > 0.0f) ? -sdd.y : dif.y);
+                                    const float2 dq = __fmul2_rn(__fmul2_rn(cw, dl), __fadd2_rn(v, vb));
+                                    dfv[i] = dq.x;
+                                    dfv[i + 1] = dq.y;
+                                }
+                            }
+                        } else {
 #pragma unroll
                         for (int i = 0; i < CW; ++i) {
                             const float dd0 = sc * __uint_as_float(dv[i]);
@@ -631,6 +671,7 @@ __global__ void __launch_bounds__(NTHREADS, 1) k_tc(const __grid_constant__ KPar
                             fv[i] = f;
                             dfv[i] = df;
                             out[i] = wdose ? dd0 : gval;
+                        }
                         }
                         // per plan column: sum over this warp's 32 points, then over the lane
                         // quarters below (fixed order)
