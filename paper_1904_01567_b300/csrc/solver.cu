@@ -23,22 +23,25 @@ namespace {
 
 constexpr unsigned kFull = 0xffffffffu;
 
+// Warp reductions as XOR butterflies: every lane ends with the same value (lanes L and L ^ o
+// add the same two operands, and addition is commutative), one shuffle fewer than a down-sweep
+// plus a broadcast, which matters on the step's serial chains.
 __device__ __forceinline__ float warp_sum_f(float v)
 {
-    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(kFull, v, o);
-    return __shfl_sync(kFull, v, 0);
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(kFull, v, o);
+    return v;
 }
 
 __device__ __forceinline__ double warp_sum_d(double v)
 {
-    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(kFull, v, o);
-    return __shfl_sync(kFull, v, 0);
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(kFull, v, o);
+    return v;
 }
 
 __device__ __forceinline__ float warp_max_f(float v)
 {
-    for (int o = 16; o > 0; o >>= 1) v = fmaxf(v, __shfl_down_sync(kFull, v, o));
-    return __shfl_sync(kFull, v, 0);
+    for (int o = 16; o > 0; o >>= 1) v = fmaxf(v, __shfl_xor_sync(kFull, v, o));
+    return v;
 }
 
 __global__ void k_solver_init(SolverState s, const float *__restrict__ W,
@@ -550,10 +553,13 @@ __device__ __forceinline__ void step_plan(const SolverState &s, const UpdatePara
                     yn[e] = (more && e < epl) ? Yn[lane + 32 * e] : 0.0f;
                 }
                 const float rho = (float)__shfl_sync(kFull, rho_l, i);
-                float d = 0.0f;
+                float d0 = 0.0f, d1 = 0.0f;   // two partial sums: half the dependent chain
 #pragma unroll
-                for (int e = 0; e < EPL; ++e) d += sc[e] * q[e];
-                const float av = rho * warp_sum_f(d);
+                for (int e = 0; e < EPL; e += 2) {
+                    d0 += sc[e] * q[e];
+                    if (e + 1 < EPL) d1 += sc[e + 1] * q[e + 1];
+                }
+                const float av = rho * warp_sum_f(d0 + d1);
                 if (lane == k) al_l = av;
 #pragma unroll
                 for (int e = 0; e < EPL; ++e) {
@@ -590,10 +596,13 @@ __device__ __forceinline__ void step_plan(const SolverState &s, const UpdatePara
                 }
                 const float rho = (float)__shfl_sync(kFull, rho_l, i);
                 const float alk = __shfl_sync(kFull, al_l, k);
-                float d = 0.0f;
+                float d0 = 0.0f, d1 = 0.0f;
 #pragma unroll
-                for (int e = 0; e < EPL; ++e) d += yc[e] * q[e];
-                const float b = rho * warp_sum_f(d);
+                for (int e = 0; e < EPL; e += 2) {
+                    d0 += yc[e] * q[e];
+                    if (e + 1 < EPL) d1 += yc[e + 1] * q[e + 1];
+                }
+                const float b = rho * warp_sum_f(d0 + d1);
 #pragma unroll
                 for (int e = 0; e < EPL; ++e) {
                     q[e] += sc[e] * (alk - b);
