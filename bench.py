@@ -271,7 +271,8 @@ def sha1_of(path):
 
 def multi_patient_section(g, torch, args, peak):
     """64 uneven patients x 256 plans solved together (one dose GEMM, one gradient GEMM and
-    one update launch per step for all patients), split length from the autotuner."""
+    one update launch per step for all patients), tiles (gradient split length and plan
+    tile) from the autotuner."""
     from synth import make_patient, multi_patient_specs, weights_dirichlet
     t0 = time.perf_counter()
     specs = multi_patient_specs(64)
@@ -282,8 +283,8 @@ def multi_patient_section(g, torch, args, peak):
     probs = [g.Problem(p.A, p.sid, p.params, precision=args.precision,
                        steps_per_poll=args.steps_per_poll) for p in pats]
     mu = g.Multi(probs)
-    cands = (0, 8, 16, 32, 64)
-    best, ms = mu.autotune(Ws, steps=8, candidates=cands)
+    cands = tuple((kb, tile) for tile in (0, 128) for kb in (0, 8, 16, 32, 64))
+    best, ms = mu.autotune_tiles(Ws, steps=8, candidates=cands)
     Wd = [torch.from_numpy(W).cuda() for W in Ws]
     stream = torch.cuda.current_stream()
     mu.solve(Wd, max_iters=500, tol=1e-6, stream=stream, want=("iters",))   # warm-up
@@ -313,8 +314,9 @@ def multi_patient_section(g, torch, args, peak):
         "iters": {"mean": float(iters.mean()), "max": int(iters.max()),
                   "status_counts": {int(k): int(np.sum(status == k)) for k in np.unique(status)}},
         "gpu_launches": int(launches), "launches_per_step": 3,
-        "autotune": {"candidates_split_kb": list(cands), "ms_per_step": [ms[c] for c in cands],
-                     "chosen_split_kb": best},
+        "autotune": {"candidates_split_kb_plan_tile": [list(c) for c in cands],
+                     "ms_per_step": [ms[c] for c in cands], "chosen": list(best),
+                     "note": "plan tile 0 = 256 plans per gradient-GEMM tile (the bf16x2 default)"},
         "full_step": {"ms": step_ms, "algorithmic_tflops": achieved,
                       "frac_of_bf16_peak": achieved / peak if peak else None,
                       "algorithmic_flops": 3.0 * flop_unit},

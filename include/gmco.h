@@ -93,6 +93,9 @@ typedef struct {
                               its last accepted point with GMCO_PLAN_MAXITER.  Every batched
                               step evaluates each running plan once, so this bounds the
                               steps of a solve.  0 (default) = no limit */
+    int32_t grad_plan_tile;/* tensor-core forms: plans per gradient-GEMM tile, 128 or 256 (one
+                              MMA of N = 256 per product where a stage of 256 fits), or 0
+                              (default) for 256 where it fits, else 128 */
 } gmco_options;
 
 /* Fills *opt with the defaults above. */
@@ -212,6 +215,12 @@ void gmco_destroy_multi(gmco_multi *multi);
 gmco_status gmco_multi_set_split(gmco_multi *multi, int32_t split_kb);
 int32_t gmco_multi_get_split(const gmco_multi *multi);
 
+/* The launch's tiles: split length as above and plans per gradient-GEMM tile (0, 128 or 256 as
+ * gmco_options.grad_plan_tile; the problems' option is the initial value).  get returns the
+ * requested tile (0 = the default). */
+gmco_status gmco_multi_set_tiles(gmco_multi *multi, int32_t split_kb, int32_t grad_plan_tile);
+int32_t gmco_multi_get_grad_tile(const gmco_multi *multi);
+
 /* Solves every patient's plans.  All arrays have n entries (host arrays of pointers); entry p
  * has the meaning and size of the same argument of gmco_solve_batch for patient p with P[p]
  * plans (P[p] >= 1).  t0 may be NULL (uniform start for everyone) and so may any output
@@ -230,6 +239,13 @@ gmco_status gmco_solve_multi(gmco_multi *multi, const float *const *penalty_weig
 gmco_status gmco_multi_autotune(gmco_multi *multi, const float *const *penalty_weights,
                                 const int64_t *P, int32_t steps, const int32_t *candidates,
                                 int32_t n_candidates, double *ms_per_step, int32_t *best);
+
+/* The same over tile configurations: candidate i is (split_kb[i], grad_plan_tile[i]) as for
+ * gmco_multi_set_tiles.  Selects the fastest and returns its index in *best_index. */
+gmco_status gmco_multi_autotune_tiles(gmco_multi *multi, const float *const *penalty_weights,
+                                      const int64_t *P, int32_t steps, const int32_t *split_kb,
+                                      const int32_t *grad_plan_tile, int32_t n_candidates,
+                                      double *ms_per_step, int32_t *best_index);
 
 /* Kernel launches made by the most recent gmco_solve_multi call. */
 int64_t gmco_multi_last_launch_count(const gmco_multi *multi);

@@ -205,11 +205,11 @@ gmco_status ensure_workspace(gmco_problem *pr, int32_t P)
     CK(a.alloc(&pr->dFpart, (size_t)nparts * cap));
     int64_t grows = max_split_rows(simt_split_plan(pb), cap);
     if (pr->opt.precision != GMCO_PREC_FP32)
-        grows = std::max(grows, max_split_rows(tc_split_plan(pb, pr->opt.grad_split_kb), cap));
+        grows = std::max(grows, max_split_rows(tc_split_plan(pb, pr->opt.grad_split_kb, pr->opt.grad_plan_tile), cap));
     CK(a.alloc(&pr->gpart, (size_t)grows * pb.nd_pad));
     if (pr->opt.precision != GMCO_PREC_FP32) {
         cudaError_t e = tc_alloc(pb, cap, pr->Fpart, pr->dFpart, pr->gpart, pr->G, s.cnt,
-                                 pr->opt.grad_split_kb, &pr->tcb, [&](void **p, size_t bytes) {
+                                 pr->opt.grad_split_kb, pr->opt.grad_plan_tile, &pr->tcb, [&](void **p, size_t bytes) {
                                      unsigned char *q = nullptr;
                                      cudaError_t r = a.alloc(&q, bytes);
                                      *p = q;
@@ -478,6 +478,7 @@ struct gmco_multi {
     int32_t n = 0;
     int32_t tc_terms = 0;
     int32_t split_kb = 16;
+    int32_t grad_tile = 0;         // plans per gradient-GEMM tile (0 = the precision's default)
     gmco_options opt{};
     cudaStream_t stream = nullptr;
     cudaEvent_t ev_in = nullptr, ev_out = nullptr;
@@ -491,7 +492,7 @@ struct gmco_multi {
     int32_t *err = nullptr;
     // workspace of the current batch shape
     std::vector<int64_t> caps, gens;
-    int32_t ws_split = -1;
+    int32_t ws_split = -1, ws_tile = -1;
     std::vector<int64_t> t_row;
     std::vector<SolverState> st;   // each patient's state, P = its plans
     __nv_bfloat16 *T[3] = {nullptr, nullptr, nullptr}, *dT[2] = {nullptr, nullptr};
@@ -506,7 +507,7 @@ struct gmco_multi {
     int32_t *d_sum = nullptr;
     // cached step graph
     std::vector<int64_t> gkey_caps;
-    int32_t gkey_split = -1, gkey_steps = -1;
+    int32_t gkey_split = -1, gkey_steps = -1, gkey_tile = -1;
     double gkey_tol = -1.0;
     cudaGraphExec_t gexec = nullptr;
     int64_t launches = 0;
@@ -529,7 +530,8 @@ gmco_status multi_workspace(gmco_multi *m, const std::vector<int64_t> &P)
         CKS(ensure_workspace(m->probs[p], (int32_t)P[p]));
         gens[p] = m->probs[p]->ws_gen;
     }
-    if (m->caps == P && m->gens == gens && m->ws_split == m->split_kb) return GMCO_OK;
+    if (m->caps == P && m->gens == gens && m->ws_split == m->split_kb && m->ws_tile == m->grad_tile)
+        return GMCO_OK;
     CK(cudaStreamSynchronize(m->stream));
     multi_destroy_graph(m);
     m->ws.release();
@@ -558,6 +560,7 @@ gmco_status multi_workspace(gmco_multi *m, const std::vector<int64_t> &P)
     bool ok = true;
     TcLaunchSet &set = m->set;
     set = TcLaunchSet{};
+    set.grad_tile = grad_bn(m->tc_terms, m->grad_tile);
     for (int i = 0; i < m->tc_terms; ++i) {
         ok = ok && tc_encode_map(&set.maps1.m[i], m->Ah[i], m->kpad_max, m->rows_A, kTcBoxCols, kTcBoxRowsA);
         ok = ok && tc_encode_map(&set.maps2.m[i], m->AhT[i], m->np_max, m->rows_AT, kTcBoxCols, kTcBoxRowsAT);
@@ -594,7 +597,7 @@ gmco_status multi_workspace(gmco_multi *m, const std::vector<int64_t> &P)
         const int32_t npt = tc_n_ptiles(pb);
         CK(a.alloc(&Fpart, (size_t)npt * cap));
         CK(a.alloc(&dFpart, (size_t)npt * cap));
-        const SplitPlan sp = tc_split_plan(pb, m->split_kb);
+        const SplitPlan sp = tc_split_plan(pb, m->split_kb, m->grad_tile);
         CK(a.alloc(&gpart, (size_t)max_split_rows(sp, cap) * pb.nd_pad));
         float *Wc = m->Wc + woff;
         woff += (int64_t)cap * pb.n_struct;
@@ -605,7 +608,7 @@ gmco_status multi_workspace(gmco_multi *m, const std::vector<int64_t> &P)
                              (int32_t)m->t_row[p], cap, (int32_t)m->np_max);
         gp[p] = tc_grad_prob(pb, s.cnt, gpart, sp, (int32_t)m->at_row[p], (int32_t)m->t_row[p]);
         set.max_items1 += ceil_div(cap, 128) * npt;
-        set.max_items2 += ceil_div(cap, grad_bn(pb.tc_terms)) * tc_n_dtiles(pb) * sp.max_split;
+        set.max_items2 += ceil_div(cap, grad_bn(pb.tc_terms, m->grad_tile)) * tc_n_dtiles(pb) * sp.max_split;
         for (int par = 0; par < 2; ++par) {
             StepDesc &d = sd[(size_t)par * n + p];
             d.s = s;
@@ -655,6 +658,7 @@ gmco_status multi_workspace(gmco_multi *m, const std::vector<int64_t> &P)
     m->caps = P;
     m->gens = gens;
     m->ws_split = m->split_kb;
+    m->ws_tile = m->grad_tile;
     return GMCO_OK;
 }
 
@@ -722,7 +726,7 @@ gmco_status multi_start(gmco_multi *m, const float *const *W, const float *const
 // step's counters), gradient GEMM, fused update.
 gmco_status multi_graph(gmco_multi *m, int steps, double tol)
 {
-    if (m->gexec && m->gkey_caps == m->caps && m->gkey_split == m->split_kb &&
+    if (m->gexec && m->gkey_caps == m->caps && m->gkey_split == m->split_kb && m->gkey_tile == m->grad_tile &&
         m->gkey_steps == steps && m->gkey_tol == tol)
         return GMCO_OK;
     multi_destroy_graph(m);
@@ -749,6 +753,7 @@ gmco_status multi_graph(gmco_multi *m, int steps, double tol)
     CK(ei);
     m->gkey_caps = m->caps;
     m->gkey_split = m->split_kb;
+    m->gkey_tile = m->grad_tile;
     m->gkey_steps = steps;
     m->gkey_tol = tol;
     return GMCO_OK;
@@ -825,6 +830,7 @@ void gmco_default_options(gmco_options *opt)
     opt->steps_per_poll = 16;
     opt->stop_window = 1;
     opt->max_evals = 0;
+    opt->grad_plan_tile = 0;
     opt->grad_split_kb = 0;
 }
 
@@ -861,7 +867,8 @@ gmco_status gmco_create_problem(const float *A, int64_t n_pnt, int64_t n_dwell,
     if (o.precision < 0 || o.precision > 4 || o.m < 1 || o.m > kMaxHist || !(o.c1 > 0.0) ||
         !(o.c1 < 1.0) || o.max_ls < 1 || o.max_ls > 60 || !(o.rx_gy > 0.0) ||
         !isfinite(o.rx_gy) || o.refine_iters < 0 || o.steps_per_poll < 1 ||
-        o.steps_per_poll > 1024 || o.stop_window < 1 || o.grad_split_kb < 0 || o.max_evals < 0) {
+        o.steps_per_poll > 1024 || o.stop_window < 1 || o.grad_split_kb < 0 || o.max_evals < 0 ||
+        (o.grad_plan_tile != 0 && o.grad_plan_tile != 128 && o.grad_plan_tile != 256)) {
         set_error_msg("gmco_create_problem: bad options");
         return GMCO_EINVAL;
     }
@@ -1334,6 +1341,7 @@ gmco_status gmco_create_multi(gmco_problem *const *probs, int32_t n, gmco_multi 
         const gmco_options &q = pr->opt;
         if (q.precision != o.precision || q.m != o.m || q.c1 != o.c1 || q.max_ls != o.max_ls ||
             q.stop_window != o.stop_window || q.max_evals != o.max_evals ||
+            q.grad_plan_tile != o.grad_plan_tile ||
             q.steps_per_poll != o.steps_per_poll ||
             pr->device != probs[0]->device) {
             set_error_msg("gmco_create_multi: problems differ in precision, solver options or device");
@@ -1342,6 +1350,7 @@ gmco_status gmco_create_multi(gmco_problem *const *probs, int32_t n, gmco_multi 
     }
     gmco_multi *m = new gmco_multi();
     m->device = probs[0]->device;
+    m->grad_tile = o.grad_plan_tile;
     m->probs.assign(probs, probs + n);
     m->n = n;
     m->opt = o;
@@ -1429,6 +1438,19 @@ gmco_status gmco_multi_set_split(gmco_multi *m, int32_t split_kb)
 
 int32_t gmco_multi_get_split(const gmco_multi *m) { return m ? m->split_kb : -1; }
 
+gmco_status gmco_multi_set_tiles(gmco_multi *m, int32_t split_kb, int32_t grad_plan_tile)
+{
+    if (!m || split_kb < 0 || (grad_plan_tile != 0 && grad_plan_tile != 128 && grad_plan_tile != 256)) {
+        set_error_msg("gmco_multi_set_tiles: bad arguments");
+        return GMCO_EINVAL;
+    }
+    m->split_kb = split_kb;
+    m->grad_tile = grad_plan_tile;
+    return GMCO_OK;
+}
+
+int32_t gmco_multi_get_grad_tile(const gmco_multi *m) { return m ? m->grad_tile : -1; }
+
 int64_t gmco_multi_last_launch_count(const gmco_multi *m) { return m ? m->launches : -1; }
 
 gmco_status gmco_solve_multi(gmco_multi *m, const float *const *penalty_weights,
@@ -1493,32 +1515,36 @@ gmco_status gmco_solve_multi(gmco_multi *m, const float *const *penalty_weights,
     return rs;
 }
 
-gmco_status gmco_multi_autotune(gmco_multi *m, const float *const *penalty_weights,
-                                const int64_t *P, int32_t steps, const int32_t *candidates,
-                                int32_t n_candidates, double *ms_per_step, int32_t *best)
+gmco_status gmco_multi_autotune_tiles(gmco_multi *m, const float *const *penalty_weights,
+                                      const int64_t *P, int32_t steps, const int32_t *split_kb,
+                                      const int32_t *grad_plan_tile, int32_t n_candidates,
+                                      double *ms_per_step, int32_t *best_index)
 {
     std::vector<int64_t> Pv;
     CKS(multi_args(m, penalty_weights, P, &Pv, "gmco_multi_autotune"));
-    if (!candidates || n_candidates < 1 || n_candidates > 64 || steps < 2 || steps > 1024) {
+    if (!split_kb || !grad_plan_tile || n_candidates < 1 || n_candidates > 64 || steps < 2 ||
+        steps > 1024) {
         set_error_msg("gmco_multi_autotune: bad arguments");
         return GMCO_EINVAL;
     }
     for (int c = 0; c < n_candidates; ++c)
-        if (candidates[c] < 0) {
-            set_error_msg("gmco_multi_autotune: negative candidate");
+        if (split_kb[c] < 0 ||
+            (grad_plan_tile[c] != 0 && grad_plan_tile[c] != 128 && grad_plan_tile[c] != 256)) {
+            set_error_msg("gmco_multi_autotune: bad candidate");
             return GMCO_EINVAL;
         }
     CK(cudaSetDevice(m->device));
     const int st = (int)round_up(steps, 2);
-    const int32_t saved = m->split_kb;
+    const int32_t saved_split = m->split_kb, saved_tile = m->grad_tile;
     cudaEvent_t e0 = nullptr, e1 = nullptr;
     CK(cudaEventCreate(&e0));
     CK(cudaEventCreate(&e1));
     gmco_status rs = GMCO_OK;
     double best_ms = INFINITY;
-    int32_t best_c = saved;
+    int32_t best_c = -1;
     for (int c = 0; c < n_candidates && rs == GMCO_OK; ++c) {
-        m->split_kb = candidates[c];
+        m->split_kb = split_kb[c];
+        m->grad_tile = grad_plan_tile[c];
         if ((rs = multi_workspace(m, Pv)) != GMCO_OK) break;
         if ((rs = multi_graph(m, st, 0.0)) != GMCO_OK) break;
         float ms = 0.0f;
@@ -1540,13 +1566,35 @@ gmco_status gmco_multi_autotune(gmco_multi *m, const float *const *penalty_weigh
         if (ms_per_step) ms_per_step[c] = per;
         if (per < best_ms) {
             best_ms = per;
-            best_c = candidates[c];
+            best_c = c;
         }
     }
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
-    m->split_kb = rs == GMCO_OK ? best_c : saved;
-    if (rs == GMCO_OK && best) *best = best_c;
+    if (rs == GMCO_OK && best_c >= 0) {
+        m->split_kb = split_kb[best_c];
+        m->grad_tile = grad_plan_tile[best_c];
+        if (best_index) *best_index = best_c;
+    } else {
+        m->split_kb = saved_split;
+        m->grad_tile = saved_tile;
+    }
+    return rs;
+}
+
+gmco_status gmco_multi_autotune(gmco_multi *m, const float *const *penalty_weights,
+                                const int64_t *P, int32_t steps, const int32_t *candidates,
+                                int32_t n_candidates, double *ms_per_step, int32_t *best)
+{
+    if (!m || !candidates || n_candidates < 1 || n_candidates > 64) {
+        set_error_msg("gmco_multi_autotune: bad arguments");
+        return GMCO_EINVAL;
+    }
+    const std::vector<int32_t> tiles((size_t)n_candidates, m->grad_tile);
+    int32_t bi = -1;
+    const gmco_status rs = gmco_multi_autotune_tiles(m, penalty_weights, P, steps, candidates,
+                                                     tiles.data(), n_candidates, ms_per_step, &bi);
+    if (rs == GMCO_OK && best) *best = candidates[bi];
     return rs;
 }
 

@@ -944,7 +944,7 @@ KParams make_params(const TcLaunchSet &set, int kind, int parity, bool with_dT, 
     k.zero_next = zero_next ? 1 : 0;
     const int nA = set.tc_terms, nT = n_t_terms(nA);
     k.nG = nT;
-    k.bn = kind == 1 ? BM : grad_bn(nA);
+    k.bn = kind == 1 ? BM : grad_bn(nA, set.grad_tile);
     // N-side slot j: dose GEMM T_j, with dT_j stacked behind it for the two terms of dT;
     // gradient GEMM G_j, both 128-row halves of a 256-plan tile
     auto slot_maps = [&](Group &g, int j) {
@@ -1032,12 +1032,13 @@ int n16_of(const DevProblem &pb) { return (int)round_up(pb.n_dwell, 16); }
 
 }  // namespace
 
-// Plans per tile of the gradient GEMM: 256 when a merged stage of all terms fits twice in
-// the ring (one MMA of N = 256 per product), else 128.
-int grad_bn(int tc_terms)
+// Plans per tile of the gradient GEMM: 128 when requested, else 256 when a merged stage of
+// all terms fits twice in the ring (one MMA of N = 256 per product), else 128.
+int grad_bn(int tc_terms, int requested)
 {
     const int nA = tc_terms, nT = n_t_terms(tc_terms);
-    return (nA + 2 * nT) * BOX <= SMEM_BUDGET / 2 ? 256 : 128;
+    const bool fits = (nA + 2 * nT) * BOX <= SMEM_BUDGET / 2;
+    return requested == 128 || !fits ? 128 : 256;
 }
 
 bool tc_encode_map(CUtensorMap *m, const void *ptr, uint64_t cols, uint64_t rows,
@@ -1072,10 +1073,10 @@ double tc_mma_units(const DevProblem &pb, bool with_dT, int which)
 }
 int32_t tc_max_split(const DevProblem &pb) { return (int32_t)std::min<int64_t>(148, pb.np_pad / BK); }
 
-SplitPlan tc_split_plan(const DevProblem &pb, int32_t kb_per_split)
+SplitPlan tc_split_plan(const DevProblem &pb, int32_t kb_per_split, int32_t grad_tile)
 {
     SplitPlan p{};
-    p.rows_per_tile = grad_bn(pb.tc_terms);
+    p.rows_per_tile = grad_bn(pb.tc_terms, grad_tile);
     p.other_tiles = tc_n_dtiles(pb);
     p.kb_total = (int32_t)(pb.np_pad / BK);
     if (kb_per_split > 0) {   // fixed split length: as many splits as that takes
@@ -1176,7 +1177,7 @@ TcGradProb tc_grad_prob(const DevProblem &pb, const int32_t *cnt, float *gpart, 
 
 cudaError_t tc_alloc(const DevProblem &pb, int32_t cap, float *Fpart, float *dFpart,
                      float *gpart, float *dose_out, const int32_t *cnt, int32_t split_kb,
-                     TcBuffers *b, const AllocFn &alloc)
+                     int32_t grad_tile, TcBuffers *b, const AllocFn &alloc)
 {
     *b = TcBuffers{};
     b->cap = cap;
@@ -1213,7 +1214,8 @@ cudaError_t tc_alloc(const DevProblem &pb, int32_t cap, float *Fpart, float *dFp
     b->dFpart = dFpart;
     b->gpart = gpart;
     b->dose_out = dose_out;
-    b->sp = tc_split_plan(pb, split_kb);
+    b->sp = tc_split_plan(pb, split_kb, grad_tile);
+    b->grad_tile = grad_bn(pb.tc_terms, grad_tile);
     const TcDoseProb dp = tc_dose_prob(pb, cnt, b->Wc, b->G, dose_out, Fpart, dFpart, 0, 0, cap,
                                        (int32_t)pb.np_pad);
     const TcGradProb gp = tc_grad_prob(pb, cnt, gpart, b->sp, 0, 0);
@@ -1235,7 +1237,8 @@ TcLaunchSet tc_single_set(const DevProblem &pb, const TcBuffers &b)
     set.tc_terms = pb.tc_terms;
     set.err = b.err;
     set.max_items1 = ceil_div(b.cap, BM) * tc_n_ptiles(pb);
-    set.max_items2 = ceil_div(b.cap, grad_bn(pb.tc_terms)) * tc_n_dtiles(pb) * b.sp.max_split;
+    set.grad_tile = b.grad_tile;
+    set.max_items2 = ceil_div(b.cap, b.grad_tile) * tc_n_dtiles(pb) * b.sp.max_split;
     return set;
 }
 

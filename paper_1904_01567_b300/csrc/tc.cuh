@@ -71,6 +71,7 @@ struct TcBuffers {
     TcGradProb *d_grad = nullptr;
     float *Fpart = nullptr, *dFpart = nullptr, *gpart = nullptr, *dose_out = nullptr;
     SplitPlan sp{};                  // split plan of the gradient GEMM
+    int32_t grad_tile = 0;           // plans per gradient-GEMM tile
 };
 
 // Where the trial rows of a problem's compact plans go (tensor-core operand layout).
@@ -91,6 +92,7 @@ struct TcLaunchSet {
     int32_t n = 0;
     int32_t tc_terms = 0;               // BF16 terms of A (all problems alike)
     int64_t max_items1 = 1, max_items2 = 1;   // work items at full capacity (grid bound)
+    int32_t grad_tile = 0;              // plans per gradient-GEMM tile (grad_bn of the request)
     int32_t *err = nullptr;
 };
 
@@ -98,10 +100,11 @@ int32_t tc_n_ptiles(const DevProblem &pb);
 int32_t tc_max_split(const DevProblem &pb);
 // Default split plan of a problem's gradient GEMM; kb_per_split > 0 fixes the number of
 // 64-point blocks per split instead.
-SplitPlan tc_split_plan(const DevProblem &pb, int32_t kb_per_split = 0);
+SplitPlan tc_split_plan(const DevProblem &pb, int32_t kb_per_split = 0, int32_t grad_tile = 0);
 int32_t tc_n_dtiles(const DevProblem &pb);
-// Plans per tile of the gradient GEMM (256, or 128 where a stage of 256 does not fit).
-int grad_bn(int tc_terms);
+// Plans per tile of the gradient GEMM: requested 128, or 256 (the default, requested 0 or 256)
+// where a stage of 256 fits, else 128.
+int grad_bn(int tc_terms, int requested = 0);
 int64_t tc_launches_per_eval();
 // MMA products per output element issued by the dose GEMM (which = 1) or gradient GEMM (2).
 double tc_mma_units(const DevProblem &pb, bool with_dT, int which);
@@ -113,7 +116,7 @@ cudaError_t tc_prepare_problem(DevProblem *pb, int precision, cudaStream_t st,
 // Compact buffers, operand maps and device descriptors of one problem with cap plan rows.
 cudaError_t tc_alloc(const DevProblem &pb, int32_t cap, float *Fpart, float *dFpart,
                      float *gpart, float *dose_out, const int32_t *cnt, int32_t split_kb,
-                     TcBuffers *b, const AllocFn &alloc);
+                     int32_t grad_tile, TcBuffers *b, const AllocFn &alloc);
 TcLaunchSet tc_single_set(const DevProblem &pb, const TcBuffers &b);
 // Descriptors of one problem inside a launch list: cnt = its two row counters, rows of its
 // operands starting at a_row (points, A maps), t_row (plans, T / dT / G maps) and at_row

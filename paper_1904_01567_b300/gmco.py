@@ -35,7 +35,7 @@ class _Options(ctypes.Structure):
                 ("max_ls", ctypes.c_int32), ("rx_gy", ctypes.c_double),
                 ("refine_iters", ctypes.c_int32), ("steps_per_poll", ctypes.c_int32),
                 ("stop_window", ctypes.c_int32), ("grad_split_kb", ctypes.c_int32),
-                ("max_evals", ctypes.c_int32)]
+                ("max_evals", ctypes.c_int32), ("grad_plan_tile", ctypes.c_int32)]
 
 
 _lib = None
@@ -86,6 +86,12 @@ def load():
         lib.gmco_multi_set_split.restype = ctypes.c_int
         lib.gmco_multi_get_split.argtypes = [_vp]
         lib.gmco_multi_get_split.restype = _i32
+        lib.gmco_multi_set_tiles.argtypes = [_vp, _i32, _i32]
+        lib.gmco_multi_set_tiles.restype = ctypes.c_int
+        lib.gmco_multi_get_grad_tile.argtypes = [_vp]
+        lib.gmco_multi_get_grad_tile.restype = _i32
+        lib.gmco_multi_autotune_tiles.argtypes = [_vp, _vp, _vp, _i32, _vp, _vp, _i32, _vp, _vp]
+        lib.gmco_multi_autotune_tiles.restype = ctypes.c_int
         lib.gmco_multi_last_launch_count.argtypes = [_vp]
         lib.gmco_multi_last_launch_count.restype = _i64
         lib.gmco_solve_multi.argtypes = [_vp, _vp, _vp, _vp, _i32, ctypes.c_double, _vp, _vp, _vp,
@@ -375,6 +381,17 @@ class Multi:
     def split(self, kb: int):
         _check(load().gmco_multi_set_split(self.handle, int(kb)), "gmco_multi_set_split")
 
+    @property
+    def tiles(self):
+        """(split length in 64-point blocks, plans per gradient-GEMM tile; 0 = default)."""
+        return (int(load().gmco_multi_get_split(self.handle)),
+                int(load().gmco_multi_get_grad_tile(self.handle)))
+
+    @tiles.setter
+    def tiles(self, value):
+        kb, tile = value
+        _check(load().gmco_multi_set_tiles(self.handle, int(kb), int(tile)), "gmco_multi_set_tiles")
+
     def last_launch_count(self) -> int:
         return int(load().gmco_multi_last_launch_count(self.handle))
 
@@ -449,6 +466,23 @@ class Multi:
                "gmco_multi_autotune")
         del keeps
         return int(best.value), {int(c): float(v) for c, v in zip(candidates, ms)}
+
+    def autotune_tiles(self, weights, steps=8, candidates=((0, 0), (16, 0), (32, 0), (32, 128))):
+        """gmco_multi_autotune_tiles: candidates are (split length, plans per gradient-GEMM
+        tile) pairs; keeps the fastest.  Returns (best pair, {pair: ms per step})."""
+        keeps, wptrs, P, _ = self._weights(weights)
+        kb = (_i32 * len(candidates))(*[int(c[0]) for c in candidates])
+        tl = (_i32 * len(candidates))(*[int(c[1]) for c in candidates])
+        ms = np.zeros(len(candidates))
+        best = _i32()
+        wa = _ptr_array(wptrs)
+        _check(load().gmco_multi_autotune_tiles(self.handle, ctypes.cast(wa, _vp), ctypes.cast(P, _vp),
+                                                int(steps), ctypes.cast(kb, _vp), ctypes.cast(tl, _vp),
+                                                len(candidates), ms.ctypes.data, ctypes.byref(best)),
+               "gmco_multi_autotune_tiles")
+        del keeps
+        pairs = [(int(c[0]), int(c[1])) for c in candidates]
+        return pairs[int(best.value)], {p: float(v) for p, v in zip(pairs, ms)}
 
     def close(self):
         if self.handle:

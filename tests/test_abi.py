@@ -42,6 +42,11 @@ def test_options_defaults(gmco_mod):
     o = gmco_mod.default_options()
     assert (o.precision, o.m, o.c1, o.max_ls, o.rx_gy) == (0, 10, 1e-4, 30, 15.0)
     assert gmco_mod.default_options(precision="bf16").precision == 1
+    prm = np.array([[1.0, 15.0, np.inf, 1.0]])
+    for bad in (dict(max_evals=-1), dict(grad_plan_tile=64)):   # rejected before any device use
+        with pytest.raises(gmco_mod.GmcoError) as e:
+            gmco_mod.create_problem(np.ones((4, 3), np.float32), np.zeros(4, np.int32), prm, **bad)
+        assert e.value.status == gmco_mod.EINVAL
 
 
 def test_no_cpu_fallback_without_device(gmco_mod):
@@ -64,9 +69,12 @@ def test_multi_host_validation(gmco_mod):
     assert lib.gmco_create_multi(ctypes.cast(arr, ctypes.c_void_p), 65, ctypes.byref(h)) == gmco_mod.EINVAL
     assert lib.gmco_multi_set_split(None, 4) == gmco_mod.EINVAL
     assert lib.gmco_multi_get_split(None) == -1
+    assert lib.gmco_multi_set_tiles(None, 4, 128) == gmco_mod.EINVAL
+    assert lib.gmco_multi_get_grad_tile(None) == -1
     assert lib.gmco_multi_last_launch_count(None) == -1
     lib.gmco_destroy_multi(None)
     assert lib.gmco_solve_multi(None, None, None, None, 1, 0.0, None, None, None, None, None,
                                 None) == gmco_mod.EINVAL
     o = gmco_mod.default_options()
     assert o.grad_split_kb == 0 and o.stop_window == 1
+    assert o.max_evals == 0 and o.grad_plan_tile == 0

@@ -8,8 +8,9 @@ from synth import make_patient, weights_dirichlet, weights_loguniform
 pytestmark = pytest.mark.gpu
 
 # (seed, catheters, dwell step, points per structure, scale) and plans per patient:
-# 96 / 224 / 352 / 72 dwells (352 > 256: gradient items that take both TMEM buffers),
-# 5 to 130 plans (130: two plan tiles), 760 to 4000 points.
+# 96 / 224 / 352 / 72 dwells (352: three dwell tiles of the gradient GEMM),
+# 5 to 130 plans (130: two plan tiles of the dose GEMM, and of the gradient GEMM with
+# 128-plan tiles), 760 to 4000 points.
 SPECS = [
     ((11, 12, 0.5, (900, 150, 250, 250), 1.0), 5),
     ((12, 14, 0.25, (2500, 300, 600, 600), 1.1), 130),
@@ -34,14 +35,15 @@ def _problems(gmco_mod, patients, precision="bf16x2", **opt):
             for p, _ in patients]
 
 
-@pytest.mark.parametrize("split", [3, 0])
-def test_multi_equals_per_patient_bitwise(gmco_mod, patients, split):
+@pytest.mark.parametrize("split,tile", [(3, 0), (0, 0), (3, 128)])
+def test_multi_equals_per_patient_bitwise(gmco_mod, patients, split, tile):
     """Every patient's T, objectives, iterations and status equal those of its own
-    gmco_solve_batch with the same split length, bit for bit."""
-    probs = _problems(gmco_mod, patients, grad_split_kb=split)
+    gmco_solve_batch with the same split length and gradient tile, bit for bit."""
+    probs = _problems(gmco_mod, patients, grad_split_kb=split, grad_plan_tile=tile)
     Ws = [W for _, W in patients]
     with gmco_mod.Multi(probs) as mu:
-        mu.split = split
+        assert mu.tiles == (16, tile)          # the problems' tile option is the initial value
+        mu.tiles = (split, tile)
         res = mu.solve(Ws, max_iters=40, tol=1e-7)
         launches = mu.last_launch_count()
     for (p, W), pr, r in zip(patients, probs, res):
@@ -89,6 +91,26 @@ def test_autotune_picks_a_candidate(gmco_mod, patients):
         # the tuned object solves normally afterwards
         res = mu.solve(Ws, max_iters=5, tol=0.0)
     assert all(np.all(r["iters"] == 5) for r in res)
+    for pr in probs:
+        pr.close()
+
+
+def test_autotune_tiles_picks_a_candidate(gmco_mod, patients):
+    """The tile autotuner times (split length, gradient plan tile) pairs, keeps the fastest,
+    and the tuned launch gives the same results as a launch set to that pair by hand."""
+    probs = _problems(gmco_mod, patients)
+    Ws = [W for _, W in patients]
+    cands = ((0, 0), (8, 128), (8, 256))
+    with gmco_mod.Multi(probs) as mu:
+        best, ms = mu.autotune_tiles(Ws, steps=4, candidates=cands)
+        assert best in cands and mu.tiles == best
+        assert ms[best] == min(ms.values()) and all(np.isfinite(v) and v > 0 for v in ms.values())
+        tuned = mu.solve(Ws, max_iters=8, tol=0.0)
+        mu.tiles = best
+        again = mu.solve(Ws, max_iters=8, tol=0.0)
+    for a, b in zip(tuned, again):
+        for k in ("T", "objectives", "iters"):
+            assert np.array_equal(a[k], b[k])
     for pr in probs:
         pr.close()
 
