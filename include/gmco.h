@@ -96,6 +96,13 @@ typedef struct {
     int32_t grad_plan_tile;/* tensor-core forms: plans per gradient-GEMM tile, 128 or 256 (one
                               MMA of N = 256 per product where a stage of 256 fits), or 0
                               (default) for 256 where it fits, else 128 */
+    int32_t sparse_grad_permille; /* tensor-core forms, solver steps of a single problem: a
+                              step whose previous step had at most this many active (plan,
+                              point) pairs per thousand (penalty term on, dF/dd != 0) forms
+                              the gradient from the active pairs alone, in FP32, instead of
+                              the gradient GEMM.  0..1000; 0 (default) = always the GEMM.
+                              At about 1% active pairs the two cost about the same: each
+                              active pair reads a whole row of A, where the GEMM reuses it */
 } gmco_options;
 
 /* Fills *opt with the defaults above. */
@@ -315,6 +322,11 @@ gmco_status gmco_problem_info(const gmco_problem *prob, int64_t *n_pnt, int64_t 
 
 /* Kernel launches made by the most recent solve or evaluate call on this problem. */
 int64_t gmco_last_launch_count(const gmco_problem *prob);
+
+/* Steps of the most recent tensor-core solve on this problem whose gradient was formed from
+ * the active pairs alone (options.sparse_grad_permille); -1 where the option is off or the
+ * form is FP32 (or the count cannot be read). */
+int64_t gmco_last_sparse_steps(const gmco_problem *prob);
 
 /* Static description of a status code. */
 const char *gmco_status_string(gmco_status s);

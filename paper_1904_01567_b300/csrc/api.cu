@@ -209,7 +209,8 @@ gmco_status ensure_workspace(gmco_problem *pr, int32_t P)
     CK(a.alloc(&pr->gpart, (size_t)grows * pb.nd_pad));
     if (pr->opt.precision != GMCO_PREC_FP32) {
         cudaError_t e = tc_alloc(pb, cap, pr->Fpart, pr->dFpart, pr->gpart, pr->G, s.cnt,
-                                 pr->opt.grad_split_kb, pr->opt.grad_plan_tile, &pr->tcb, [&](void **p, size_t bytes) {
+                                 pr->opt.grad_split_kb, pr->opt.grad_plan_tile,
+                                 pr->opt.sparse_grad_permille, &pr->tcb, [&](void **p, size_t bytes) {
                                      unsigned char *q = nullptr;
                                      cudaError_t r = a.alloc(&q, bytes);
                                      *p = q;
@@ -337,6 +338,7 @@ gmco_status record_steps(gmco_problem *pr, int form, int steps, const UpdatePara
             CK(tc_launch_gemms(tc_single_set(pb, pr->tcb), k & 1, true, false, true, st, &nl));
             a.n_ptiles = tc_n_ptiles(pb);
             a.sp = pr->tcb.sp;
+            a.sp_flag = pr->tcb.act ? pr->tcb.act + 2 + (k & 1) : nullptr;
             a.fmt = 1;
             for (int j = 0; j < 3; ++j) a.Tb[j] = pr->tcb.T[j];
             a.dTb[0] = pr->tcb.dT[0];
@@ -360,6 +362,11 @@ gmco_status run_loop(gmco_problem *pr, int form, int32_t P, const UpdateParams &
     // rows of the first step: every plan in INIT or TRIAL, by compaction and preparation
     {
         SolverState s0 = pr->s;
+        if (form != 0 && pr->tcb.act) {
+            // active-set counters: the first step reads a count above any threshold (dense)
+            CK(cudaMemsetAsync(pr->tcb.act, 0, kTcActWords * sizeof(int32_t), pr->stream));
+            CK(cudaMemsetAsync(pr->tcb.act + 1, 0x7f, sizeof(int32_t), pr->stream));
+        }
         CK(launch_compact(s0, 0, pr->stream));
         if (form == 0) {
             CK(launch_prep_fp32(s0, pr->pb, pr->Tc, pr->dTc, pr->Wc, false, pr->stream));
@@ -396,8 +403,9 @@ gmco_status run_loop(gmco_problem *pr, int form, int32_t P, const UpdateParams &
         CK(ei);
         pr->gkey[form] = key;
     }
-    // launches per graph: steps x (dose GEMM + gradient GEMM + k_step); memsets not counted
-    const int64_t per_graph = (int64_t)steps * 3;
+    // launches per graph: steps x (dose GEMM + gradient GEMM [+ active-set gradient] + k_step);
+    // memsets not counted
+    const int64_t per_graph = (int64_t)steps * (form != 0 && pr->tcb.act ? 4 : 3);
     int64_t done = 0;
     for (;;) {
         CK(cudaGraphLaunch(pr->gexec[form], pr->stream));
@@ -832,6 +840,7 @@ void gmco_default_options(gmco_options *opt)
     opt->max_evals = 0;
     opt->grad_plan_tile = 0;
     opt->grad_split_kb = 0;
+    opt->sparse_grad_permille = 0;
 }
 
 const char *gmco_status_string(gmco_status s)
@@ -868,7 +877,8 @@ gmco_status gmco_create_problem(const float *A, int64_t n_pnt, int64_t n_dwell,
         !(o.c1 < 1.0) || o.max_ls < 1 || o.max_ls > 60 || !(o.rx_gy > 0.0) ||
         !isfinite(o.rx_gy) || o.refine_iters < 0 || o.steps_per_poll < 1 ||
         o.steps_per_poll > 1024 || o.stop_window < 1 || o.grad_split_kb < 0 || o.max_evals < 0 ||
-        (o.grad_plan_tile != 0 && o.grad_plan_tile != 128 && o.grad_plan_tile != 256)) {
+        (o.grad_plan_tile != 0 && o.grad_plan_tile != 128 && o.grad_plan_tile != 256) ||
+        o.sparse_grad_permille < 0 || o.sparse_grad_permille > 1000) {
         set_error_msg("gmco_create_problem: bad options");
         return GMCO_EINVAL;
     }
@@ -1014,6 +1024,17 @@ gmco_status gmco_problem_info(const gmco_problem *pr, int64_t *n_pnt, int64_t *n
 }
 
 int64_t gmco_last_launch_count(const gmco_problem *pr) { return pr ? pr->launches : -1; }
+
+int64_t gmco_last_sparse_steps(const gmco_problem *pr)
+{
+    if (!pr || !pr->tcb.act) return -1;
+    int32_t v = 0;
+    if (cudaMemcpy(&v, pr->tcb.act + 4, sizeof v, cudaMemcpyDeviceToHost) != cudaSuccess) {
+        cudaGetLastError();
+        return -1;
+    }
+    return v;
+}
 
 gmco_status gmco_solve_batch(gmco_problem *pr, const float *penalty_weights, int64_t P,
                              const float *t0, int32_t max_iters, double tol, float *T_out,

@@ -106,6 +106,8 @@ struct StepArgs {
     const float *gpart;              // n_split x rows x nd_pad
     int32_t n_ptiles, cap;
     SplitPlan sp;
+    const int32_t *sp_flag;          // nonzero: this step's gradient is split 0 alone (the
+                                     // active-set gradient); null or zero: the split plan
     const int32_t *rows_cur;         // rows evaluated this step
     int32_t *rows_next;              // slot counter of the next step
     int32_t fmt;                     // 0: FP32 rows (Tc, dTc), 1: BF16 split rows (Tb, dTb)

@@ -340,6 +340,7 @@ __device__ __forceinline__ void step_plan(const SolverState &s, const UpdatePara
     const double dF = warp_sum_d(dfsum);
     int kbps, n_split;
     split_plan(a.sp, R, &kbps, &n_split);
+    if (a.sp_flag && *a.sp_flag) n_split = 1;
     // sum over the splits in split order; each split's EPL loads are independent, so the
     // latency chain is one load per batch of splits rather than one per element and split
     float gtv[EPL];

@@ -213,6 +213,7 @@ struct KParams {
     const void *probs;        // TcDoseProb[n_probs] (dose GEMM) or TcGradProb[n_probs]
     int32_t n_probs, parity;
     int32_t has_dT, write_dose, zero_next;
+    int32_t sparse_ok;        // a solver step: the active-set gradient may be chosen
     int32_t nG;               // BF16 terms of G written by the dose epilogue
     int32_t bn;               // plans per tile: 128 (dose GEMM), 256 or 128 (gradient GEMM)
     int32_t n_groups;
@@ -341,7 +342,9 @@ __global__ void __launch_bounds__(NTHREADS, 1) k_tc(const __grid_constant__ KPar
     __shared__ int32_t s_per[kMaxMulti];         // work items per plan tile
     __shared__ int32_t s_kbps[kMaxMulti];        // gradient GEMM: K blocks per split
     __shared__ int32_t s_nsplit[kMaxMulti];      // gradient GEMM: splits
+    __shared__ int32_t s_sparse[kMaxMulti];      // dose GEMM: this step's path is the active-set gradient
     __shared__ int32_t s_fail;
+    __shared__ int32_t s_act;                    // dose GEMM: active (plan, point) pairs of this CTA
     __shared__ __align__(16) float s_cl[8][kClStride], s_ch[8][kClStride];   // w/N w_min, w/N w_max per plan
     __shared__ float s_part[2][4][BM];           // per lane quarter and plan: partial F, dF
 
@@ -359,20 +362,32 @@ __global__ void __launch_bounds__(NTHREADS, 1) k_tc(const __grid_constant__ KPar
         const int p = threadIdx.x;
         const Prob &d = gprob[p];
         const int rows = *d.n_rows[kp.parity];
-        int per = 1, kbps = 0, nsplit = 1;
+        int per = 1, kbps = 0, nsplit = 1, rows_run = rows;
         if constexpr (KIND == 1) {
             per = d.n_ptiles;
             if (kp.zero_next && blockIdx.x == 0) *const_cast<int32_t *>(d.n_rows[kp.parity ^ 1]) = 0;
+            // path of this step, from the previous step's active-pair count (every CTA decides
+            // alike; CTA 0 records it for the gradient kernels and the update)
+            int sparse = 0;
+            if (d.act) {
+                sparse = kp.sparse_ok && (int64_t)d.act[kp.parity ^ 1] <= (int64_t)d.sp_thr * rows ? 1 : 0;
+                if (blockIdx.x == 0) d.act[2 + kp.parity] = sparse;
+            }
+            s_sparse[p] = sparse;
         } else {
             split_plan(d.sp, rows, &kbps, &nsplit);
             per = d.n_dt * nsplit;
+            if (d.act && d.act[2 + kp.parity]) rows_run = 0;   // the active-set gradient serves this step
         }
-        s_rows[p] = rows;
+        s_rows[p] = rows_run;
         s_per[p] = per;
         s_kbps[p] = kbps;
         s_nsplit[p] = nsplit;
     }
-    if (threadIdx.x == 0) s_fail = 0;
+    if (threadIdx.x == 0) {
+        s_fail = 0;
+        s_act = 0;
+    }
     __syncthreads();
     if (threadIdx.x == 0) {
         int acc = 0;
@@ -532,6 +547,7 @@ __global__ void __launch_bounds__(NTHREADS, 1) k_tc(const __grid_constant__ KPar
         const int q = warp & 3, h = warp >> 2;
         int p = 0, nb = 0;
         uint32_t use[2] = {0u, 0u};
+        int32_t n_act = 0;   // dose GEMM of a solver step: active (plan, point) pairs seen
         for (int item = blockIdx.x; item < n_items; item += gridDim.x) {
             const Item w = decode_item<KIND>(s_start, s_per, s_nsplit, s_rows, kp.bn, p, item);
             p = w.p;
@@ -575,6 +591,8 @@ __global__ void __launch_bounds__(NTHREADS, 1) k_tc(const __grid_constant__ KPar
                 if (ok) {
                     const bool has_dT = kp.has_dT != 0;
                     const bool wdose = kp.write_dose != 0;
+                    const bool count = kp.sparse_ok && d.act != nullptr;
+                    const bool sparse = s_sparse[p] != 0;
                     const float lo = pt.x, hi = pt.y, sc = pt.z;
                     const float *clr = s_cl[sv < 0 ? 0 : sv], *chr = s_ch[sv < 0 ? 0 : sv];
                     constexpr int CW = 8;                  // plan columns per TMEM load
@@ -681,6 +699,31 @@ __global__ void __launch_bounds__(NTHREADS, 1) k_tc(const __grid_constant__ KPar
                             s_part[0][q][c + ((lane >> 2) & 7)] = fsum;
                             s_part[1][q][c + ((lane >> 2) & 7)] = dfsum;
                         }
+                        // active pairs: dF/dd != 0 (a penalty term is on), live rows only
+                        const int row0 = w.ptile * BM + c;
+                        if (count && sparse) {
+                            // this step's gradient is formed from the active pairs alone: per
+                            // plan row, the mask word of these 32 points and their dF/dd in FP32
+                            uint32_t mine = 0u;
+#pragma unroll
+                            for (int i = 0; i < CW; ++i) {
+                                const uint32_t bal = __ballot_sync(0xffffffffu, out[i] != 0.0f);
+                                if (lane == i) mine = bal;
+                            }
+                            if (lane < CW && row0 + lane < n_rows) {
+                                d.mask[((size_t)(row0 + lane) * d.n_ptiles + w.sub) * 4 + q] = mine;
+                                n_act += __popc(mine);
+                            }
+#pragma unroll
+                            for (int i = 0; i < CW; ++i)
+                                if (out[i] != 0.0f && row0 + i < n_rows)
+                                    d.Gs[(size_t)(row0 + i) * d.ld_g + pt_i] = out[i];
+                            continue;
+                        }
+                        if (count) {
+#pragma unroll
+                            for (int i = 0; i < CW; ++i) n_act += (out[i] != 0.0f && row0 + i < n_rows) ? 1 : 0;
+                        }
                         // rows of G (or of the dose) run over points: the 8 x 8 blocks of (plan,
                         // point) values are transposed within each group of 8 lanes, so that a
                         // lane writes 8 consecutive points of one plan, 16 bytes per term
@@ -762,9 +805,21 @@ __global__ void __launch_bounds__(NTHREADS, 1) k_tc(const __grid_constant__ KPar
             nb = buf ^ 1;
             if (!ok) break;
         }
+        if constexpr (KIND == 1) {
+            if (kp.sparse_ok) {
+#pragma unroll
+                for (int o = 16; o > 0; o >>= 1) n_act += __shfl_xor_sync(0xffffffffu, n_act, o);
+                if (lane == 0 && n_act > 0) atomicAdd(&s_act, n_act);
+            }
+        }
     }
     fence_before();
     __syncthreads();
+    if constexpr (KIND == 1) {
+        // one count per CTA into the single problem's counter of this step
+        if (threadIdx.x == 0 && kp.sparse_ok && s_prob[0].act && s_act > 0)
+            atomicAdd(s_prob[0].act + kp.parity, s_act);
+    }
     if (warp == W_TMEM) {
         fence_after();
         tmem_dealloc(tmem, (uint32_t)TMEM_COLS);
@@ -942,6 +997,7 @@ KParams make_params(const TcLaunchSet &set, int kind, int parity, bool with_dT, 
     k.has_dT = kind == 1 && with_dT ? 1 : 0;
     k.write_dose = write_dose ? 1 : 0;
     k.zero_next = zero_next ? 1 : 0;
+    k.sparse_ok = zero_next ? 1 : 0;
     const int nA = set.tc_terms, nT = n_t_terms(nA);
     k.nG = nT;
     k.bn = kind == 1 ? BM : grad_bn(nA, set.grad_tile);
@@ -1177,7 +1233,8 @@ TcGradProb tc_grad_prob(const DevProblem &pb, const int32_t *cnt, float *gpart, 
 
 cudaError_t tc_alloc(const DevProblem &pb, int32_t cap, float *Fpart, float *dFpart,
                      float *gpart, float *dose_out, const int32_t *cnt, int32_t split_kb,
-                     int32_t grad_tile, TcBuffers *b, const AllocFn &alloc)
+                     int32_t grad_tile, int32_t sparse_permille, TcBuffers *b,
+                     const AllocFn &alloc)
 {
     *b = TcBuffers{};
     b->cap = cap;
@@ -1214,11 +1271,28 @@ cudaError_t tc_alloc(const DevProblem &pb, int32_t cap, float *Fpart, float *dFp
     b->dFpart = dFpart;
     b->gpart = gpart;
     b->dose_out = dose_out;
+    b->cnt = cnt;
     b->sp = tc_split_plan(pb, split_kb, grad_tile);
     b->grad_tile = grad_bn(pb.tc_terms, grad_tile);
-    const TcDoseProb dp = tc_dose_prob(pb, cnt, b->Wc, b->G, dose_out, Fpart, dFpart, 0, 0, cap,
-                                       (int32_t)pb.np_pad);
-    const TcGradProb gp = tc_grad_prob(pb, cnt, gpart, b->sp, 0, 0);
+    TcDoseProb dp = tc_dose_prob(pb, cnt, b->Wc, b->G, dose_out, Fpart, dFpart, 0, 0, cap,
+                                 (int32_t)pb.np_pad);
+    TcGradProb gp = tc_grad_prob(pb, cnt, gpart, b->sp, 0, 0);
+    if (sparse_permille > 0) {
+        // active-set gradient: the FP32 dF/dd of the active pairs go to the dose buffer (a
+        // solver step writes no dose); counts start with the first step on the dense path
+        const size_t words = (size_t)cap * tc_n_ptiles(pb) * 4;
+        if ((e = alloc(reinterpret_cast<void **>(&b->mask), words * 4)) != cudaSuccess) return e;
+        if ((e = alloc(reinterpret_cast<void **>(&b->act), kTcActWords * 4)) != cudaSuccess) return e;
+        if ((e = cudaMemset(b->mask, 0, words * 4)) != cudaSuccess) return e;
+        if ((e = cudaMemset(b->act, 0, kTcActWords * 4)) != cudaSuccess) return e;
+        b->Gs = dose_out;
+        b->sp_thr = (int32_t)std::max<int64_t>(0, (int64_t)sparse_permille * pb.n_pnt / 1000);
+        dp.mask = b->mask;
+        dp.Gs = b->Gs;
+        dp.act = b->act;
+        dp.sp_thr = b->sp_thr;
+        gp.act = b->act;
+    }
     if ((e = alloc(reinterpret_cast<void **>(&b->d_dose), sizeof(TcDoseProb))) != cudaSuccess) return e;
     if ((e = alloc(reinterpret_cast<void **>(&b->d_grad), sizeof(TcGradProb))) != cudaSuccess) return e;
     if ((e = cudaMemcpy(b->d_dose, &dp, sizeof dp, cudaMemcpyHostToDevice)) != cudaSuccess) return e;
@@ -1239,6 +1313,21 @@ TcLaunchSet tc_single_set(const DevProblem &pb, const TcBuffers &b)
     set.max_items1 = ceil_div(b.cap, BM) * tc_n_ptiles(pb);
     set.grad_tile = b.grad_tile;
     set.max_items2 = ceil_div(b.cap, b.grad_tile) * tc_n_dtiles(pb) * b.sp.max_split;
+    if (b.act) {
+        set.gs_rows[0] = b.cnt;
+        set.gs_rows[1] = b.cnt + 1;
+        set.gs_mask = b.mask;
+        set.gs_G = b.Gs;
+        for (int j = 0; j < pb.tc_terms; ++j) set.gs_A[j] = pb.Ah[j];
+        set.gs_act = b.act;
+        set.gs_out = b.gpart;
+        set.gs_ld = (int32_t)pb.np_pad;
+        set.gs_nd = (int32_t)pb.nd_pad;
+        set.gs_ptiles = tc_n_ptiles(pb);
+        set.gs_kpad = (int32_t)pb.kpad;
+        set.gs_terms = pb.tc_terms;
+        set.gs_cap = b.cap;
+    }
     return set;
 }
 
@@ -1253,6 +1342,135 @@ TcRows tc_rows(const DevProblem &pb, const TcBuffers &b)
     r.kpad = (int32_t)pb.kpad;
     r.nT = n_t_terms(pb.tc_terms);
     return r;
+}
+
+// ------------------------------------------------------------------ active-set gradient
+// Gradient of Eq. (4) from the active pairs only: g_j = sum over points i with dF/dd_i != 0 of
+// dF/dd_i A_ij, the same sum the gradient GEMM forms over every point, now over the few points
+// whose penalty term is on (their set shrinks to about 1% of a plan's points within a few tens
+// of iterations).  One CTA of four warps per compact plan row.  In each pass every warp lists
+// the active points of 2048 consecutive points from the dose epilogue's mask; the warps then
+// share the pass's list (entry k to warp (k / BATCH) mod 4) and add the A rows of their
+// entries; the four partial sums are added in warp order at the end.  CTA 0 also clears the
+// next step's active-pair counter.
+constexpr int kGsWarps = 4, kGsSeg = 2048, kGsPairs = 8;   // kpad <= 512
+
+template <int NT>
+__global__ void __launch_bounds__(kGsWarps * 32)
+k_gsparse(const int32_t *__restrict__ rows, const uint32_t *__restrict__ mask,
+          const float *__restrict__ G, const __nv_bfloat16 *__restrict__ A0,
+          const __nv_bfloat16 *__restrict__ A1, const __nv_bfloat16 *__restrict__ A2,
+          int32_t *act, float *__restrict__ out, int32_t ld, int32_t nd, int32_t n_ptiles,
+          int32_t kpad, int32_t parity)
+{
+    constexpr int BATCH = NT == 3 ? 2 : 4;   // points in flight per warp
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+        act[parity ^ 1] = 0;                 // next step's count
+        if (act[2 + parity]) ++act[4];       // steps of this solve on this path
+    }
+    if (act[2 + parity] == 0) return;        // dense step (uniform over the grid)
+    const int r = blockIdx.x;
+    if (r >= *rows) return;                  // uniform over the CTA
+    __shared__ int32_t s_pt[kGsWarps][kGsSeg];
+    __shared__ int32_t s_n[kGsWarps];
+    __shared__ float2 s_acc[kGsWarps - 1][kGsPairs][32];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const uint2 *mrow = reinterpret_cast<const uint2 *>(mask + (size_t)r * n_ptiles * 4);
+    const int n2 = n_ptiles * 2;             // mask words of the row, in pairs
+    const float *grow = G + (size_t)r * ld;
+    const int kp = kpad / 64;                // dwell pairs per lane
+    const __nv_bfloat16 *Aterm[3] = {A0, A1, A2};
+    float2 acc[kGsPairs];
+#pragma unroll
+    for (int e = 0; e < kGsPairs; ++e) acc[e] = make_float2(0.0f, 0.0f);
+
+    for (int pbase = 0; pbase < n2; pbase += kGsWarps * 32) {
+        // this warp's 64 words (2048 points) of the pass: list its active points in order
+        const int base = pbase + warp * 32;
+        const uint2 wv = base + lane < n2 ? mrow[base + lane] : make_uint2(0u, 0u);
+        const int c = __popc(wv.x) + __popc(wv.y);
+        int incl = c;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const int t = __shfl_up_sync(0xffffffffu, incl, o);
+            if (lane >= o) incl += t;
+        }
+        int pos = incl - c;
+        const int pt0 = (base + lane) * 64;   // first point of this lane's two words
+        uint32_t w0 = wv.x, w1 = wv.y;
+        while (w0) {
+            s_pt[warp][pos++] = pt0 + __ffs(w0) - 1;
+            w0 &= w0 - 1u;
+        }
+        while (w1) {
+            s_pt[warp][pos++] = pt0 + 32 + __ffs(w1) - 1;
+            w1 &= w1 - 1u;
+        }
+        if (lane == 31) s_n[warp] = incl;
+        __syncthreads();
+        const int c0 = s_n[0], c1 = c0 + s_n[1], c2 = c1 + s_n[2], E = c2 + s_n[3];
+        for (int k0 = warp * BATCH; k0 < E; k0 += kGsWarps * BATCH) {
+            int pj[BATCH];
+            float gj[BATCH];
+            __nv_bfloat162 v[BATCH][NT][kGsPairs];
+#pragma unroll
+            for (int j = 0; j < BATCH; ++j) {
+                const int k = k0 + j < E ? k0 + j : k0;
+                const int sg = k < c0 ? 0 : (k < c1 ? 1 : (k < c2 ? 2 : 3));
+                const int off = k - (sg == 0 ? 0 : (sg == 1 ? c0 : (sg == 2 ? c1 : c2)));
+                pj[j] = s_pt[sg][off];
+            }
+#pragma unroll
+            for (int j = 0; j < BATCH; ++j) {
+                gj[j] = k0 + j < E ? grow[pj[j]] : 0.0f;
+#pragma unroll
+                for (int t = 0; t < NT; ++t) {
+                    const __nv_bfloat162 *ar =
+                        reinterpret_cast<const __nv_bfloat162 *>(Aterm[t] + (size_t)pj[j] * kpad) + lane;
+#pragma unroll
+                    for (int e = 0; e < kGsPairs; ++e)
+                        if (e < kp) v[j][t][e] = ar[32 * e];
+                }
+            }
+#pragma unroll
+            for (int j = 0; j < BATCH; ++j)
+#pragma unroll
+                for (int e = 0; e < kGsPairs; ++e) {
+                    if (e >= kp) continue;
+                    float2 a = __bfloat1622float2(v[j][0][e]);
+#pragma unroll
+                    for (int t = 1; t < NT; ++t) {
+                        const float2 b = __bfloat1622float2(v[j][t][e]);
+                        a.x += b.x;
+                        a.y += b.y;
+                    }
+                    acc[e].x = fmaf(gj[j], a.x, acc[e].x);
+                    acc[e].y = fmaf(gj[j], a.y, acc[e].y);
+                }
+        }
+        __syncthreads();   // the lists are rewritten by the next pass
+    }
+    if (warp > 0) {
+#pragma unroll
+        for (int e = 0; e < kGsPairs; ++e) s_acc[warp - 1][e][lane] = acc[e];
+    }
+    __syncthreads();
+    if (warp == 0) {
+        float *orow = out + (size_t)r * nd;
+#pragma unroll
+        for (int e = 0; e < kGsPairs; ++e) {
+            const int dw = 64 * e + 2 * lane;
+            if (e < kp && dw < nd) {
+                float2 a = acc[e];
+#pragma unroll
+                for (int w = 0; w < kGsWarps - 1; ++w) {
+                    a.x += s_acc[w][e][lane].x;
+                    a.y += s_acc[w][e][lane].y;
+                }
+                *reinterpret_cast<float2 *>(orow + dw) = a;
+            }
+        }
+    }
 }
 
 cudaError_t tc_launch_gemms(const TcLaunchSet &set, int32_t parity, bool with_dT,
@@ -1276,6 +1494,29 @@ cudaError_t tc_launch_gemms(const TcLaunchSet &set, int32_t parity, bool with_dT
                   dyn_smem(k2), st>>>(k2);
         if ((e = cudaGetLastError()) != cudaSuccess) return e;
         ++nl;
+        if (zero_next && set.gs_act) {   // solver step of a single problem with the active-set option
+            const unsigned grid = (unsigned)set.gs_cap;   // one CTA per plan row
+            const int32_t *rows = set.gs_rows[parity & 1];
+            switch (set.gs_terms) {
+            case 1:
+                k_gsparse<1><<<grid, kGsWarps * 32, 0, st>>>(rows, set.gs_mask, set.gs_G, set.gs_A[0],
+                                                          set.gs_A[0], set.gs_A[0], set.gs_act, set.gs_out,
+                                                          set.gs_ld, set.gs_nd, set.gs_ptiles, set.gs_kpad, parity);
+                break;
+            case 2:
+                k_gsparse<2><<<grid, kGsWarps * 32, 0, st>>>(rows, set.gs_mask, set.gs_G, set.gs_A[0],
+                                                          set.gs_A[1], set.gs_A[1], set.gs_act, set.gs_out,
+                                                          set.gs_ld, set.gs_nd, set.gs_ptiles, set.gs_kpad, parity);
+                break;
+            default:
+                k_gsparse<3><<<grid, kGsWarps * 32, 0, st>>>(rows, set.gs_mask, set.gs_G, set.gs_A[0],
+                                                          set.gs_A[1], set.gs_A[2], set.gs_act, set.gs_out,
+                                                          set.gs_ld, set.gs_nd, set.gs_ptiles, set.gs_kpad, parity);
+                break;
+            }
+            if ((e = cudaGetLastError()) != cudaSuccess) return e;
+            ++nl;
+        }
     }
     *n_launches = nl;
     return cudaSuccess;

@@ -16,6 +16,7 @@ namespace gmco {
 using AllocFn = std::function<cudaError_t(void **, size_t)>;
 
 constexpr int kMaxMulti = 64;    // problems in one GEMM launch (descriptors in shared memory)
+constexpr int kTcActWords = 8;   // active-set counters of a problem (TcDoseProb::act)
 
 // Operand maps.  Dose GEMM: m[0..2] A terms (rows = points, columns = dwells), m[3..5] T terms
 // (rows = plans, columns = dwells), m[6], m[7] the two terms of dT.  Gradient GEMM: m[0..2] A^T terms (rows = dwells,
@@ -44,6 +45,17 @@ struct TcDoseProb {
     int32_t n_struct;
     int32_t cap;                // plan rows of Fpart / dFpart
     int32_t ld_g;               // row stride of G and dose_out (elements)
+    // active-set gradient (single problems; null / 0 otherwise): where the previous step's
+    // count of active (plan, point) pairs was at most sp_thr per row of this step, this step
+    // writes, instead of the BF16 terms of G, a bit mask of the active points (per row and
+    // point tile, 4 words of 32 points) and the FP32 dF/dd of the active pairs only (row r at
+    // Gs + r * ld_g, in the units of G)
+    uint32_t *mask;             // cap x n_ptiles x 4
+    float *Gs;
+    int32_t *act;               // [0..1] active-pair counts of even / odd steps, [2..3] the
+                                // steps' path (1 = active-set gradient), [4] steps on that path
+    int32_t sp_thr;
+    int32_t pad2_;
 };
 
 // Per-problem part of a gradient-GEMM launch.
@@ -56,6 +68,8 @@ struct TcGradProb {
     int32_t kb;                 // K blocks of 64 points
     int32_t n_dt;               // dwell tiles of 128 (TMEM lanes)
     int32_t nd_pad;
+    const int32_t *act;         // as TcDoseProb::act, or null: a step whose path is the
+                                // active-set gradient has no work here
 };
 
 // Compact per-evaluation operands of one problem (cap plan rows) and its operand maps.
@@ -72,6 +86,11 @@ struct TcBuffers {
     float *Fpart = nullptr, *dFpart = nullptr, *gpart = nullptr, *dose_out = nullptr;
     SplitPlan sp{};                  // split plan of the gradient GEMM
     int32_t grad_tile = 0;           // plans per gradient-GEMM tile
+    uint32_t *mask = nullptr;        // active-set gradient (sparse_permille > 0), see TcDoseProb
+    int32_t *act = nullptr;
+    float *Gs = nullptr;
+    int32_t sp_thr = 0;
+    const int32_t *cnt = nullptr;    // the two row counters
 };
 
 // Where the trial rows of a problem's compact plans go (tensor-core operand layout).
@@ -93,6 +112,14 @@ struct TcLaunchSet {
     int32_t tc_terms = 0;               // BF16 terms of A (all problems alike)
     int64_t max_items1 = 1, max_items2 = 1;   // work items at full capacity (grid bound)
     int32_t grad_tile = 0;              // plans per gradient-GEMM tile (grad_bn of the request)
+    // active-set gradient of a single problem (gs_act non-null): its kernel's arguments
+    const int32_t *gs_rows[2] = {nullptr, nullptr};
+    const uint32_t *gs_mask = nullptr;
+    const float *gs_G = nullptr;                                   // dF/dd of the active pairs
+    const __nv_bfloat16 *gs_A[3] = {nullptr, nullptr, nullptr};    // A / row_scale terms
+    int32_t *gs_act = nullptr;
+    float *gs_out = nullptr;                                       // gradient, split 0 of gpart
+    int32_t gs_ld = 0, gs_nd = 0, gs_ptiles = 0, gs_kpad = 0, gs_terms = 0, gs_cap = 0;
     int32_t *err = nullptr;
 };
 
@@ -116,7 +143,8 @@ cudaError_t tc_prepare_problem(DevProblem *pb, int precision, cudaStream_t st,
 // Compact buffers, operand maps and device descriptors of one problem with cap plan rows.
 cudaError_t tc_alloc(const DevProblem &pb, int32_t cap, float *Fpart, float *dFpart,
                      float *gpart, float *dose_out, const int32_t *cnt, int32_t split_kb,
-                     int32_t grad_tile, TcBuffers *b, const AllocFn &alloc);
+                     int32_t grad_tile, int32_t sparse_permille, TcBuffers *b,
+                     const AllocFn &alloc);
 TcLaunchSet tc_single_set(const DevProblem &pb, const TcBuffers &b);
 // Descriptors of one problem inside a launch list: cnt = its two row counters, rows of its
 // operands starting at a_row (points, A maps), t_row (plans, T / dT / G maps) and at_row

@@ -35,7 +35,8 @@ class _Options(ctypes.Structure):
                 ("max_ls", ctypes.c_int32), ("rx_gy", ctypes.c_double),
                 ("refine_iters", ctypes.c_int32), ("steps_per_poll", ctypes.c_int32),
                 ("stop_window", ctypes.c_int32), ("grad_split_kb", ctypes.c_int32),
-                ("max_evals", ctypes.c_int32), ("grad_plan_tile", ctypes.c_int32)]
+                ("max_evals", ctypes.c_int32), ("grad_plan_tile", ctypes.c_int32),
+                ("sparse_grad_permille", ctypes.c_int32)]
 
 
 _lib = None
@@ -74,6 +75,8 @@ def load():
         lib.gmco_problem_info.restype = ctypes.c_int
         lib.gmco_last_launch_count.argtypes = [_vp]
         lib.gmco_last_launch_count.restype = _i64
+        lib.gmco_last_sparse_steps.argtypes = [_vp]
+        lib.gmco_last_sparse_steps.restype = _i64
         lib.gmco_status_string.argtypes = [ctypes.c_int]
         lib.gmco_status_string.restype = ctypes.c_char_p
         lib.gmco_last_error.argtypes = []
@@ -334,6 +337,10 @@ class Problem:
 
     def last_launch_count(self):
         return last_launch_count(self.handle)
+
+    def last_sparse_steps(self):
+        """Steps of the last tensor-core solve with the active-set gradient (-1: option off)."""
+        return int(load().gmco_last_sparse_steps(self.handle))
 
     def close(self):
         if self.handle:

@@ -93,3 +93,49 @@ def test_bf16x3_solve_reaches_exact_optimum(gmco_mod, oracle_mod):
     assert min(gaps) >= -1e-9
     assert sum(g <= 1e-4 for g in gaps) >= 5
     assert max(gaps) <= 2e-3
+
+
+@pytest.mark.parametrize("form", ["bf16x2", "bf16x3"])
+def test_active_set_gradient_solve(gmco_mod, oracle_mod, form):
+    """Solves whose gradient is formed from the active (plan, point) pairs alone on every step
+    after the first (threshold 1000 per thousand) reach the exact optimum as the gradient
+    GEMM's solves do; the objective each reports is the oracle's at its returned dwell times."""
+    p, W, _ = workload("prostate-2k-8plans")
+    fstar = read_fstar("prostate-2k-8plans")
+    res = {}
+    for perm in (0, 1000):
+        with gmco_mod.Problem(p.A, p.sid, p.params, precision=form,
+                              sparse_grad_permille=perm) as pr:
+            out = pr.solve_batch(W, max_iters=20000, tol=1e-10)
+            res[perm] = (out, pr.last_sparse_steps())
+    (out0, s0), (out1, s1) = res[0], res[1000]
+    assert s0 == -1
+    assert s1 > 0 and s1 >= int(out1["iters"].max()) - 1, (s1, out1["iters"])
+    tol_f = FORMS[form][1]
+    gaps = {0: [], 1000: []}
+    for perm, (out, _) in res.items():
+        for j in range(W.shape[0]):
+            F = oracle_mod.objective(p.A, p.sid, p.params, W[j], np.sqrt(out["T"][j]))[0]
+            assert abs(out["objectives"][j] / F - 1.0) <= tol_f, (perm, j)
+            gaps[perm].append(F / fstar[j] - 1.0)
+    print(form, "GEMM gaps", gaps[0], "active-set gaps", gaps[1000], out1["iters"], out1["status"])
+    assert min(gaps[1000]) >= -1e-9
+    assert sum(g <= 1e-4 for g in gaps[1000]) >= sum(g <= 1e-4 for g in gaps[0]) - 1
+    assert max(gaps[1000]) <= 2e-3
+
+
+def test_active_set_gradient_engages_at_three_percent(gmco_mod):
+    """With a threshold of 30 per thousand a long solve takes most of its steps on the
+    active-set gradient (the active pairs fall to a few per cent of the points), and the
+    results are reproducible bit for bit."""
+    p, W, _ = workload("prostate-2k-8plans")
+    outs = []
+    with gmco_mod.Problem(p.A, p.sid, p.params, precision="bf16x2",
+                          sparse_grad_permille=30) as pr:
+        for _ in range(2):
+            out = pr.solve_batch(W, max_iters=300, tol=1e-9)
+            outs.append((out, pr.last_sparse_steps()))
+    (a, sa), (b, sb) = outs
+    assert sa == sb and sa > int(a["iters"].max()) // 2, (sa, a["iters"])
+    for k in ("T", "objectives", "iters", "status"):
+        assert np.array_equal(a[k], b[k]), k
