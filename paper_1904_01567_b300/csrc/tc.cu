@@ -39,7 +39,8 @@ constexpr int EPI_GROUPS = EPI_WARPS / 4;   // column groups of the epilogue
 constexpr int W_TMA = EPI_WARPS, W_MMA = EPI_WARPS + 1, W_TMEM = EPI_WARPS + 2;
 constexpr int NTHREADS = (EPI_WARPS + 3) * 32;   // epilogue, TMA, MMA, TMEM owner
 constexpr int MAX_STAGES = 4;
-constexpr int SMEM_BUDGET = 200 * 1024;   // dynamic ring; static shared memory adds ~25 KB
+constexpr int SMEM_BUDGET = 194 * 1024;   // dynamic ring; with ~32 KB of static shared memory
+                                          // the total stays within the 227 KB of a CTA
 constexpr int TMEM_COLS = 512;          // two accumulator buffers
 constexpr int BUF_COLS = 256;
 constexpr long long kSpinCycles = 2000000000LL;   // about 1 s at 2 GHz
@@ -347,6 +348,7 @@ __global__ void __launch_bounds__(NTHREADS, 1) k_tc(const __grid_constant__ KPar
     __shared__ int32_t s_act;                    // dose GEMM: active (plan, point) pairs of this CTA
     __shared__ __align__(16) float s_cl[8][kClStride], s_ch[8][kClStride];   // w/N w_min, w/N w_max per plan
     __shared__ float s_part[2][4][BM];           // per lane quarter and plan: partial F, dF
+    __shared__ __align__(16) uint16_t s_gst[KIND == 1 ? EPI_WARPS : 1][8 * 32];   // dose GEMM: G staging per warp
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int np = kp.n_probs;
@@ -724,39 +726,52 @@ __global__ void __launch_bounds__(NTHREADS, 1) k_tc(const __grid_constant__ KPar
 #pragma unroll
                             for (int i = 0; i < CW; ++i) n_act += (out[i] != 0.0f && row0 + i < n_rows) ? 1 : 0;
                         }
-                        // rows of G (or of the dose) run over points: the 8 x 8 blocks of (plan,
-                        // point) values are transposed within each group of 8 lanes, so that a
-                        // lane writes 8 consecutive points of one plan, 16 bytes per term
-                        uint32_t wv[CW], wv3[CW];   // BF16 terms 1 | 2 (or the FP32 dose), term 3
+                        if (wdose) {
+                            // rows of the dose run over points: the 8 x 8 blocks of (plan, point)
+                            // values are transposed within each group of 8 lanes, so that a lane
+                            // writes 8 consecutive points of one plan
+                            uint32_t wv[CW];
 #pragma unroll
-                        for (int i = 0; i < CW; ++i) {
-                            if (wdose) {
-                                wv[i] = __float_as_uint(out[i]);
-                                wv3[i] = 0u;
-                            } else {   // terms 1 and 2 packed by one conversion; term 3 for bf16x3
-                                const float r1 = out[i] - __bfloat162float(__float2bfloat16_rn(out[i]));
-                                const __nv_bfloat162 b12 = __floats2bfloat162_rn(out[i], r1);
-                                wv[i] = *reinterpret_cast<const uint32_t *>(&b12);
-                                wv3[i] = kp.nG > 2 ? (uint32_t)__bfloat16_as_ushort(__float2bfloat16_rn(
-                                                         r1 - __bfloat162float(b12.y)))
-                                                   : 0u;
-                            }
-                        }
-                        transpose8(wv, lane);
-                        if (kp.nG > 2 && !wdose) transpose8(wv3, lane);
-                        const int row = w.ptile * BM + c + (lane & 7);   // compact row of this lane's plan
-                        if (row < n_rows) {
-                            const size_t off = (size_t)row * d.ld_g + w.sub * BM + q * 32 + (lane >> 3) * 8;
-                            if (wdose) {
+                            for (int i = 0; i < CW; ++i) wv[i] = __float_as_uint(out[i]);
+                            transpose8(wv, lane);
+                            const int row = w.ptile * BM + c + (lane & 7);
+                            if (row < n_rows) {
+                                const size_t off = (size_t)row * d.ld_g + w.sub * BM + q * 32 + (lane >> 3) * 8;
                                 float4 *o4 = reinterpret_cast<float4 *>(d.dose_out + off);
                                 o4[0] = make_float4(__uint_as_float(wv[0]), __uint_as_float(wv[1]),
                                                     __uint_as_float(wv[2]), __uint_as_float(wv[3]));
                                 o4[1] = make_float4(__uint_as_float(wv[4]), __uint_as_float(wv[5]),
                                                     __uint_as_float(wv[6]), __uint_as_float(wv[7]));
-                            } else {
-                                *reinterpret_cast<uint4 *>(d.G[0] + off) = pick16(wv, 0x5410u);
-                                *reinterpret_cast<uint4 *>(d.G[1] + off) = pick16(wv, 0x7632u);
-                                if (kp.nG > 2) *reinterpret_cast<uint4 *>(d.G[2] + off) = pick16(wv3, 0x5410u);
+                            }
+                        } else {
+                            // rows of G run over points: each BF16 term passes through this warp's
+                            // 512 bytes of shared memory as [plan][point], from which every lane
+                            // takes 8 consecutive points of one plan (one 16-byte store)
+                            uint32_t t12[CW];   // terms 1 | 2, packed by one conversion
+                            uint16_t t3[CW];    // term 3 (bf16x3)
+#pragma unroll
+                            for (int i = 0; i < CW; ++i) {
+                                const float r1 = out[i] - __bfloat162float(__float2bfloat16_rn(out[i]));
+                                const __nv_bfloat162 b12 = __floats2bfloat162_rn(out[i], r1);
+                                t12[i] = *reinterpret_cast<const uint32_t *>(&b12);
+                                t3[i] = kp.nG > 2 ? __bfloat16_as_ushort(__float2bfloat16_rn(r1 - __bfloat162float(b12.y)))
+                                                  : (uint16_t)0;
+                            }
+                            uint16_t *stg = s_gst[warp];
+                            const int prow = lane >> 2, pseg = (lane & 3) * 8;   // plan, first point written
+                            const int row = w.ptile * BM + c + prow;
+                            const size_t off = (size_t)row * d.ld_g + w.sub * BM + q * 32 + pseg;
+#pragma unroll
+                            for (int term = 0; term < 3; ++term) {
+                                if (term >= kp.nG) break;
+#pragma unroll
+                                for (int i = 0; i < CW; ++i)
+                                    stg[i * 32 + lane] = term == 0 ? (uint16_t)(t12[i] & 0xffffu)
+                                                       : term == 1 ? (uint16_t)(t12[i] >> 16) : t3[i];
+                                __syncwarp();
+                                const uint4 v = *reinterpret_cast<const uint4 *>(stg + prow * 32 + pseg);
+                                if (row < n_rows) *reinterpret_cast<uint4 *>(d.G[term] + off) = v;
+                                __syncwarp();
                             }
                         }
                     }
