@@ -529,6 +529,7 @@ __device__ __forceinline__ void step_plan(const SolverState &s, const UpdatePara
             // cache; fully unrolled, one warp's pass over straight-line code is fetch-bound)
             // and alpha_k of the first loop is kept on lane k for the second.
             float al_l = 0.0f;
+            const float rho_f = (float)rho_l;   // lane i: rho of slot i, one shuffle per use
             float sc[EPL], yc[EPL];
             {
                 const int i0 = nw;
@@ -540,12 +541,12 @@ __device__ __forceinline__ void step_plan(const SolverState &s, const UpdatePara
                     yc[e] = e < epl ? Yi[lane + 32 * e] : 0.0f;
                 }
             }
+            int i = nw;   // slot of pair k (newest first); no integer division in the loop
 #pragma unroll 1
             for (int k = 0; k < cnt; ++k) {
-                const int i = (nw - k + m) % m;
                 float sn[EPL], yn[EPL];
                 const bool more = k + 1 < cnt;
-                const int i1 = (nw - k - 1 + m) % m;
+                const int i1 = i == 0 ? m - 1 : i - 1;
                 const float *Sn = HS + (size_t)i1 * nd;
                 const float *Yn = HY + (size_t)i1 * nd;
 #pragma unroll
@@ -553,7 +554,7 @@ __device__ __forceinline__ void step_plan(const SolverState &s, const UpdatePara
                     sn[e] = (more && e < epl) ? Sn[lane + 32 * e] : 0.0f;
                     yn[e] = (more && e < epl) ? Yn[lane + 32 * e] : 0.0f;
                 }
-                const float rho = (float)__shfl_sync(kFull, rho_l, i);
+                const float rho = __shfl_sync(kFull, rho_f, i);
                 float d0 = 0.0f, d1 = 0.0f;   // two partial sums: half the dependent chain
 #pragma unroll
                 for (int e = 0; e < EPL; e += 2) {
@@ -568,12 +569,13 @@ __device__ __forceinline__ void step_plan(const SolverState &s, const UpdatePara
                     sc[e] = sn[e];
                     yc[e] = yn[e];
                 }
+                i = i1;
             }
             const float gamf = (float)gam;
 #pragma unroll
             for (int e = 0; e < EPL; ++e) q[e] *= gamf;
+            const int io = (nw - (cnt - 1) + m) % m;   // oldest pair first
             {
-                const int io = (nw - (cnt - 1) + m) % m;   // oldest pair first
                 const float *Si = HS + (size_t)io * nd;
                 const float *Yi = HY + (size_t)io * nd;
 #pragma unroll
@@ -582,12 +584,12 @@ __device__ __forceinline__ void step_plan(const SolverState &s, const UpdatePara
                     yc[e] = e < epl ? Yi[lane + 32 * e] : 0.0f;
                 }
             }
+            i = io;
 #pragma unroll 1
             for (int k = cnt - 1; k >= 0; --k) {
-                const int i = (nw - k + m) % m;
                 float sn[EPL], yn[EPL];
                 const bool more = k > 0;
-                const int i1 = (nw - k + 1 + m) % m;
+                const int i1 = i == m - 1 ? 0 : i + 1;
                 const float *Sn = HS + (size_t)i1 * nd;
                 const float *Yn = HY + (size_t)i1 * nd;
 #pragma unroll
@@ -595,7 +597,7 @@ __device__ __forceinline__ void step_plan(const SolverState &s, const UpdatePara
                     sn[e] = (more && e < epl) ? Sn[lane + 32 * e] : 0.0f;
                     yn[e] = (more && e < epl) ? Yn[lane + 32 * e] : 0.0f;
                 }
-                const float rho = (float)__shfl_sync(kFull, rho_l, i);
+                const float rho = __shfl_sync(kFull, rho_f, i);
                 const float alk = __shfl_sync(kFull, al_l, k);
                 float d0 = 0.0f, d1 = 0.0f;
 #pragma unroll
@@ -610,6 +612,7 @@ __device__ __forceinline__ void step_plan(const SolverState &s, const UpdatePara
                     sc[e] = sn[e];
                     yc[e] = yn[e];
                 }
+                i = i1;
             }
         }
         double gtp = 0.0;

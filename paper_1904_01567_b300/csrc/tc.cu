@@ -311,12 +311,6 @@ __device__ __forceinline__ void transpose8(uint32_t (&v)[8], int lane)
     }
 }
 
-__device__ __forceinline__ uint4 pick16(const uint32_t (&v)[8], uint32_t sel)
-{
-    return make_uint4(__byte_perm(v[0], v[1], sel), __byte_perm(v[2], v[3], sel),
-                      __byte_perm(v[4], v[5], sel), __byte_perm(v[6], v[7], sel));
-}
-
 constexpr int kClStride = 132;   // row stride of the per-plan weight tables (bank spread)
 
 // Persistent: the grid is at most one CTA per SM, and each CTA walks the work items of all
