@@ -318,8 +318,7 @@ __device__ __forceinline__ void step_plan(const SolverState &s, const UpdatePara
     const float *HS = s.S + (size_t)j * m * nd, *HY = s.Y + (size_t)j * m * nd;
     if (hS) {
         const int q4 = nd >> 2;   // 16-byte chunks per row
-        for (int k = 0; k < cnt; ++k) {
-            const int i = (nw - k + m) % m;
+        for (int k = 0, i = nw; k < cnt; ++k, i = i == 0 ? m - 1 : i - 1) {   // newest first
             for (int c = lane; c < q4; c += 32) {
                 cp_async16(hS + (size_t)i * nd + 4 * c, HS + (size_t)i * nd + 4 * c);
                 cp_async16(hY + (size_t)i * nd + 4 * c, HY + (size_t)i * nd + 4 * c);
@@ -403,7 +402,7 @@ __device__ __forceinline__ void step_plan(const SolverState &s, const UpdatePara
         const bool ok = isfinite(dF) && isfinite(Ft) && dF <= u.c1 * alpha * gtp;
         if (ok) {
             float sv[EPL], yv[EPL];
-            double sy = 0.0, yy = 0.0;
+            double sy = 0.0, yy = 0.0, sy1 = 0.0, yy1 = 0.0;   // two partial sums each
             bool fin = true;
 #pragma unroll
             for (int e = 0; e < EPL; ++e) {
@@ -415,8 +414,13 @@ __device__ __forceinline__ void step_plan(const SolverState &s, const UpdatePara
                     const float xn = xtv[e], gn = gtv[e];
                     sv[e] = xn - xv[e];
                     yv[e] = gn - gov[e];
-                    sy += (double)sv[e] * (double)yv[e];
-                    yy += (double)yv[e] * (double)yv[e];
+                    if (e & 1) {
+                        sy1 += (double)sv[e] * (double)yv[e];
+                        yy1 += (double)yv[e] * (double)yv[e];
+                    } else {
+                        sy += (double)sv[e] * (double)yv[e];
+                        yy += (double)yv[e] * (double)yv[e];
+                    }
                     fin = fin && isfinite(gn);
                     gmax = fmaxf(gmax, fabsf(gn));
                     x[l] = xn;
@@ -425,8 +429,8 @@ __device__ __forceinline__ void step_plan(const SolverState &s, const UpdatePara
                     gv[e] = gn;
                 }
             }
-            sy = warp_sum_d(sy);   // curvature products in FP64
-            yy = warp_sum_d(yy);
+            sy = warp_sum_d(sy + sy1);   // curvature products in FP64
+            yy = warp_sum_d(yy + yy1);
             fin = __all_sync(kFull, fin);
             gmax = warp_max_f(gmax);
             if (fin && sy > 1e-12 * yy) {
@@ -615,11 +619,14 @@ __device__ __forceinline__ void step_plan(const SolverState &s, const UpdatePara
                 i = i1;
             }
         }
-        double gtp = 0.0;
+        double gtp = 0.0, gtp1 = 0.0;   // two partial sums: half the chain of FP64 adds
 #pragma unroll
         for (int e = 0; e < EPL; ++e)
-            if (e < epl) gtp += (double)gv[e] * (double)(-q[e]);
-        gtp = warp_sum_d(gtp);   // directional derivative for the Armijo test, FP64
+            if (e < epl) {
+                if (e & 1) gtp1 += (double)gv[e] * (double)(-q[e]);
+                else gtp += (double)gv[e] * (double)(-q[e]);
+            }
+        gtp = warp_sum_d(gtp + gtp1);   // directional derivative for the Armijo test, FP64
         double alpha0 = (cnt == 0) ? fmin(1.0, 1.0 / (double)gmax) : 1.0;
         if (!(gtp < 0.0)) {       // not a descent direction: steepest descent, fresh history
             cnt = 0;
