@@ -139,3 +139,90 @@ def test_active_set_gradient_engages_at_three_percent(gmco_mod):
     assert sa == sb and sa > int(a["iters"].max()) // 2, (sa, a["iters"])
     for k in ("T", "objectives", "iters", "status"):
         assert np.array_equal(a[k], b[k]), k
+
+
+def _limit_case(rng, n_pnt, n_dwell, n_struct):
+    """Seeded dense case at a size limit: inverse-square-like dose rates (0.002-0.2 Gy/s), so
+    that a uniform start gives about 10-40 Gy, structures of uneven size, and per structure a
+    lower bound, an upper bound or both around those doses."""
+    r2 = rng.uniform(0.5, 12.0, (n_pnt, n_dwell))
+    A = (0.1 / r2).astype(np.float32)
+    sid = rng.choice(n_struct, n_pnt, p=np.arange(1, n_struct + 1) / (n_struct * (n_struct + 1) / 2))
+    sid[:n_struct] = np.arange(n_struct)   # every structure has points
+    d_mid = A.sum(axis=1).mean()
+    params = np.empty((n_struct, 4))
+    for s in range(n_struct):
+        kind = s % 3
+        lo = d_mid * rng.uniform(0.8, 0.95 if kind == 2 else 1.1) if kind != 1 else -np.inf
+        hi = d_mid * rng.uniform(1.05, 1.3) if kind != 0 else np.inf
+        params[s] = (rng.uniform(0.5, 2.0), lo, hi, rng.uniform(0.5, 2.0))
+    return A, sid.astype(np.int32), params
+
+
+def _penalty_at(params, sid, w, d):
+    """Eq. (1) in FP64 at given doses d: F and h = dF/dd per point."""
+    N = np.bincount(sid, minlength=params.shape[0]).astype(np.float64)
+    k = (np.asarray(w, np.float64) / N)[sid]
+    a, lo, hi, b = (params[sid, c] for c in range(4))
+    u = np.maximum(lo - d, 0.0)
+    o = np.maximum(d - hi, 0.0)
+    return float(np.sum(k * (a * u * u + b * o * o))), 2.0 * k * (b * o - a * u)
+
+
+# split depth of each form: relative error of A / s and of one dF/dd value in its BF16 terms
+SPLIT_EPS = {"bf16x3": 2.0 ** -23, "bf16x2": 2.0 ** -16, "fp32": 0.0}
+
+
+@pytest.mark.parametrize("form,n_dwell,n_struct", [
+    ("bf16x3", 512, 8),   # tensor-core limits: 512 dwells (8 K blocks of 64), 8 structures
+    ("bf16x2", 512, 8),
+    ("fp32", 1024, 16),   # FP32 SIMT limits: the step kernel's widest form
+])
+def test_size_limits(gmco_mod, oracle_mod, form, n_dwell, n_struct):
+    """At the largest sizes each form accepts:
+
+    - doses match the oracle within the form's bound;
+    - F is the Eq. (1) sum over the kernel's own doses up to FP32 rounding (1e-6), and the
+      gradient is 2 x A^T dF/dd of those doses within the bound its arithmetic gives: the BF16
+      split of A and of dF/dd (SPLIT_EPS each) and FP32 accumulation over the points;
+    - a short solve reports the oracle's objective at its returned dwell times (zero where it
+      meets every bound), below the uniform start's;
+    - one dwell or one structure more is refused before any device work."""
+    rng = np.random.default_rng(n_dwell + n_struct)
+    A, sid, params = _limit_case(rng, 1500, n_dwell, n_struct)
+    W = rng.uniform(0.1, 10.0, (6, n_struct)).astype(np.float32)
+    X = rng.uniform(0.5, 1.5, (6, n_dwell)).astype(np.float32)
+    with gmco_mod.Problem(A, sid, params, precision=form) as pr:
+        out = pr.evaluate(W, X, objectives=True, grad=True, dose=True)
+        sol = pr.solve_batch(W, max_iters=30, tol=0.0)
+    bd = FORMS[form][0] if form in FORMS else 1e-5
+    A64 = A.astype(np.float64)
+    acc = A.shape[0] * 2.0 ** -24
+    for j in range(W.shape[0]):
+        _, _, d, _ = oracle_mod.objective(A, sid, params, W[j], X[j])
+        dg = out["dose"][j].astype(np.float64)
+        assert np.max(np.abs(dg - d) / d) <= bd
+        Fg, hg = _penalty_at(params, sid, W[j], dg)
+        assert abs(out["objectives"][j] / Fg - 1.0) <= 1e-6, (j, out["objectives"][j], Fg)
+        x = X[j].astype(np.float64)
+        g_own = 2.0 * x * (A64.T @ hg)
+        bound = 2.0 * x * (A64.T @ np.abs(hg)) * (2.0 * SPLIT_EPS[form] + acc)
+        err = np.abs(out["grad"][j] - g_own)
+        assert np.all(err <= 2.0 * bound + 1e-12 * np.max(np.abs(g_own))), (j, np.max(err / bound))
+    for j in range(W.shape[0]):
+        F = oracle_mod.objective(A, sid, params, W[j], np.sqrt(sol["T"][j]))[0]
+        F0 = oracle_mod.objective(A, sid, params, W[j], np.ones(n_dwell))[0]
+        # where the FP32 doses meet every bound (F = 0), the FP64 doses of the same dwell times
+        # may cross one by the dose tolerance 1e-5 d: F <= k (1e-5 d)^2, about 1e-8 of the
+        # start's k (0.1 d)^2
+        assert abs(sol["objectives"][j] - F) <= 1e-4 * F + 1e-8 * F0
+        assert F < F0
+    refused = gmco_mod.EUNSUPPORTED if form != "fp32" else gmco_mod.EINVAL
+    A2, sid2, params2 = _limit_case(rng, 64, n_dwell + 1, n_struct)
+    with pytest.raises(gmco_mod.GmcoError) as e:
+        gmco_mod.Problem(A2, sid2, params2, precision=form)
+    assert e.value.status == refused
+    A3, sid3, params3 = _limit_case(rng, 64, 16, n_struct + 1)
+    with pytest.raises(gmco_mod.GmcoError) as e:
+        gmco_mod.Problem(A3, sid3, params3, precision=form)
+    assert e.value.status == refused
