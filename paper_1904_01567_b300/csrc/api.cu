@@ -298,7 +298,7 @@ gmco_status launch_dose_eval(gmco_problem *pr, const SolverState &s, cudaStream_
 // reset of the next step's row counter, and the fused update (k_step) that writes the next
 // step's rows.  Step k uses counter k % 2; `steps` is even so a graph starts on counter 0.
 gmco_status record_steps(gmco_problem *pr, int form, int steps, const UpdateParams &u,
-                         cudaStream_t st)
+                         int32_t P, cudaStream_t st)
 {
     SolverState s = pr->s;
     const DevProblem &pb = pr->pb;
@@ -335,7 +335,17 @@ gmco_status record_steps(gmco_problem *pr, int form, int steps, const UpdatePara
         } else {
             // the dose GEMM also clears the next step's counter
             int32_t nl = 0;
-            CK(tc_launch_gemms(tc_single_set(pb, pr->tcb), k & 1, true, false, true, st, &nl));
+            // the update that follows reads the plans' history rows and vectors: the gradient
+            // GEMM brings them into L2
+            TcLaunchSet set = tc_single_set(pb, pr->tcb);
+            const int64_t vbytes = (int64_t)P * pb.nd_pad * (int64_t)sizeof(float);
+            const void *ranges[kTcPrefetch] = {s.S, s.Y, s.x, s.p, s.g, s.xt};
+            const int64_t sizes[kTcPrefetch] = {vbytes * s.m, vbytes * s.m, vbytes, vbytes, vbytes, vbytes};
+            for (int r = 0; r < kTcPrefetch; ++r) {
+                set.pf_ptr[r] = ranges[r];
+                set.pf_bytes[r] = sizes[r];
+            }
+            CK(tc_launch_gemms(set, k & 1, true, false, true, st, &nl));
             a.n_ptiles = tc_n_ptiles(pb);
             a.sp = pr->tcb.sp;
             a.sp_flag = pr->tcb.act ? pr->tcb.act + 2 + (k & 1) : nullptr;
@@ -390,7 +400,7 @@ gmco_status run_loop(gmco_problem *pr, int form, int32_t P, const UpdateParams &
         cudaGraph_t g = nullptr;
         CK(cudaStreamBeginCapture(pr->stream, cudaStreamCaptureModeThreadLocal));
         const int64_t l0 = pr->launches;
-        gmco_status rs = record_steps(pr, form, steps, u, pr->stream);
+        gmco_status rs = record_steps(pr, form, steps, u, P, pr->stream);
         pr->launches = l0;
         cudaError_t ee = cudaStreamEndCapture(pr->stream, &g);
         if (rs != GMCO_OK) {

@@ -100,6 +100,12 @@ __device__ __forceinline__ void tma_load_2d(uint32_t dst, const CUtensorMap *map
         : "memory");
 }
 
+// Asks L2 to fetch [p, p + bytes) (16-byte aligned, a multiple of 16 bytes); no completion.
+__device__ __forceinline__ void prefetch_l2(const void *p, uint32_t bytes)
+{
+    asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(p), "r"(bytes) : "memory");
+}
+
 __device__ __forceinline__ void tmem_alloc(uint32_t holder, uint32_t ncols)
 {
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(holder),
@@ -221,6 +227,8 @@ struct KParams {
     Group g[3];
     int32_t n_stages, stage_bytes, slot_bytes;   // ring stage size, size of one N-side slot
     int32_t b_off;                               // offset of the N-side slots in a stage
+    const void *pf_ptr[kTcPrefetch];             // gradient GEMM: L2 prefetch ranges (bytes)
+    int64_t pf_bytes[kTcPrefetch];
     int32_t *err;
 };
 
@@ -824,6 +832,24 @@ __global__ void __launch_bounds__(NTHREADS, 1) k_tc(const __grid_constant__ KPar
     }
     fence_before();
     __syncthreads();
+    if constexpr (KIND == 2) {
+        if (warp == W_TMEM) {
+            // L2 prefetch of the update's operands, in 16 KB pieces shared out over the CTAs
+            // that had work, issued as each CTA finishes so that the reads overlap the end of
+            // this kernel and the start of the next
+            constexpr int64_t PIECE = 16384;
+            const int64_t ctas = min((int64_t)gridDim.x, (int64_t)n_items);
+            for (int r = 0; r < kTcPrefetch; ++r) {
+                const char *base = static_cast<const char *>(kp.pf_ptr[r]);
+                const int64_t bytes = kp.pf_bytes[r];
+                const int64_t pieces = (bytes + PIECE - 1) / PIECE;
+                for (int64_t c = blockIdx.x + lane * ctas; c < pieces; c += 32 * ctas) {
+                    const int64_t off = c * PIECE;
+                    prefetch_l2(base + off, (uint32_t)min(PIECE, bytes - off));
+                }
+            }
+        }
+    }
     if constexpr (KIND == 1) {
         // one count per CTA into the single problem's counter of this step
         if (threadIdx.x == 0 && kp.sparse_ok && s_prob[0].act && s_act > 0)
@@ -1075,6 +1101,11 @@ KParams make_params(const TcLaunchSet &set, int kind, int parity, bool with_dT, 
     k.stage_bytes = k.b_off + max_b * k.slot_bytes;
     k.n_stages = std::max(1, std::min(MAX_STAGES, SMEM_BUDGET / k.stage_bytes));
     k.err = set.err;
+    if (kind == 2)
+        for (int r = 0; r < kTcPrefetch; ++r) {
+            k.pf_ptr[r] = set.pf_ptr[r];
+            k.pf_bytes[r] = set.pf_ptr[r] ? set.pf_bytes[r] & ~(int64_t)15 : 0;
+        }
     return k;
 }
 
@@ -1149,11 +1180,12 @@ SplitPlan tc_split_plan(const DevProblem &pb, int32_t kb_per_split, int32_t grad
         p.max_split = (int32_t)ceil_div(p.kb_total, kb_per_split);
         p.min_kb = 1;
     } else {
-        // about one wave of CTAs, but splits of at least 128 points: a few plan rows would
-        // otherwise get up to 148 splits whose partial sums the step kernel adds
+        // about one wave of CTAs, but splits of at least 384 points: a few plan rows would
+        // otherwise get up to 148 splits whose partial sums the step kernel adds (measured at
+        // 1-256 plans of 12000 points: 384 points per split beat 128, 512 and longer ones)
         p.target_ctas = 148;
         p.max_split = tc_max_split(pb);
-        p.min_kb = 2;
+        p.min_kb = 6;
     }
     return p;
 }

@@ -17,6 +17,7 @@ using AllocFn = std::function<cudaError_t(void **, size_t)>;
 
 constexpr int kMaxMulti = 64;    // problems in one GEMM launch (descriptors in shared memory)
 constexpr int kTcActWords = 8;   // active-set counters of a problem (TcDoseProb::act)
+constexpr int kTcPrefetch = 6;   // L2 prefetch ranges of a gradient-GEMM launch
 
 // Operand maps.  Dose GEMM: m[0..2] A terms (rows = points, columns = dwells), m[3..5] T terms
 // (rows = plans, columns = dwells), m[6], m[7] the two terms of dT.  Gradient GEMM: m[0..2] A^T terms (rows = dwells,
@@ -120,6 +121,11 @@ struct TcLaunchSet {
     int32_t *gs_act = nullptr;
     float *gs_out = nullptr;                                       // gradient, split 0 of gpart
     int32_t gs_ld = 0, gs_nd = 0, gs_ptiles = 0, gs_kpad = 0, gs_terms = 0, gs_cap = 0;
+    // byte ranges the gradient GEMM prefetches into L2 for the update that follows it (the
+    // plans' history rows and vectors): that kernel is bound by the MMA issue and leaves DRAM
+    // bandwidth to spare, while the update waits on these reads
+    const void *pf_ptr[kTcPrefetch] = {};
+    int64_t pf_bytes[kTcPrefetch] = {};
     int32_t *err = nullptr;
 };
 
