@@ -469,6 +469,23 @@ __global__ void __launch_bounds__(NTHREADS, 1) k_tc(const __grid_constant__ KPar
                 }
             }
         }
+        if constexpr (KIND == 2) {
+            // once this CTA's operand loads are all issued (its MMAs and epilogue still to
+            // come), L2 prefetch of the update's operands, in 16 KB pieces shared out over the
+            // CTAs that have work
+            __syncwarp();
+            constexpr int64_t PIECE = 16384;
+            const int64_t ctas = min((int64_t)gridDim.x, (int64_t)n_items);
+            for (int r = 0; r < kTcPrefetch; ++r) {
+                const char *base = static_cast<const char *>(kp.pf_ptr[r]);
+                const int64_t bytes = kp.pf_bytes[r];
+                const int64_t pieces = (bytes + PIECE - 1) / PIECE;
+                for (int64_t c = blockIdx.x + lane * ctas; c < pieces; c += 32 * ctas) {
+                    const int64_t off = c * PIECE;
+                    prefetch_l2(base + off, (uint32_t)min(PIECE, bytes - off));
+                }
+            }
+        }
     } else if (warp == W_MMA) {
         // ---------------- MMA issuer (the whole warp walks the items; one elected lane issues)
         {
@@ -832,24 +849,6 @@ __global__ void __launch_bounds__(NTHREADS, 1) k_tc(const __grid_constant__ KPar
     }
     fence_before();
     __syncthreads();
-    if constexpr (KIND == 2) {
-        if (warp == W_TMEM) {
-            // L2 prefetch of the update's operands, in 16 KB pieces shared out over the CTAs
-            // that had work, issued as each CTA finishes so that the reads overlap the end of
-            // this kernel and the start of the next
-            constexpr int64_t PIECE = 16384;
-            const int64_t ctas = min((int64_t)gridDim.x, (int64_t)n_items);
-            for (int r = 0; r < kTcPrefetch; ++r) {
-                const char *base = static_cast<const char *>(kp.pf_ptr[r]);
-                const int64_t bytes = kp.pf_bytes[r];
-                const int64_t pieces = (bytes + PIECE - 1) / PIECE;
-                for (int64_t c = blockIdx.x + lane * ctas; c < pieces; c += 32 * ctas) {
-                    const int64_t off = c * PIECE;
-                    prefetch_l2(base + off, (uint32_t)min(PIECE, bytes - off));
-                }
-            }
-        }
-    }
     if constexpr (KIND == 1) {
         // one count per CTA into the single problem's counter of this step
         if (threadIdx.x == 0 && kp.sparse_ok && s_prob[0].act && s_act > 0)
