@@ -277,7 +277,7 @@ __device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wai
 
 // hS / hY: this plan's history rows in shared memory (m x nd each, the same slots as s.S / s.Y),
 // or null to read them from global memory
-template <int EPL>
+template <int EPL, bool ONE_TRIP = false>
 __device__ __forceinline__ void step_plan(const SolverState &s, const UpdateParams &u,
                                           const StepArgs &a, const int j, const int lane,
                                           float *hS = nullptr, float *hY = nullptr)
@@ -347,6 +347,25 @@ __device__ __forceinline__ void step_plan(const SolverState &s, const UpdatePara
     for (int e = 0; e < EPL; ++e) gtv[e] = 0.0f;
     constexpr int QB = EPL <= 12 ? 8 : 4;   // splits in flight (registers: QB x EPL)
     int q = 0;
+    if constexpr (ONE_TRIP) {
+        // the last, partial batch of splits as one masked round trip (the single-problem
+        // kernel has the registers for it; the multi-problem one would spill)
+        for (; q < n_split; q += QB) {
+            float v[QB][EPL];
+#pragma unroll
+            for (int r = 0; r < QB; ++r) {
+                const bool on = q + r < n_split;
+                const float *gq = a.gpart + ((size_t)(on ? q + r : q) * R + slot) * nd + lane;
+#pragma unroll
+                for (int e = 0; e < EPL; ++e) v[r][e] = on && e < epl ? gq[32 * e] : 0.0f;
+            }
+#pragma unroll
+            for (int r = 0; r < QB; ++r)
+#pragma unroll
+                for (int e = 0; e < EPL; ++e)
+                    if (e < epl && q + r < n_split) gtv[e] += v[r][e];
+        }
+    }
     for (; q + QB <= n_split; q += QB) {
         float v[QB][EPL];
 #pragma unroll
@@ -674,7 +693,7 @@ __global__ void __launch_bounds__(256) k_step(SolverState s, UpdateParams u, Ste
         hS = hist + (size_t)(threadIdx.x >> 5) * 2 * s.m * s.nd_pad;
         hY = hS + (size_t)s.m * s.nd_pad;
     }
-    step_plan<EPL>(s, u, a, j, threadIdx.x & 31, hS, hY);
+    step_plan<EPL, true>(s, u, a, j, threadIdx.x & 31, hS, hY);
     if (use_smem) cp_async_wait_all();   // nothing in flight into shared memory at exit
 }
 
