@@ -639,6 +639,41 @@ __global__ void __launch_bounds__(NTHREADS, 1) k_tc(const __grid_constant__ KPar
                             const float2 a2 = make_float2(-sg * sc, -sg * sc), b2 = make_float2(sg * bnd, sg * bnd);
                             const float2 s2 = make_float2(sg * sc, sg * sc), g2 = make_float2(-2.0f * sg * sc, -2.0f * sg * sc);
                             const float *wrow = mode == 1 ? clr : chr;
+                            // a chunk whose 8 x 32 pairs all have v = v_b = 0 (most of them once
+                            // the plans near their optima) gives zeros only: F and dF parts, dF/dd
+                            bool act = false;
+#pragma unroll
+                            for (int i = 0; i < CW; i += 2) {
+                                const float2 acc = make_float2(__uint_as_float(dv[i]), __uint_as_float(dv[i + 1]));
+                                const float2 t = __ffma2_rn(a2, acc, b2);
+                                act = act || t.x > 0.0f || t.y > 0.0f;
+                                if (has_dT) {
+                                    const float2 dacc = make_float2(__uint_as_float(ddv[i]), __uint_as_float(ddv[i + 1]));
+                                    const float2 tb = __ffma2_rn(s2, dacc, t);
+                                    act = act || tb.x > 0.0f || tb.y > 0.0f;
+                                }
+                            }
+                            if (!__any_sync(0xffffffffu, act)) {
+                                if ((lane & 3) == 0) {
+                                    s_part[0][q][c + ((lane >> 2) & 7)] = 0.0f;
+                                    s_part[1][q][c + ((lane >> 2) & 7)] = 0.0f;
+                                }
+                                const int row0 = w.ptile * BM + c;
+                                if (count && sparse) {   // no active point: empty mask words
+                                    if (lane < CW && row0 + lane < n_rows)
+                                        d.mask[((size_t)(row0 + lane) * d.n_ptiles + w.sub) * 4 + q] = 0u;
+                                    continue;
+                                }
+                                const int prow = lane >> 2, pseg = (lane & 3) * 8;   // as in the staged stores
+                                if (row0 + prow < n_rows) {
+                                    const size_t off = (size_t)(row0 + prow) * d.ld_g + w.sub * BM + q * 32 + pseg;
+#pragma unroll
+                                    for (int term = 0; term < 3; ++term)
+                                        if (term < kp.nG)
+                                            *reinterpret_cast<uint4 *>(d.G[term] + off) = make_uint4(0u, 0u, 0u, 0u);
+                                }
+                                continue;
+                            }
 #pragma unroll
                             for (int i = 0; i < CW; i += 2) {
                                 const float2 acc = make_float2(__uint_as_float(dv[i]), __uint_as_float(dv[i + 1]));
