@@ -267,20 +267,58 @@ __device__ __forceinline__ void write_trial_row(const SolverState &s, const Step
 // The step is one warp's dependent chain, so its global loads are issued together at the start
 // (the plan's scalars, rho of every history slot on the lanes, x, p, g, x_t) and the vectors
 // stay in registers until the next trial row is written.
-__device__ __forceinline__ void cp_async16(void *smem, const void *gmem)
+// The history rows go to shared memory by bulk copies (the copy engine, one instruction per
+// row) tracked by one mbarrier per plan, so that the warp's load/store unit stays free for the
+// objective and gradient partials read meanwhile.
+__device__ __forceinline__ uint32_t smem_addr(const void *p)
 {
-    asm volatile("cp.async.ca.shared.global [%0], [%1], 16;" ::"r"((uint32_t)__cvta_generic_to_shared(smem)),
-                 "l"(gmem)
+    return (uint32_t)__cvta_generic_to_shared(p);
+}
+__device__ __forceinline__ void hbar_init(uint64_t *b)
+{
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_addr(b)) : "memory");
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+__device__ __forceinline__ void hbar_expect(uint64_t *b, uint32_t bytes)
+{
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_addr(b)), "r"(bytes)
                  : "memory");
 }
-__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;" ::: "memory"); }
+__device__ __forceinline__ void bulk_to_smem(void *dst, const void *src, uint32_t bytes, uint64_t *b)
+{
+    asm volatile(
+        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+            smem_addr(dst)),
+        "l"(src), "r"(bytes), "r"(smem_addr(b))
+        : "memory");
+}
+// Waits (every lane) for the barrier's first phase; gives up after about a second.
+__device__ __forceinline__ bool hbar_wait(uint64_t *b)
+{
+    const long long t0 = clock64();
+    for (;;) {
+        uint32_t done;
+        asm volatile(
+            "{\n\t.reg .pred p;\n\t"
+            "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], 0;\n\t"
+            "selp.b32 %0, 1, 0, p;\n\t}"
+            : "=r"(done)
+            : "r"(smem_addr(b))
+            : "memory");
+        if (done) return true;
+        if (clock64() - t0 > 2000000000LL) return false;
+    }
+}
 
 // hS / hY: this plan's history rows in shared memory (m x nd each, the same slots as s.S / s.Y),
 // or null to read them from global memory
+// hbar: with hS, the mbarrier of the bulk history copies; *hbar_used is set once they are
+// issued (the caller then waits for them before the block exits).
 template <int EPL, bool ONE_TRIP = false>
 __device__ __forceinline__ void step_plan(const SolverState &s, const UpdateParams &u,
                                           const StepArgs &a, const int j, const int lane,
-                                          float *hS = nullptr, float *hY = nullptr)
+                                          float *hS = nullptr, float *hY = nullptr,
+                                          uint64_t *hbar = nullptr, bool *hbar_used = nullptr)
 {
     const int nd = s.nd_pad, epl = nd >> 5, m = s.m;
     const size_t vb = (size_t)j * nd;
@@ -316,17 +354,31 @@ __device__ __forceinline__ void step_plan(const SolverState &s, const UpdatePara
     // the history rows the two-loop will read, copied asynchronously while the partial sums
     // below are added (16-byte copies; rows are nd_pad floats, a multiple of 32)
     const float *HS = s.S + (size_t)j * m * nd, *HY = s.Y + (size_t)j * m * nd;
-    if (hS) {
-        const int q4 = nd >> 2;   // 16-byte chunks per row
-        for (int k = 0, i = nw; k < cnt; ++k, i = i == 0 ? m - 1 : i - 1) {   // newest first
-            for (int c = lane; c < q4; c += 32) {
-                cp_async16(hS + (size_t)i * nd + 4 * c, HS + (size_t)i * nd + 4 * c);
-                cp_async16(hY + (size_t)i * nd + 4 * c, HY + (size_t)i * nd + 4 * c);
+    const float *HSg = HS, *HYg = HY;   // the global rows, kept for a wait that gives up
+    if (hS) {   // rows of nd_pad floats: 16-byte aligned, a multiple of 16 bytes
+        if (lane == 0) {
+            hbar_expect(hbar, (uint32_t)cnt * 2u * (uint32_t)nd * 4u);
+            for (int k = 0, i = nw; k < cnt; ++k, i = i == 0 ? m - 1 : i - 1) {   // newest first
+                bulk_to_smem(hS + (size_t)i * nd, HS + (size_t)i * nd, (uint32_t)nd * 4u, hbar);
+                bulk_to_smem(hY + (size_t)i * nd, HY + (size_t)i * nd, (uint32_t)nd * 4u, hbar);
             }
         }
+        *hbar_used = true;
         HS = hS;
         HY = hY;
     }
+    // every copy into shared memory has landed; if a bulk copy's wait gave up (never expected),
+    // the history is read from global memory instead and shared memory is left alone
+    bool staged = hS != nullptr;
+    auto history_ready = [&]() {
+        if (!staged) return;
+        if (!__all_sync(kFull, hbar_wait(hbar))) {
+            staged = false;
+            HS = HSg;
+            HY = HYg;
+        }
+        __syncwarp();
+    };
 
     // ---- results of this step's evaluation (fixed summation order)
     double fsum = 0.0, dfsum = 0.0;
@@ -456,16 +508,13 @@ __device__ __forceinline__ void step_plan(const SolverState &s, const UpdatePara
                 nw = (nw + 1) % m;
                 float *Sd = s.S + ((size_t)j * m + nw) * nd;
                 float *Yd = s.Y + ((size_t)j * m + nw) * nd;
-                if (hS) {   // every lane's copy of the slot being replaced has landed
-                    cp_async_wait_all();
-                    __syncwarp();
-                }
+                history_ready();   // the copy of the slot being replaced has landed
 #pragma unroll
                 for (int e = 0; e < EPL; ++e)
                     if (e < epl) {
                         Sd[lane + 32 * e] = sv[e];
                         Yd[lane + 32 * e] = yv[e];
-                        if (hS) {
+                        if (staged) {
                             hS[(size_t)nw * nd + lane + 32 * e] = sv[e];
                             hY[(size_t)nw * nd + lane + 32 * e] = yv[e];
                         }
@@ -478,7 +527,7 @@ __device__ __forceinline__ void step_plan(const SolverState &s, const UpdatePara
                     s.rho[(size_t)j * m + nw] = rho_new;
                     s.gamma[j] = gam;
                 }
-                if (hS) __syncwarp();   // the new pair is read back by every lane below
+                if (staged) __syncwarp();   // the new pair is read back by every lane below
             }
             const double Fprev = F_old;
             ++it;
@@ -543,10 +592,7 @@ __device__ __forceinline__ void step_plan(const SolverState &s, const UpdatePara
         float q[EPL];
 #pragma unroll
         for (int e = 0; e < EPL; ++e) q[e] = gv[e];
-        if (hS) {
-            cp_async_wait_all();
-            __syncwarp();
-        }
+        history_ready();
         if (cnt > 0) {
             // The history loops stay rolled (their bodies are reused from the instruction
             // cache; fully unrolled, one warp's pass over straight-line code is fetch-bound)
@@ -686,15 +732,19 @@ __global__ void __launch_bounds__(256) k_step(SolverState s, UpdateParams u, Ste
                                               int32_t use_smem)
 {
     extern __shared__ __align__(16) float hist[];
+    __shared__ __align__(8) uint64_t hbar;   // bulk history copies (one plan per block)
     const int j = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     if (j >= s.P) return;
     float *hS = nullptr, *hY = nullptr;
     if (use_smem) {
         hS = hist + (size_t)(threadIdx.x >> 5) * 2 * s.m * s.nd_pad;
         hY = hS + (size_t)s.m * s.nd_pad;
+        if ((threadIdx.x & 31) == 0) hbar_init(&hbar);
+        __syncwarp();
     }
-    step_plan<EPL, true>(s, u, a, j, threadIdx.x & 31, hS, hY);
-    if (use_smem) cp_async_wait_all();   // nothing in flight into shared memory at exit
+    bool used = false;
+    step_plan<EPL, true>(s, u, a, j, threadIdx.x & 31, hS, hY, use_smem ? &hbar : nullptr, &used);
+    if (used) hbar_wait(&hbar);   // nothing in flight into shared memory at exit
 }
 
 // The same step for the plans of several problems; each block's problem descriptor is
