@@ -206,7 +206,8 @@ gmco_status gmco_profile_evaluate(gmco_problem *prob, const float *penalty_weigh
  * graphs of steps_per_poll steps.  The paper solves one patient at a time; this is an
  * extension of its batched solve (Sec. 2.3.2) to many patients.
  * Results of patient p are bit for bit those of gmco_solve_batch on its own problem created
- * with options.grad_split_kb equal to the multi object's split setting.
+ * with options.grad_split_kb equal to the multi object's split setting (and the active-set
+ * gradient off, the default: the multi launch always forms the gradient with the GEMM).
  * The multi object keeps stacked copies of the problems' BF16 terms of A; the problems must
  * outlive it and must not be used by another call while a multi call runs. */
 
