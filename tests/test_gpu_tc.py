@@ -170,12 +170,14 @@ def _penalty_at(params, sid, w, d):
 
 
 # split depth of each form: relative error of A / s and of one dF/dd value in its BF16 terms
-SPLIT_EPS = {"bf16x3": 2.0 ** -23, "bf16x2": 2.0 ** -16, "fp32": 0.0}
+SPLIT_EPS = {"bf16x3": 2.0 ** -23, "bf16x2": 2.0 ** -16, "bf16": 2.0 ** -9, "fp8": 2.0 ** -4, "fp32": 0.0}
 
 
 @pytest.mark.parametrize("form,n_dwell,n_struct", [
     ("bf16x3", 512, 8),   # tensor-core limits: 512 dwells (8 K blocks of 64), 8 structures
     ("bf16x2", 512, 8),
+    ("bf16", 512, 8),     # one term of A: 2^-9 relative per element
+    ("fp8", 512, 8),      # E4M3 grid of A: 2^-4
     ("fp32", 1024, 16),   # FP32 SIMT limits: the step kernel's widest form
 ])
 def test_size_limits(gmco_mod, oracle_mod, form, n_dwell, n_struct):
@@ -215,7 +217,8 @@ def test_size_limits(gmco_mod, oracle_mod, form, n_dwell, n_struct):
         # where the FP32 doses meet every bound (F = 0), the FP64 doses of the same dwell times
         # may cross one by the dose tolerance 1e-5 d: F <= k (1e-5 d)^2, about 1e-8 of the
         # start's k (0.1 d)^2
-        assert abs(sol["objectives"][j] - F) <= 1e-4 * F + 1e-8 * F0
+        tol_f = max(1e-4, FORMS[form][1]) if form in FORMS else 1e-4   # the form's dose error
+        assert abs(sol["objectives"][j] - F) <= tol_f * F + 1e-8 * F0
         assert F < F0
     refused = gmco_mod.EUNSUPPORTED if form != "fp32" else gmco_mod.EINVAL
     A2, sid2, params2 = _limit_case(rng, 64, n_dwell + 1, n_struct)
