@@ -505,7 +505,7 @@ __device__ __forceinline__ void step_plan(const SolverState &s, const UpdatePara
             fin = __all_sync(kFull, fin);
             gmax = warp_max_f(gmax);
             if (fin && sy > 1e-12 * yy) {
-                nw = (nw + 1) % m;
+                nw = nw + 1 == m ? 0 : nw + 1;
                 float *Sd = s.S + ((size_t)j * m + nw) * nd;
                 float *Yd = s.Y + ((size_t)j * m + nw) * nd;
                 history_ready();   // the copy of the slot being replaced has landed
@@ -520,7 +520,7 @@ __device__ __forceinline__ void step_plan(const SolverState &s, const UpdatePara
                         }
                     }
                 cnt = min(cnt + 1, m);
-                const double rho_new = 1.0 / sy;
+                const double rho_new = __drcp_rn(sy);   // 1 / sy, correctly rounded
                 gam = sy / yy;
                 if (lane == nw) rho_l = rho_new;
                 if (lane == 0) {
@@ -643,7 +643,7 @@ __device__ __forceinline__ void step_plan(const SolverState &s, const UpdatePara
             const float gamf = (float)gam;
 #pragma unroll
             for (int e = 0; e < EPL; ++e) q[e] *= gamf;
-            const int io = (nw - (cnt - 1) + m) % m;   // oldest pair first
+            const int io = nw - (cnt - 1) < 0 ? nw - (cnt - 1) + m : nw - (cnt - 1);   // oldest pair first
             {
                 const float *Si = HS + (size_t)io * nd;
                 const float *Yi = HY + (size_t)io * nd;
