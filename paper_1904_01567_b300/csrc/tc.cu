@@ -1420,10 +1420,10 @@ TcRows tc_rows(const DevProblem &pb, const TcBuffers &b)
 }
 
 // ------------------------------------------------------------------ active-set gradient
-// Gradient of Eq. (4) from the active pairs only: g_j = sum over points i with dF/dd_i != 0 of
-// dF/dd_i A_ij, the same sum the gradient GEMM forms over every point, now over the few points
-// whose penalty term is on (their set shrinks to about 1% of a plan's points within a few tens
-// of iterations).  One CTA of four warps per compact plan row.  In each pass every warp lists
+// The A^T G part of the gradient, Eq. (2), from the active pairs only: g_j = sum over points i
+// with dF/dd_i != 0 of dF/dd_i A_ij, the sum the gradient GEMM forms over every point, over the
+// few points whose penalty term is on (their set shrinks to about 1% of a plan's points within a
+// few tens of iterations).  One CTA of four warps per compact plan row.  In each pass every warp lists
 // the active points of 2048 consecutive points from the dose epilogue's mask; the warps then
 // share the pass's list (entry k to warp (k / BATCH) mod 4) and add the A rows of their
 // entries; the four partial sums are added in warp order at the end.  CTA 0 also clears the
