@@ -280,6 +280,29 @@ def multi_patient_section(g, torch, args, peak):
             for s in specs]
     Ws = [weights_dirichlet(s["seed"], 256) for s in specs]
     gen_s = time.perf_counter() - t0
+    # step (i) on the GPU: the 64 patients' dose rate matrices from their point and dwell
+    # coordinates (device in and out), against the host generation above
+    geo = [(torch.from_numpy(p.points.astype(np.float32)).cuda(),
+            torch.from_numpy(p.dwells.astype(np.float32)).cuda()) for p in pats]
+    g.dose_rate_matrix(*geo[0])   # warm-up
+    torch.cuda.synchronize()
+    t1 = time.perf_counter()
+    for pts, dws in geo:
+        g.dose_rate_matrix(pts, dws)
+    torch.cuda.synchronize()
+    rate_s = time.perf_counter() - t1
+    rate_bytes = sum(4.0 * p.n_pnt * p.n_dwell for p in pats)
+    del geo
+    # one large call (the HBM write of A dominates the call's fixed cost there)
+    big_pts = torch.rand(262144, 3, device="cuda") * 6.0 - 3.0
+    big_dws = torch.rand(512, 3, device="cuda") * 4.0 - 2.0
+    g.dose_rate_matrix(big_pts, big_dws)
+    torch.cuda.synchronize()
+    t2 = time.perf_counter()
+    g.dose_rate_matrix(big_pts, big_dws)
+    big_s = time.perf_counter() - t2
+    big_bytes = 4.0 * 262144 * 512
+    del big_pts, big_dws
     probs = [g.Problem(p.A, p.sid, p.params, precision=args.precision,
                        steps_per_poll=args.steps_per_poll) for p in pats]
     mu = g.Multi(probs)
@@ -321,6 +344,14 @@ def multi_patient_section(g, torch, args, peak):
                       "frac_of_bf16_peak": achieved / peak if peak else None,
                       "algorithmic_flops": 3.0 * flop_unit},
         "generation_s": gen_s,
+        "dose_rate_gpu": {"s_all_patients": rate_s, "bytes_written": rate_bytes,
+                          "gbs_incl_call_overhead": rate_bytes / rate_s / 1e9,
+                          "large_call": {"points": 262144, "dwells": 512, "ms": 1e3 * big_s,
+                                         "gbs": big_bytes / big_s / 1e9,
+                                         "frac_of_hbm": big_bytes / big_s / 1e9 / load_peaks()[0]["hbm_gbs"]},
+                          "note": "gmco_dose_rate_matrix per patient (synchronous calls, device "
+                                  "buffers); generation_s is the host input generator, which "
+                                  "also samples the geometry"},
     }
 
 

@@ -108,6 +108,34 @@ typedef struct {
 /* Fills *opt with the defaults above. */
 void gmco_default_options(gmco_options *opt);
 
+/* ---- dose rate matrix ----
+ * Step (i) of the GPU planning flow (Sec. 2.2.1): the dose rate of every dwell position at
+ * every dose calculation point, the A of Eq. (dose).  The paper does not state its dose-rate
+ * model; this is the isotropic point source
+ *   A_il = lambda * sk * unit * g(r) / r^2,  r = max(|p_i - q_l|, r_min),  g = g0 + g1 r + g2 r^2,
+ * with r in cm.  Defaults (gmco_default_source): lambda = 1.109 cGy h^-1 U^-1, sk = 40700 U,
+ * unit = 1 / 360000 (cGy/h to Gy/s, so that dwell times are seconds), r_min = 0.1 cm,
+ * g = 1 + 0.005 r - 0.002 r^2. */
+typedef struct gmco_source {
+    double lambda, sk, unit, r_min, g0, g1, g2;
+} gmco_source;
+
+void gmco_default_source(gmco_source *src);
+
+/* Computes A on the current device in FP32.
+ *   points   n_pnt x 3 dose calculation point coordinates, cm (host or device, row-major)
+ *   dwells   n_dwell x 3 dwell position coordinates, cm (host or device)
+ *   src      the model, or NULL for the defaults
+ *   A_out    n_pnt x n_dwell, row-major, Gy/s (host or device; the layout gmco_create_problem
+ *            takes, which accepts the device buffer directly)
+ * 1 <= n_dwell <= 1024, 1 <= n_pnt <= 2^31.  Returns GMCO_EINVAL for bad sizes, NULL pointers,
+ * non-finite model constants or coordinates, r_min <= 0, or a distance where g(r) <= 0 (the
+ * model's radial fit is negative beyond about 23.6 cm).  Queued on cuda_stream (NULL: the
+ * default stream) and complete on return. */
+gmco_status gmco_dose_rate_matrix(const float *points, int64_t n_pnt, const float *dwells,
+                                  int64_t n_dwell, const gmco_source *src, float *A_out,
+                                  void *cuda_stream);
+
 /* Creates a problem on the current CUDA device.
  *   A               n_pnt x n_dwell dose-rate matrix, Gy/s, finite and >= 0 (Eq. (dose));
  *                   copied (and quantised for BF16/FP8), the caller may free it afterwards

@@ -7,6 +7,8 @@ from .oracle import (  # noqa: F401
     build,
     load,
     dose,
+    dose_rate,
+    DEFAULT_SOURCE,
     point_penalty,
     point_dpenalty,
     objective,

@@ -40,6 +40,27 @@ double oracle_point_dpenalty(double d, const double *prm)
     return 0.0;
 }
 
+/* ---------------------------------------------------------------- dose rate matrix */
+int oracle_dose_rate(const double *pts, int64_t n_pnt, const double *dw, int64_t n_dwell,
+                     const double *src, double *A)
+{
+    if (!pts || !dw || !src || !A || n_pnt < 0 || n_dwell < 0 || !(src[3] > 0.0)) return -1;
+    const double K = src[0] * src[1] * src[2];
+    for (int64_t i = 0; i < n_pnt; ++i) {
+        for (int64_t l = 0; l < n_dwell; ++l) {
+            const double dx = pts[3 * i] - dw[3 * l];
+            const double dy = pts[3 * i + 1] - dw[3 * l + 1];
+            const double dz = pts[3 * i + 2] - dw[3 * l + 2];
+            double r = sqrt(dx * dx + dy * dy + dz * dz);
+            if (r < src[3]) r = src[3];
+            const double g = src[4] + src[5] * r + src[6] * r * r;
+            if (!(g > 0.0)) return -1;
+            A[i * n_dwell + l] = K * g / (r * r);
+        }
+    }
+    return 0;
+}
+
 /* ---------------------------------------------------------------- Eq. (obj), Eq. (2) */
 int oracle_objective(const double *A, int64_t n_pnt, int64_t n_dwell, const int32_t *sid,
                      int32_t n_struct, const double *params, const double *w, const double *x,

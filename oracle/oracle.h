@@ -29,6 +29,15 @@ extern "C" {
 
 enum { ORACLE_CONVERGED = 0, ORACLE_MAXITER = 1, ORACLE_LSFAIL = 2, ORACLE_NONFINITE = 3 };
 
+/* Step (i) of the planning flow (Sec. 2.2.1), the dose rate matrix A of Eq. (dose).  The
+ * paper gives no dose-rate model; this is the isotropic point source the workload names:
+ *   A_il = lambda * sk * unit * g(r) / r^2,  r = max(|p_i - q_l|, r_min),  g = g0 + g1 r + g2 r^2
+ * pts n_pnt x 3, dw n_dwell x 3 (cm), src = {lambda, sk, unit, r_min, g0, g1, g2}.
+ * Returns 0, or -1 on invalid arguments or where g(r) <= 0.  Pinned: the rate 0.12575 Gy/s at
+ * 1 cm of the workload's constants, the clamp below r_min, the inverse-square ratio. */
+int oracle_dose_rate(const double *pts, int64_t n_pnt, const double *dw, int64_t n_dwell,
+                     const double *src, double *A);
+
 /* Eq. (dose): d_i = sum_l A_il t_l.  Pinned: closed-form single source, exact sums. */
 void oracle_dose(const double *A, int64_t n_pnt, int64_t n_dwell, const double *t, double *d);
 

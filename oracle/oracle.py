@@ -42,6 +42,8 @@ def load():
         lib = ctypes.CDLL(_LIB)
         lib.oracle_dose.argtypes = [_dp, _i64, _i64, _dp, _dp]
         lib.oracle_dose.restype = None
+        lib.oracle_dose_rate.argtypes = [_dp, _i64, _dp, _i64, _dp, _dp]
+        lib.oracle_dose_rate.restype = ctypes.c_int
         lib.oracle_point_penalty.argtypes = [_f64, _dp]
         lib.oracle_point_penalty.restype = _f64
         lib.oracle_point_dpenalty.argtypes = [_f64, _dp]
@@ -73,6 +75,20 @@ def _i(a):
 
 def _p(a, t=_dp):
     return None if a is None else a.ctypes.data_as(t)
+
+
+# the workload's point-source constants: Lambda (cGy h^-1 U^-1), S_K (U), cGy/h -> Gy/s,
+# r_min (cm), g(r) = g0 + g1 r + g2 r^2
+DEFAULT_SOURCE = (1.109, 40700.0, 1.0 / 360000.0, 0.1, 1.0, 0.005, -0.002)
+
+
+def dose_rate(points, dwells, source=DEFAULT_SOURCE):
+    """Dose rate matrix (n_pnt x n_dwell, Gy/s) of the isotropic point source."""
+    pts = _d(points).reshape(-1, 3); dw = _d(dwells).reshape(-1, 3); src = _d(source)
+    out = np.empty((pts.shape[0], dw.shape[0]))
+    if load().oracle_dose_rate(_p(pts), pts.shape[0], _p(dw), dw.shape[0], _p(src), _p(out)) != 0:
+        raise ValueError("oracle_dose_rate: invalid arguments or g(r) <= 0")
+    return out
 
 
 def dose(A, t):

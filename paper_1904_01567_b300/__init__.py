@@ -18,6 +18,8 @@ from .gmco import (  # noqa: F401
     EUNSUPPORTED,
     GmcoError,
     create_problem,
+    default_source,
+    dose_rate_matrix,
     destroy_problem,
     solve_batch,
     evaluate,

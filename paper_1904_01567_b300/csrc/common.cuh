@@ -149,6 +149,10 @@ cudaError_t launch_step_multi(const StepDesc *d, const int32_t *block_start, int
                               cudaStream_t st);
 // *sum = sum over p < n of *counters[p].
 cudaError_t launch_sum_counters(int32_t *const *counters, int32_t n, int32_t *sum, cudaStream_t st);
+// Dose rate matrix (doserate.cu): src = Lambda, S_K, unit factor, r_min, g0, g1, g2; *bad is
+// set to 1 where g(r) <= 0.  n_dwell <= 1024.
+cudaError_t launch_dose_rate(const float *pts, int64_t n_pnt, const float *dw, int32_t n_dwell,
+                             const double *src, float *A, int32_t *bad, cudaStream_t st);
 cudaError_t launch_count_live(const SolverState &s, cudaStream_t st);
 cudaError_t launch_reopen(const SolverState &s, int32_t extra_iters, cudaStream_t st);
 cudaError_t launch_profile_setup(const SolverState &s, cudaStream_t st);

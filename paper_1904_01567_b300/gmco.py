@@ -39,6 +39,12 @@ class _Options(ctypes.Structure):
                 ("sparse_grad_permille", ctypes.c_int32)]
 
 
+class _Source(ctypes.Structure):
+    _fields_ = [("lambda_", ctypes.c_double), ("sk", ctypes.c_double), ("unit", ctypes.c_double),
+                ("r_min", ctypes.c_double), ("g0", ctypes.c_double), ("g1", ctypes.c_double),
+                ("g2", ctypes.c_double)]
+
+
 _lib = None
 _vp = ctypes.c_void_p
 _i64 = ctypes.c_int64
@@ -54,6 +60,10 @@ def load():
         lib = ctypes.CDLL(LIB_PATH)
         lib.gmco_default_options.argtypes = [ctypes.POINTER(_Options)]
         lib.gmco_default_options.restype = None
+        lib.gmco_default_source.argtypes = [ctypes.POINTER(_Source)]
+        lib.gmco_default_source.restype = None
+        lib.gmco_dose_rate_matrix.argtypes = [_vp, _i64, _vp, _i64, ctypes.POINTER(_Source), _vp, _vp]
+        lib.gmco_dose_rate_matrix.restype = ctypes.c_int
         lib.gmco_create_problem.argtypes = [_vp, _i64, _i64, _vp, _i32, _vp,
                                             ctypes.POINTER(_Options), ctypes.POINTER(_vp)]
         lib.gmco_create_problem.restype = ctypes.c_int
@@ -182,6 +192,30 @@ def default_options(**overrides) -> _Options:
             v = PREC[v]
         setattr(o, k, v)
     return o
+
+
+def default_source(**overrides) -> _Source:
+    """gmco_default_source, with fields replaced by keyword (lambda_, sk, unit, r_min, g0..g2)."""
+    s = _Source()
+    load().gmco_default_source(ctypes.byref(s))
+    for k, v in overrides.items():
+        setattr(s, k, v)
+    return s
+
+
+def dose_rate_matrix(points, dwells, source=None, stream=None):
+    """gmco_dose_rate_matrix: the n_pnt x n_dwell dose-rate matrix (Gy/s, FP32) of the given
+    points and dwell positions (n x 3, cm).  Torch CUDA inputs give a CUDA tensor, else numpy."""
+    lib = load()
+    p_keep, p_ptr, cuda = _prep(points, np.float32, "float32")
+    d_keep, d_ptr, cuda_d = _prep(dwells, np.float32, "float32")
+    cuda = cuda or cuda_d
+    n_pnt, n_dwell = int(p_keep.shape[0]), int(d_keep.shape[0])
+    out, o_ptr = _alloc((n_pnt, n_dwell), np.float32, "float32", cuda)
+    src = source if source is not None else default_source()
+    _check(lib.gmco_dose_rate_matrix(p_ptr, n_pnt, d_ptr, n_dwell, ctypes.byref(src), o_ptr,
+                                     _stream_ptr(stream, cuda)), "gmco_dose_rate_matrix")
+    return out
 
 
 def create_problem(A, structure_ids, penalty_params, **options):

@@ -65,6 +65,27 @@ def test_single_source_dose(oracle_mod):
     assert d[1] == pytest.approx(2 * 12.5438793, rel=1e-8)
 
 
+def test_dose_rate_matrix_pins(oracle_mod):
+    """Dose rate matrix of the point-source model: 0.125754747 Gy/s at 1 cm and 12.5438793
+    Gy/s at the 0.1 cm clamp (the values above), the same rate anywhere inside the clamp,
+    invariance under a common shift and an axis permutation of points and dwells, agreement
+    with the input generator's separate numpy evaluation, and refusal where g(r) <= 0."""
+    a = oracle_mod.dose_rate([[0, 0, 1.0], [0.05, 0, 0], [0, 0.1, 0], [0, 0, 0]], np.zeros((1, 3)))
+    assert a[0, 0] == pytest.approx(0.125754747, rel=1e-8)
+    assert a[1, 0] == pytest.approx(12.5438793, rel=1e-8)
+    assert a[1, 0] == a[2, 0] == a[3, 0]
+    p = make_patient(11, 12, 0.5, (120, 20, 30, 30))
+    A = oracle_mod.dose_rate(p.points, p.dwells)
+    shift = np.array([3.0, -1.5, 0.25])
+    assert np.allclose(oracle_mod.dose_rate(p.points + shift, p.dwells + shift), A, rtol=1e-12, atol=0)
+    perm = [2, 0, 1]
+    assert np.allclose(oracle_mod.dose_rate(p.points[:, perm], p.dwells[:, perm]), A, rtol=1e-14, atol=0)
+    from synth import dose_rate_matrix
+    assert np.allclose(A, dose_rate_matrix(p.points, p.dwells), rtol=1e-14, atol=0)
+    with pytest.raises(ValueError):
+        oracle_mod.dose_rate([[30.0, 0, 0]], np.zeros((1, 3)))
+
+
 def test_dose_is_exact_matvec(oracle_mod):
     rng = np.random.default_rng(0)
     A = rng.integers(0, 8, size=(37, 11)).astype(np.float64)   # small integers: sums are exact
