@@ -224,6 +224,38 @@ gmco_status gmco_dvh_from_dose(gmco_problem *prob, const float *dose, int64_t P,
 gmco_status gmco_profile_evaluate(gmco_problem *prob, const float *penalty_weights, int64_t P,
                                   const float *X, int32_t reps, double *ms, double *flops);
 
+/* ---- plan pool post-processing ----
+ * RTOG evaluation (Sec. 2.3.1: target V100 >= 90 %, urethra D10 < 118 % of the prescription,
+ * bladder and rectum V75 < 1 cc; RTOG+ asks V100 >= 95 %) and the selection of one plan from
+ * the pool (Sec. 2.4: RTOG+ valid first, then RTOG valid, each by the highest target V100; else
+ * an invalid plan, preferring those that meet the target and urethra criteria, by the lowest
+ * rectum plus bladder V75; ties go to the lower index).  The V75 of a DVH row are % of the
+ * structure's points; vol_cc turns them into cc. */
+typedef struct gmco_rtog {
+    double v100_min;        /* % of the target, RTOG: 90 */
+    double v100_min_plus;   /* RTOG+: 95 */
+    double d10_max;         /* urethra D10 below this, % of the prescription: 118 */
+    double v75_max_cc;      /* rectum and bladder V75 below this, cc: 1 */
+    double vol_cc[2];       /* volumes of structures 2 (rectum) and 3 (bladder), cc; no default */
+} gmco_rtog;
+
+/* The protocol's values above; vol_cc set to 0 (the caller supplies the volumes). */
+void gmco_default_rtog(gmco_rtog *crit);
+
+/* dvh: P x GMCO_DVH_K rows as gmco_solve_batch writes them (host or device).  cls (P values,
+ * may be NULL): 2 = RTOG+ valid, 1 = RTOG valid, 0 = invalid; *selected: index of the selected
+ * plan.  Outputs host or device.  GMCO_EINVAL for P < 1, NULL dvh / selected / crit, or
+ * non-finite or negative volumes.  Complete on return. */
+gmco_status gmco_rtog_select(const float *dvh, int64_t P, const gmco_rtog *crit, int32_t *cls,
+                             int32_t *selected, void *cuda_stream);
+
+/* Non-dominated filter of a plan pool (Sec. 2.2.4): obj is P x K objective values (K <= 16,
+ * all minimised, FP64, host or device); nondominated[i] = 1 when no plan is no worse in every
+ * objective and better in one, else 0 (host or device).  Equal rows do not dominate each
+ * other.  GMCO_EINVAL for bad sizes or NULL pointers.  Complete on return. */
+gmco_status gmco_pareto_filter(const double *obj, int64_t P, int32_t K, int32_t *nondominated,
+                               void *cuda_stream);
+
 /* ---- several patients in one launch (uneven batching) ----
  * A gmco_multi groups 1..64 problems (patients with their own dwell and point counts) that
  * share one tensor-core precision and the same m, c1, max_ls, stop_window and

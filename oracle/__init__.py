@@ -9,6 +9,9 @@ from .oracle import (  # noqa: F401
     dose,
     dose_rate,
     DEFAULT_SOURCE,
+    rtog_select,
+    pareto,
+    RTOG,
     point_penalty,
     point_dpenalty,
     objective,

@@ -61,6 +61,66 @@ int oracle_dose_rate(const double *pts, int64_t n_pnt, const double *dw, int64_t
     return 0;
 }
 
+/* ---------------------------------------------------------------- plan pool */
+int oracle_rtog_select(const double *dvh, int64_t P, const double *crit, int32_t *cls,
+                       int32_t *selected)
+{
+    if (!dvh || !crit || !cls || !selected || P < 1) return -1;
+    /* classify every plan */
+    for (int64_t i = 0; i < P; ++i) {
+        const double *r = dvh + 5 * i;
+        const double rect_cc = r[3] * crit[4] / 100.0, blad_cc = r[4] * crit[5] / 100.0;
+        const int target = r[0] >= crit[0], urethra = r[2] < crit[2];
+        const int oars = rect_cc < crit[3] && blad_cc < crit[3];
+        cls[i] = (target && urethra && oars) ? (r[0] >= crit[1] ? 2 : 1) : 0;
+    }
+    /* RTOG+ valid plans first, then RTOG valid ones: the highest target V100 */
+    for (int want = 2; want >= 1; --want) {
+        int64_t best = -1;
+        for (int64_t i = 0; i < P; ++i)
+            if (cls[i] == want && (best < 0 || dvh[5 * i] > dvh[5 * best])) best = i;
+        if (best >= 0) {
+            *selected = (int32_t)best;
+            return 0;
+        }
+    }
+    /* no valid plan: the lowest rectum + bladder V75 (cc), among the plans meeting the target
+       and urethra criteria when there are any */
+    int any_tu = 0;
+    for (int64_t i = 0; i < P; ++i) any_tu = any_tu || (dvh[5 * i] >= crit[0] && dvh[5 * i + 2] < crit[2]);
+    int64_t best = -1;
+    double best_cc = 0.0;
+    for (int64_t i = 0; i < P; ++i) {
+        const double *r = dvh + 5 * i;
+        if (any_tu && !(r[0] >= crit[0] && r[2] < crit[2])) continue;
+        const double cc = r[3] * crit[4] / 100.0 + r[4] * crit[5] / 100.0;
+        if (best < 0 || cc < best_cc) {
+            best = i;
+            best_cc = cc;
+        }
+    }
+    *selected = (int32_t)best;
+    return 0;
+}
+
+int oracle_pareto(const double *obj, int64_t P, int32_t K, int32_t *nondom)
+{
+    if (!obj || !nondom || P < 1 || K < 1) return -1;
+    for (int64_t i = 0; i < P; ++i) {
+        int dominated = 0;
+        for (int64_t j = 0; j < P && !dominated; ++j) {
+            int no_worse = 1, better = 0;
+            for (int32_t k = 0; k < K; ++k) {
+                if (obj[j * K + k] > obj[i * K + k]) no_worse = 0;
+                if (obj[j * K + k] < obj[i * K + k]) better = 1;
+            }
+            dominated = no_worse && better;
+        }
+        nondom[i] = dominated ? 0 : 1;
+    }
+    return 0;
+}
+
 /* ---------------------------------------------------------------- Eq. (obj), Eq. (2) */
 int oracle_objective(const double *A, int64_t n_pnt, int64_t n_dwell, const int32_t *sid,
                      int32_t n_struct, const double *params, const double *w, const double *x,

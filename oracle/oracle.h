@@ -38,6 +38,21 @@ enum { ORACLE_CONVERGED = 0, ORACLE_MAXITER = 1, ORACLE_LSFAIL = 2, ORACLE_NONFI
 int oracle_dose_rate(const double *pts, int64_t n_pnt, const double *dw, int64_t n_dwell,
                      const double *src, double *A);
 
+/* Plan evaluation and selection (Sec. 2.3.1, Sec. 2.4).  dvh is P x 5 (target V100 %, D90 %,
+ * urethra D10 %, rectum V75 %, bladder V75 % of the structure's points); crit = {V100 min
+ * (RTOG), V100 min (RTOG+), urethra D10 max, V75 max cc, rectum cc, bladder cc}.  cls[i]: 2 RTOG+
+ * valid, 1 RTOG valid, 0 invalid.  *selected: among RTOG+ valid plans, else RTOG valid plans,
+ * the highest V100; with no valid plan, among plans meeting the target and urethra criteria
+ * (else among all) the lowest rectum + bladder V75 in cc; the first index on ties.  Returns 0,
+ * or -1 on invalid arguments.  Pinned: hand-made rows at each criterion's boundary. */
+int oracle_rtog_select(const double *dvh, int64_t P, const double *crit, int32_t *cls,
+                       int32_t *selected);
+
+/* Non-dominated plans of a pool (Sec. 2.2.4): nondom[i] = 1 unless some plan is no worse in
+ * all K objectives (minimised) and better in one.  Brute force over all pairs.  Pinned: a
+ * hand-made front with duplicates, the one-objective case. */
+int oracle_pareto(const double *obj, int64_t P, int32_t K, int32_t *nondom);
+
 /* Eq. (dose): d_i = sum_l A_il t_l.  Pinned: closed-form single source, exact sums. */
 void oracle_dose(const double *A, int64_t n_pnt, int64_t n_dwell, const double *t, double *d);
 

@@ -44,6 +44,10 @@ def load():
         lib.oracle_dose.restype = None
         lib.oracle_dose_rate.argtypes = [_dp, _i64, _dp, _i64, _dp, _dp]
         lib.oracle_dose_rate.restype = ctypes.c_int
+        lib.oracle_rtog_select.argtypes = [_dp, _i64, _dp, _ip, _ip]
+        lib.oracle_rtog_select.restype = ctypes.c_int
+        lib.oracle_pareto.argtypes = [_dp, _i64, _i32, _ip]
+        lib.oracle_pareto.restype = ctypes.c_int
         lib.oracle_point_penalty.argtypes = [_f64, _dp]
         lib.oracle_point_penalty.restype = _f64
         lib.oracle_point_dpenalty.argtypes = [_f64, _dp]
@@ -88,6 +92,32 @@ def dose_rate(points, dwells, source=DEFAULT_SOURCE):
     out = np.empty((pts.shape[0], dw.shape[0]))
     if load().oracle_dose_rate(_p(pts), pts.shape[0], _p(dw), dw.shape[0], _p(src), _p(out)) != 0:
         raise ValueError("oracle_dose_rate: invalid arguments or g(r) <= 0")
+    return out
+
+
+# the RTOG 0924 values of the plan evaluation: V100 >= 90 % (RTOG+ 95 %), urethra D10 < 118 %,
+# rectum and bladder V75 < 1 cc
+RTOG = (90.0, 95.0, 118.0, 1.0)
+
+
+def rtog_select(dvh, rectum_cc, bladder_cc, crit=RTOG):
+    """(classes, selected index) of a pool's DVH rows (P x 5)."""
+    d = _d(dvh).reshape(-1, 5)
+    c = _d(list(crit) + [rectum_cc, bladder_cc])
+    cls = np.empty(d.shape[0], np.int32)
+    sel = np.zeros(1, np.int32)
+    if load().oracle_rtog_select(_p(d), d.shape[0], _p(c), _p(cls, _ip), _p(sel, _ip)) != 0:
+        raise ValueError("oracle_rtog_select: invalid arguments")
+    return cls, int(sel[0])
+
+
+def pareto(obj):
+    """Non-dominated flags (1 / 0) of the rows of obj (P x K, minimised)."""
+    o = _d(obj)
+    o = o.reshape(o.shape[0], -1)
+    out = np.empty(o.shape[0], np.int32)
+    if load().oracle_pareto(_p(o), o.shape[0], o.shape[1], _p(out, _ip)) != 0:
+        raise ValueError("oracle_pareto: invalid arguments")
     return out
 
 

@@ -920,6 +920,121 @@ gmco_status gmco_dose_rate_matrix(const float *points, int64_t n_pnt, const floa
     return GMCO_OK;
 }
 
+namespace {
+
+// Device view of a caller buffer: the buffer itself when it is device memory, else a stream-
+// ordered device copy (copied in when `in`); `back` copies a device copy out to the caller.
+struct Staged {
+    void *user = nullptr, *dev = nullptr;
+    size_t bytes = 0;
+    cudaStream_t st = nullptr;
+    bool own = false;
+    ~Staged() { if (own && dev) cudaFreeAsync(dev, st); }
+    cudaError_t init(void *p, size_t n, cudaStream_t s, bool in)
+    {
+        user = p;
+        bytes = n;
+        st = s;
+        cudaPointerAttributes a{};
+        bool on_dev = false;
+        if (p && cudaPointerGetAttributes(&a, p) == cudaSuccess)
+            on_dev = a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+        cudaGetLastError();
+        if (on_dev) {
+            dev = p;
+            return cudaSuccess;
+        }
+        own = true;
+        cudaError_t e = cudaMallocAsync(&dev, n, s);
+        if (e != cudaSuccess || !in || !p) return e;
+        return cudaMemcpyAsync(dev, p, n, cudaMemcpyHostToDevice, s);
+    }
+    cudaError_t back() const
+    {
+        return (own && user) ? cudaMemcpyAsync(user, dev, bytes, cudaMemcpyDeviceToHost, st) : cudaSuccess;
+    }
+};
+
+bool have_device()
+{
+    int n = 0;
+    if (cudaGetDeviceCount(&n) != cudaSuccess || n < 1) {
+        cudaGetLastError();
+        return false;
+    }
+    return true;
+}
+
+}  // namespace
+
+void gmco_default_rtog(gmco_rtog *c)
+{
+    if (!c) return;
+    c->v100_min = 90.0;
+    c->v100_min_plus = 95.0;
+    c->d10_max = 118.0;
+    c->v75_max_cc = 1.0;
+    c->vol_cc[0] = c->vol_cc[1] = 0.0;
+}
+
+gmco_status gmco_rtog_select(const float *dvh, int64_t P, const gmco_rtog *crit, int32_t *cls,
+                             int32_t *selected, void *cuda_stream)
+{
+    if (!dvh || !crit || !selected || P < 1 || P > (1LL << 30)) {
+        set_error_msg("gmco_rtog_select: bad arguments");
+        return GMCO_EINVAL;
+    }
+    const double c[6] = {crit->v100_min, crit->v100_min_plus, crit->d10_max, crit->v75_max_cc,
+                         crit->vol_cc[0], crit->vol_cc[1]};
+    for (double v : c)
+        if (!isfinite(v)) {
+            set_error_msg("gmco_rtog_select: non-finite criteria");
+            return GMCO_EINVAL;
+        }
+    if (c[4] < 0.0 || c[5] < 0.0) {
+        set_error_msg("gmco_rtog_select: negative volume");
+        return GMCO_EINVAL;
+    }
+    if (!have_device()) {
+        set_error_msg("gmco_rtog_select: no CUDA device");
+        return GMCO_ECUDA;
+    }
+    cudaStream_t st = static_cast<cudaStream_t>(cuda_stream);
+    Staged d, k, sc, ss;
+    CK(d.init(const_cast<float *>(dvh), (size_t)P * GMCO_DVH_K * sizeof(float), st, true));
+    CK(k.init(nullptr, sizeof c, st, false));
+    CK(cudaMemcpyAsync(k.dev, c, sizeof c, cudaMemcpyHostToDevice, st));
+    CK(sc.init(cls, (size_t)P * sizeof(int32_t), st, false));
+    CK(ss.init(selected, sizeof(int32_t), st, false));
+    CK(launch_rtog(static_cast<const float *>(d.dev), P, static_cast<const double *>(k.dev),
+                   static_cast<int32_t *>(sc.dev), static_cast<int32_t *>(ss.dev), st));
+    CK(sc.back());
+    CK(ss.back());
+    CK(cudaStreamSynchronize(st));
+    return GMCO_OK;
+}
+
+gmco_status gmco_pareto_filter(const double *obj, int64_t P, int32_t K, int32_t *nondominated,
+                               void *cuda_stream)
+{
+    if (!obj || !nondominated || P < 1 || P > (1LL << 30) || K < 1 || K > 16) {
+        set_error_msg("gmco_pareto_filter: bad arguments");
+        return GMCO_EINVAL;
+    }
+    if (!have_device()) {
+        set_error_msg("gmco_pareto_filter: no CUDA device");
+        return GMCO_ECUDA;
+    }
+    cudaStream_t st = static_cast<cudaStream_t>(cuda_stream);
+    Staged o, n;
+    CK(o.init(const_cast<double *>(obj), (size_t)P * K * sizeof(double), st, true));
+    CK(n.init(nondominated, (size_t)P * sizeof(int32_t), st, false));
+    CK(launch_pareto(static_cast<const double *>(o.dev), P, K, static_cast<int32_t *>(n.dev), st));
+    CK(n.back());
+    CK(cudaStreamSynchronize(st));
+    return GMCO_OK;
+}
+
 void gmco_default_options(gmco_options *opt)
 {
     if (!opt) return;

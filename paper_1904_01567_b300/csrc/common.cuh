@@ -153,6 +153,11 @@ cudaError_t launch_sum_counters(int32_t *const *counters, int32_t n, int32_t *su
 // set to 1 where g(r) <= 0.  n_dwell <= 1024.
 cudaError_t launch_dose_rate(const float *pts, int64_t n_pnt, const float *dw, int32_t n_dwell,
                              const double *src, float *A, int32_t *bad, cudaStream_t st);
+// Plan pool (pool.cu): RTOG classes and the selected plan of P DVH rows (crit: 6 values, see
+// gmco_rtog); non-dominated flags of P objective rows of K <= 16 values (all minimised).
+cudaError_t launch_rtog(const float *dvh, int64_t P, const double *crit, int32_t *cls, int32_t *selected,
+                        cudaStream_t st);
+cudaError_t launch_pareto(const double *obj, int64_t P, int32_t K, int32_t *nondom, cudaStream_t st);
 cudaError_t launch_count_live(const SolverState &s, cudaStream_t st);
 cudaError_t launch_reopen(const SolverState &s, int32_t extra_iters, cudaStream_t st);
 cudaError_t launch_profile_setup(const SolverState &s, cudaStream_t st);

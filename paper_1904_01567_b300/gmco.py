@@ -45,6 +45,12 @@ class _Source(ctypes.Structure):
                 ("g2", ctypes.c_double)]
 
 
+class _Rtog(ctypes.Structure):
+    _fields_ = [("v100_min", ctypes.c_double), ("v100_min_plus", ctypes.c_double),
+                ("d10_max", ctypes.c_double), ("v75_max_cc", ctypes.c_double),
+                ("vol_cc", ctypes.c_double * 2)]
+
+
 _lib = None
 _vp = ctypes.c_void_p
 _i64 = ctypes.c_int64
@@ -64,6 +70,12 @@ def load():
         lib.gmco_default_source.restype = None
         lib.gmco_dose_rate_matrix.argtypes = [_vp, _i64, _vp, _i64, ctypes.POINTER(_Source), _vp, _vp]
         lib.gmco_dose_rate_matrix.restype = ctypes.c_int
+        lib.gmco_default_rtog.argtypes = [ctypes.POINTER(_Rtog)]
+        lib.gmco_default_rtog.restype = None
+        lib.gmco_rtog_select.argtypes = [_vp, _i64, ctypes.POINTER(_Rtog), _vp, _vp, _vp]
+        lib.gmco_rtog_select.restype = ctypes.c_int
+        lib.gmco_pareto_filter.argtypes = [_vp, _i64, _i32, _vp, _vp]
+        lib.gmco_pareto_filter.restype = ctypes.c_int
         lib.gmco_create_problem.argtypes = [_vp, _i64, _i64, _vp, _i32, _vp,
                                             ctypes.POINTER(_Options), ctypes.POINTER(_vp)]
         lib.gmco_create_problem.restype = ctypes.c_int
@@ -215,6 +227,35 @@ def dose_rate_matrix(points, dwells, source=None, stream=None):
     src = source if source is not None else default_source()
     _check(lib.gmco_dose_rate_matrix(p_ptr, n_pnt, d_ptr, n_dwell, ctypes.byref(src), o_ptr,
                                      _stream_ptr(stream, cuda)), "gmco_dose_rate_matrix")
+    return out
+
+
+def rtog_select(dvh, rectum_cc, bladder_cc, stream=None, **criteria):
+    """gmco_rtog_select: (classes[P] with 2 = RTOG+, 1 = RTOG, 0 = invalid, selected index).
+    dvh is P x 5 as solve_batch returns it; criteria override gmco_default_rtog fields."""
+    lib = load()
+    d_keep, d_ptr, cuda = _prep(dvh, np.float32, "float32")
+    P = int(d_keep.shape[0])
+    c = _Rtog()
+    lib.gmco_default_rtog(ctypes.byref(c))
+    for k, v in criteria.items():
+        setattr(c, k, v)
+    c.vol_cc[0], c.vol_cc[1] = float(rectum_cc), float(bladder_cc)
+    cls, c_ptr = _alloc((P,), np.int32, "int32", cuda)
+    sel = np.zeros(1, np.int32)
+    _check(lib.gmco_rtog_select(d_ptr, P, ctypes.byref(c), c_ptr, sel.ctypes.data,
+                                _stream_ptr(stream, cuda)), "gmco_rtog_select")
+    return cls, int(sel[0])
+
+
+def pareto_filter(obj, stream=None):
+    """gmco_pareto_filter: 1 for the non-dominated rows of obj (P x K, minimised), else 0."""
+    lib = load()
+    o_keep, o_ptr, cuda = _prep(obj, np.float64, "float64")
+    P, K = int(o_keep.shape[0]), int(o_keep.shape[1])
+    out, n_ptr = _alloc((P,), np.int32, "int32", cuda)
+    _check(lib.gmco_pareto_filter(o_ptr, P, K, n_ptr, _stream_ptr(stream, cuda)),
+           "gmco_pareto_filter")
     return out
 
 

@@ -1,0 +1,50 @@
+"""Plan-pool post-processing on the GPU (gmco_rtog_select, gmco_pareto_filter) against the FP64
+oracle: classes, the selected index and the non-dominated flags are integers, compared exactly
+(both sides take every decision in FP64 from the same FP32 DVH values)."""
+import numpy as np
+import pytest
+
+pytestmark = pytest.mark.gpu
+
+
+def _pool(rng, P):
+    """DVH rows of a plan pool around the RTOG boundaries, with exact boundary values and ties."""
+    dvh = np.empty((P, 5), np.float32)
+    dvh[:, 0] = rng.choice([85.0, 89.99, 90.0, 93.0, 95.0, 97.5, 99.0], P) + rng.choice([0.0, 0.25], P)
+    dvh[:, 1] = rng.uniform(95, 110, P)
+    dvh[:, 2] = rng.choice([105.0, 117.5, 118.0, 121.0], P)
+    dvh[:, 3] = rng.choice([0.0, 0.5, 1.0, 1.5, 2.0, 3.0], P)   # % of a 50 cc rectum: 1 cc at 2 %
+    dvh[:, 4] = rng.choice([0.0, 0.5, 1.0, 2.0], P)             # % of a 100 cc bladder: 1 cc at 1 %
+    return dvh
+
+
+def test_rtog_select_matches_oracle(gmco_mod, oracle_mod):
+    rng = np.random.default_rng(3)
+    for P in (1, 7, 1000, 5000):
+        dvh = _pool(rng, P)
+        cls, sel = gmco_mod.rtog_select(dvh, 50.0, 100.0)
+        ref_cls, ref_sel = oracle_mod.rtog_select(dvh, 50.0, 100.0)
+        assert np.array_equal(cls, ref_cls) and sel == ref_sel, (P, sel, ref_sel)
+    # no valid plan at all (every urethra D10 over the limit), on device buffers
+    import torch
+    dvh = _pool(rng, 700)
+    dvh[:, 2] = 125.0
+    cls, sel = gmco_mod.rtog_select(torch.from_numpy(dvh).cuda(), 50.0, 100.0)
+    ref_cls, ref_sel = oracle_mod.rtog_select(dvh, 50.0, 100.0)
+    assert cls.is_cuda and np.array_equal(cls.cpu().numpy(), ref_cls) and sel == ref_sel
+    with pytest.raises(gmco_mod.GmcoError):
+        gmco_mod.rtog_select(dvh, -1.0, 100.0)
+
+
+def test_pareto_filter_matches_oracle(gmco_mod, oracle_mod):
+    rng = np.random.default_rng(4)
+    for P, K in ((1, 1), (6, 2), (1000, 4), (3000, 4), (513, 16)):
+        obj = rng.integers(0, 12, size=(P, K)).astype(np.float64)   # many ties and duplicates
+        nd = gmco_mod.pareto_filter(obj)
+        assert np.array_equal(nd, oracle_mod.pareto(obj)), (P, K)
+    obj = rng.uniform(0, 1, (2000, 4))
+    import torch
+    nd = gmco_mod.pareto_filter(torch.from_numpy(obj).cuda())
+    assert nd.is_cuda and np.array_equal(nd.cpu().numpy(), oracle_mod.pareto(obj))
+    with pytest.raises(gmco_mod.GmcoError):
+        gmco_mod.pareto_filter(np.zeros((3, 17)))

@@ -330,3 +330,46 @@ def test_dvh_hand_made(oracle_mod):
     d7 = np.array([5.0, 1.0, 7.0, 3.0, 2.0, 6.0, 4.0])
     assert oracle_mod.dvh(d7, np.zeros(7, np.int32), 1, 10.0)[1] == pytest.approx(10.0)
     assert np.isnan(oracle_mod.dvh(d7, np.zeros(7, np.int32), 1, 10.0)[2])
+
+
+def test_rtog_classes_and_selection_hand_made(oracle_mod):
+    """Plan evaluation at each criterion's boundary (V100 >= 90 % and >= 95 % for RTOG+,
+    urethra D10 < 118 %, rectum and bladder V75 < 1 cc) and the selection order: RTOG+ valid,
+    then RTOG valid, each by the highest V100; with none valid, the lowest rectum + bladder V75
+    among plans meeting the target and urethra criteria (else among all), first index on ties.
+    Volumes 50 cc (rectum) and 100 cc (bladder): 1 cc is 2 % and 1 %."""
+    ok = [0.5, 0.5]
+    rows = [[90.0, 100, 117.9] + ok,      # RTOG: V100 exactly at 90 %
+            [95.0, 100, 117.9] + ok,      # RTOG+: exactly at 95 %
+            [89.99, 100, 110] + ok,       # target fails
+            [99.0, 100, 118.0] + ok,      # urethra D10 exactly 118 % fails
+            [99.0, 100, 110, 2.0, 0.5],   # rectum exactly 1 cc fails
+            [99.0, 100, 110, 0.5, 1.0],   # bladder exactly 1 cc fails
+            [99.0, 100, 110, 1.99, 0.99]]  # both just below 1 cc: RTOG+
+    cls, sel = oracle_mod.rtog_select(rows, 50.0, 100.0)
+    assert list(cls) == [1, 2, 0, 0, 0, 0, 2]
+    assert sel == 6                                   # RTOG+ with the higher V100 (99 > 95)
+    cls, sel = oracle_mod.rtog_select([rows[0], [93.0, 100, 100] + ok, [93.0, 100, 100] + ok], 50.0, 100.0)
+    assert list(cls) == [1, 1, 1] and sel == 1        # highest V100, first of equals
+    invalid = [[99.0, 100, 120, 0.2, 0.2],            # urethra fails: set aside while others pass
+               [91.0, 100, 110, 4.0, 3.0],            # 2 + 3 cc
+               [92.0, 100, 110, 3.0, 2.0],            # 1.5 + 2 cc: the lowest
+               [80.0, 100, 110, 0.0, 0.0]]            # target fails
+    cls, sel = oracle_mod.rtog_select(invalid, 50.0, 100.0)
+    assert list(cls) == [0, 0, 0, 0] and sel == 2
+    cls, sel = oracle_mod.rtog_select([invalid[0], invalid[3]], 50.0, 100.0)
+    assert sel == 1                                   # none meets target and urethra: lowest V75
+
+
+def test_pareto_front_hand_made(oracle_mod):
+    """(1,3), (2,2), (3,1) are non-dominated, (2,3) is dominated by (2,2) and (1,3), (4,4) by
+    all; equal rows do not dominate each other; with one objective only the minima remain."""
+    obj = [[1, 3], [2, 2], [3, 1], [2, 3], [4, 4], [2, 2]]
+    assert list(oracle_mod.pareto(obj)) == [1, 1, 1, 0, 0, 1]
+    assert list(oracle_mod.pareto([[3.0], [1.0], [2.0], [1.0]])) == [0, 1, 0, 1]
+    rng = np.random.default_rng(0)
+    o = rng.integers(0, 6, size=(60, 3)).astype(float)
+    nd = oracle_mod.pareto(o).astype(bool)
+    # every plan off the front is dominated by a plan on it (dominance is transitive)
+    for i in np.where(~nd)[0]:
+        assert any(np.all(o[j] <= o[i]) and np.any(o[j] < o[i]) for j in np.where(nd)[0])
