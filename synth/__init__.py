@@ -13,6 +13,10 @@ from .patient import (  # noqa: F401
     make_patient,
     dose_rate_matrix,
     class_penalty_params,
+    TABLE1,
+    surface_points,
+    make_class_solution_patient,
+    group_weights,
     weights_loguniform,
     weights_dirichlet,
     workload,

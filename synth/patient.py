@@ -148,6 +148,69 @@ def class_penalty_params() -> np.ndarray:
     ])
 
 
+# The paper's class solution (Table 1) for a 15 Gy prostate boost: per organ, the quadratic
+# objectives of Eq. (1) on its surface and on its volume dose calculation points,
+# (w_min, D_min, D_max, w_max) with doses in Gy.
+TABLE1 = {
+    "prostate": ((200.0, 15.0, 22.5, 80.0), (200.0, 15.0, 22.5, 1.0)),
+    "urethra": ((30.0, 14.0, 16.0, 160.0), (30.0, 14.0, 16.0, 160.0)),
+    "bladder": ((0.0, 0.0, 7.5, 60.0), (0.0, 0.0, 7.5, 60.0)),
+    "rectum": ((0.0, 0.0, 7.5, 15.0), (0.0, 0.0, 7.5, 15.0)),
+}
+
+
+def _unit_vectors(rng, n):
+    v = rng.normal(size=(n, 3))
+    return v / np.linalg.norm(v, axis=1, keepdims=True)
+
+
+def surface_points(g: "Geometry", rng, n_per_organ) -> list:
+    """Dose points on each organ's surface, in STRUCTURES order: the prostate ellipsoid, the
+    urethra and rectum cylinders (side walls), the bladder sphere."""
+    n_pro, n_ure, n_rec, n_bla = n_per_organ
+    pro = _unit_vectors(rng, n_pro) * np.array([g.a, g.b, g.c])
+    th = rng.uniform(0.0, 2.0 * np.pi, n_ure)
+    ure = np.column_stack([g.urethra_r * np.cos(th), g.urethra_r * np.sin(th),
+                           rng.uniform(-g.c, g.c, n_ure)])
+    th = rng.uniform(0.0, 2.0 * np.pi, n_rec)
+    rec = np.column_stack([g.rectum_r * np.cos(th), g.rectum_y + g.rectum_r * np.sin(th),
+                           rng.uniform(-g.rectum_half_len, g.rectum_half_len, n_rec)])
+    bla = _unit_vectors(rng, n_bla) * g.bladder_r + np.array([0.0, 0.0, g.bladder_z])
+    return [pro, ure, rec, bla]
+
+
+def make_class_solution_patient(seed: int, n_catheters: int = 12, dwell_step: float = 0.5,
+                                n_volume=(1200, 200, 300, 300), n_surface=(300, 100, 200, 200),
+                                scale: float = 1.0) -> Patient:
+    """A patient with the paper's full class solution (Table 1): eight point groups, the
+    surface (group 2 s) and volume (group 2 s + 1) points of organ s in STRUCTURES order, each
+    with its own two-sided objective.  `organ` of the returned record maps groups to organs."""
+    base = make_patient(seed, n_catheters, dwell_step, n_volume, scale)
+    rng = np.random.default_rng(np.random.SeedSequence([seed, 1]))
+    surf = surface_points(base.geometry, rng, n_surface)
+    groups, sid, params = [], [], []
+    for s, name in enumerate(STRUCTURES):
+        groups += [surf[s], base.points[base.sid == s]]
+        sid += [np.full(len(surf[s]), 2 * s, np.int32), np.full(int(np.sum(base.sid == s)), 2 * s + 1, np.int32)]
+        params += [TABLE1[name][0], TABLE1[name][1]]
+    points = np.concatenate(groups, axis=0)
+    A64 = dose_rate_matrix(points, base.dwells)
+    pat = Patient(geometry=base.geometry, points=points, sid=np.concatenate(sid), dwells=base.dwells,
+                  catheter=base.catheter, catheter_xy=base.catheter_xy, A=A64.astype(np.float32),
+                  params=np.array(params, dtype=np.float64), volumes_cc=base.volumes_cc)
+    pat.organ = np.repeat(np.arange(len(STRUCTURES)), 2)
+    return pat
+
+
+def group_weights(organ_weights, sid, organ) -> np.ndarray:
+    """Per-group hidden weights for the library (which normalises each group by its own point
+    count) that reproduce Eq. (obj)'s per-organ normalisation: w_group = w_organ N_group / N_organ."""
+    n_group = np.bincount(sid, minlength=len(organ)).astype(np.float64)
+    n_organ = np.bincount(organ, weights=n_group)
+    w = np.asarray(organ_weights, dtype=np.float64)
+    return (w[..., organ] * (n_group / n_organ[organ])).astype(np.float32)
+
+
 def _sample_points(rng, n, lo, hi, accept):
     out = np.empty((0, 3))
     lo = np.asarray(lo, dtype=np.float64)

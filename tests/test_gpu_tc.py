@@ -229,3 +229,26 @@ def test_size_limits(gmco_mod, oracle_mod, form, n_dwell, n_struct):
     with pytest.raises(gmco_mod.GmcoError) as e:
         gmco_mod.Problem(A3, sid3, params3, precision=form)
     assert e.value.status == refused
+
+
+@pytest.mark.parametrize("form", ["fp32", "bf16x3", "bf16x2"])
+def test_class_solution_objective(gmco_mod, oracle_mod, form):
+    """The paper's full class solution (Table 1: surface and volume point groups of four organs,
+    two-sided penalties on every group, eight groups) evaluated and solved: doses, F and the
+    gradient against the oracle within the form's bounds, and each solve's reported objective
+    equal to the oracle's at its dwell times."""
+    from synth import make_class_solution_patient, group_weights
+    p = make_class_solution_patient(5)
+    rng = np.random.default_rng(5)
+    W = group_weights(rng.dirichlet(np.ones(4), 16), p.sid, p.organ)
+    X = rng.uniform(0.5, 1.5, (16, p.n_dwell)).astype(np.float32)
+    with gmco_mod.Problem(p.A, p.sid, p.params, precision=form) as pr:
+        out = pr.evaluate(W, X, objectives=True, grad=True, dose=True)
+        sol = pr.solve_batch(W, max_iters=200, tol=1e-9)
+    bd, bF, bg = FORMS.get(form, (1e-5, 2e-5, 2e-5))
+    ed, eF, eg = _errors(oracle_mod, p.A, p.sid, p.params, W, X, out)
+    print(f"class solution {form}: dose {ed:.2e} F {eF:.2e} grad {eg:.2e}")
+    assert ed <= bd and eF <= bF and eg <= bg, (ed, eF, eg)
+    for j in range(W.shape[0]):
+        F = oracle_mod.objective(p.A, p.sid, p.params, W[j], np.sqrt(sol["T"][j]))[0]
+        assert abs(sol["objectives"][j] / F - 1.0) <= max(1e-4, bF)

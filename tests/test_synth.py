@@ -69,3 +69,24 @@ def test_multi_patient_specs():
     for sp in specs:
         assert 12 <= sp["n_catheters"] <= 20 and 0.8 <= sp["scale"] <= 1.3
         assert 5000 <= sum(sp["n_points"]) <= 20000
+
+
+def test_class_solution_patient_and_group_weights(oracle_mod):
+    """The full class solution (Table 1): eight groups (surface, volume) per organ with the
+    table's parameters; per-group weights w_organ N_group / N_organ make the library's
+    per-group normalisation equal Eq. (obj)'s per-organ one, checked through the oracle's
+    per-group objectives."""
+    from synth import TABLE1, STRUCTURES, make_class_solution_patient, group_weights
+    p = make_class_solution_patient(11, n_volume=(400, 80, 100, 100), n_surface=(120, 40, 60, 60))
+    assert list(np.bincount(p.sid)) == [120, 400, 40, 80, 60, 100, 60, 100]
+    for s, name in enumerate(STRUCTURES):
+        assert tuple(p.params[2 * s]) == TABLE1[name][0] and tuple(p.params[2 * s + 1]) == TABLE1[name][1]
+    rng = np.random.default_rng(0)
+    w_org = rng.dirichlet(np.ones(4))
+    wg = group_weights(w_org, p.sid, p.organ).astype(np.float64)
+    x = rng.uniform(0.5, 1.5, p.n_dwell)
+    F, _, _, f_group = oracle_mod.objective(p.A, p.sid, p.params, wg, x)
+    n_group = np.bincount(p.sid).astype(np.float64)
+    per_organ = sum(w_org[j] / n_group[p.organ == j].sum() * np.sum(n_group[p.organ == j] * f_group[p.organ == j])
+                    for j in range(4))
+    assert F == pytest.approx(per_organ, rel=1e-6)   # group weights are rounded to FP32
