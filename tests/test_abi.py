@@ -38,6 +38,27 @@ def test_host_validation_before_device_use(gmco_mod):
     assert e.value.status == 1
 
 
+def test_planning_steps_host_validation(gmco_mod):
+    """Dose rate matrix, plan selection and non-dominated filter: defaults, and bad sizes or
+    constants refused on the host before any device use (so also without a device)."""
+    s = gmco_mod.default_source()
+    assert (s.lambda_, s.sk, s.r_min, s.g0, s.g1, s.g2) == (1.109, 40700.0, 0.1, 1.0, 0.005, -0.002)
+    assert s.unit == pytest.approx(1.0 / 360000.0)
+    pts, dws = np.zeros((4, 3), np.float32), np.zeros((2, 3), np.float32)
+    for bad in ((pts, np.zeros((0, 3), np.float32), None), (pts, np.zeros((1025, 3), np.float32), None),
+                (pts, dws, gmco_mod.default_source(r_min=0.0)),
+                (pts, dws, gmco_mod.default_source(lambda_=float("nan")))):
+        with pytest.raises(gmco_mod.GmcoError) as e:
+            gmco_mod.dose_rate_matrix(bad[0], bad[1], source=bad[2])
+        assert e.value.status == gmco_mod.EINVAL
+    with pytest.raises(gmco_mod.GmcoError) as e:
+        gmco_mod.rtog_select(np.zeros((3, 5), np.float32), -1.0, 10.0)   # negative volume
+    assert e.value.status == gmco_mod.EINVAL
+    with pytest.raises(gmco_mod.GmcoError) as e:
+        gmco_mod.pareto_filter(np.zeros((3, 17)))                          # more than 16 objectives
+    assert e.value.status == gmco_mod.EINVAL
+
+
 def test_options_defaults(gmco_mod):
     o = gmco_mod.default_options()
     assert (o.precision, o.m, o.c1, o.max_ls, o.rx_gy) == (0, 10, 1e-4, 30, 15.0)
