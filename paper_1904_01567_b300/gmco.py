@@ -395,6 +395,17 @@ class Problem:
         self.handle = create_problem(A, structure_ids, penalty_params, **options)
         self.info = problem_info(self.handle)
 
+    @classmethod
+    def from_geometry(cls, points, structure_ids, dwells, penalty_params, source=None, **options):
+        """Step (i) on the device: the dose rate matrix of the points and dwell positions
+        (n x 3, cm; gmco_dose_rate_matrix), then the problem created from that device matrix."""
+        import torch
+        pts = torch.as_tensor(np.asarray(points, np.float32)).cuda()
+        dws = torch.as_tensor(np.asarray(dwells, np.float32)).cuda()
+        A = dose_rate_matrix(pts, dws, source=source)
+        torch.cuda.synchronize()
+        return cls(A, structure_ids, penalty_params, **options)
+
     def solve_batch(self, penalty_weights, t0=None, max_iters=500, tol=1e-6, **kw):
         return solve_batch(self.handle, penalty_weights, t0, max_iters, tol, **kw)
 

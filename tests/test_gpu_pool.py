@@ -48,3 +48,22 @@ def test_pareto_filter_matches_oracle(gmco_mod, oracle_mod):
     assert nd.is_cuda and np.array_equal(nd.cpu().numpy(), oracle_mod.pareto(obj))
     with pytest.raises(gmco_mod.GmcoError):
         gmco_mod.pareto_filter(np.zeros((3, 17)))
+
+
+def test_planning_flow_from_geometry(gmco_mod, oracle_mod):
+    """The whole gMCO flow on the device: dose rate matrix from coordinates, a pool of plans
+    solved, their DVH indices, the RTOG classes and the selected plan, and the non-dominated
+    plans of the pool by (-V100, urethra D10, rectum V75, bladder V75); the classes, selection
+    and flags equal the oracle's on the same DVH rows."""
+    from synth import make_patient, weights_dirichlet
+    p = make_patient(8, 12, 0.5, (700, 100, 150, 150))
+    with gmco_mod.Problem.from_geometry(p.points, p.sid, p.dwells, p.params, precision="bf16x2") as pr:
+        out = pr.solve_batch(weights_dirichlet(8, 64), max_iters=300, tol=1e-6)
+    dvh = np.asarray(out["dvh"], np.float32)
+    rect_cc, blad_cc = float(p.volumes_cc[2]), float(p.volumes_cc[3])
+    cls, sel = gmco_mod.rtog_select(dvh, rect_cc, blad_cc)
+    ref_cls, ref_sel = oracle_mod.rtog_select(dvh, rect_cc, blad_cc)
+    assert np.array_equal(cls, ref_cls) and sel == ref_sel
+    obj = np.column_stack([-dvh[:, 0], dvh[:, 2], dvh[:, 3], dvh[:, 4]]).astype(np.float64)
+    assert np.array_equal(gmco_mod.pareto_filter(obj), oracle_mod.pareto(obj))
+    assert np.all(np.isfinite(out["objectives"]))
