@@ -836,90 +836,6 @@ gmco_status multi_args(gmco_multi *m, const float *const *W, const int64_t *P,
 
 extern "C" {
 
-void gmco_default_source(gmco_source *src)
-{
-    if (!src) return;
-    src->lambda = 1.109;
-    src->sk = 40700.0;
-    src->unit = 1.0 / 360000.0;
-    src->r_min = 0.1;
-    src->g0 = 1.0;
-    src->g1 = 0.005;
-    src->g2 = -0.002;
-}
-
-gmco_status gmco_dose_rate_matrix(const float *points, int64_t n_pnt, const float *dwells,
-                                  int64_t n_dwell, const gmco_source *src, float *A_out,
-                                  void *cuda_stream)
-{
-    gmco_source m;
-    gmco_default_source(&m);
-    if (src) m = *src;
-    const double c[7] = {m.lambda, m.sk, m.unit, m.r_min, m.g0, m.g1, m.g2};
-    bool fin = true;
-    for (double v : c) fin = fin && isfinite(v);
-    if (!points || !dwells || !A_out || n_pnt < 1 || n_pnt > (1LL << 31) || n_dwell < 1 ||
-        n_dwell > kMaxDwell || !fin || !(m.r_min > 0.0)) {
-        set_error_msg("gmco_dose_rate_matrix: bad arguments");
-        return GMCO_EINVAL;
-    }
-    int dev_count = 0;
-    if (cudaGetDeviceCount(&dev_count) != cudaSuccess || dev_count < 1) {
-        cudaGetLastError();
-        set_error_msg("gmco_dose_rate_matrix: no CUDA device");
-        return GMCO_ECUDA;
-    }
-    cudaStream_t st = static_cast<cudaStream_t>(cuda_stream);
-    const size_t pb = (size_t)n_pnt * 3 * sizeof(float), db = (size_t)n_dwell * 3 * sizeof(float);
-    const size_t ab = (size_t)n_pnt * (size_t)n_dwell * sizeof(float);
-    auto on_device = [](const void *p) {
-        cudaPointerAttributes a{};
-        if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
-            cudaGetLastError();
-            return false;
-        }
-        return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
-    };
-    // device copies of whatever the caller passed in host memory, stream-ordered allocations
-    // freed on every return
-    struct Buf {
-        void *p = nullptr;
-        cudaStream_t s = nullptr;
-        ~Buf() { if (p) cudaFreeAsync(p, s); }
-    } dpts, ddw, dA, dbad;
-    dpts.s = ddw.s = dA.s = dbad.s = st;
-    const float *P = points, *D = dwells;
-    float *Aw = A_out;
-    const bool a_dev = on_device(A_out);
-    CK(cudaMallocAsync(&dbad.p, sizeof(int32_t), st));
-    if (!on_device(points)) {
-        CK(cudaMallocAsync(&dpts.p, pb, st));
-        CK(cudaMemcpyAsync(dpts.p, points, pb, cudaMemcpyHostToDevice, st));
-        P = static_cast<const float *>(dpts.p);
-    }
-    if (!on_device(dwells)) {
-        CK(cudaMallocAsync(&ddw.p, db, st));
-        CK(cudaMemcpyAsync(ddw.p, dwells, db, cudaMemcpyHostToDevice, st));
-        D = static_cast<const float *>(ddw.p);
-    }
-    if (!a_dev) {
-        CK(cudaMallocAsync(&dA.p, ab, st));
-        Aw = static_cast<float *>(dA.p);
-    }
-    // non-finite coordinates give non-finite rates: checked on the result below
-    CK(cudaMemsetAsync(dbad.p, 0, sizeof(int32_t), st));
-    CK(launch_dose_rate(P, n_pnt, D, (int32_t)n_dwell, c, Aw, static_cast<int32_t *>(dbad.p), st));
-    int32_t bad = 0;
-    CK(cudaMemcpyAsync(&bad, dbad.p, sizeof bad, cudaMemcpyDeviceToHost, st));
-    if (!a_dev) CK(cudaMemcpyAsync(A_out, Aw, ab, cudaMemcpyDeviceToHost, st));
-    CK(cudaStreamSynchronize(st));
-    if (bad) {
-        set_error_msg("gmco_dose_rate_matrix: g(r) <= 0 or a non-finite rate");
-        return GMCO_EINVAL;
-    }
-    return GMCO_OK;
-}
-
 namespace {
 
 // Device view of a caller buffer: the buffer itself when it is device memory, else a stream-
@@ -966,6 +882,61 @@ bool have_device()
 }
 
 }  // namespace
+
+void gmco_default_source(gmco_source *src)
+{
+    if (!src) return;
+    src->lambda = 1.109;
+    src->sk = 40700.0;
+    src->unit = 1.0 / 360000.0;
+    src->r_min = 0.1;
+    src->g0 = 1.0;
+    src->g1 = 0.005;
+    src->g2 = -0.002;
+}
+
+gmco_status gmco_dose_rate_matrix(const float *points, int64_t n_pnt, const float *dwells,
+                                  int64_t n_dwell, const gmco_source *src, float *A_out,
+                                  void *cuda_stream)
+{
+    gmco_source m;
+    gmco_default_source(&m);
+    if (src) m = *src;
+    const double c[7] = {m.lambda, m.sk, m.unit, m.r_min, m.g0, m.g1, m.g2};
+    bool fin = true;
+    for (double v : c) fin = fin && isfinite(v);
+    if (!points || !dwells || !A_out || n_pnt < 1 || n_pnt > (1LL << 31) || n_dwell < 1 ||
+        n_dwell > kMaxDwell || !fin || !(m.r_min > 0.0)) {
+        set_error_msg("gmco_dose_rate_matrix: bad arguments");
+        return GMCO_EINVAL;
+    }
+    if (!have_device()) {
+        set_error_msg("gmco_dose_rate_matrix: no CUDA device");
+        return GMCO_ECUDA;
+    }
+    cudaStream_t st = static_cast<cudaStream_t>(cuda_stream);
+    const size_t pb = (size_t)n_pnt * 3 * sizeof(float), db = (size_t)n_dwell * 3 * sizeof(float);
+    const size_t ab = (size_t)n_pnt * (size_t)n_dwell * sizeof(float);
+    Staged P, D, Aw, flag;
+    CK(P.init(const_cast<float *>(points), pb, st, true));
+    CK(D.init(const_cast<float *>(dwells), db, st, true));
+    CK(Aw.init(A_out, ab, st, false));
+    CK(flag.init(nullptr, sizeof(int32_t), st, false));
+    // non-finite coordinates give non-finite rates, caught with g(r) <= 0 by the kernel
+    CK(cudaMemsetAsync(flag.dev, 0, sizeof(int32_t), st));
+    CK(launch_dose_rate(static_cast<const float *>(P.dev), n_pnt, static_cast<const float *>(D.dev),
+                        (int32_t)n_dwell, c, static_cast<float *>(Aw.dev), static_cast<int32_t *>(flag.dev), st));
+    int32_t bad = 0;
+    CK(cudaMemcpyAsync(&bad, flag.dev, sizeof bad, cudaMemcpyDeviceToHost, st));
+    CK(Aw.back());
+    CK(cudaStreamSynchronize(st));
+    if (bad) {
+        set_error_msg("gmco_dose_rate_matrix: g(r) <= 0 or a non-finite rate");
+        return GMCO_EINVAL;
+    }
+    return GMCO_OK;
+}
+
 
 void gmco_default_rtog(gmco_rtog *c)
 {
