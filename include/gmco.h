@@ -185,6 +185,35 @@ gmco_status gmco_evaluate(gmco_problem *prob, const float *penalty_weights, int6
                           const float *X, double *objectives, float *grad_x, float *dose,
                           float *dvh, void *cuda_stream);
 
+/* The stochastic engine gSA (Sec. 2.2.1, steps (ii)-(v) repeated), the paper's second GPU
+ * engine, for comparison with gmco_solve_batch.  The paper gives neither its move nor its
+ * cooling schedule; this engine's, with f = k / (iterations - 1) over iterations k:
+ *   start x = sqrt(t0) (t0 NULL: 1 s);
+ *   move   x'_l = x_l + delta_k (2 u - 1) for every dwell l of every plan, t = x'^2,
+ *          delta_k = step0 (step_final / step0)^f;
+ *   accept when F(x') - F(x) <= -T_k F(x_0) ln v, T_k = T0 (T_final / T0)^f (temperatures are
+ *          fractions of the plan's start objective);
+ * u and v are uniform draws: the top 53 bits of output n of SplitMix64 (Steele, Lea and Flood
+ * 2014) seeded with `seed`, times 2^-53 (u in [0, 1)), plus one (v in (0, 1]), at
+ * n = k 2^42 + p 2^21 + l for plan p (its row in this call) and dwell l (l = 2^21 - 1: v).
+ * Every objective is the problem's precision form (the same kernels as gmco_evaluate).
+ *   iterations  0 <= K < 2^22; seed any value; T0, T_final, step0, step_final finite and
+ *               >= 0, with T0 = 0 exactly when T_final = 0 (and the same for the steps)
+ * Outputs (any may be NULL): T_out (P x n_dwell) the best dwell times seen, objectives (P) their
+ * objectives, accepts (P) the accepted moves.  n_dwell < 2^21 - 1 and P < 2^21. */
+typedef struct {
+    int32_t iterations;      /* default 1000 */
+    uint64_t seed;           /* default 1 */
+    double T0, T_final;      /* default 1e-2, 1e-5 */
+    double step0, step_final;/* default 0.2, 0.002 (units of x = sqrt(t), sqrt(s)) */
+} gmco_sa_options;
+
+void gmco_default_sa_options(gmco_sa_options *opt);
+
+gmco_status gmco_solve_sa(gmco_problem *prob, const float *penalty_weights, int64_t P,
+                          const float *t0, const gmco_sa_options *opt, float *T_out,
+                          double *objectives, int32_t *accepts, void *cuda_stream);
+
 /* Allocation-free variant of gmco_evaluate, for callers that cannot allocate device memory
  * while they run (a fixed memory budget, a real-time loop that cannot take cudaMalloc's
  * implicit synchronisation, an application that owns every allocation).  The paper has no

@@ -18,6 +18,9 @@ from .oracle import (  # noqa: F401
     two_loop,
     lbfgs,
     lbfgs_batch,
+    splitmix64,
+    sa,
+    sa_batch,
     dvh,
     CONVERGED,
     MAXITER,

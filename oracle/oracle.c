@@ -351,6 +351,121 @@ int oracle_lbfgs_batch(const double *A, int64_t n_pnt, int64_t n_dwell, const in
     return bad ? -1 : 0;
 }
 
+/* ------------------------------------------------ simulated annealing engine (gSA, Sec. 2.2.1) */
+/* Output n of the SplitMix64 generator (Steele, Lea and Flood, OOPSLA 2014) seeded with
+ * `seed`: the state after n + 1 steps of the Weyl sequence seed + k * 0x9E3779B97F4A7C15,
+ * passed through the generator's finaliser. */
+uint64_t oracle_splitmix64(uint64_t seed, uint64_t n)
+{
+    uint64_t z = seed + (n + 1) * 0x9E3779B97F4A7C15ull;
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+    return z ^ (z >> 31);
+}
+
+/* Counter of the draw for plan p, iteration k and dwell l (l = 2^21 - 1: the acceptance draw) */
+static uint64_t sa_counter(int64_t p, int32_t k, int64_t l)
+{
+    return ((uint64_t)k << 42) | ((uint64_t)p << 21) | (uint64_t)l;
+}
+
+/* Geometric interpolation from a to b over the run: a (b / a)^(k / (K - 1)); 0 when a = 0 */
+static double sa_schedule(double a, double b, int32_t k, int32_t K)
+{
+    if (a == 0.0) return 0.0;
+    const double f = K > 1 ? (double)k / (double)(K - 1) : 0.0;
+    return a * pow(b / a, f);
+}
+
+int oracle_sa(const double *A, int64_t n_pnt, int64_t n_dwell, const int32_t *sid,
+              int32_t n_struct, const double *params, const double *w, const double *t0,
+              int64_t plan, int32_t iters, uint64_t seed, double T0, double T_final, double step0,
+              double step_final, double *t_out, double *F_out, int32_t *accepts_out,
+              double *min_margin_out, double *trace)
+{
+    if (!A || !sid || !params || !w || !t_out || !F_out || n_dwell < 1 || n_dwell >= (1 << 21) - 1 ||
+        plan < 0 || plan >= (1 << 21) || iters < 0 || iters >= (1 << 22) || !(T0 >= 0.0) ||
+        !(T_final >= 0.0) || !(step0 >= 0.0) || !(step_final >= 0.0) || !isfinite(T0) ||
+        !isfinite(T_final) || !isfinite(step0) || !isfinite(step_final) ||
+        (T0 == 0.0) != (T_final == 0.0) || (step0 == 0.0) != (step_final == 0.0))
+        return -1;
+    double *x = malloc((size_t)n_dwell * sizeof(double));
+    double *xt = malloc((size_t)n_dwell * sizeof(double));
+    double *xb = malloc((size_t)n_dwell * sizeof(double));
+    for (int64_t l = 0; l < n_dwell; ++l) {
+        x[l] = t0 ? sqrt(t0[l]) : 1.0;
+        xb[l] = x[l];
+    }
+    double F0 = 0.0;
+    if (oracle_objective(A, n_pnt, n_dwell, sid, n_struct, params, w, x, &F0, NULL, NULL, NULL) != 0) {
+        free(x); free(xt); free(xb);
+        return -1;
+    }
+    double F = F0, Fb = F0, min_margin = INFINITY;
+    int32_t acc = 0;
+    if (trace) trace[0] = F;
+    for (int32_t k = 0; k < iters; ++k) {
+        /* step (ii): every dwell weight moves by a uniform draw in [-delta_k, delta_k) */
+        const double delta = sa_schedule(step0, step_final, k, iters);
+        const double temp = sa_schedule(T0, T_final, k, iters);
+        for (int64_t l = 0; l < n_dwell; ++l) {
+            const uint64_t z = oracle_splitmix64(seed, sa_counter(plan, k, l));
+            const double r = 2.0 * ((double)(z >> 11) * 0x1.0p-53) - 1.0;
+            xt[l] = x[l] + delta * r;
+        }
+        /* steps (iii)-(v): dose, penalties and the plan's objective at the moved weights */
+        double Ft = 0.0;
+        oracle_objective(A, n_pnt, n_dwell, sid, n_struct, params, w, xt, &Ft, NULL, NULL, NULL);
+        /* Metropolis: accept when F_t - F <= -T_k F_0 ln v, v uniform in (0, 1] */
+        const uint64_t zv = oracle_splitmix64(seed, sa_counter(plan, k, (1 << 21) - 1));
+        const double v = ((double)(zv >> 11) + 1.0) * 0x1.0p-53;
+        const double theta = -temp * F0 * log(v);
+        const double dF = Ft - F;
+        const double scale = fmax(fabs(F), fabs(Ft));
+        const double margin = fabs(dF - theta) / (scale > 0.0 ? scale : 1.0);
+        if (margin < min_margin) min_margin = margin;
+        if (dF <= theta) {
+            F = Ft;
+            memcpy(x, xt, (size_t)n_dwell * sizeof(double));
+            ++acc;
+            if (Ft < Fb) {
+                Fb = Ft;
+                memcpy(xb, xt, (size_t)n_dwell * sizeof(double));
+            }
+        }
+        if (trace) trace[k + 1] = F;
+    }
+    for (int64_t l = 0; l < n_dwell; ++l) t_out[l] = xb[l] * xb[l];
+    *F_out = Fb;
+    if (accepts_out) *accepts_out = acc;
+    if (min_margin_out) *min_margin_out = min_margin;
+    free(x); free(xt); free(xb);
+    return 0;
+}
+
+int oracle_sa_batch(const double *A, int64_t n_pnt, int64_t n_dwell, const int32_t *sid,
+                    int32_t n_struct, const double *params, const double *W, int64_t P,
+                    const double *T0s, int32_t iters, uint64_t seed, double T0, double T_final,
+                    double step0, double step_final, double *T_out, double *F_out,
+                    int32_t *accepts_out, double *min_margin_out, int32_t n_threads)
+{
+    int bad = 0;
+#ifdef _OPENMP
+    if (n_threads <= 0) n_threads = omp_get_max_threads();
+#pragma omp parallel for schedule(dynamic, 1) num_threads(n_threads) reduction(| : bad)
+#endif
+    for (int64_t j = 0; j < P; ++j) {
+        int r = oracle_sa(A, n_pnt, n_dwell, sid, n_struct, params, W + j * n_struct,
+                          T0s ? T0s + j * n_dwell : NULL, j, iters, seed, T0, T_final, step0,
+                          step_final, T_out + j * n_dwell, F_out + j,
+                          accepts_out ? accepts_out + j : NULL,
+                          min_margin_out ? min_margin_out + j : NULL, NULL);
+        bad |= (r != 0);
+    }
+    (void)n_threads;
+    return bad ? -1 : 0;
+}
+
 /* ---------------------------------------------------------------- DVH indices (Sec. 2.3.1) */
 static int cmp_desc(const void *a, const void *b)
 {

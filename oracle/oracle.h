@@ -102,6 +102,39 @@ int oracle_lbfgs_batch(const double *A, int64_t n_pnt, int64_t n_dwell, const in
                        double *F_out, int32_t *iters_out, int32_t *status_out, int64_t *n_evals,
                        int32_t n_threads);
 
+/* Output n (0-based) of SplitMix64 seeded with `seed` (Steele, Lea and Flood 2014): the
+ * counter-based generator both engines draw the annealing's random numbers from.  Pinned: the
+ * generator's published first outputs. */
+uint64_t oracle_splitmix64(uint64_t seed, uint64_t n);
+
+/* The stochastic engine gSA (Sec. 2.2.1, steps (ii)-(v) repeated) for one plan, index `plan`
+ * of its batch.  The paper gives neither the move nor the cooling schedule; read here as:
+ *   x = sqrt(t0) (t0 NULL: 1 s); for k = 0 .. iters-1, with f = k / (iters - 1),
+ *   delta_k = step0 (step_final / step0)^f,  T_k = T0 (T_final / T0)^f  (0 when step0 / T0 is 0),
+ *   x'_l = x_l + delta_k (2 u_kl - 1)   for every dwell l,  u_kl = top 53 bits of draw
+ *          (plan, k, l) times 2^-53,
+ *   accept x' when F(x') - F(x) <= -T_k F(x_0) ln v_k,  v_k = (top 53 bits + 1) 2^-53 of
+ *          draw (plan, k, 2^21 - 1);
+ * draw (p, k, l) = oracle_splitmix64(seed, k 2^42 + p 2^21 + l).  Returns the best point seen
+ * (t_out = x_best^2, F_out), the number of accepted moves, and min_margin = the smallest
+ * |F(x') - F(x) + T_k F_0 ln v_k| / max(|F(x)|, |F(x')|) over the run (how close a decision came
+ * to flipping, relative to the objectives whose rounding could flip it).
+ * trace (optional, iters + 1) holds F(x) after each iteration, trace[0] = F(x_0).
+ * Parity unpinned beyond its invariants (the method's move and schedule are not in the
+ * paper).  Returns 0 or -1 on invalid arguments. */
+int oracle_sa(const double *A, int64_t n_pnt, int64_t n_dwell, const int32_t *sid,
+              int32_t n_struct, const double *params, const double *w, const double *t0,
+              int64_t plan, int32_t iters, uint64_t seed, double T0, double T_final, double step0,
+              double step_final, double *t_out, double *F_out, int32_t *accepts_out,
+              double *min_margin_out, double *trace);
+
+/* P plans of oracle_sa (plan j = row j of W and T0s), one per OpenMP thread. */
+int oracle_sa_batch(const double *A, int64_t n_pnt, int64_t n_dwell, const int32_t *sid,
+                    int32_t n_struct, const double *params, const double *W, int64_t P,
+                    const double *T0s, int32_t iters, uint64_t seed, double T0, double T_final,
+                    double step0, double step_final, double *T_out, double *F_out,
+                    int32_t *accepts_out, double *min_margin_out, int32_t n_threads);
+
 /* DVH indices of one dose vector (Sec. 2.3.1 definitions), rx = prescription (Gy):
  *   out[0] V100 of structure 0 (% of its points with d >= rx)
  *   out[1] D90  of structure 0 (% of rx): k-th largest dose, k = ceil(0.9 N_0)

@@ -65,6 +65,15 @@ def load():
         lib.oracle_lbfgs_batch.restype = ctypes.c_int
         lib.oracle_dvh.argtypes = [_dp, _ip, _i64, _i32, _f64, _dp]
         lib.oracle_dvh.restype = None
+        _u64 = ctypes.c_uint64
+        lib.oracle_splitmix64.argtypes = [_u64, _u64]
+        lib.oracle_splitmix64.restype = _u64
+        lib.oracle_sa.argtypes = [_dp, _i64, _i64, _ip, _i32, _dp, _dp, _dp, _i64, _i32, _u64,
+                                  _f64, _f64, _f64, _f64, _dp, _dp, _ip, _dp, _dp]
+        lib.oracle_sa.restype = ctypes.c_int
+        lib.oracle_sa_batch.argtypes = [_dp, _i64, _i64, _ip, _i32, _dp, _dp, _i64, _dp, _i32, _u64,
+                                        _f64, _f64, _f64, _f64, _dp, _dp, _ip, _dp, _i32]
+        lib.oracle_sa_batch.restype = ctypes.c_int
         _lib = lib
     return _lib
 
@@ -197,6 +206,47 @@ def lbfgs_batch(A, sid, params, W, T0=None, max_iters=200, tol=1e-6, m=10, c1=1e
     if rc != 0:
         raise ValueError("oracle_lbfgs_batch: invalid arguments")
     return dict(T=T, F=F, iters=it, status=st, evals=ev)
+
+
+def splitmix64(seed, n):
+    """Output n (0-based) of SplitMix64 seeded with `seed`."""
+    return int(load().oracle_splitmix64(int(seed) & (2**64 - 1), int(n) & (2**64 - 1)))
+
+
+def sa(A, sid, params, w, t0=None, iters=1000, seed=1, T0=1e-2, T_final=1e-5, step0=0.2,
+       step_final=2e-3, plan=0, trace=False):
+    """One plan of the annealing engine (plan = its index in the batch, which keys its draws).
+    Returns dict(t, F, accepts, min_margin[, trace])."""
+    A = _d(A); sid = _i(sid); params = _d(params); w = _d(w)
+    t0 = None if t0 is None else _d(t0)
+    n = A.shape[1]
+    t = np.empty(n); F = np.zeros(1); acc = np.zeros(1, np.int32); mm = np.zeros(1)
+    tr = np.full(iters + 1, np.nan) if trace else None
+    rc = load().oracle_sa(_p(A), A.shape[0], n, _p(sid, _ip), params.shape[0], _p(params), _p(w),
+                          _p(t0), int(plan), int(iters), int(seed), T0, T_final, step0, step_final,
+                          _p(t), _p(F), _p(acc, _ip), _p(mm), _p(tr))
+    if rc != 0:
+        raise ValueError("oracle_sa: invalid arguments")
+    out = dict(t=t, F=float(F[0]), accepts=int(acc[0]), min_margin=float(mm[0]))
+    if trace:
+        out["trace"] = tr
+    return out
+
+
+def sa_batch(A, sid, params, W, T0s=None, iters=1000, seed=1, T0=1e-2, T_final=1e-5, step0=0.2,
+             step_final=2e-3, n_threads=0):
+    """P plans of the annealing engine.  Returns dict(T, F, accepts, min_margin)."""
+    A = _d(A); sid = _i(sid); params = _d(params); W = _d(W)
+    P = W.shape[0]
+    n = A.shape[1]
+    T0s = None if T0s is None else _d(T0s)
+    T = np.empty((P, n)); F = np.empty(P); acc = np.empty(P, np.int32); mm = np.empty(P)
+    rc = load().oracle_sa_batch(_p(A), A.shape[0], n, _p(sid, _ip), params.shape[0], _p(params),
+                                _p(W), P, _p(T0s), int(iters), int(seed), T0, T_final, step0,
+                                step_final, _p(T), _p(F), _p(acc, _ip), _p(mm), int(n_threads))
+    if rc != 0:
+        raise ValueError("oracle_sa_batch: invalid arguments")
+    return dict(T=T, F=F, accepts=acc, min_margin=mm)
 
 
 def dvh(d, sid, n_struct=4, rx=15.0):

@@ -1372,6 +1372,119 @@ gmco_status gmco_evaluate(gmco_problem *pr, const float *penalty_weights, int64_
     return GMCO_OK;
 }
 
+void gmco_default_sa_options(gmco_sa_options *opt)
+{
+    if (!opt) return;
+    opt->iterations = 1000;
+    opt->seed = 1;
+    opt->T0 = 1e-2;
+    opt->T_final = 1e-5;
+    opt->step0 = 0.2;
+    opt->step_final = 2e-3;
+}
+
+namespace {
+
+// Geometric interpolation from a to b over K iterations: a (b / a)^(k / (K - 1)); 0 when a = 0.
+double sa_schedule(double a, double b, int32_t k, int32_t K)
+{
+    if (a == 0.0) return 0.0;
+    const double f = K > 1 ? (double)k / (double)(K - 1) : 0.0;
+    return a * pow(b / a, f);
+}
+
+bool sa_pair_ok(double a, double b)
+{
+    return isfinite(a) && isfinite(b) && a >= 0.0 && b >= 0.0 && ((a == 0.0) == (b == 0.0));
+}
+
+}  // namespace
+
+gmco_status gmco_solve_sa(gmco_problem *pr, const float *penalty_weights, int64_t P,
+                          const float *t0, const gmco_sa_options *opt, float *T_out,
+                          double *objectives, int32_t *accepts, void *cuda_stream)
+{
+    if (!pr || !penalty_weights || !opt || P < 1 || P >= (1 << 21) || opt->iterations < 0 ||
+        opt->iterations >= (1 << 22) || !sa_pair_ok(opt->T0, opt->T_final) ||
+        !sa_pair_ok(opt->step0, opt->step_final) || pr->pb.n_dwell >= (1 << 21) - 1) {
+        set_error_msg("gmco_solve_sa: bad arguments");
+        return GMCO_EINVAL;
+    }
+    pr->launches = 0;
+    CKS(begin_call(pr, cuda_stream));
+    CKS(ensure_workspace(pr, (int32_t)P));
+    const DevProblem &pb = pr->pb;
+    const int32_t S = pb.n_struct;
+    CKS(stage_in(pr, penalty_weights, pr->dW, (size_t)P * S * sizeof(float)));
+    if (t0) CKS(stage_in(pr, t0, pr->dT0, (size_t)P * pb.n_dwell * sizeof(float)));
+    int32_t bad = 0;
+    CKS(count_bad(pr, pr->dW, P * S, false, &bad));
+    if (!bad && t0) {
+        int32_t b2 = 0;
+        CKS(count_bad(pr, pr->dT0, P * pb.n_dwell, false, &b2));
+        bad += b2;
+    }
+    if (bad) {
+        set_error_msg("gmco_solve_sa: negative or non-finite weights or start times");
+        return GMCO_EINVAL;
+    }
+    SolverState s = pr->s;
+    s.P = (int32_t)P;
+    SolverState saved = pr->s;
+    pr->s = s;
+    struct Restore {
+        gmco_problem *p;
+        SolverState st;
+        ~Restore() { p->s = st; }
+    } restore{pr, saved};
+    cudaStream_t st = pr->stream;
+    CK(launch_solver_init(s, pb, pr->dW, t0 ? pr->dT0 : nullptr, 0, st));
+    pr->launches++;
+    // The annealing keeps its state in the solver workspace: s.x holds the moved weights that
+    // the evaluation reads, s.g the current and s.p the best weights; s.F, s.alpha and s.gtp the
+    // current, best and start objectives; s.iters the accepted moves.
+    float *xc = s.g, *xb = s.p;
+    double *Fc = s.F, *Fb = s.alpha, *F0 = s.gtp;
+    const int form = pr->opt.precision == GMCO_PREC_FP32 ? 0 : 1;
+    if (form != 0) {
+        CK(launch_compact(s, 1, st));   // every plan, every iteration
+        pr->launches++;
+    }
+    auto evaluate_all = [&]() -> gmco_status {
+        if (form == 0) return launch_dose_eval(pr, s, st);
+        int32_t nl = 0;
+        CK(tc_launch_eval(pb, s, pr->tcb, pr->cap, false, true, true, st, &nl));
+        pr->launches += nl;
+        return GMCO_OK;
+    };
+    const uint64_t seed = opt->seed;
+    CKS(evaluate_all());
+    CK(launch_sa_accept(s.x, xc, xb, P, pb.nd_pad, s.Ft, Fc, Fb, F0, s.iters, seed, -1, 0.0, st));
+    pr->launches++;
+    const int32_t K = opt->iterations;
+    for (int32_t k = 0; k < K; ++k) {
+        const double delta = sa_schedule(opt->step0, opt->step_final, k, K);
+        const double temp = sa_schedule(opt->T0, opt->T_final, k, K);
+        CK(launch_sa_propose(s.x, xc, P, pb.n_dwell, pb.nd_pad, seed, k, delta, st));
+        CKS(evaluate_all());
+        CK(launch_sa_accept(s.x, xc, xb, P, pb.nd_pad, s.Ft, Fc, Fb, F0, s.iters, seed, k, temp, st));
+        pr->launches += 2;
+    }
+    CKS(check_tc_error(pr));
+    if (T_out) {
+        CK(launch_square(xb, pr->dTout, P, pb.n_dwell, pb.nd_pad, st));
+        pr->launches++;
+        CK(cudaMemcpyAsync(T_out, pr->dTout, (size_t)P * pb.n_dwell * sizeof(float),
+                           cudaMemcpyDefault, st));
+    }
+    if (objectives)
+        CK(cudaMemcpyAsync(objectives, Fb, (size_t)P * sizeof(double), cudaMemcpyDefault, st));
+    if (accepts)
+        CK(cudaMemcpyAsync(accepts, s.iters, (size_t)P * sizeof(int32_t), cudaMemcpyDefault, st));
+    CKS(end_call(pr, cuda_stream));
+    return GMCO_OK;
+}
+
 gmco_status gmco_profile_evaluate(gmco_problem *pr, const float *penalty_weights, int64_t P,
                                   const float *X, int32_t reps, double *ms, double *flops)
 {

@@ -158,6 +158,13 @@ cudaError_t launch_dose_rate(const float *pts, int64_t n_pnt, const float *dw, i
 cudaError_t launch_rtog(const float *dvh, int64_t P, const double *crit, int32_t *cls, int32_t *selected,
                         cudaStream_t st);
 cudaError_t launch_pareto(const double *obj, int64_t P, int32_t K, int32_t *nondom, cudaStream_t st);
+// Annealing engine (sa.cu): moved weights x = xc + delta (2u - 1) of iteration k, and the
+// Metropolis decision on their objectives Ft (k < 0: the start point's evaluation).
+cudaError_t launch_sa_propose(float *x, const float *xc, int64_t P, int64_t nd, int64_t nd_pad,
+                              uint64_t seed, int32_t k, double delta, cudaStream_t st);
+cudaError_t launch_sa_accept(const float *x, float *xc, float *xb, int64_t P, int64_t nd_pad,
+                             const double *Ft, double *Fc, double *Fb, double *F0, int32_t *acc,
+                             uint64_t seed, int32_t k, double temp, cudaStream_t st);
 cudaError_t launch_count_live(const SolverState &s, cudaStream_t st);
 cudaError_t launch_reopen(const SolverState &s, int32_t extra_iters, cudaStream_t st);
 cudaError_t launch_profile_setup(const SolverState &s, cudaStream_t st);

@@ -51,6 +51,12 @@ class _Rtog(ctypes.Structure):
                 ("vol_cc", ctypes.c_double * 2)]
 
 
+class _SaOptions(ctypes.Structure):
+    _fields_ = [("iterations", ctypes.c_int32), ("seed", ctypes.c_uint64), ("T0", ctypes.c_double),
+                ("T_final", ctypes.c_double), ("step0", ctypes.c_double),
+                ("step_final", ctypes.c_double)]
+
+
 _lib = None
 _vp = ctypes.c_void_p
 _i64 = ctypes.c_int64
@@ -84,6 +90,10 @@ def load():
         lib.gmco_solve_batch.argtypes = [_vp, _vp, _i64, _vp, _i32, ctypes.c_double, _vp, _vp,
                                          _vp, _vp, _vp, _vp]
         lib.gmco_solve_batch.restype = ctypes.c_int
+        lib.gmco_default_sa_options.argtypes = [_vp]
+        lib.gmco_default_sa_options.restype = None
+        lib.gmco_solve_sa.argtypes = [_vp, _vp, _i64, _vp, _vp, _vp, _vp, _vp, _vp]
+        lib.gmco_solve_sa.restype = ctypes.c_int
         lib.gmco_evaluate.argtypes = [_vp, _vp, _i64, _vp, _vp, _vp, _vp, _vp, _vp]
         lib.gmco_evaluate.restype = ctypes.c_int
         lib.gmco_evaluate_noalloc.argtypes = [_vp, _vp, _i64, _vp, _vp, _vp, _vp]
@@ -320,6 +330,36 @@ def solve_batch(h, penalty_weights, t0=None, max_iters=500, tol=1e-6, stream=Non
     return out
 
 
+def default_sa_options(**overrides) -> _SaOptions:
+    """gmco_default_sa_options, with fields replaced by keyword (iterations, seed, T0, T_final,
+    step0, step_final)."""
+    o = _SaOptions()
+    load().gmco_default_sa_options(ctypes.byref(o))
+    for k, v in overrides.items():
+        setattr(o, k, v)
+    return o
+
+
+def solve_sa(h, penalty_weights, t0=None, stream=None, **sa_options):
+    """gmco_solve_sa (the annealing engine).  Returns dict(T, objectives, accepts): the best
+    dwell times seen, their objectives and the accepted moves of each plan."""
+    info = problem_info(h)
+    w_keep, w_ptr, cuda = _prep(penalty_weights, np.float32, "float32")
+    P = int(w_keep.shape[0])
+    t_keep, t_ptr, _ = _prep(t0, np.float32, "float32")
+    opt = default_sa_options(**sa_options)
+    out, ptrs = {}, {}
+    for k, (shape, dt, tdt) in dict(T=((P, info["n_dwell"]), np.float32, "float32"),
+                                    objectives=((P,), np.float64, "float64"),
+                                    accepts=((P,), np.int32, "int32")).items():
+        out[k], ptrs[k] = _alloc(shape, dt, tdt, cuda)
+    _check(load().gmco_solve_sa(h, w_ptr, P, t_ptr, ctypes.byref(opt), ptrs["T"],
+                                ptrs["objectives"], ptrs["accepts"], _stream_ptr(stream, cuda)),
+           "gmco_solve_sa")
+    del w_keep, t_keep
+    return out
+
+
 def evaluate(h, penalty_weights, X, objectives=True, grad=True, dose=False, dvh=False,
              stream=None):
     """gmco_evaluate at dwell weights X (P x n_dwell)."""
@@ -408,6 +448,9 @@ class Problem:
 
     def solve_batch(self, penalty_weights, t0=None, max_iters=500, tol=1e-6, **kw):
         return solve_batch(self.handle, penalty_weights, t0, max_iters, tol, **kw)
+
+    def solve_sa(self, penalty_weights, t0=None, **kw):
+        return solve_sa(self.handle, penalty_weights, t0, **kw)
 
     def evaluate(self, penalty_weights, X, **kw):
         return evaluate(self.handle, penalty_weights, X, **kw)
