@@ -100,3 +100,17 @@ def test_multi_host_validation(gmco_mod):
     o = gmco_mod.default_options()
     assert o.grad_split_kb == 0 and o.stop_window == 1
     assert o.max_evals == 0 and o.grad_plan_tile == 0 and o.sparse_grad_permille == 0
+
+
+def test_annealing_options_and_host_validation(gmco_mod):
+    """gmco_default_sa_options fills the documented defaults; gmco_solve_sa refuses a missing
+    problem or options before any device use."""
+    import ctypes
+    o = gmco_mod.default_sa_options()
+    assert (o.iterations, o.seed, o.T0, o.T_final, o.step0, o.step_final) == (1000, 1, 1e-2, 1e-5, 0.2, 2e-3)
+    o2 = gmco_mod.default_sa_options(iterations=5, seed=2**64 - 1)
+    assert o2.iterations == 5 and o2.seed == 2**64 - 1
+    lib = gmco_mod.load()
+    w = (ctypes.c_float * 4)(1, 1, 1, 1)
+    assert lib.gmco_solve_sa(None, w, 1, None, ctypes.byref(o), None, None, None, None) == gmco_mod.EINVAL
+    assert lib.gmco_solve_sa(None, w, 1, None, None, None, None, None, None) == gmco_mod.EINVAL
