@@ -330,6 +330,31 @@ def solve_batch(h, penalty_weights, t0=None, max_iters=500, tol=1e-6, stream=Non
     return out
 
 
+def dvh_at(h, T, penalty_weights=None, stream=None):
+    """DVH indices (P x DVH_K) of dwell times T (P x n_dwell, s) on this problem's points, by
+    gmco_evaluate's DVH output at x = sqrt(T).  A problem built on a separate, denser point set
+    of the same structures and dwell positions gives the DVH of plans optimised on a coarser
+    one; build it with precision="fp32" for FP32 doses.  The weights only feed the objective
+    part of the evaluation and default to ones."""
+    info = problem_info(h)
+    try:
+        import torch
+        is_t = isinstance(T, torch.Tensor)
+    except ImportError:
+        is_t = False
+    if is_t:
+        X = torch.sqrt(T.to(torch.float32)).contiguous()
+        if penalty_weights is None:
+            penalty_weights = torch.ones((X.shape[0], info["n_struct"]), dtype=torch.float32,
+                                         device=X.device)
+    else:
+        X = np.sqrt(np.asarray(T, np.float32))
+        if penalty_weights is None:
+            penalty_weights = np.ones((X.shape[0], info["n_struct"]), np.float32)
+    return evaluate(h, penalty_weights, X, objectives=False, grad=False, dvh=True,
+                    stream=stream)["dvh"]
+
+
 def default_sa_options(**overrides) -> _SaOptions:
     """gmco_default_sa_options, with fields replaced by keyword (iterations, seed, T0, T_final,
     step0, step_final)."""
@@ -448,6 +473,9 @@ class Problem:
 
     def solve_batch(self, penalty_weights, t0=None, max_iters=500, tol=1e-6, **kw):
         return solve_batch(self.handle, penalty_weights, t0, max_iters, tol, **kw)
+
+    def dvh_at(self, T, penalty_weights=None, **kw):
+        return dvh_at(self.handle, T, penalty_weights, **kw)
 
     def solve_sa(self, penalty_weights, t0=None, **kw):
         return solve_sa(self.handle, penalty_weights, t0, **kw)

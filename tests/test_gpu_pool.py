@@ -67,3 +67,34 @@ def test_planning_flow_from_geometry(gmco_mod, oracle_mod):
     obj = np.column_stack([-dvh[:, 0], dvh[:, 2], dvh[:, 3], dvh[:, 4]]).astype(np.float64)
     assert np.array_equal(gmco_mod.pareto_filter(obj), oracle_mod.pareto(obj))
     assert np.all(np.isfinite(out["objectives"]))
+
+
+def test_dvh_on_a_denser_point_set(gmco_mod, oracle_mod):
+    """DVH indices on a separate, denser set of dose points of the same structures and dwell
+    positions (Sec. 2.1, the DVH point sets): against the oracle's indices of its FP64 doses on
+    that set.  V100 / V75 are point counts, so they may differ by the few points whose FP32 and
+    FP64 doses fall on either side of the threshold; D90 / D10 are doses, within FP32 rounding."""
+    from synth import make_patient, weights_dirichlet
+    coarse = make_patient(8, 12, 0.5, (700, 100, 150, 150))
+    dense = make_patient(8, 12, 0.5, (4000, 600, 900, 900))
+    assert np.array_equal(coarse.dwells, dense.dwells)
+    rng = np.random.default_rng(9)
+    T = rng.uniform(0.5, 1.5, (6, dense.n_dwell))
+    d1 = oracle_mod.dose(dense.A, np.ones(dense.n_dwell))
+    T = (T * 15.0 / np.median(d1[dense.sid == 0])).astype(np.float32)   # doses around 15 Gy
+    counts = np.bincount(dense.sid, minlength=4)
+    with gmco_mod.Problem(dense.A, dense.sid, dense.params, precision="fp32") as pd:
+        dv = pd.dvh_at(T)
+        for j in range(6):
+            ref = oracle_mod.dvh(oracle_mod.dose(dense.A, T[j].astype(np.float64)), dense.sid)
+            assert abs(dv[j, 0] - ref[0]) <= 200.0 / counts[0] + 1e-4
+            assert abs(dv[j, 3] - ref[3]) <= 200.0 / counts[2] + 1e-4
+            assert abs(dv[j, 4] - ref[4]) <= 200.0 / counts[3] + 1e-4
+            assert abs(dv[j, 1] / ref[1] - 1) <= 1e-5 and abs(dv[j, 2] / ref[2] - 1) <= 1e-5
+        assert 0.0 < np.median(dv[:, 0]) < 100.0    # the threshold is exercised
+        # plans solved on the coarse set, evaluated on the dense one (device buffers)
+        with gmco_mod.Problem(coarse.A, coarse.sid, coarse.params, precision="bf16x2") as pc:
+            import torch
+            out = pc.solve_batch(torch.from_numpy(weights_dirichlet(8, 4)).cuda(), max_iters=200, tol=1e-6)
+        dd = pd.dvh_at(out["T"])
+        assert dd.is_cuda and tuple(dd.shape) == (4, 5) and bool(torch.isfinite(dd).all())
