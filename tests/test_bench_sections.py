@@ -1,0 +1,86 @@
+"""Host logic of the benchmark's annealing and stopping-criterion sections, run on the CPU with
+stand-ins for the library and the CUDA events (no device): the keys of their JSON objects, the
+ratios they derive and the per-structure one-hot weights they evaluate with."""
+import sys
+import types
+import os
+
+import numpy as np
+import torch
+
+sys.path.insert(0, os.path.dirname(os.path.dirname(os.path.abspath(__file__))))
+import bench  # noqa: E402
+
+
+class _Event:
+    def __init__(self, enable_timing=True):
+        pass
+
+    def record(self, stream=None):
+        pass
+
+    def elapsed_time(self, other):
+        return 2.0
+
+
+_fake_torch = types.SimpleNamespace(
+    cuda=types.SimpleNamespace(Event=_Event, synchronize=lambda: None),
+    sqrt=torch.sqrt, zeros=lambda shape, dtype, device: torch.zeros(shape, dtype=dtype),
+    float32=torch.float32)
+
+
+class _Solver:
+    def __init__(self):
+        self.tols = []
+
+    def solve_batch(self, W, max_iters, tol, stream=None, allow_timeout=False):
+        self.tols.append(tol)
+        P = W.shape[0]
+        return {"T": torch.full((P, 3), 4.0), "iters": torch.full((P,), 9, dtype=torch.int32)}
+
+    def solve_sa(self, W, iterations, stream=None):
+        P = W.shape[0]
+        return {"objectives": torch.full((P,), 3.0, dtype=torch.float64),
+                "accepts": torch.full((P,), iterations // 2, dtype=torch.int32)}
+
+    def last_launch_count(self):
+        return 5
+
+
+def test_eps_sweep_section_host_logic():
+    seen = []
+
+    class _P32:
+        def __init__(self, *a, **k):
+            pass
+
+        def __enter__(self):
+            return self
+
+        def __exit__(self, *a):
+            return False
+
+        def evaluate(self, Wk, X, objectives, grad):
+            seen.append(Wk.clone())
+            return {"objectives": torch.arange(X.shape[0], dtype=torch.float64)}
+
+    g = types.SimpleNamespace(Problem=_P32, pareto_filter=lambda f: (np.arange(len(f)) < 2).astype(np.int32))
+    pat = types.SimpleNamespace(A=None, sid=None, params=np.zeros((4, 4)))
+    solver = _Solver()
+    r = bench.eps_sweep_section(g, _fake_torch, solver, pat, torch.zeros(5, 4), 10, None,
+                                eps_list=(1e-7, 1e-3))
+    assert [row["eps"] for row in r["rows"]] == [1e-7, 1e-3]
+    assert solver.tols == [1e-7, 1e-7, 1e-3, 1e-3]           # one warm-up and one timed solve each
+    assert all(row["frac_nondominated"] == 0.4 and row["speedup_vs_first"] == 1.0 for row in r["rows"])
+    assert len(seen) == 8                                    # one evaluation per structure and eps
+    for k, Wk in enumerate(seen[:4]):
+        assert torch.equal(Wk, torch.nn.functional.one_hot(torch.full((5,), k), 4).float())
+
+
+def test_gsa_section_host_logic():
+    fstar = np.full(4, 1.5)
+    r = bench.gsa_section(None, _fake_torch, _Solver(), torch.zeros(4, 4), fstar, 100, 8.0, None)
+    assert r["iterations"] == 100 and r["plans"] == 4 and r["ms"] == 2.0
+    assert r["plan_iterations_per_s"] == 4 * 100 / 2e-3
+    assert r["rel_gap_vs_fstar"]["median"] == 1.0 and r["plans_within_1e-4"] == 0
+    assert r["accept_rate_median"] == 0.5 and r["ms_ratio_gsa_over_lbfgs"] == 0.25
