@@ -103,6 +103,15 @@ typedef struct {
                               the gradient GEMM.  0..1000; 0 (default) = always the GEMM.
                               At about 1% active pairs the two cost about the same: each
                               active pair reads a whole row of A, where the GEMM reuses it */
+    int32_t wait_limit_us; /* tensor-core forms: every wait inside the GEMM kernels (a stage of
+                              operands landing, an accumulator handed between the MMA issuer
+                              and the epilogue) gives up after this many microseconds; the
+                              kernel then waits (at most 1 s more) for its own copies and MMAs
+                              in flight, frees its tensor memory and exits, and the call
+                              returns GMCO_ECUDA.  1..60000000; default 1000000 (1 s).  No
+                              wait takes longer than a few microseconds in a correct run, so
+                              only a fault elsewhere (or a limit set far too short, as a test
+                              does) ever reaches it */
 } gmco_options;
 
 /* Fills *opt with the defaults above. */
@@ -246,9 +255,11 @@ gmco_status gmco_dvh_from_dose(gmco_problem *prob, const float *dose, int64_t P,
  * one warm-up, with CUDA events between its kernels on the problem's stream.
  *   ms     4 averages (milliseconds): trial-point preparation, dose GEMM with the penalty
  *          epilogue, gradient GEMM, reduction of partial sums
- *   flops  4 values or NULL: algorithmic FLOPs of the dose GEMM (d and dd, 4 P n_pnt n_dwell)
- *          and of the gradient GEMM (2 P n_pnt n_dwell), then the FLOPs the kernels issue
- *          (tensor-core split terms over padded tiles; equal to the algorithmic for FP32).
+ *   flops  4 values or NULL: algorithmic FLOPs of the dose GEMM (the dose d = A t of
+ *          Eq. (dose), 2 P n_pnt n_dwell; the dose change dd it also forms for the line search
+ *          is not counted) and of the gradient GEMM (2 P n_pnt n_dwell), then the FLOPs the
+ *          kernels issue (tensor-core split terms of d and dd over padded tiles; for FP32 the
+ *          dose kernel's d and dd, 4 P n_pnt n_dwell, and the gradient's 2 P n_pnt n_dwell).
  * Synchronous. */
 gmco_status gmco_profile_evaluate(gmco_problem *prob, const float *penalty_weights, int64_t P,
                                   const float *X, int32_t reps, double *ms, double *flops);

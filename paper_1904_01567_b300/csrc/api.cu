@@ -217,6 +217,7 @@ gmco_status ensure_workspace(gmco_problem *pr, int32_t P)
                                      return r;
                                  });
         CK(e);
+        pr->tcb.wait_ns = (int64_t)pr->opt.wait_limit_us * 1000;
     }
     CK(a.alloc(&pr->dW, (size_t)cap * S));
     CK(a.alloc(&pr->dT0, (size_t)cap * pb.n_dwell));
@@ -365,6 +366,8 @@ gmco_status record_steps(gmco_problem *pr, int form, int steps, const UpdatePara
 }
 
 // Runs the step loop with evaluation `form` until every plan is DONE.
+gmco_status check_tc_error(gmco_problem *pr);
+
 gmco_status run_loop(gmco_problem *pr, int form, int32_t P, const UpdateParams &u,
                      int64_t max_steps, int64_t *steps_done)
 {
@@ -423,7 +426,15 @@ gmco_status run_loop(gmco_problem *pr, int form, int32_t P, const UpdateParams &
         done += steps;
         CK(cudaMemcpyAsync(pr->h_pinned, pr->s.n_act, sizeof(int32_t), cudaMemcpyDeviceToHost,
                            pr->stream));
+        if (form != 0 && pr->tcb.err)
+            CK(cudaMemcpyAsync(pr->h_pinned + 1, pr->tcb.err, sizeof(int32_t),
+                               cudaMemcpyDeviceToHost, pr->stream));
         CK(cudaStreamSynchronize(pr->stream));
+        if (form != 0 && pr->tcb.err && pr->h_pinned[1] != 0) {
+            // a pipeline wait gave up: stop stepping; check_tc_error reports and clears it
+            *steps_done = done;
+            return check_tc_error(pr);
+        }
         if (pr->h_pinned[0] == 0) break;
         if (done >= max_steps) {
             *steps_done = done;
@@ -673,6 +684,7 @@ gmco_status multi_workspace(gmco_multi *m, const std::vector<int64_t> &P)
     set.n = n;
     set.tc_terms = m->tc_terms;
     set.err = m->err;
+    set.wait_ns = (int64_t)m->probs[0]->opt.wait_limit_us * 1000;
     m->caps = P;
     m->gens = gens;
     m->ws_split = m->split_kb;
@@ -1021,6 +1033,7 @@ void gmco_default_options(gmco_options *opt)
     opt->grad_plan_tile = 0;
     opt->grad_split_kb = 0;
     opt->sparse_grad_permille = 0;
+    opt->wait_limit_us = 1000000;
 }
 
 const char *gmco_status_string(gmco_status s)
@@ -1058,7 +1071,8 @@ gmco_status gmco_create_problem(const float *A, int64_t n_pnt, int64_t n_dwell,
         !isfinite(o.rx_gy) || o.refine_iters < 0 || o.steps_per_poll < 1 ||
         o.steps_per_poll > 1024 || o.stop_window < 1 || o.grad_split_kb < 0 || o.max_evals < 0 ||
         (o.grad_plan_tile != 0 && o.grad_plan_tile != 128 && o.grad_plan_tile != 256) ||
-        o.sparse_grad_permille < 0 || o.sparse_grad_permille > 1000) {
+        o.sparse_grad_permille < 0 || o.sparse_grad_permille > 1000 || o.wait_limit_us < 1 ||
+        o.wait_limit_us > 60000000) {
         set_error_msg("gmco_create_problem: bad options");
         return GMCO_EINVAL;
     }
@@ -1533,9 +1547,12 @@ gmco_status gmco_profile_evaluate(gmco_problem *pr, const float *penalty_weights
     if (rs != GMCO_OK) return rs;
     for (int k = 0; k < 4; ++k) ms[k] = acc[k] / reps;
     if (flops) {
-        // algorithmic: dose d and dose change dd (2 contractions), gradient (1 contraction)
+        // algorithmic, the method's count: the dose d = A t of Eq. (dose) and the gradient
+        // contraction A^T G of Eq. (2), one 2 P n_pnt n_dwell each.  The dose change dd that the
+        // dose GEMM also forms for the line search is this library's numerical device, not
+        // work of the method, and is left out (it is in the issued figure).
         const double c = 2.0 * (double)P * (double)pb.n_pnt * (double)pb.n_dwell;
-        flops[0] = 2.0 * c;
+        flops[0] = c;
         flops[1] = c;
         // issued on the tensor cores (split terms, padded tiles); FP32 form: algorithmic
         if (form == 1) {
@@ -1544,8 +1561,8 @@ gmco_status gmco_profile_evaluate(gmco_problem *pr, const float *penalty_weights
             flops[2] = tc_mma_units(pb, true, 1) * cp;
             flops[3] = tc_mma_units(pb, true, 2) * cp;
         } else {
-            flops[2] = flops[0];
-            flops[3] = flops[1];
+            flops[2] = 2.0 * c;   // d and dd
+            flops[3] = c;
         }
     }
     CKS(check_tc_error(pr));
@@ -1573,6 +1590,10 @@ gmco_status gmco_evaluate_noalloc(const gmco_problem *pr, const float *penalty_w
         }
         if (a.type != cudaMemoryTypeDevice && a.type != cudaMemoryTypeManaged) {
             set_error_msg("gmco_evaluate_noalloc: buffers must be device memory");
+            return GMCO_EINVAL;
+        }
+        if (a.type == cudaMemoryTypeDevice && a.device != pr->device) {
+            set_error_msg("gmco_evaluate_noalloc: buffers must be on the problem's device");
             return GMCO_EINVAL;
         }
     }
@@ -1656,7 +1677,7 @@ gmco_status gmco_create_multi(gmco_problem *const *probs, int32_t n, gmco_multi 
         if (q.precision != o.precision || q.m != o.m || q.c1 != o.c1 || q.max_ls != o.max_ls ||
             q.stop_window != o.stop_window || q.max_evals != o.max_evals ||
             q.grad_plan_tile != o.grad_plan_tile ||
-            q.steps_per_poll != o.steps_per_poll ||
+            q.steps_per_poll != o.steps_per_poll || q.wait_limit_us != o.wait_limit_us ||
             pr->device != probs[0]->device) {
             set_error_msg("gmco_create_multi: problems differ in precision, solver options or device");
             return GMCO_EINVAL;

@@ -65,17 +65,18 @@ __global__ void k_na_prep(const float *__restrict__ X, const float *__restrict__
     if (threadIdx.x < S) Wc[(size_t)i * S + threadIdx.x] = W[(size_t)i * S + threadIdx.x] * inv_count[threadIdx.x];
 }
 
-// F = fixed-order FP64 sum of the per-tile partials; dF/dx = 2 x * sum over the splits.
+// F = fixed-order FP64 sum of the per-tile partials; dF/dx = 2 x * sum over the n_split
+// splits that the gradient GEMM wrote (the same split plan decides both).
 __global__ void k_na_finish(const float *__restrict__ X, const float *__restrict__ Fpart,
                             const float *__restrict__ gpart, int32_t P, int32_t nd,
-                            int32_t nd_pad, int32_t n_ptiles, double *__restrict__ F,
-                            float *__restrict__ grad)
+                            int32_t nd_pad, int32_t n_ptiles, int32_t n_split,
+                            double *__restrict__ F, float *__restrict__ grad)
 {
     const int i = blockIdx.x;
     if (grad) {
         for (int l = threadIdx.x; l < nd; l += blockDim.x) {
             float acc = 0.0f;
-            for (int q = 0; q < kSplit; ++q) acc += gpart[((size_t)q * P + i) * nd_pad + l];
+            for (int q = 0; q < n_split; ++q) acc += gpart[((size_t)q * P + i) * nd_pad + l];
             grad[(size_t)i * nd + l] = 2.0f * X[(size_t)i * nd + l] * acc;
         }
     }
@@ -138,17 +139,22 @@ cudaError_t noalloc_evaluate(const DevProblem &pb, const float *W, int64_t P, co
     ea.dFpart = nullptr;
     ea.gpart = reinterpret_cast<float *>(b + L.gpart);
     ea.sp = simt_split_plan(pb);
-    ea.sp.target_ctas = 1 << 30;     // always exactly kSplit point splits
+    ea.sp.target_ctas = 1 << 30;     // at most kSplit point splits (the scratch holds that many)
     ea.sp.max_split = kSplit;
     ea.sp.min_kb = 1;
+    // the splits the gradient GEMM writes: fewer than kSplit when the points fill fewer
+    // K blocks; the finish kernel adds exactly these
+    int32_t kbps = 0, n_split = 0;
+    split_plan(ea.sp, (int32_t)P, &kbps, &n_split);
+    if (n_split < 1 || n_split > kSplit) return cudaErrorInvalidValue;
     k_na_prep<<<(unsigned)P, 128, 0, st>>>(X, W, pb.inv_count, (int32_t)P, (int32_t)pb.n_dwell,
                                            (int32_t)pb.nd_pad, pb.n_struct, Tc, Wc, n_rows);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
     if ((e = launch_gemm1_simt(ea, MODE_G, st)) != cudaSuccess) return e;
     if (grad && (e = launch_gemm2_simt(ea, st)) != cudaSuccess) return e;
     k_na_finish<<<(unsigned)P, 128, 0, st>>>(X, ea.Fpart, grad ? ea.gpart : nullptr, (int32_t)P,
-                                             (int32_t)pb.n_dwell, (int32_t)pb.nd_pad, n_ptiles, F,
-                                             grad);
+                                             (int32_t)pb.n_dwell, (int32_t)pb.nd_pad, n_ptiles,
+                                             n_split, F, grad);
     return cudaGetLastError();
 }
 

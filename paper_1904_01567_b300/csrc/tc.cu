@@ -1,7 +1,7 @@
 // Tensor-core evaluation of Eq. (dose), Eq. (1), Eq. (obj) and Eq. (2) on sm_103a:
 // tcgen05.mma (kind::f16, BF16 operands, FP32 accumulators in TMEM), operands staged by TMA
 // (cp.async.bulk.tensor, 128-byte swizzle) through an mbarrier ring, one elected thread
-// issuing the MMAs, eight epilogue warps reading TMEM with tcgen05.ld.
+// issuing the MMAs, sixteen epilogue warps (four per TMEM lane quarter) reading TMEM with tcgen05.ld.
 //
 // A row i of A is scaled by a power of two s_i (exact) and split into BF16 terms
 // A/s = A1 + A2 + A3; t and dF/dd are split the same way.  Products A_i T_j are exact in FP32,
@@ -43,7 +43,7 @@ constexpr int SMEM_BUDGET = 194 * 1024;   // dynamic ring; with ~32 KB of static
                                           // the total stays within the 227 KB of a CTA
 constexpr int TMEM_COLS = 512;          // two accumulator buffers
 constexpr int BUF_COLS = 256;
-constexpr long long kSpinCycles = 2000000000LL;   // about 1 s at 2 GHz
+constexpr long long kDrainNs = 1000000000LL;   // wind-down waits after a failed wait: 1 s
 
 // ------------------------------------------------------------------ PTX wrappers
 __device__ __forceinline__ uint32_t smem_u32(const void *p)
@@ -75,15 +75,25 @@ __device__ __forceinline__ bool mbar_test(uint32_t bar, uint32_t parity)
     return ok != 0;
 }
 
-// Waits for the phase with the given parity; gives up after about a second, records `code`
-// in *err and returns false so that the kernel can still wind down and free its TMEM.
-__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, int32_t *err, int code)
+__device__ __forceinline__ long long global_ns()
+{
+    long long t;
+    asm volatile("mov.u64 %0, %globaltimer;" : "=l"(t));
+    return t;
+}
+
+// Waits for the phase with the given parity; gives up after limit_ns nanoseconds (the
+// problem's wait limit, 1 s by default), records `code` in *err (when err is given) and returns
+// false so that the kernel can still wind down: wait for its own copies and MMAs in flight and
+// free its TMEM.
+__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, int32_t *err, int code,
+                                          long long limit_ns)
 {
     if (mbar_test(bar, parity)) return true;
-    const long long t0 = clock64();
+    const long long t0 = global_ns();
     while (!mbar_test(bar, parity)) {
-        if (clock64() - t0 > kSpinCycles) {
-            atomicExch(err, code);
+        if (global_ns() - t0 > limit_ns) {
+            if (err) atomicExch(err, code);
             return false;
         }
     }
@@ -230,6 +240,7 @@ struct KParams {
     const void *pf_ptr[kTcPrefetch];             // gradient GEMM: L2 prefetch ranges (bytes)
     int64_t pf_bytes[kTcPrefetch];
     int32_t *err;
+    int64_t wait_ns;                             // limit of every pipeline wait
 };
 
 template <int KIND>
@@ -338,6 +349,9 @@ __global__ void __launch_bounds__(NTHREADS, 1) k_tc(const __grid_constant__ KPar
         (reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~static_cast<uintptr_t>(1023));
     __shared__ __align__(8) uint64_t full_bar[MAX_STAGES], empty_bar[MAX_STAGES];
     __shared__ __align__(8) uint64_t accf_bar[2], acce_bar[2];
+    __shared__ __align__(8) uint64_t drain_bar;   // MMA completion after a failed wait
+    __shared__ int32_t s_wound;                   // some role of this CTA gave up a wait
+    __shared__ int32_t s_prod_it;                 // ring stages the producer armed
     __shared__ uint32_t tmem_holder;
     __shared__ __align__(16) Prob s_prob[kMaxMulti];
     __shared__ int32_t s_start[kMaxMulti + 1];   // first work item of each problem
@@ -391,6 +405,8 @@ __global__ void __launch_bounds__(NTHREADS, 1) k_tc(const __grid_constant__ KPar
     if (threadIdx.x == 0) {
         s_fail = 0;
         s_act = 0;
+        s_wound = 0;
+        s_prod_it = 0;
     }
     __syncthreads();
     if (threadIdx.x == 0) {
@@ -414,6 +430,7 @@ __global__ void __launch_bounds__(NTHREADS, 1) k_tc(const __grid_constant__ KPar
             mbar_init(smem_u32(&accf_bar[b]), 1);
             mbar_init(smem_u32(&acce_bar[b]), EPI_WARPS);   // one arrival per epilogue warp
         }
+        mbar_init(smem_u32(&drain_bar), 1);
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
     if (warp == W_TMEM) tmem_alloc(smem_u32(&tmem_holder), (uint32_t)TMEM_COLS);
@@ -451,7 +468,7 @@ __global__ void __launch_bounds__(NTHREADS, 1) k_tc(const __grid_constant__ KPar
                     for (int kb = kb0; kb < kb1; ++kb, ++it) {
                         const int s = it % kp.n_stages;
                         const uint32_t ph = (uint32_t)(it / kp.n_stages) & 1u;
-                        if (!mbar_wait(smem_u32(&empty_bar[s]), ph ^ 1u, kp.err, 1)) { ok = false; break; }
+                        if (!mbar_wait(smem_u32(&empty_bar[s]), ph ^ 1u, kp.err, 1, kp.wait_ns)) { ok = false; break; }
                         uint8_t *st = smem + (size_t)s * kp.stage_bytes;
                         const uint32_t fb = smem_u32(&full_bar[s]);
                         mbar_expect_tx(fb, bytes);
@@ -468,6 +485,8 @@ __global__ void __launch_bounds__(NTHREADS, 1) k_tc(const __grid_constant__ KPar
                     }
                 }
             }
+            s_prod_it = it;   // stages armed, for the wind-down after a failed wait
+            if (!ok) s_wound = 1;
         }
         if constexpr (KIND == 2) {
             // once this CTA's operand loads are all issued (its MMAs and epilogue still to
@@ -509,7 +528,7 @@ __global__ void __launch_bounds__(NTHREADS, 1) k_tc(const __grid_constant__ KPar
                     k16_total = 1 << 30;
                 }
                 const int buf = nb;
-                if (!__all_sync(0xffffffffu, mbar_wait(smem_u32(&acce_bar[buf]), (use[buf] & 1u) ^ 1u, kp.err, 4)))
+                if (!__all_sync(0xffffffffu, mbar_wait(smem_u32(&acce_bar[buf]), (use[buf] & 1u) ^ 1u, kp.err, 4, kp.wait_ns)))
                     break;
                 fence_after();
                 const uint32_t tbuf = tmem + (uint32_t)(buf * BUF_COLS);
@@ -530,7 +549,7 @@ __global__ void __launch_bounds__(NTHREADS, 1) k_tc(const __grid_constant__ KPar
                     for (int kb = kb0; kb < kb1; ++kb, ++it) {
                         const int s = it % kp.n_stages;
                         const uint32_t ph = (uint32_t)(it / kp.n_stages) & 1u;
-                        if (!__all_sync(0xffffffffu, mbar_wait(smem_u32(&full_bar[s]), ph, kp.err, 2))) {
+                        if (!__all_sync(0xffffffffu, mbar_wait(smem_u32(&full_bar[s]), ph, kp.err, 2, kp.wait_ns))) {
                             ok = false;   // warp-uniform
                             break;
                         }
@@ -562,6 +581,7 @@ __global__ void __launch_bounds__(NTHREADS, 1) k_tc(const __grid_constant__ KPar
                 ++use[buf];
                 nb = buf ^ 1;
             }
+            if (!ok && lane == 0) s_wound = 1;
         }
     } else if (warp < EPI_WARPS) {
         // ---------------- epilogue: TMEM lane quarter q, column quarter h
@@ -607,7 +627,7 @@ __global__ void __launch_bounds__(NTHREADS, 1) k_tc(const __grid_constant__ KPar
                 // warp-uniform: tcgen05.ld below is warp-collective; every named barrier of this
                 // loop is reached by all epilogue threads whatever the outcome
                 ok = __all_sync(0xffffffffu,
-                                mbar_wait(smem_u32(&accf_bar[buf]), use[buf] & 1u, kp.err, 3));
+                                mbar_wait(smem_u32(&accf_bar[buf]), use[buf] & 1u, kp.err, 3, kp.wait_ns));
                 fence_after();
                 if (ok) {
                     const bool has_dT = kp.has_dT != 0;
@@ -852,7 +872,7 @@ __global__ void __launch_bounds__(NTHREADS, 1) k_tc(const __grid_constant__ KPar
                 const int ncols = w.half ? 128 : kp.bn;
                 const int cw = ncols / EPI_GROUPS;          // plan columns of this warp
                 ok = __all_sync(0xffffffffu,
-                                mbar_wait(smem_u32(&accf_bar[buf]), use[buf] & 1u, kp.err, 3));
+                                mbar_wait(smem_u32(&accf_bar[buf]), use[buf] & 1u, kp.err, 3, kp.wait_ns));
                 fence_after();
                 if (ok) {
                     float *out = d.gpart + (size_t)w.sub * n_rows * d.nd_pad + dw;
@@ -872,7 +892,10 @@ __global__ void __launch_bounds__(NTHREADS, 1) k_tc(const __grid_constant__ KPar
             }
             ++use[buf];
             nb = buf ^ 1;
-            if (!ok) break;
+            if (!ok) {
+                if (lane == 0) s_wound = 1;
+                break;
+            }
         }
         if constexpr (KIND == 1) {
             if (kp.sparse_ok) {
@@ -884,6 +907,26 @@ __global__ void __launch_bounds__(NTHREADS, 1) k_tc(const __grid_constant__ KPar
     }
     fence_before();
     __syncthreads();
+    if (s_wound) {
+        // a wait gave up: before the CTA frees its TMEM and exits, wait (bounded) for the TMA
+        // copies it armed and the MMAs it issued, which may still be writing its shared memory
+        // and TMEM
+        if (warp == W_TMA && lane == 0) {
+            const int it = s_prod_it;
+            for (int st = 0; st < kp.n_stages; ++st) {
+                if (it <= st) continue;   // never armed
+                const int last = it - 1 - ((it - 1 - st) % kp.n_stages);   // last arm of stage st
+                mbar_wait(smem_u32(&full_bar[st]), (uint32_t)(last / kp.n_stages) & 1u, nullptr, 0,
+                          kDrainNs);
+            }
+        } else if (warp == W_MMA) {
+            // the commit's phase completes once every MMA issued before it has finished
+            mma_commit_elect(smem_u32(&drain_bar));
+            mbar_wait(smem_u32(&drain_bar), 0u, nullptr, 0, kDrainNs);
+        }
+        fence_before();
+        __syncthreads();
+    }
     if constexpr (KIND == 1) {
         // one count per CTA into the single problem's counter of this step
         if (threadIdx.x == 0 && kp.sparse_ok && s_prob[0].act && s_act > 0)
@@ -1135,6 +1178,7 @@ KParams make_params(const TcLaunchSet &set, int kind, int parity, bool with_dT, 
     k.stage_bytes = k.b_off + max_b * k.slot_bytes;
     k.n_stages = std::max(1, std::min(MAX_STAGES, SMEM_BUDGET / k.stage_bytes));
     k.err = set.err;
+    k.wait_ns = set.wait_ns;
     if (kind == 2)
         for (int r = 0; r < kTcPrefetch; ++r) {
             k.pf_ptr[r] = set.pf_ptr[r];
@@ -1385,6 +1429,7 @@ TcLaunchSet tc_single_set(const DevProblem &pb, const TcBuffers &b)
     set.n = 1;
     set.tc_terms = pb.tc_terms;
     set.err = b.err;
+    set.wait_ns = b.wait_ns;
     set.max_items1 = ceil_div(b.cap, BM) * tc_n_ptiles(pb);
     set.grad_tile = b.grad_tile;
     set.max_items2 = ceil_div(b.cap, b.grad_tile) * tc_n_dtiles(pb) * b.sp.max_split;

@@ -80,6 +80,7 @@ struct TcBuffers {
     __nv_bfloat16 *G[3] = {nullptr, nullptr, nullptr};   // cap x np_pad, split terms of dF/dd
     float *Wc = nullptr;                                 // cap x n_struct
     int32_t *err = nullptr;  // device flag: nonzero after a pipeline wait gave up
+    int64_t wait_ns = 1000000000;   // limit of every pipeline wait (gmco_options.wait_limit_us)
     int32_t cap = 0;
     TcMaps maps1{}, maps2{};         // dose GEMM, gradient GEMM
     TcDoseProb *d_dose = nullptr;    // device descriptors of this problem (one each)
@@ -127,6 +128,7 @@ struct TcLaunchSet {
     const void *pf_ptr[kTcPrefetch] = {};
     int64_t pf_bytes[kTcPrefetch] = {};
     int32_t *err = nullptr;
+    int64_t wait_ns = 1000000000;       // limit of every pipeline wait, nanoseconds
 };
 
 int32_t tc_n_ptiles(const DevProblem &pb);

@@ -36,7 +36,7 @@ class _Options(ctypes.Structure):
                 ("refine_iters", ctypes.c_int32), ("steps_per_poll", ctypes.c_int32),
                 ("stop_window", ctypes.c_int32), ("grad_split_kb", ctypes.c_int32),
                 ("max_evals", ctypes.c_int32), ("grad_plan_tile", ctypes.c_int32),
-                ("sparse_grad_permille", ctypes.c_int32)]
+                ("sparse_grad_permille", ctypes.c_int32), ("wait_limit_us", ctypes.c_int32)]
 
 
 class _Source(ctypes.Structure):
@@ -433,10 +433,23 @@ def evaluate_noalloc(h, penalty_weights, X, objectives=None, grad=None, stream=N
     w = penalty_weights.detach().to(torch.float32).contiguous()
     x = X.detach().to(torch.float32).contiguous()
     P = int(w.shape[0])
+    # the C call takes P from here and trusts the row lengths, so every shape is checked
+    if tuple(w.shape) != (P, info["n_struct"]):
+        raise ValueError(f"penalty_weights must be P x {info['n_struct']}, got {tuple(w.shape)}")
+    if tuple(x.shape) != (P, info["n_dwell"]):
+        raise ValueError(f"X must be {P} x {info['n_dwell']}, got {tuple(x.shape)}")
+    if not (w.is_cuda and x.is_cuda) or w.device != x.device:
+        raise ValueError("penalty_weights and X must be CUDA tensors on the problem's device")
     if objectives is None:
         objectives = torch.empty(P, dtype=torch.float64, device=w.device)
     if grad is None:
         grad = torch.empty((P, info["n_dwell"]), dtype=torch.float32, device=w.device)
+    if (tuple(objectives.shape) != (P,) or objectives.dtype != torch.float64
+            or not objectives.is_contiguous() or objectives.device != w.device):
+        raise ValueError("objectives must be a contiguous float64 CUDA tensor of P values")
+    if (tuple(grad.shape) != (P, info["n_dwell"]) or grad.dtype != torch.float32
+            or not grad.is_contiguous() or grad.device != w.device):
+        raise ValueError("grad must be a contiguous float32 CUDA tensor of P x n_dwell")
     _check(load().gmco_evaluate_noalloc(h, w.data_ptr(), P, x.data_ptr(), objectives.data_ptr(),
                                         grad.data_ptr(), _stream_ptr(stream, True)),
            "gmco_evaluate_noalloc")

@@ -64,8 +64,10 @@ def test_options_defaults(gmco_mod):
     assert (o.precision, o.m, o.c1, o.max_ls, o.rx_gy) == (0, 10, 1e-4, 30, 15.0)
     assert gmco_mod.default_options(precision="bf16").precision == 1
     prm = np.array([[1.0, 15.0, np.inf, 1.0]])
+    assert o.wait_limit_us == 1000000                       # 1 s
     for bad in (dict(max_evals=-1), dict(grad_plan_tile=64), dict(sparse_grad_permille=-1),
-                dict(sparse_grad_permille=1001)):   # rejected before any device use
+                dict(sparse_grad_permille=1001), dict(wait_limit_us=0),
+                dict(wait_limit_us=60000001)):   # rejected before any device use
         with pytest.raises(gmco_mod.GmcoError) as e:
             gmco_mod.create_problem(np.ones((4, 3), np.float32), np.zeros(4, np.int32), prm, **bad)
         assert e.value.status == gmco_mod.EINVAL

@@ -42,10 +42,35 @@ def test_predict_matches_oracle(gmco_mod):
         tf = net.predict(F, W, t_floor=0.5)
     ref, _ = M.forward(_bf16_weights(p), M.dense_inputs(F, W))
     ref = ref.reshape(len(W), len(F))
-    err = np.max(np.abs(t - ref)) / np.mean(np.abs(ref))
-    print("predict rel err %.2e" % err)
-    assert err < 2e-2
+    # per element: 2e-2 relative, with a floor of 1e-2 of the mean prediction for the
+    # elements near zero (BF16 activations round each layer's inputs to 2^-9)
+    bound = 2e-2 * np.abs(ref) + 1e-2 * np.mean(np.abs(ref))
+    ratio = np.abs(t - ref) / bound
+    w = np.unravel_index(np.argmax(ratio), ratio.shape)
+    print("predict: worst element %s, |t - ref| = %.3e, bound %.3e" % (w, abs(t[w] - ref[w]), bound[w]))
+    assert np.all(ratio <= 1.0)
     assert np.array_equal(tf, np.maximum(t, 0.5))
+
+
+def _grad_magnitude(params, X, target):
+    """The FP64 backward with every term taken in absolute value: per parameter, the sum of
+    the magnitudes of the products whose sum is its gradient.  Rounding the activations and
+    deltas to BF16 perturbs each product by a few 2^-9 of its size, so a parameter's error is
+    bounded by a small multiple of this sum, whatever the cancellation in the gradient."""
+    pr = M.unpack(params)
+    t, c = M.forward(params, X)
+    R = len(t)
+    # e = t - target: its terms' magnitudes, since t carries the forward pass's rounding
+    e = np.abs(t) + np.abs(np.asarray(target, dtype=np.float64))
+    do = 2.0 * e / R * M.sigmoid(c["o"])
+    g = {"b4": np.array([do.sum()]), "w4": np.abs(c["h3"]).T @ do}
+    dz3 = np.outer(do, np.abs(pr["w4"])) * np.abs(M.gelu_prime(c["z3"]))
+    g["W3"], g["b3"] = np.abs(c["h2"]).T @ dz3, dz3.sum(axis=0)
+    dz2 = (dz3 @ np.abs(pr["W3"]).T) * np.abs(M.gelu_prime(c["z2"]))
+    g["W2"], g["b2"] = np.abs(c["h1"]).T @ dz2, dz2.sum(axis=0)
+    dz1 = (dz2 @ np.abs(pr["W2"]).T) * np.abs(M.gelu_prime(c["z1"]))
+    g["W1"], g["b1"] = np.abs(c["h0"]).T @ dz1, dz1.sum(axis=0)
+    return M.pack(g)
 
 
 @pytest.mark.parametrize("R", [1000, 20000])
@@ -56,15 +81,22 @@ def test_gradient_matches_oracle(gmco_mod, R):
     p = _params(5)
     with gmco_mod.Mlp(p) as net:
         loss, g = net.gradient(F, W, pairs, target)
-    lref, gref = M.loss_grad(_bf16_weights(p), M.inputs(F, W, pairs), target)
+    X = M.inputs(F, W, pairs)
+    lref, gref = M.loss_grad(_bf16_weights(p), X, target)
+    gmag = _grad_magnitude(_bf16_weights(p), X, target)
     assert abs(loss / lref - 1.0) < 1e-2, (loss, lref)
+    # every element: |g - g_ref| <= 2e-2 |g_ref| + 1e-2 sum|terms| (see _grad_magnitude;
+    # 1e-2 is about five BF16 roundings of 2^-9 along the chain)
     o = 0
     for name, shape in M.SHAPES:
         n = int(np.prod(shape))
-        a, b = g[o:o + n], gref[o:o + n]
-        rel = np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-30)
-        print(f"{name}: rel {rel:.2e}")
-        assert rel < 2e-2, (name, rel)
+        a, b, mg = g[o:o + n], gref[o:o + n], gmag[o:o + n]
+        bound = 2e-2 * np.abs(b) + 1e-2 * mg
+        ratio = np.abs(a - b) / np.maximum(bound, 1e-30)
+        k = int(np.argmax(ratio))
+        print(f"{name}: worst element {k}: gpu {a[k]:.4e} ref {b[k]:.4e} |terms| {mg[k]:.3e} "
+              f"(error / bound {ratio[k]:.3f}); block rel {np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-30):.2e}")
+        assert np.all(ratio <= 1.0), (name, k, a[k], b[k], mg[k])
         o += n
 
 

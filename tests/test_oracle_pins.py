@@ -312,6 +312,32 @@ def test_evaluation_budget_stops_on_the_same_path(oracle_mod):
     r = oracle_mod.lbfgs(p.A, p.sid, p.params, W[j], None, max_iters=150, tol=0.0, max_evals=0)
     assert r["evals"] == full["evals"] and r["F"] == full["F"]
 
+def test_stop_window_is_the_first_run_of_small_changes(oracle_mod):
+    """Sec. 2.2.3's stop rule over a window of w accepted iterations: the run stops at the first
+    iteration k whose last w relative objective changes |F_(i-1) - F_i| / |F_(i-1)| are all
+    <= tol, along the path that a run without the stop rule takes (the window changes when
+    the path ends, not the path)."""
+    p, W, _ = workload("prostate-2k-8plans")
+    tol = 1e-3
+    for j in (0, 3, 6):
+        full = oracle_mod.lbfgs(p.A, p.sid, p.params, W[j], None, max_iters=400, tol=0.0,
+                                trace=True)
+        F = full["trace"][:, 0]
+        small = np.abs(F[:-1] - F[1:]) <= tol * np.abs(F[:-1])   # small[i]: iteration i + 1
+        for w in (1, 2, 3, 5):
+            r = oracle_mod.lbfgs(p.A, p.sid, p.params, W[j], None, max_iters=400, tol=tol,
+                                 stop_window=w)
+            run, expect = 0, None
+            for i, ok in enumerate(small):
+                run = run + 1 if ok else 0
+                if run >= w:
+                    expect = i + 1
+                    break
+            assert expect is not None and expect < 400
+            assert r["status"] == oracle_mod.CONVERGED and r["iters"] == expect, (j, w, r["iters"], expect)
+            assert r["F"] == F[expect]
+
+
 # ---------------------------------------------------------------- DVH indices
 def test_dvh_hand_made(oracle_mod):
     pro = np.arange(2.0, 21.0, 2.0)            # 2, 4, ..., 20 (N = 10)
