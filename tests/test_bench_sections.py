@@ -36,7 +36,8 @@ class _Solver:
     def solve_batch(self, W, max_iters, tol, stream=None, allow_timeout=False):
         self.tols.append(tol)
         P = W.shape[0]
-        return {"T": torch.full((P, 3), 4.0), "iters": torch.full((P,), 9, dtype=torch.int32)}
+        return {"T": torch.full((P, 3), 4.0), "iters": torch.full((P,), 9, dtype=torch.int32),
+                "objectives": torch.full((P,), 2.0, dtype=torch.float64)}
 
     def solve_sa(self, W, iterations, stream=None):
         P = W.shape[0]
@@ -67,12 +68,14 @@ def test_eps_sweep_section_host_logic():
     g = types.SimpleNamespace(Problem=_P32, pareto_filter=lambda f: (np.arange(len(f)) < 2).astype(np.int32))
     pat = types.SimpleNamespace(A=None, sid=None, params=np.zeros((4, 4)))
     solver = _Solver()
-    r = bench.eps_sweep_section(g, _fake_torch, solver, pat, torch.zeros(5, 4), 10, None,
+    fstar = np.array([2.0, 2.0, 1.0, 2.0, 2.0])
+    r = bench.eps_sweep_section(g, _fake_torch, solver, pat, torch.zeros(5, 4), 10, None, fstar,
                                 eps_list=(1e-7, 1e-3))
     assert [row["eps"] for row in r["rows"]] == [1e-7, 1e-3]
     assert solver.tols == [1e-7, 1e-7, 1e-3, 1e-3]           # one warm-up and one timed solve each
     assert all(row["frac_nondominated"] == 0.4 and row["speedup_vs_first"] == 1.0 for row in r["rows"])
     assert len(seen) == 8                                    # one evaluation per structure and eps
+    assert all(row["median_gap_vs_fstar"] == 0.0 and row["plans_within_1e-4"] == 4 for row in r["rows"])
     for k, Wk in enumerate(seen[:4]):
         assert torch.equal(Wk, torch.nn.functional.one_hot(torch.full((5,), k), 4).float())
 
@@ -84,3 +87,10 @@ def test_gsa_section_host_logic():
     assert r["plan_iterations_per_s"] == 4 * 100 / 2e-3
     assert r["rel_gap_vs_fstar"]["median"] == 1.0 and r["plans_within_1e-4"] == 0
     assert r["accept_rate_median"] == 0.5 and r["ms_ratio_gsa_over_lbfgs"] == 0.25
+
+
+def test_section_summary_keeps_key_figures():
+    sec = {"rows": [{"eps": 1e-3, "ms": 12.3456, "frac_nondominated": 0.56789, "median_gap_vs_fstar": 1e-3}]}
+    assert bench.section_summary("eps_sweep", sec) == {"0.001": [12.35, 0.5679, 1e-3]}
+    assert bench.section_summary("gsa", {"error": "boom"}) == {"error": "boom"}
+    assert "summary_error" in bench.section_summary("gsa", {"ms": 1.0})
