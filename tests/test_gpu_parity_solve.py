@@ -34,6 +34,8 @@ QUALITY = 1e-4
 RULE = dict(tol=1e-10, max_iters=3000)
 MAX_EVALS = 3000
 FORM_EPS = {"fp32": 2.0 ** -16, "bf16x3": 2.0 ** -16}
+FLOOR_F = {"fp32": 1e-5, "bf16x3": 1e-5}   # the forms' objective error bound (evaluation tests)
+FLOOR_T = {"fp32": 1e-5, "bf16x3": 1e-4}
 # the reported objective is the FP32 re-evaluation at the returned T: its error against
 # Eq. (obj) in FP64 is 1e-5 on the small workload and up to 6e-5 at 12 000 points (the
 # evaluation tests' bounds), where objectives near the optimum are small sums of squares
@@ -169,8 +171,10 @@ def test_path_past_history_wrap(gmco_mod, oracle_mod, form, m, k):
         assert out["status"][j] == r["status"] == oracle_mod.MAXITER
         dF = abs(out["objectives"][j] / r["F"] - 1.0)
         dT = float(np.max(np.abs(out["T"][j] - r["t"])) / np.max(np.abs(r["t"])))
-        tol_F = max(10.0 * s["dF"], 1e-6)
-        tol_T = max(10.0 * s["dT"], 1e-5)
+        # floors: the forms' own accumulation errors, which a perturbation of A models only in
+        # part (FP32 sums over 2000 points, and for bf16x3 its 2.2e-6 dose error)
+        tol_F = max(10.0 * s["dF"], FLOOR_F[form])
+        tol_T = max(10.0 * s["dT"], FLOOR_T[form])
         worst.append((round(dF / tol_F, 3), round(dT / tol_T, 3)))
         assert dF <= tol_F, (j, dF, s["dF"])
         assert dT <= tol_T, (j, dT, s["dT"])
