@@ -64,6 +64,10 @@ def parse_args():
     ap.add_argument("--no-warm", action="store_true", help="skip the warm-start section")
     ap.add_argument("--no-gsa", action="store_true", help="skip the annealing-engine section")
     ap.add_argument("--no-eps-sweep", action="store_true", help="skip the stopping-criterion sweep")
+    ap.add_argument("--no-fp32-form", action="store_true", help="skip the FP32-form section")
+    ap.add_argument("--no-refine", action="store_true", help="skip the FP32-refinement section")
+    ap.add_argument("--refine-list", default="300,1000",
+                    help="FP32 refinement iterations tried after the tensor-core solve")
     ap.add_argument("--gsa-iters", type=int, default=1000,
                     help="iterations of the annealing engine (the paper's timing setting: 1000)")
     return ap.parse_args()
@@ -546,6 +550,70 @@ def gsa_section(g, torch, prob, Wd, fstar, iters, lbfgs_ms, stream):
                         "temperature 1e-2 -> 1e-5 of the start objective, geometric"}
 
 
+def fp32_form_section(g, torch, args, pat, W, Wd, fstar, stream):
+    """The plain method in FP32 (the workload's stated precision) on the headline workload and
+    rule: plans within 1e-4 of F* per second, and the FP32 dose kernel against the device's
+    measured FP32 FMA peak (the library's own throughput kernel, CUDA events)."""
+    peak = g.fp32_peak()
+    P = int(Wd.shape[0])
+    with g.Problem(pat.A, pat.sid, pat.params, precision="fp32", steps_per_poll=args.steps_per_poll,
+                   max_evals=args.max_evals) as p32:
+        p32.solve_batch(Wd, max_iters=args.max_iters, tol=args.tol, stream=stream, allow_timeout=True)
+        torch.cuda.synchronize()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        out = p32.solve_batch(Wd, max_iters=args.max_iters, tol=args.tol, stream=stream, allow_timeout=True)
+        b.record(stream)
+        torch.cuda.synchronize()
+        ms = a.elapsed_time(b)
+        launches = p32.last_launch_count()
+        gap = out["objectives"].cpu().numpy() / fstar - 1.0
+        X = np.sqrt(out["T"].cpu().numpy()).astype(np.float32)
+        prof = p32.profile_evaluate(W, X, reps=max(2, args.profile_reps // 2))
+    ok = int(np.sum(gap <= QUALITY))
+    ms_dose = prof["ms"]["dose_gemm"]
+    alg = prof["flops"]["dose_algorithmic"] / (ms_dose * 1e-3) / 1e12
+    issued = prof["flops"]["dose_issued"] / (ms_dose * 1e-3) / 1e12
+    return {"precision_form": "fp32", "plans": P, "plans_within_1e-4": ok,
+            "ms_per_solve": ms, "plans_within_1e-4_per_s": ok / (ms * 1e-3),
+            "median_gap_vs_fstar": float(np.median(gap)), "gpu_launches": int(launches),
+            "roofline": {"bound": "alu", "kernel": "k_gemm1 (FP32 SIMT dose GEMM, d and dd)",
+                         "achieved": alg, "unit": "TFLOP/s", "peak": peak["ffma"],
+                         "frac": alg / peak["ffma"], "issued_tflops": issued,
+                         "issued_frac": issued / peak["ffma"],
+                         "peak_source": "measured scalar FFMA throughput (gmco_fp32_peak), the "
+                                        "instruction the kernel issues",
+                         "peak_paired_ffma2": peak["ffma2"], "ms_per_launch": ms_dose},
+            "kernel_ms": prof["ms"]}
+
+
+def refine_section(g, torch, args, pat, Wd, fstar, stream):
+    """After the tensor-core solve, up to R further iterations with the FP32 evaluation
+    (gmco_options.refine_iters): plans within 1e-4 of F* and the time, for each R."""
+    rows = []
+    for R in [int(r) for r in args.refine_list.split(",") if r]:
+        with g.Problem(pat.A, pat.sid, pat.params, precision=args.precision,
+                       steps_per_poll=args.steps_per_poll, max_evals=args.max_evals,
+                       refine_iters=R) as pr:
+            pr.solve_batch(Wd, max_iters=args.max_iters, tol=args.tol, stream=stream, allow_timeout=True)
+            torch.cuda.synchronize()
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            out = pr.solve_batch(Wd, max_iters=args.max_iters, tol=args.tol, stream=stream,
+                                 allow_timeout=True)
+            b.record(stream)
+            torch.cuda.synchronize()
+        gap = out["objectives"].cpu().numpy() / fstar - 1.0
+        ms = a.elapsed_time(b)
+        ok = int(np.sum(gap <= QUALITY))
+        rows.append({"refine_iters": R, "plans_within_1e-4": ok, "ms_per_solve": ms,
+                     "plans_within_1e-4_per_s": ok / (ms * 1e-3),
+                     "median_gap_vs_fstar": float(np.median(gap))})
+    return {"precision_form": args.precision, "rows": rows,
+            "note": "refinement: plans re-opened after the tensor-core solve for up to R more "
+                    "iterations of the FP32 evaluation, with their own evaluation budget"}
+
+
 def eps_sweep_section(g, torch, prob, pat, Wd, max_iters, stream, fstar,
                       eps_list=(1e-7, 1e-6, 1e-5, 1e-4, 1e-3, 1e-2)):
     """The stopping-criterion sweep of Sec. 2.2.4 (the paper's Fig. 4a, on this workload): for
@@ -603,6 +671,13 @@ def section_summary(name, sec):
         if name == "gsa":
             return {"ms": sec["ms"], "plans_within_1e-4": sec["plans_within_1e-4"],
                     "median_gap": sec["rel_gap_vs_fstar"]["median"]}
+        if name == "fp32_form":
+            return {"plans_within_1e-4": sec["plans_within_1e-4"],
+                    "plans_within_1e-4_per_s": sec["plans_within_1e-4_per_s"],
+                    "dose_kernel_frac_of_fp32_peak": sec["roofline"]["frac"]}
+        if name == "refine":
+            return {str(r["refine_iters"]): [r["plans_within_1e-4"], round(r["ms_per_solve"], 1)]
+                    for r in sec["rows"]}
         if name == "warm_start":
             return {v: {b: [round(e["ms"], 1), e["within_1e-4"]] for b, e in d.items()}
                     for v, d in sec["by_start"].items()}
@@ -739,6 +814,10 @@ def run_ours(args):
                                                               stream, fstar)
         if not args.no_gsa:
             sections["gsa"] = lambda: gsa_section(g, torch, prob, Wd, fstar, args.gsa_iters, step_ms, stream)
+        if not args.no_fp32_form:
+            sections["fp32_form"] = lambda: fp32_form_section(g, torch, args, pat, W, Wd, fstar, stream)
+        if not args.no_refine and args.precision != "fp32":
+            sections["refine"] = lambda: refine_section(g, torch, args, pat, Wd, fstar, stream)
         if not args.no_warm:
             sections["warm_start"] = lambda: warm_start_section(g, torch, args)
         summary = {}

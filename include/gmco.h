@@ -145,6 +145,35 @@ gmco_status gmco_dose_rate_matrix(const float *points, int64_t n_pnt, const floa
                                   int64_t n_dwell, const gmco_source *src, float *A_out,
                                   void *cuda_stream);
 
+/* Dose calculation points of the workload's analytic structures (the sampling half of step
+ * (i); the clinical flow creates points from contours, which needs DICOM data): structure 0
+ * the prostate ellipsoid (semi-axes a, b, c at the origin) without the urethra, 1 the urethra
+ * (cylinder of radius urethra_r on the z axis, |z| <= c), 2 the rectum (cylinder of radius
+ * rectum_r parallel to z through (0, rectum_y), |z| <= rectum_half_len) outside the prostate,
+ * 3 the bladder (sphere of radius bladder_r at (0, 0, bladder_z)) outside the prostate and
+ * the rectum.  Sizes in cm.
+ * Rule (uniform rejection sampling with a counter-based generator, reproducible anywhere):
+ * candidate k of structure s is lo + u w in the structure's bounding box (corner lo, widths w,
+ * per axis), u = top 24 bits of SplitMix64 output s 2^40 + 4 k + axis (axis 0, 1, 2 = x, y, z)
+ * seeded with `seed`, times 2^-24; point i of structure s is its i-th accepted candidate.  The
+ * geometry is rounded to FP32 and every arithmetic step is one IEEE FP32 operation in a fixed
+ * order (see points.cu), so the points are reproducible bit for bit.
+ *   counts   4 point counts (>= 0, total 1..2^31)
+ *   points   sum(counts) x 3 FP32 coordinates, structure-major (host or device)
+ *   sid      sum(counts) structure ids 0..3 (host or device)
+ * GMCO_EINVAL for non-finite or non-positive sizes, bad counts, NULL pointers, or a structure
+ * that accepts too few candidates (empty, or covered by what it excludes).  Synchronous on
+ * cuda_stream. */
+typedef struct gmco_geometry {
+    double a, b, c;                              /* prostate semi-axes */
+    double urethra_r;
+    double rectum_r, rectum_y, rectum_half_len;
+    double bladder_r, bladder_z;
+} gmco_geometry;
+
+gmco_status gmco_sample_points(const gmco_geometry *geo, const int64_t *counts, uint64_t seed,
+                               float *points, int32_t *sid, void *cuda_stream);
+
 /* Creates a problem on the current CUDA device.
  *   A               n_pnt x n_dwell dose-rate matrix, Gy/s, finite and >= 0 (Eq. (dose));
  *                   copied (and quantised for BF16/FP8), the caller may free it afterwards
@@ -245,6 +274,15 @@ gmco_status gmco_evaluate_noalloc(const gmco_problem *prob, const float *penalty
                                   int64_t P, const float *X, double *objectives, float *grad_x,
                                   void *cuda_stream);
 
+/* DVH indices (GMCO_DVH_K per plan, see above) of given dwell times: T is P x n_dwell (s,
+ * finite and >= 0; host or device).  The doses A t of Eq. (dose) are formed with the FP32 form
+ * whatever the problem's precision, and the indices are counted exactly on them.  A problem
+ * built on a separate, denser point set of the same structures and dwell positions gives the
+ * DVH of plans optimised on a coarser one (Sec. 2.1: the paper evaluates DVHs on their own
+ * point set).  GMCO_EINVAL for bad sizes, NULL pointers or negative / non-finite times. */
+gmco_status gmco_dvh_at(gmco_problem *prob, const float *T, int64_t P, float *dvh,
+                        void *cuda_stream);
+
 /* DVH indices (GMCO_DVH_K per plan, see above) of given doses: dose is P x n_pnt (Gy).
  * Exact on the given FP32 values: counts and k-th largest values, no interpolation. */
 gmco_status gmco_dvh_from_dose(gmco_problem *prob, const float *dose, int64_t P, float *dvh,
@@ -263,6 +301,14 @@ gmco_status gmco_dvh_from_dose(gmco_problem *prob, const float *dose, int64_t P,
  * Synchronous. */
 gmco_status gmco_profile_evaluate(gmco_problem *prob, const float *penalty_weights, int64_t P,
                                   const float *X, int32_t reps, double *ms, double *flops);
+
+/* Measurement aid: the device's FP32 fused multiply-add throughput in TFLOP/s, the pipe peak
+ * against which the FP32 form's SIMT contractions are reported: tflops[0] with scalar FFMA
+ * (the instruction the FP32 form's kernels issue), tflops[1] with paired FP32 FMA (two FP32
+ * lanes per instruction).  Each is the best of `reps` launches of `iters` iterations of 16
+ * independent FMA chains per thread on 8 resident blocks of 256 threads per SM, timed with CUDA
+ * events.  Synchronous; uses the current device and stream 0; allocates one small buffer. */
+gmco_status gmco_fp32_peak(int32_t iters, int32_t reps, double *tflops);
 
 /* ---- plan pool post-processing ----
  * RTOG evaluation (Sec. 2.3.1: target V100 >= 90 %, urethra D10 < 118 % of the prescription,
@@ -380,6 +426,17 @@ gmco_status gmco_mlp_create(const float *params, gmco_mlp **out);
 void gmco_mlp_destroy(gmco_mlp *mlp);
 /* Current FP32 master parameters. */
 gmco_status gmco_mlp_get_params(gmco_mlp *mlp, float *params);
+
+/* Checkpoint of a network and its training state, so that training resumes exactly: the file
+ * holds the line "GMCO-MLP", one line of JSON (format, version 1, GMCO_MLP_NPARAM, the Adam step
+ * count, the arrays, the parameter layout), then three arrays of GMCO_MLP_NPARAM little-endian
+ * FP32 values: the master parameters and Adam's first and second moments.  Training steps after
+ * gmco_mlp_load give the same parameters, bit for bit, as the same steps of the network that
+ * was saved.  save: GMCO_EINVAL when the file cannot be written.  load: creates a network on the
+ * current device; GMCO_EINVAL for a file that is missing, of another format, version or size,
+ * or holds non-finite values or negative second moments (checked before any device use). */
+gmco_status gmco_mlp_save(gmco_mlp *mlp, const char *path);
+gmco_status gmco_mlp_load(const char *path, gmco_mlp **out);
 
 /* Predicted dwell times of P plans of one patient: t_out[p][l] for features[l] (n_dwell x
  * 10) and penalty_weights[p] (P x 4), each at least t_floor. */

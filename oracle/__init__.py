@@ -29,3 +29,4 @@ from .oracle import (  # noqa: F401
 )
 from .optimum import fstar, objective_t, kkt_residual  # noqa: F401,E402
 from . import mlp  # noqa: F401,E402
+from . import points  # noqa: F401,E402

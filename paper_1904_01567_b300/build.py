@@ -15,7 +15,7 @@ CSRC = os.path.join(HERE, "csrc")
 INCLUDE = os.path.join(ROOT, "include")
 BUILD = os.path.join(ROOT, "_build")
 LIB = os.path.join(HERE, "libgmco.so")
-SOURCES = ["api.cu", "solver.cu", "eval_simt.cu", "dvh.cu", "tc.cu", "noalloc.cu", "mlp.cu", "doserate.cu", "pool.cu", "sa.cu"]
+SOURCES = ["api.cu", "solver.cu", "eval_simt.cu", "dvh.cu", "tc.cu", "noalloc.cu", "mlp.cu", "doserate.cu", "pool.cu", "sa.cu", "peak.cu", "points.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "--expt-relaxed-constexpr",
          "-I", INCLUDE, "-I", CSRC]

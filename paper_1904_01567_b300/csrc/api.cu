@@ -78,6 +78,23 @@ __global__ void k_count_bad(const float *v, int64_t n, int32_t allow_negative, i
 
 }  // namespace
 
+// Compact rows of P plans at given dwell times T (P x nd, s): row i = plan i, t padded with
+// zeros to nd_pad, weights zero (only doses are formed from these rows).
+__global__ void k_rows_from_times(const float *__restrict__ T, int32_t P, int32_t nd, int32_t nd_pad,
+                                  int32_t S, float *__restrict__ Tc, float *__restrict__ Wc,
+                                  int32_t *__restrict__ list, int32_t *__restrict__ n_act)
+{
+    const int i = blockIdx.x;
+    if (i >= P) return;
+    for (int l = threadIdx.x; l < nd_pad; l += blockDim.x)
+        Tc[(size_t)i * nd_pad + l] = l < nd ? T[(size_t)i * nd + l] : 0.0f;
+    if (threadIdx.x < S) Wc[(size_t)i * S + threadIdx.x] = 0.0f;
+    if (threadIdx.x == 0) {
+        list[i] = i;
+        if (i == 0) *n_act = P;
+    }
+}
+
 struct gmco_problem {
     int device = 0;
     gmco_options opt{};
@@ -1610,6 +1627,125 @@ gmco_status gmco_evaluate_noalloc(const gmco_problem *pr, const float *penalty_w
     CK(cudaSetDevice(pr->device));
     CK(noalloc_evaluate(pr->pb, penalty_weights, P, X, objectives, grad_x,
                         (cudaStream_t)cuda_stream));
+    return GMCO_OK;
+}
+
+gmco_status gmco_sample_points(const gmco_geometry *geo, const int64_t *counts, uint64_t seed,
+                               float *points, int32_t *sid, void *cuda_stream)
+{
+    if (!geo || !counts || !points || !sid) {
+        set_error_msg("gmco_sample_points: null pointer");
+        return GMCO_EINVAL;
+    }
+    const double g[9] = {geo->a, geo->b, geo->c, geo->urethra_r, geo->rectum_r, geo->rectum_y,
+                         geo->rectum_half_len, geo->bladder_r, geo->bladder_z};
+    for (int i = 0; i < 9; ++i)
+        if (!isfinite(g[i]) || (i != 5 && i != 8 && !(g[i] > 0.0))) {
+            set_error_msg("gmco_sample_points: sizes must be finite and positive, centres finite");
+            return GMCO_EINVAL;
+        }
+    int64_t total = 0;
+    for (int s = 0; s < 4; ++s) {
+        if (counts[s] < 0 || counts[s] > (1LL << 31)) {
+            set_error_msg("gmco_sample_points: bad point count");
+            return GMCO_EINVAL;
+        }
+        total += counts[s];
+    }
+    if (total < 1 || total > (1LL << 31)) {
+        set_error_msg("gmco_sample_points: total point count outside 1..2^31");
+        return GMCO_EINVAL;
+    }
+    int dev_count = 0;
+    if (cudaGetDeviceCount(&dev_count) != cudaSuccess || dev_count < 1) {
+        cudaGetLastError();
+        set_error_msg("gmco_sample_points: no CUDA device");
+        return GMCO_ECUDA;
+    }
+    cudaStream_t st = (cudaStream_t)cuda_stream;
+    // outputs in host memory are written through device buffers
+    auto on_device = [](const void *q) {
+        cudaPointerAttributes a;
+        if (cudaPointerGetAttributes(&a, q) != cudaSuccess) {
+            cudaGetLastError();
+            return false;
+        }
+        return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+    };
+    const bool dp = on_device(points), ds = on_device(sid);
+    float *d_pts = points;
+    int32_t *d_sid = sid;
+    if (!dp) CK(cudaMalloc(&d_pts, (size_t)total * 3 * sizeof(float)));
+    if (!ds && cudaMalloc(&d_sid, (size_t)total * sizeof(int32_t)) != cudaSuccess) {
+        if (!dp) cudaFree(d_pts);
+        set_error_msg("gmco_sample_points: device allocation failed");
+        return GMCO_ENOMEM;
+    }
+    int32_t short_s = -1;
+    cudaError_t e = sample_points_dev(g, counts, seed, d_pts, d_sid, st, &short_s);
+    if (e == cudaSuccess && !dp)
+        e = cudaMemcpyAsync(points, d_pts, (size_t)total * 3 * sizeof(float), cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess && !ds)
+        e = cudaMemcpyAsync(sid, d_sid, (size_t)total * sizeof(int32_t), cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    if (!dp) cudaFree(d_pts);
+    if (!ds) cudaFree(d_sid);
+    if (e != cudaSuccess) {
+        set_error("gmco_sample_points", e);
+        return GMCO_ECUDA;
+    }
+    if (short_s >= 0) {
+        char buf[160];
+        snprintf(buf, sizeof buf,
+                 "gmco_sample_points: structure %d accepts too few candidates (empty or covered "
+                 "by the structures it excludes)", short_s);
+        set_error_msg(buf);
+        return GMCO_EINVAL;
+    }
+    return GMCO_OK;
+}
+
+gmco_status gmco_dvh_at(gmco_problem *pr, const float *T, int64_t P, float *dvh, void *cuda_stream)
+{
+    if (!pr || !T || !dvh || P < 1 || P > (1 << 20)) {
+        set_error_msg("gmco_dvh_at: bad arguments");
+        return GMCO_EINVAL;
+    }
+    pr->launches = 0;
+    CKS(begin_call(pr, cuda_stream));
+    CKS(ensure_workspace(pr, (int32_t)P));
+    const DevProblem &pb = pr->pb;
+    CKS(stage_in(pr, T, pr->dT0, (size_t)P * pb.n_dwell * sizeof(float)));
+    int32_t bad = 0;
+    CKS(count_bad(pr, pr->dT0, P * pb.n_dwell, false, &bad));
+    if (bad) {
+        set_error_msg("gmco_dvh_at: negative or non-finite dwell times");
+        return GMCO_EINVAL;
+    }
+    const SolverState &s = pr->s;
+    k_rows_from_times<<<(unsigned)P, 128, 0, pr->stream>>>(pr->dT0, (int32_t)P, (int32_t)pb.n_dwell,
+                                                          (int32_t)pb.nd_pad, pb.n_struct, pr->Tc,
+                                                          pr->Wc, s.list, s.n_act);
+    CK(cudaGetLastError());
+    // the doses A t with the FP32 form, into the rows of G (dose mode)
+    EvalArgs e{};
+    e.pb = pb;
+    e.n_rows = s.n_act;
+    e.cap = pr->cap;
+    e.Tt = pr->Tc;
+    e.dT = nullptr;
+    e.Wc = pr->Wc;
+    e.G = pr->G;
+    e.Fpart = pr->Fpart;
+    e.dFpart = nullptr;
+    e.gpart = nullptr;
+    e.sp = simt_split_plan(pb);
+    CK(launch_gemm1_simt(e, MODE_DOSE, pr->stream));
+    CK(launch_dvh(pb, pr->G, pb.np_pad, s.list, (int32_t)P, pr->opt.rx_gy, pr->dDvh, pr->stream));
+    pr->launches += 3;
+    CK(cudaMemcpyAsync(dvh, pr->dDvh, (size_t)P * GMCO_DVH_K * sizeof(float), cudaMemcpyDefault,
+                       pr->stream));
+    CKS(end_call(pr, cuda_stream));
     return GMCO_OK;
 }
 

@@ -184,6 +184,13 @@ size_t noalloc_required_bytes(const DevProblem &pb, int64_t P);
 cudaError_t noalloc_evaluate(const DevProblem &pb, const float *W, int64_t P, const float *X,
                              double *F, float *grad, cudaStream_t st);
 
+// Dose calculation points of the analytic structures (points.cu): geo = a, b, c, urethra_r,
+// rectum_r, rectum_y, rectum_half_len, bladder_r, bladder_z; counts[4] per structure; writes
+// structure-major points (x, y, z) and ids to device buffers.  *short_struct = the structure
+// whose candidates ran out (or -1).  Synchronises st.
+cudaError_t sample_points_dev(const double *geo, const int64_t *counts, uint64_t seed, float *pts,
+                              int32_t *sid, cudaStream_t st, int32_t *short_struct);
+
 // DVH indices of P dose rows (P x np_pad, row stride ld)
 cudaError_t launch_dvh(const DevProblem &pb, const float *D, int64_t ld, const int32_t *rows,
                        int32_t P, double rx, float *dvh_out, cudaStream_t st);

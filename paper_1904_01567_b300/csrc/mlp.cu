@@ -22,6 +22,9 @@
 //   k_mlp_adam              Adam on the FP32 master weights, then the BF16 copies
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
+
+#include <cstdio>
+#include <cstring>
 #include <math.h>
 #include <stdint.h>
 #include <stdio.h>
@@ -748,6 +751,99 @@ gmco_status gmco_mlp_get_params(gmco_mlp *q, float *params)
     MCK(cudaSetDevice(q->device));
     MCK(cudaStreamSynchronize(q->stream));
     MCK(cudaMemcpy(params, q->p, NPARAM * sizeof(float), cudaMemcpyDefault));
+    return GMCO_OK;
+}
+
+// Checkpoint file: the line "GMCO-MLP", one line of JSON describing the contents, then three
+// arrays of GMCO_MLP_NPARAM little-endian FP32 values: the master parameters, Adam's first and
+// second moments.  The header carries the Adam step count, the format version and the layout.
+static const char kMlpMagic[] = "GMCO-MLP\n";
+
+gmco_status gmco_mlp_save(gmco_mlp *q, const char *path)
+{
+    if (!q || !path) {
+        g_mlp_err = "gmco_mlp_save: bad arguments";
+        return GMCO_EINVAL;
+    }
+    std::vector<float> buf((size_t)3 * NPARAM);
+    MCK(cudaSetDevice(q->device));
+    MCK(cudaStreamSynchronize(q->stream));
+    MCK(cudaMemcpy(buf.data(), q->p, NPARAM * sizeof(float), cudaMemcpyDeviceToHost));
+    MCK(cudaMemcpy(buf.data() + NPARAM, q->m, NPARAM * sizeof(float), cudaMemcpyDeviceToHost));
+    MCK(cudaMemcpy(buf.data() + 2 * (size_t)NPARAM, q->v, NPARAM * sizeof(float), cudaMemcpyDeviceToHost));
+    FILE *f = fopen(path, "wb");
+    if (!f) {
+        g_mlp_err = std::string("gmco_mlp_save: cannot open ") + path;
+        return GMCO_EINVAL;
+    }
+    char hdr[512];
+    snprintf(hdr, sizeof hdr,
+             "{\"format\": \"gmco-mlp\", \"version\": 1, \"nparam\": %d, \"step\": %lld, "
+             "\"arrays\": [\"params\", \"adam_m\", \"adam_v\"], \"dtype\": \"float32-le\", "
+             "\"adam\": {\"beta1\": 0.9, \"beta2\": 0.999, \"eps\": 1e-08}, "
+             "\"layout\": [[\"W1\", 14, 128], [\"b1\", 128], [\"W2\", 128, 128], [\"b2\", 128], "
+             "[\"W3\", 128, 128], [\"b3\", 128], [\"w4\", 128], [\"b4\", 1]]}\n",
+             (int)NPARAM, (long long)q->step);
+    const bool ok = fputs(kMlpMagic, f) >= 0 && fputs(hdr, f) >= 0 &&
+                    fwrite(buf.data(), sizeof(float), buf.size(), f) == buf.size();
+    if (fclose(f) != 0 || !ok) {
+        g_mlp_err = std::string("gmco_mlp_save: write failed for ") + path;
+        return GMCO_EINVAL;
+    }
+    return GMCO_OK;
+}
+
+gmco_status gmco_mlp_load(const char *path, gmco_mlp **out)
+{
+    if (!out) return GMCO_EINVAL;
+    *out = nullptr;
+    if (!path) {
+        g_mlp_err = "gmco_mlp_load: bad arguments";
+        return GMCO_EINVAL;
+    }
+    FILE *f = fopen(path, "rb");
+    if (!f) {
+        g_mlp_err = std::string("gmco_mlp_load: cannot open ") + path;
+        return GMCO_EINVAL;
+    }
+    char magic[16] = {0}, hdr[1024] = {0};
+    std::vector<float> buf((size_t)3 * NPARAM);
+    bool ok = fgets(magic, sizeof magic, f) && strcmp(magic, kMlpMagic) == 0 && fgets(hdr, sizeof hdr, f);
+    long long step = -1, nparam = -1, version = -1;
+    if (ok) {
+        const char *a = strstr(hdr, "\"nparam\":"), *b = strstr(hdr, "\"step\":"),
+                   *c = strstr(hdr, "\"version\":");
+        ok = a && b && c && strstr(hdr, "\"float32-le\"");
+        if (ok) {
+            nparam = strtoll(a + 9, nullptr, 10);
+            step = strtoll(b + 7, nullptr, 10);
+            version = strtoll(c + 10, nullptr, 10);
+        }
+        ok = ok && version == 1 && nparam == NPARAM && step >= 0;
+    }
+    ok = ok && fread(buf.data(), sizeof(float), buf.size(), f) == buf.size() && fgetc(f) == EOF;
+    fclose(f);
+    if (!ok) {
+        g_mlp_err = std::string("gmco_mlp_load: not a version-1 checkpoint of this network: ") + path;
+        return GMCO_EINVAL;
+    }
+    for (size_t i = 0; i < buf.size(); ++i)
+        if (!std::isfinite(buf[i]) || (i >= 2 * (size_t)NPARAM && buf[i] < 0.0f)) {
+            g_mlp_err = "gmco_mlp_load: non-finite value or negative second moment";
+            return GMCO_EINVAL;
+        }
+    gmco_mlp *q = nullptr;
+    gmco_status r = gmco_mlp_create(buf.data(), &q);
+    if (r != GMCO_OK) return r;
+    if (cudaMemcpy(q->m, buf.data() + NPARAM, NPARAM * sizeof(float), cudaMemcpyHostToDevice) != cudaSuccess ||
+        cudaMemcpy(q->v, buf.data() + 2 * (size_t)NPARAM, NPARAM * sizeof(float), cudaMemcpyHostToDevice) !=
+            cudaSuccess) {
+        g_mlp_err = "gmco_mlp_load: cannot copy the optimiser state";
+        gmco_mlp_destroy(q);
+        return GMCO_ECUDA;
+    }
+    q->step = step;
+    *out = q;
     return GMCO_OK;
 }
 

@@ -39,6 +39,11 @@ class _Options(ctypes.Structure):
                 ("sparse_grad_permille", ctypes.c_int32), ("wait_limit_us", ctypes.c_int32)]
 
 
+class _Geometry(ctypes.Structure):
+    _fields_ = [(k, ctypes.c_double) for k in ("a", "b", "c", "urethra_r", "rectum_r", "rectum_y",
+                                             "rectum_half_len", "bladder_r", "bladder_z")]
+
+
 class _Source(ctypes.Structure):
     _fields_ = [("lambda_", ctypes.c_double), ("sk", ctypes.c_double), ("unit", ctypes.c_double),
                 ("r_min", ctypes.c_double), ("g0", ctypes.c_double), ("g1", ctypes.c_double),
@@ -96,6 +101,12 @@ def load():
         lib.gmco_solve_sa.restype = ctypes.c_int
         lib.gmco_evaluate.argtypes = [_vp, _vp, _i64, _vp, _vp, _vp, _vp, _vp, _vp]
         lib.gmco_evaluate.restype = ctypes.c_int
+        lib.gmco_sample_points.argtypes = [ctypes.POINTER(_Geometry), _vp, ctypes.c_uint64, _vp, _vp, _vp]
+        lib.gmco_sample_points.restype = ctypes.c_int
+        lib.gmco_fp32_peak.argtypes = [_i32, _i32, _vp]
+        lib.gmco_fp32_peak.restype = ctypes.c_int
+        lib.gmco_dvh_at.argtypes = [_vp, _vp, _i64, _vp, _vp]
+        lib.gmco_dvh_at.restype = ctypes.c_int
         lib.gmco_evaluate_noalloc.argtypes = [_vp, _vp, _i64, _vp, _vp, _vp, _vp]
         lib.gmco_evaluate_noalloc.restype = ctypes.c_int
         lib.gmco_dvh_from_dose.argtypes = [_vp, _vp, _i64, _vp, _vp]
@@ -140,6 +151,10 @@ def load():
         lib.gmco_mlp_destroy.restype = None
         lib.gmco_mlp_get_params.argtypes = [_vp, _vp]
         lib.gmco_mlp_get_params.restype = ctypes.c_int
+        lib.gmco_mlp_save.argtypes = [_vp, ctypes.c_char_p]
+        lib.gmco_mlp_save.restype = ctypes.c_int
+        lib.gmco_mlp_load.argtypes = [ctypes.c_char_p, ctypes.POINTER(_vp)]
+        lib.gmco_mlp_load.restype = ctypes.c_int
         lib.gmco_mlp_predict.argtypes = [_vp, _vp, _i64, _vp, _i64, ctypes.c_float, _vp, _vp]
         lib.gmco_mlp_predict.restype = ctypes.c_int
         lib.gmco_mlp_gradient.argtypes = [_vp, _vp, _i64, _vp, _i64, _vp, _vp, _i64, _vp, _vp, _vp]
@@ -330,29 +345,39 @@ def solve_batch(h, penalty_weights, t0=None, max_iters=500, tol=1e-6, stream=Non
     return out
 
 
-def dvh_at(h, T, penalty_weights=None, stream=None):
-    """DVH indices (P x DVH_K) of dwell times T (P x n_dwell, s) on this problem's points, by
-    gmco_evaluate's DVH output at x = sqrt(T).  A problem built on a separate, denser point set
-    of the same structures and dwell positions gives the DVH of plans optimised on a coarser
-    one; build it with precision="fp32" for FP32 doses.  The weights only feed the objective
-    part of the evaluation and default to ones."""
-    info = problem_info(h)
-    try:
-        import torch
-        is_t = isinstance(T, torch.Tensor)
-    except ImportError:
-        is_t = False
-    if is_t:
-        X = torch.sqrt(T.to(torch.float32)).contiguous()
-        if penalty_weights is None:
-            penalty_weights = torch.ones((X.shape[0], info["n_struct"]), dtype=torch.float32,
-                                         device=X.device)
-    else:
-        X = np.sqrt(np.asarray(T, np.float32))
-        if penalty_weights is None:
-            penalty_weights = np.ones((X.shape[0], info["n_struct"]), np.float32)
-    return evaluate(h, penalty_weights, X, objectives=False, grad=False, dvh=True,
-                    stream=stream)["dvh"]
+def sample_points(geometry, counts, seed, device=False, stream=None):
+    """gmco_sample_points: (points (N x 3), sid (N,)) of the analytic structures.  `geometry`
+    has the attributes (or keys) a, b, c, urethra_r, rectum_r, rectum_y, rectum_half_len,
+    bladder_r, bladder_z (cm); counts: 4 point counts.  device=True returns torch CUDA tensors."""
+    get = (lambda k: geometry[k]) if isinstance(geometry, dict) else (lambda k: getattr(geometry, k))
+    geo = _Geometry(*[float(get(k)) for k, _ in _Geometry._fields_])
+    cnt = np.ascontiguousarray(counts, dtype=np.int64)
+    assert cnt.shape == (4,)
+    n = int(cnt.sum())
+    pts, pptr = _alloc((n, 3), np.float32, "float32", device)
+    sid, sptr = _alloc((n,), np.int32, "int32", device)
+    _check(load().gmco_sample_points(ctypes.byref(geo), cnt.ctypes.data, ctypes.c_uint64(int(seed) & (2**64 - 1)),
+                                     pptr, sptr, _stream_ptr(stream, device)), "gmco_sample_points")
+    return pts, sid
+
+
+def fp32_peak(iters=4096, reps=5):
+    """gmco_fp32_peak: (scalar FFMA, paired FP32 FMA) throughput of the current device, TFLOP/s."""
+    out = np.zeros(2)
+    _check(load().gmco_fp32_peak(int(iters), int(reps), out.ctypes.data), "gmco_fp32_peak")
+    return dict(ffma=float(out[0]), ffma2=float(out[1]))
+
+
+def dvh_at(h, T, stream=None):
+    """gmco_dvh_at: DVH indices (P x DVH_K) of dwell times T (P x n_dwell, s) on this problem's
+    points, from FP32 doses.  A problem built on a separate, denser point set of the same
+    structures and dwell positions gives the DVH of plans optimised on a coarser one."""
+    t_keep, t_ptr, cuda = _prep(T, np.float32, "float32")
+    P = int(t_keep.shape[0])
+    out, optr = _alloc((P, DVH_K), np.float32, "float32", cuda)
+    _check(load().gmco_dvh_at(h, t_ptr, P, optr, _stream_ptr(stream, cuda)), "gmco_dvh_at")
+    del t_keep
+    return out
 
 
 def default_sa_options(**overrides) -> _SaOptions:
@@ -487,8 +512,8 @@ class Problem:
     def solve_batch(self, penalty_weights, t0=None, max_iters=500, tol=1e-6, **kw):
         return solve_batch(self.handle, penalty_weights, t0, max_iters, tol, **kw)
 
-    def dvh_at(self, T, penalty_weights=None, **kw):
-        return dvh_at(self.handle, T, penalty_weights, **kw)
+    def dvh_at(self, T, **kw):
+        return dvh_at(self.handle, T, **kw)
 
     def solve_sa(self, penalty_weights, t0=None, **kw):
         return solve_sa(self.handle, penalty_weights, t0, **kw)
@@ -693,12 +718,26 @@ class Mlp:
     """Owning wrapper of gmco_mlp (per-dwell warm-start network).  `params`: the
     GMCO_MLP_NPARAM initial parameters (see include/gmco.h for the layout)."""
 
-    def __init__(self, params):
+    def __init__(self, params=None, handle=None):
+        if handle is not None:
+            self.handle = handle
+            return
         keep, ptr, _ = _prep(params, np.float32, "float32")
         assert int(np.prod(keep.shape)) == MLP_NPARAM
         h = _vp()
         _check_mlp(load().gmco_mlp_create(ptr, ctypes.byref(h)), "gmco_mlp_create")
         self.handle = h.value
+
+    def save(self, path):
+        """gmco_mlp_save: parameters, Adam moments and step count to `path`."""
+        _check_mlp(load().gmco_mlp_save(self.handle, os.fsencode(path)), "gmco_mlp_save")
+
+    @classmethod
+    def load(cls, path):
+        """gmco_mlp_load: a network restored from a checkpoint written by save()."""
+        h = _vp()
+        _check_mlp(load().gmco_mlp_load(os.fsencode(path), ctypes.byref(h)), "gmco_mlp_load")
+        return cls(handle=h.value)
 
     def params(self):
         out = np.empty(MLP_NPARAM, np.float32)

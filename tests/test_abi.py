@@ -116,3 +116,30 @@ def test_annealing_options_and_host_validation(gmco_mod):
     w = (ctypes.c_float * 4)(1, 1, 1, 1)
     assert lib.gmco_solve_sa(None, w, 1, None, ctypes.byref(o), None, None, None, None) == gmco_mod.EINVAL
     assert lib.gmco_solve_sa(None, w, 1, None, None, None, None, None, None) == gmco_mod.EINVAL
+
+
+def test_mlp_checkpoint_refused_before_device_use(gmco_mod, tmp_path):
+    """gmco_mlp_load checks the file (magic line, format version, parameter count, size, finite
+    values) before any device use: malformed checkpoints give GMCO_EINVAL with or without a GPU."""
+    import ctypes
+    lib = gmco_mod.load()
+    h = ctypes.c_void_p()
+    assert lib.gmco_mlp_load(str(tmp_path / "missing.bin").encode(), ctypes.byref(h)) == gmco_mod.EINVAL
+    n = gmco_mod.MLP_NPARAM
+    good_hdr = ('{"format": "gmco-mlp", "version": 1, "nparam": %d, "step": 3, "dtype": "float32-le"}\n' % n)
+    body = np.zeros(3 * n, np.float32)
+    cases = {
+        "magic": b"NOT-MLP\n" + good_hdr.encode() + body.tobytes(),
+        "version": b"GMCO-MLP\n" + good_hdr.replace('"version": 1', '"version": 2').encode() + body.tobytes(),
+        "nparam": b"GMCO-MLP\n" + good_hdr.replace(str(n), str(n - 1)).encode() + body.tobytes(),
+        "short": b"GMCO-MLP\n" + good_hdr.encode() + body[:-1].tobytes(),
+        "long": b"GMCO-MLP\n" + good_hdr.encode() + body.tobytes() + b"\0",
+        "nan": b"GMCO-MLP\n" + good_hdr.encode() + np.where(np.arange(3 * n) == 7, np.nan, 0).astype(np.float32).tobytes(),
+        "neg_v": b"GMCO-MLP\n" + good_hdr.encode() + np.where(np.arange(3 * n) == 2 * n + 1, -1.0, 0).astype(np.float32).tobytes(),
+    }
+    for name, data in cases.items():
+        path = tmp_path / f"{name}.bin"
+        path.write_bytes(data)
+        assert lib.gmco_mlp_load(str(path).encode(), ctypes.byref(h)) == gmco_mod.EINVAL, name
+        assert h.value is None
+    assert lib.gmco_mlp_save(None, str(tmp_path / "x.bin").encode()) == gmco_mod.EINVAL

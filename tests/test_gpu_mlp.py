@@ -125,3 +125,24 @@ def test_training_reduces_loss(gmco_mod):
     print("loss %.4f -> %.4f" % (first, last))
     assert last < 0.1 * first
     assert launches > 0
+
+
+def test_checkpoint_resumes_training_bit_for_bit(gmco_mod, tmp_path):
+    """save -> load -> train_step gives the parameters of the uninterrupted run, bit for bit
+    (the checkpoint holds the FP32 master parameters, both Adam moments and the step count)."""
+    F, W, pairs, target = _batch(14, 4096)
+    with gmco_mod.Mlp(_params(9)) as net:
+        for _ in range(3):
+            net.train_step(F, W, pairs, target, lr=1e-3)
+        path = tmp_path / "net.gmco"
+        net.save(path)
+        saved = net.params()
+        with gmco_mod.Mlp.load(path) as back:
+            assert np.array_equal(back.params(), saved)
+            for k in range(4):
+                la = net.train_step(F, W, pairs, target, lr=1e-3)
+                lb = back.train_step(F, W, pairs, target, lr=1e-3)
+                assert la == lb, k
+            assert np.array_equal(back.params(), net.params())
+    hdr = path.read_bytes().split(b"\n", 2)
+    assert hdr[0] == b"GMCO-MLP" and b'"step": 3' in hdr[1]
