@@ -503,8 +503,12 @@ class Problem:
         """Step (i) on the device: the dose rate matrix of the points and dwell positions
         (n x 3, cm; gmco_dose_rate_matrix), then the problem created from that device matrix."""
         import torch
-        pts = torch.as_tensor(np.asarray(points, np.float32)).cuda()
-        dws = torch.as_tensor(np.asarray(dwells, np.float32)).cuda()
+
+        def dev(a):
+            if isinstance(a, torch.Tensor):
+                return a.detach().to(device="cuda", dtype=torch.float32).contiguous()
+            return torch.as_tensor(np.asarray(a, np.float32)).cuda()
+        pts, dws = dev(points), dev(dwells)
         A = dose_rate_matrix(pts, dws, source=source)
         torch.cuda.synchronize()
         return cls(A, structure_ids, penalty_params, **options)

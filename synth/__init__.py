@@ -11,6 +11,7 @@ from .patient import (  # noqa: F401
     WORKLOADS,
     Patient,
     make_patient,
+    dwell_positions,
     dose_rate_matrix,
     class_penalty_params,
     TABLE1,

@@ -248,6 +248,18 @@ def _catheter_xy(g: Geometry, n: int, margin: float = 0.3, urethra_clear: float 
     return cand[chosen]
 
 
+def dwell_positions(g: Geometry, n_catheters: int, dwell_step: float):
+    """(dwells (N_d, 3) cm, catheter index of each, catheter xy): n catheters parallel to z
+    (template grid, farthest-point selection), dwell positions every `dwell_step` cm over the
+    prostate's cranio-caudal extent |z| <= c."""
+    cxy = _catheter_xy(g, n_catheters)
+    n_z = int(np.floor(2.0 * g.c / dwell_step + 1e-9)) + 1
+    zs = (np.arange(n_z) - 0.5 * (n_z - 1)) * dwell_step
+    dwells = np.array([[x, y, z] for (x, y) in cxy for z in zs])
+    catheter = np.repeat(np.arange(len(cxy), dtype=np.int32), n_z)
+    return dwells, catheter, cxy
+
+
 def make_patient(seed: int, n_catheters: int = 12, dwell_step: float = 0.5,
                  n_points=(1200, 200, 300, 300), scale: float = 1.0) -> Patient:
     geom = Geometry().scaled(scale)
@@ -270,11 +282,7 @@ def make_patient(seed: int, n_catheters: int = 12, dwell_step: float = 0.5,
     sid = np.concatenate([np.full(len(x), s, dtype=np.int32)
                           for s, x in enumerate((pro, ure, rec, bla))])
 
-    cxy = _catheter_xy(g, n_catheters)
-    n_z = int(np.floor(2.0 * g.c / dwell_step + 1e-9)) + 1
-    zs = (np.arange(n_z) - 0.5 * (n_z - 1)) * dwell_step
-    dwells = np.array([[x, y, z] for (x, y) in cxy for z in zs])
-    catheter = np.repeat(np.arange(len(cxy), dtype=np.int32), n_z)
+    dwells, catheter, cxy = dwell_positions(g, n_catheters, dwell_step)
 
     A64 = dose_rate_matrix(points, dwells)
     return Patient(geometry=geom, points=points, sid=sid, dwells=dwells, catheter=catheter,
