@@ -7,16 +7,21 @@
 // activations in the products, FP32 accumulation, FP32 master weights.  The paper has no
 // learned component: this is the warm-start extension of its batched solve.
 //
-// Kernels (warp-level BF16 tensor-core MMA, m16n8k16, FP32 accumulators in registers):
-//   k_mlp_fwd<TRAIN=false>  fused 4-layer forward of 16-row tiles per warp, activations
-//                           carried from one layer's accumulators to the next layer's
-//                           operand fragments in registers, weights in shared memory;
-//                           persistent grid (each CTA loads the weights once)
-//   k_mlp_fwd<TRAIN=true>   the same forward, then the loss and the backward pass of each
-//                           tile in registers (dz_3 -> dh_2 -> dz_2 -> dh_1 -> dz_1 with the
-//                           transposed products h W^T); writes the layer inputs H_{l-1} and
-//                           the pre-activation gradients dZ_l feature-major for the weight
-//                           gradients, and per-CTA partial sums of the bias gradients
+// Kernels:
+//   k_mlp_infer_tc          inference on the fifth-generation tensor cores: tcgen05.mma with
+//                           the weights copied into shared memory by the TMA unit, FP32
+//                           accumulators in TMEM, bias + GELU epilogues that write the next
+//                           layer's BF16 operand; persistent grid, two 128-row tiles in
+//                           flight per CTA
+//   k_mlp_train             training forward and backward of 16-row tiles per warp on
+//                           warp-level BF16 MMA (m16n8k16, FP32 accumulators in registers):
+//                           activations carried from one layer's accumulators to the next
+//                           layer's operand fragments in registers, weights in shared memory;
+//                           the loss and the backward pass of each tile in registers
+//                           (dz_3 -> dh_2 -> dz_2 -> dh_1 -> dz_1 with the transposed products
+//                           h W^T); writes the layer inputs H_{l-1} and the pre-activation
+//                           gradients dZ_l feature-major for the weight gradients, and per-CTA
+//                           partial sums of the bias gradients
 //   k_mlp_dw                dW_l = H_{l-1}^T dZ_l, split over row ranges, per-CTA partials
 //   k_mlp_reduce            fixed-order sums of the per-CTA partials into the gradient
 //   k_mlp_adam              Adam on the FP32 master weights, then the BF16 copies
@@ -35,6 +40,7 @@
 #include <vector>
 
 #include "gmco.h"
+#include "tcgen05.cuh"
 
 namespace {
 
@@ -56,6 +62,7 @@ struct DevWeights {
     __nv_bfloat16 *Wt2, *Wt3;  // [128][128] W^T (n, k): forward operand
     __nv_bfloat16 *W2, *W3;    // [128][128] W (k, n): backward operand
     float *bias;               // b1, b2, b3, w4 (4 x 128) and b4
+    uint8_t *img;              // shared-memory image of W1^T, W2^T, W3^T for k_mlp_infer_tc
 };
 
 // Rows of one call: dense (row = plan * n_dwell + dwell) or listed (pairs[row] = (feature
@@ -187,19 +194,17 @@ __device__ __forceinline__ void col_sums(const float (&v)[16][4], float *sum, in
     }
 }
 
-template <bool TRAIN>
-__global__ void __launch_bounds__(WARPS * 32, 1)
-    k_mlp_fwd(DevWeights wt, RowSrc src, float t_floor, float *__restrict__ t_out, TrainOut tr)
+__global__ void __launch_bounds__(WARPS * 32, 1) k_mlp_train(DevWeights wt, RowSrc src, TrainOut tr)
 {
     extern __shared__ __align__(16) uint8_t sm[];
     __nv_bfloat16 *sWt1 = reinterpret_cast<__nv_bfloat16 *>(sm);       // [128][LD1]
     __nv_bfloat16 *sWt2 = sWt1 + HID * LD1;                              // [128][LDH]
     __nv_bfloat16 *sWt3 = sWt2 + HID * LDH;
-    __nv_bfloat16 *sW2 = sWt3 + HID * LDH;                               // TRAIN only
+    __nv_bfloat16 *sW2 = sWt3 + HID * LDH;                               // backward operands
     __nv_bfloat16 *sW3 = sW2 + HID * LDH;
-    __nv_bfloat16 *sZ = sW3 + HID * LDH;                                 // TRAIN: [2][8][16][128]
+    __nv_bfloat16 *sZ = sW3 + HID * LDH;                                 // [2][8][16][128]
     __shared__ float sb[4 * HID + 1];
-    __shared__ float sacc[WARPS][4 * HID + 2];   // TRAIN: per warp db1, db2, db3, dw4, db4, loss
+    __shared__ float sacc[WARPS][4 * HID + 2];   // per warp db1, db2, db3, dw4, db4, loss
 
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31, g = lane >> 2, t = lane & 3;
     for (int i = tid; i < HID * KIN; i += blockDim.x) sWt1[(i / KIN) * LD1 + i % KIN] = wt.Wt1[i];
@@ -207,14 +212,11 @@ __global__ void __launch_bounds__(WARPS * 32, 1)
         const int r = i / HID, c = i % HID;
         sWt2[r * LDH + c] = wt.Wt2[i];
         sWt3[r * LDH + c] = wt.Wt3[i];
-        if (TRAIN) {
-            sW2[r * LDH + c] = wt.W2[i];
-            sW3[r * LDH + c] = wt.W3[i];
-        }
+        sW2[r * LDH + c] = wt.W2[i];
+        sW3[r * LDH + c] = wt.W3[i];
     }
     for (int i = tid; i < 4 * HID + 1; i += blockDim.x) sb[i] = wt.bias[i];
-    if (TRAIN)
-        for (int i = lane; i < 4 * HID + 2; i += 32) sacc[warp][i] = 0.0f;
+    for (int i = lane; i < 4 * HID + 2; i += 32) sacc[warp][i] = 0.0f;
     __syncthreads();
     const float *b1 = sb, *b2 = sb + HID, *b3 = sb + 2 * HID, *w4 = sb + 3 * HID;
     const float b4 = sb[4 * HID];
@@ -237,7 +239,7 @@ __global__ void __launch_bounds__(WARPS * 32, 1)
             uint32_t a0[4];
 #pragma unroll
             for (int q = 0; q < 4; ++q) a0[q] = pack_bf16(x[q][0], x[q][1]);
-            if (TRAIN) {
+            {
                 const int64_t ld = tr.Rp;
                 tr.H0[(size_t)(2 * t) * ld + rA] = __float2bfloat16_rn(x[0][0]);
                 tr.H0[(size_t)(2 * t + 1) * ld + rA] = __float2bfloat16_rn(x[0][1]);
@@ -260,7 +262,7 @@ __global__ void __launch_bounds__(WARPS * 32, 1)
         // ---- layers 2 and 3; z_1, z_2 kept (BF16) for the backward pass
 #pragma unroll 1
         for (int l = 1; l <= 2; ++l) {
-            if (TRAIN) {
+            {
                 __nv_bfloat16 *z = l == 1 ? sZ1 : sZ2;
 #pragma unroll
                 for (int j = 0; j < 16; ++j) {
@@ -272,7 +274,7 @@ __global__ void __launch_bounds__(WARPS * 32, 1)
             for (int j = 0; j < 16; ++j)
 #pragma unroll
                 for (int q = 0; q < 4; ++q) acc[j][q] = gelu(acc[j][q]);
-            if (TRAIN) store_t(l == 1 ? tr.H1 : tr.H2, tr.Rp, r0, acc, g, t);
+            store_t(l == 1 ? tr.H1 : tr.H2, tr.Rp, r0, acc, g, t);
             to_frag(acc, a);
             const float *bb = l == 1 ? b2 : b3;
 #pragma unroll
@@ -296,13 +298,6 @@ __global__ void __launch_bounds__(WARPS * 32, 1)
         pB += __shfl_xor_sync(0xffffffffu, pB, 2);
         const float oA = pA + b4, oB = pB + b4;
         const float yA = softplus(oA), yB = softplus(oB);
-        if (!TRAIN) {
-            if (t == 0) {
-                if (rA < src.R) t_out[rA] = fmaxf(yA, t_floor);
-                if (rB < src.R) t_out[rB] = fmaxf(yB, t_floor);
-            }
-            continue;
-        }
         // ---- loss and backward
         const bool vA = rA < src.R, vB = rB < src.R;
         const float eA = vA ? yA - src.target[rA] : 0.0f, eB = vB ? yB - src.target[rB] : 0.0f;
@@ -361,7 +356,7 @@ __global__ void __launch_bounds__(WARPS * 32, 1)
         col_sums(acc, &sacc[warp][0], g, t);   // db1
         store_t(tr.dZ1, tr.Rp, r0, acc, g, t);
     }
-    if (TRAIN) {
+    {
         __syncthreads();
         for (int i = tid; i < NPART; i += blockDim.x) {
             // partial layout: loss, db1, db2, db3, dw4, db4
@@ -447,6 +442,231 @@ __global__ void k_mlp_adam(float *__restrict__ p, float *__restrict__ m, float *
     p[i] -= lr * (mi / c1) / (sqrtf(vi / c2) + eps);
 }
 
+// ------------------------------------------------------------------ tcgen05 inference
+// Operand images in shared memory, K-major with the 128-byte swizzle that the MMA descriptors
+// name: a block holds 128 rows x 64 BF16 columns, row n at n * 128 bytes, its 16-byte chunk j
+// (columns 8j .. 8j + 7) at (j xor (n mod 8)) * 16.  The weights' image is W1^T (one block,
+// columns 14.. zero), W2^T and W3^T (two blocks each), built by k_mlp_pack in global memory and
+// copied whole by the TMA unit; a tile's activations H (128 rows x 128 columns) are two blocks.
+constexpr uint32_t BLK = HID * 128;                           // bytes of one block: 16 KB
+constexpr uint32_t IMG_W1 = 0, IMG_W2 = BLK, IMG_W3 = 3 * BLK, IMG_BYTES = 5 * BLK;
+constexpr int TC_GROUPS = 2;                                  // 128-row tiles in flight per CTA
+constexpr int TC_THREADS = TC_GROUPS * 128;                   // one thread per row of a tile
+constexpr size_t TC_SMEM = IMG_BYTES + (size_t)TC_GROUPS * 2 * BLK + 1024;   // + alignment
+constexpr uint32_t TC_TMEM_COLS = TC_GROUPS * HID;            // one FP32 accumulator per group
+constexpr long long kMlpWaitNs = 1000000000LL;                // 1 s per wait, then an error
+
+// Byte offset of element (row, col) in a stack of blocks (col / 64 selects the block).
+__host__ __device__ __forceinline__ uint32_t swz(uint32_t row, uint32_t col)
+{
+    return (col >> 6) * BLK + row * 128 + ((((col & 63) >> 3) ^ (row & 7)) << 4) + (col & 7) * 2;
+}
+
+__device__ __forceinline__ void img_put(uint8_t *img, uint32_t base, int n, int k, float v)
+{
+    *reinterpret_cast<__nv_bfloat16 *>(img + base + swz((uint32_t)n, (uint32_t)k)) = __float2bfloat16_rn(v);
+}
+
+__device__ __forceinline__ void tmem_ld_wait16(uint32_t (&a)[16])
+{
+    asm volatile("tcgen05.wait::ld.sync.aligned;"
+                 : "+r"(a[0]), "+r"(a[1]), "+r"(a[2]), "+r"(a[3]), "+r"(a[4]), "+r"(a[5]),
+                   "+r"(a[6]), "+r"(a[7]), "+r"(a[8]), "+r"(a[9]), "+r"(a[10]), "+r"(a[11]),
+                   "+r"(a[12]), "+r"(a[13]), "+r"(a[14]), "+r"(a[15])
+                 :
+                 : "memory");
+}
+
+// The 14 inputs of row r (two zero columns after them; zeros past the row count) into the
+// tile's first block, BF16.
+__device__ __forceinline__ void put_inputs(const RowSrc &s, int64_t r, uint8_t *sH, uint32_t row)
+{
+    float x[16];
+#pragma unroll
+    for (int c = 0; c < 16; ++c) x[c] = 0.0f;
+    if (r < s.R) {
+        int64_t fr, wr;
+        if (s.pairs) {
+            fr = s.pairs[2 * r];
+            wr = s.pairs[2 * r + 1];
+        } else {
+            fr = r % s.n_dwell;
+            wr = r / s.n_dwell;
+        }
+#pragma unroll
+        for (int c = 0; c < NFEAT; ++c) x[c] = s.feat[fr * NFEAT + c];
+#pragma unroll
+        for (int c = 0; c < NW; ++c) x[NFEAT + c] = log10f(fmaxf(s.w[wr * NW + c], 1e-3f));
+    }
+    uint4 lo, hi;
+    lo.x = pack_bf16(x[0], x[1]);   lo.y = pack_bf16(x[2], x[3]);
+    lo.z = pack_bf16(x[4], x[5]);   lo.w = pack_bf16(x[6], x[7]);
+    hi.x = pack_bf16(x[8], x[9]);   hi.y = pack_bf16(x[10], x[11]);
+    hi.z = pack_bf16(x[12], x[13]); hi.w = pack_bf16(x[14], x[15]);
+    *reinterpret_cast<uint4 *>(sH + swz(row, 0)) = lo;
+    *reinterpret_cast<uint4 *>(sH + swz(row, 8)) = hi;
+}
+
+// Hidden-layer epilogue of one row: h = GELU(z + b) from the accumulator's 128 columns
+// (TMEM lane = row), BF16 into the tile's blocks as the next layer's A operand.
+__device__ __forceinline__ void epi_hidden(uint32_t taddr, const float *b, uint8_t *sH, uint32_t row)
+{
+#pragma unroll
+    for (int half = 0; half < 2; ++half) {
+        uint32_t v[4][16];
+#pragma unroll
+        for (int c4 = 0; c4 < 4; ++c4) gmco::tmem_ld16(taddr + (uint32_t)(64 * half + 16 * c4), v[c4]);
+#pragma unroll
+        for (int c4 = 0; c4 < 4; ++c4) tmem_ld_wait16(v[c4]);
+#pragma unroll
+        for (int c4 = 0; c4 < 4; ++c4) {
+            const int c0 = 64 * half + 16 * c4;
+            uint32_t h[8];
+#pragma unroll
+            for (int e = 0; e < 8; ++e)
+                h[e] = pack_bf16(gelu(__uint_as_float(v[c4][2 * e]) + b[c0 + 2 * e]),
+                                 gelu(__uint_as_float(v[c4][2 * e + 1]) + b[c0 + 2 * e + 1]));
+            *reinterpret_cast<uint4 *>(sH + swz(row, (uint32_t)c0)) = make_uint4(h[0], h[1], h[2], h[3]);
+            *reinterpret_cast<uint4 *>(sH + swz(row, (uint32_t)c0 + 8)) = make_uint4(h[4], h[5], h[6], h[7]);
+        }
+    }
+}
+
+// Output unit of one row: o = sum_c GELU(z_3c + b_3c) w_4c (FP32, in column order) + b_4.
+__device__ __forceinline__ float epi_out(uint32_t taddr, const float *b3, const float *w4, float b4)
+{
+    float o = 0.0f;
+#pragma unroll
+    for (int half = 0; half < 2; ++half) {
+        uint32_t v[4][16];
+#pragma unroll
+        for (int c4 = 0; c4 < 4; ++c4) gmco::tmem_ld16(taddr + (uint32_t)(64 * half + 16 * c4), v[c4]);
+#pragma unroll
+        for (int c4 = 0; c4 < 4; ++c4) tmem_ld_wait16(v[c4]);
+#pragma unroll
+        for (int c4 = 0; c4 < 4; ++c4)
+#pragma unroll
+            for (int e = 0; e < 16; ++e) {
+                const int c = 64 * half + 16 * c4 + e;
+                o = fmaf(gelu(__uint_as_float(v[c4][e]) + b3[c]), w4[c], o);
+            }
+    }
+    return o + b4;
+}
+
+// Forward pass of the network for inference on the fifth-generation tensor cores.  Persistent
+// CTAs of TC_GROUPS groups of four warps; a group owns one 128-row tile at a time (thread =
+// row = TMEM lane), 128 accumulator columns of TMEM and two activation blocks.  Per tile: the
+// threads write the inputs, one elected thread issues the layer's tcgen05.mma (M = N = 128,
+// K = 16 for layer 1, 128 for layers 2 and 3) and commits it to the group's mbarrier, the
+// threads read the accumulator with tcgen05.ld, add the bias, apply GELU and write BF16
+// activations for the next layer; the output unit and softplus finish in registers.  The two
+// groups interleave, so one group's MMAs run under the other's epilogue.  Every wait is
+// bounded: a wait that runs out sets *err, the group stops at its next barrier, and the CTA
+// waits (bounded) for its MMAs and copies in flight before freeing TMEM.
+__global__ void __launch_bounds__(TC_THREADS, 1)
+    k_mlp_infer_tc(const uint8_t *__restrict__ img, const float *__restrict__ bias, RowSrc src,
+                   float t_floor, float *__restrict__ t_out, int32_t *__restrict__ err)
+{
+    using namespace gmco;
+    extern __shared__ uint8_t dyn[];
+    __shared__ float sb[4 * HID + 1];
+    __shared__ __align__(8) uint64_t w_bar, mma_bar[TC_GROUPS], drain_bar[TC_GROUPS];
+    __shared__ uint32_t tmem_holder;
+    uint8_t *base = reinterpret_cast<uint8_t *>(((uintptr_t)dyn + 1023) & ~(uintptr_t)1023);
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int grp = warp >> 2;
+    const uint32_t row = (uint32_t)(32 * (warp & 3) + lane);
+    const bool issuer = (warp & 3) == 0;   // the group's first warp issues its MMAs
+    const uint32_t s_img = smem_u32(base);
+    uint8_t *sH = base + IMG_BYTES + (size_t)grp * 2 * BLK;
+    const uint32_t s_h = smem_u32(sH);
+
+    if (tid == 0) {
+        mbar_init(smem_u32(&w_bar), 1);
+        for (int g = 0; g < TC_GROUPS; ++g) {
+            mbar_init(smem_u32(&mma_bar[g]), 1);
+            mbar_init(smem_u32(&drain_bar[g]), 1);
+        }
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    if (warp == 0) tmem_alloc(smem_u32(&tmem_holder), TC_TMEM_COLS);
+    for (int i = tid; i < 4 * HID + 1; i += TC_THREADS) sb[i] = bias[i];
+    fence_before();
+    __syncthreads();
+    fence_after();
+    const uint32_t tmem = tmem_holder;
+    if (tid == 0) {
+        mbar_expect_tx(smem_u32(&w_bar), IMG_BYTES);
+        for (uint32_t c = 0; c < IMG_BYTES / BLK; ++c) bulk_load(s_img + c * BLK, img + c * BLK, BLK, smem_u32(&w_bar));
+    }
+    const bool w_ok = mbar_wait(smem_u32(&w_bar), 0u, err, 1, kMlpWaitNs);
+    const bool w_fail = __syncthreads_or(!w_ok);
+    if (w_fail && tid == 0) mbar_wait(smem_u32(&w_bar), 0u, nullptr, 0, kMlpWaitNs);   // copies in flight
+
+    const uint32_t d_col = tmem + (uint32_t)(grp * HID);           // accumulator (lane 0)
+    const uint32_t t_row = d_col + ((uint32_t)(32 * (warp & 3)) << 16);   // this warp's lanes
+    const uint32_t idesc = idesc_bf16(HID);
+    const uint32_t bar = smem_u32(&mma_bar[grp]);
+    const float *b1 = sb, *b2 = sb + HID, *b3 = sb + 2 * HID, *w4 = sb + 3 * HID;
+    const float b4 = sb[4 * HID];
+    const int64_t n_tiles = (src.R + 127) / 128;
+    uint32_t parity = 0;
+    bool pending = false;   // this thread's last MMA wait gave up
+    bool failed = w_fail;   // uniform over the group
+    for (int64_t tile = (int64_t)blockIdx.x * TC_GROUPS + grp; !failed && tile < n_tiles;
+         tile += (int64_t)gridDim.x * TC_GROUPS) {
+        const int64_t r = tile * 128 + row;
+        put_inputs(src, r, sH, row);
+        float o = 0.0f;
+#pragma unroll 1
+        for (int l = 0; l < 3; ++l) {
+            // the threads' operand writes and TMEM reads are done before the MMAs start
+            fence_proxy_async_smem();
+            fence_before();
+            if (bar_any(1 + grp, 128, pending)) {
+                failed = true;
+                break;
+            }
+            if (issuer) {
+                fence_after();
+                if (l == 0) {
+                    mma_bf16_elect(d_col, DESC_FIXED | desc_lo(s_h), DESC_FIXED | desc_lo(s_img + IMG_W1), idesc, 0u);
+                } else {
+                    const uint32_t wb = s_img + (l == 1 ? IMG_W2 : IMG_W3);
+#pragma unroll
+                    for (int k = 0; k < HID / 16; ++k) {
+                        const uint32_t off = (uint32_t)(k >> 2) * BLK + (uint32_t)(k & 3) * 32;
+                        mma_bf16_elect(d_col, DESC_FIXED | desc_lo(s_h + off), DESC_FIXED | desc_lo(wb + off),
+                                       idesc, k > 0 ? 1u : 0u);
+                    }
+                }
+                mma_commit_elect(bar);
+            }
+            pending = !mbar_wait(bar, parity, err, 2, kMlpWaitNs);
+            parity ^= 1u;
+            fence_after();
+            if (l < 2) epi_hidden(t_row, l == 0 ? b1 : b2, sH, row);
+            else o = epi_out(t_row, b3, w4, b4);
+        }
+        if (!failed && r < src.R) t_out[r] = fmaxf(softplus(o), t_floor);
+    }
+    fence_before();
+    if (!failed) failed = bar_any(1 + grp, 128, pending);
+    if (failed && !w_fail && issuer) {
+        // MMAs issued before a wait gave up may still be running: their commit completes once
+        // they have all finished
+        mma_commit_elect(smem_u32(&drain_bar[grp]));
+        mbar_wait(smem_u32(&drain_bar[grp]), 0u, nullptr, 0, kMlpWaitNs);
+    }
+    fence_before();
+    __syncthreads();
+    if (warp == 0) {
+        fence_after();
+        tmem_dealloc(tmem, TC_TMEM_COLS);
+    }
+}
+
 // BF16 copies of the FP32 master parameters in the kernels' layouts.
 __global__ void k_mlp_pack(const float *__restrict__ p, DevWeights w)
 {
@@ -462,6 +682,15 @@ __global__ void k_mlp_pack(const float *__restrict__ p, DevWeights w)
         const int n = i / KIN, k = i % KIN;   // Wt1[n][k]
         w.Wt1[i] = __float2bfloat16_rn(k < NIN ? p[OFF_W1 + k * HID + n] : 0.0f);
     }
+    if (i < HID * 64) {
+        const int n = i / 64, k = i % 64;     // one 64-column block of W1^T, columns 14.. zero
+        img_put(w.img, IMG_W1, n, k, k < NIN ? p[OFF_W1 + k * HID + n] : 0.0f);
+    }
+    if (i < HID * HID) {
+        const int k = i / HID, n = i % HID;
+        img_put(w.img, IMG_W2, n, k, p[OFF_W2 + i]);
+        img_put(w.img, IMG_W3, n, k, p[OFF_W3 + i]);
+    }
     if (i < 4 * HID + 1) {
         // bias[] = b1, b2, b3, w4 (128 each), then b4
         const int blk = i / HID, o = i % HID;
@@ -470,11 +699,9 @@ __global__ void k_mlp_pack(const float *__restrict__ p, DevWeights w)
     }
 }
 
-size_t fwd_smem(bool train)
+size_t train_smem()
 {
-    size_t b = (size_t)HID * LD1 * 2 + 2 * (size_t)HID * LDH * 2;
-    if (train) b += 2 * (size_t)HID * LDH * 2 + 2 * (size_t)WARPS * ROWS_W * HID * 2;
-    return b;
+    return (size_t)HID * LD1 * 2 + 4 * (size_t)HID * LDH * 2 + 2 * (size_t)WARPS * ROWS_W * HID * 2;
 }
 
 thread_local std::string g_mlp_err;
@@ -488,6 +715,7 @@ struct gmco_mlp {
     std::vector<void *> allocs;
     float *p = nullptr, *m = nullptr, *v = nullptr, *grad = nullptr;   // FP32, NPARAM each
     DevWeights w{};
+    int32_t *err = nullptr;   // wait status of the inference kernel (0 = none ran out)
     int64_t step = 0;
     // training workspace
     int64_t cap_rows = 0;
@@ -606,10 +834,10 @@ gmco_status gradient(gmco_mlp *q, const RowSrc &src, float *loss_out)
     tr.inv_R = 1.0f / (float)R;
     // rows R..Rp of the feature-major arrays are written by the kernel (tiles cover Rp)
     const int ctas = n_ctas(R);
-    const size_t smem = fwd_smem(true);
-    MCK(cudaFuncSetAttribute(k_mlp_fwd<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    const size_t smem = train_smem();
+    MCK(cudaFuncSetAttribute(k_mlp_train, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     RowSrc s2 = src;
-    k_mlp_fwd<true><<<ctas, WARPS * 32, smem, q->stream>>>(q->w, s2, 0.0f, nullptr, tr);
+    k_mlp_train<<<ctas, WARPS * 32, smem, q->stream>>>(q->w, s2, tr);
     MCK(cudaGetLastError());
     q->launches++;
     // bias and output-unit gradients, loss
@@ -733,12 +961,14 @@ gmco_status gmco_mlp_create(const float *params, gmco_mlp **out)
         dalloc(q, &q->v, NPARAM) != cudaSuccess || dalloc(q, &q->grad, NPARAM + 1) != cudaSuccess ||
         dalloc(q, &q->w.Wt1, HID * KIN) != cudaSuccess || dalloc(q, &q->w.Wt2, HID * HID) != cudaSuccess ||
         dalloc(q, &q->w.Wt3, HID * HID) != cudaSuccess || dalloc(q, &q->w.W2, HID * HID) != cudaSuccess ||
-        dalloc(q, &q->w.W3, HID * HID) != cudaSuccess || dalloc(q, &q->w.bias, 4 * HID + 1) != cudaSuccess)
+        dalloc(q, &q->w.W3, HID * HID) != cudaSuccess || dalloc(q, &q->w.bias, 4 * HID + 1) != cudaSuccess ||
+        dalloc(q, &q->w.img, IMG_BYTES) != cudaSuccess || dalloc(q, &q->err, 1) != cudaSuccess)
         return fail(GMCO_ENOMEM);
     if (cudaMemcpy(q->p, hp.data(), NPARAM * sizeof(float), cudaMemcpyHostToDevice) != cudaSuccess ||
         cudaMemset(q->m, 0, NPARAM * sizeof(float)) != cudaSuccess ||
         cudaMemset(q->v, 0, NPARAM * sizeof(float)) != cudaSuccess ||
-        cudaMemset(q->grad, 0, (NPARAM + 1) * sizeof(float)) != cudaSuccess)
+        cudaMemset(q->grad, 0, (NPARAM + 1) * sizeof(float)) != cudaSuccess ||
+        cudaMemset(q->err, 0, sizeof(int32_t)) != cudaSuccess)
         return fail(GMCO_ECUDA);
     if (pack(q) != GMCO_OK || cudaStreamSynchronize(q->stream) != cudaSuccess) return fail(GMCO_ECUDA);
     *out = q;
@@ -879,14 +1109,29 @@ gmco_status gmco_mlp_predict(gmco_mlp *q, const float *features, int64_t n_dwell
         st.ptrs.push_back(d);
         dst = static_cast<float *>(d);
     }
-    const size_t smem = fwd_smem(false);
-    MCK(cudaFuncSetAttribute(k_mlp_fwd<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-    k_mlp_fwd<false><<<n_ctas(s.R), WARPS * 32, smem, q->stream>>>(q->w, s, t_floor, dst, TrainOut{});
+    int n_sm = 0;
+    MCK(cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, q->device));
+    const int64_t n_tiles = (s.R + 127) / 128;
+    const int ctas = (int)std::min<int64_t>(n_sm, (n_tiles + TC_GROUPS - 1) / TC_GROUPS);
+    MCK(cudaFuncSetAttribute(k_mlp_infer_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)TC_SMEM));
+    k_mlp_infer_tc<<<ctas, TC_THREADS, TC_SMEM, q->stream>>>(q->w.img, q->w.bias, s, t_floor, dst, q->err);
     MCK(cudaGetLastError());
     q->launches++;
     if (!dev_out)
         MCK(cudaMemcpyAsync(t_out, dst, (size_t)s.R * sizeof(float), cudaMemcpyDeviceToHost, q->stream));
-    return finish(q, cuda_stream);
+    MCK(cudaMemcpyAsync(q->h_pinned + 1, q->err, sizeof(int32_t), cudaMemcpyDeviceToHost, q->stream));
+    if ((r = finish(q, cuda_stream)) != GMCO_OK) return r;
+    int32_t code = 0;
+    memcpy(&code, q->h_pinned + 1, sizeof code);
+    if (code != 0) {
+        // a bounded wait of the kernel ran out: the predictions are not valid
+        cudaMemsetAsync(q->err, 0, sizeof(int32_t), q->stream);
+        cudaStreamSynchronize(q->stream);
+        g_mlp_err = "gmco_mlp_predict: a tensor-core wait of the inference kernel ran out (code " +
+                    std::to_string(code) + ")";
+        return GMCO_ECUDA;
+    }
+    return GMCO_OK;
 }
 
 gmco_status gmco_mlp_gradient(gmco_mlp *q, const float *features, int64_t n_feat,

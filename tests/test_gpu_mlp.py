@@ -52,6 +52,38 @@ def test_predict_matches_oracle(gmco_mod):
     assert np.array_equal(tf, np.maximum(t, 0.5))
 
 
+def _check_predict(t, ref, label):
+    bound = 2e-2 * np.abs(ref) + 1e-2 * np.mean(np.abs(ref))
+    ratio = np.abs(t - ref) / bound
+    w = np.unravel_index(np.argmax(ratio), ratio.shape)
+    print("%s: worst element %s, |t - ref| = %.3e, bound %.3e" % (label, w, abs(t[w] - ref[w]), bound[w]))
+    assert np.all(np.isfinite(t)) and np.all(ratio <= 1.0)
+
+
+@pytest.mark.parametrize("n_cath,n_dwell,n_plans", [
+    (18, None, 250),   # 324 dwells x 250 plans = 81000 rows: every CTA loops, ragged last tile
+    (12, None, 1),     # fewer rows than one tile: the CTA's second tile group has no work
+    (12, 128, 4),      # whole tiles only
+    (12, 1, 1),        # a single row
+])
+def test_predict_tensor_core_sizes(gmco_mod, n_cath, n_dwell, n_plans):
+    """The tcgen05 inference kernel per element against the FP64 forward of the same BF16
+    weights, from one row to many persistent-loop rounds, host and device buffers."""
+    import torch
+    pat = make_patient(40 + n_cath, n_catheters=n_cath)
+    F = dwell_features(pat)[:n_dwell]
+    W = weights_dirichlet(41, n_plans)
+    W[0, 0] = 0.0   # log10 max(w, 1e-3) at its floor
+    p = _params(4)
+    with gmco_mod.Mlp(p) as net:
+        t = net.predict(F, W, t_floor=0.0)
+        td = net.predict(torch.from_numpy(F).cuda(), torch.from_numpy(W).cuda(), t_floor=0.0)
+        assert net.last_launch_count() == 1
+    assert np.array_equal(td.cpu().numpy(), t)
+    ref, _ = M.forward(_bf16_weights(p), M.dense_inputs(F, W))
+    _check_predict(t, ref.reshape(len(W), len(F)), f"predict {n_plans}x{len(F)}")
+
+
 def _grad_magnitude(params, X, target):
     """The FP64 backward with every term taken in absolute value: per parameter, the sum of
     the magnitudes of the products whose sum is its gradient.  Rounding the activations and
