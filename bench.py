@@ -62,6 +62,9 @@ def parse_args():
     ap.add_argument("--cpu-sample", type=int, default=0, help="plans in the CPU sample (0: auto)")
     ap.add_argument("--no-multi", action="store_true", help="skip the multi-patient section")
     ap.add_argument("--no-warm", action="store_true", help="skip the warm-start section")
+    ap.add_argument("--warm-scale", choices=sorted(WARM_SCALES), default="bench",
+                    help="warm-start section size: bench (48 x 256 training plans, 4 x 256 held "
+                         "out) or full (200 x 1000 training plans, 16 x 1000 held out)")
     ap.add_argument("--no-gsa", action="store_true", help="skip the annealing-engine section")
     ap.add_argument("--no-eps-sweep", action="store_true", help="skip the stopping-criterion sweep")
     ap.add_argument("--no-fp32-form", action="store_true", help="skip the FP32-form section")
@@ -478,106 +481,167 @@ def multi_quality_run(g, torch, args, pats, Wd, tiles, stream):
                     "solves / time"}
 
 
+WARM_SCALES = {
+    # training patients x plans, held-out patients x plans, Adam steps of 16384 rows
+    "bench": dict(n_train=48, plans_train=256, n_held=4, plans_held=256, steps=4000),
+    "full": dict(n_train=200, plans_train=1000, n_held=16, plans_held=1000, steps=30000),
+}
+WARM_LADDER = (100, 200, 400, 800, 1600, 3200)
+
+
 def warm_start_section(g, torch, args):
-    """Learned warm start: a network trained with the library's kernels on plans the
-    multi-patient solver converged for 48 training patients, measured on held-out patients
-    against the uniform start (FP32 form and tensor-core form) at fixed iteration budgets."""
-    from synth import (dwell_features, make_patient, mlp_init_params, multi_patient_specs,
-                       weights_dirichlet)
-    n_train, n_held, plans = 48, 2, 256
-    t0 = time.perf_counter()
+    """Learned warm start: a network trained with the library's kernels on plans that the
+    multi-patient solver converged (relative change 1e-8, at most 2000 iterations) for seeded
+    training patients of the uneven workload, measured on held-out patients against the
+    uniform start, in the tensor-core form and the FP32 form.  Two measures: (1) the stop rule
+    relative change <= 1e-4 (iterations, wall time, gap at the stop), (2) a ladder of fixed
+    iteration budgets, from which each plan's iterations to reach 1e-4 of the reference
+    objective follow (to the ladder's resolution).  Reference objective per plan: the lowest of
+    every run here and of a long FP32 solve (relative change 1e-12, 8000 iterations) from the
+    better start.  Problems are built on the device (points, dose rates) as in the planning
+    flow; every solve is one multi-patient launch over the held-out patients."""
+    import types
+    from synth import (Geometry, class_penalty_params, dwell_features, dwell_positions,
+                       mlp_init_params, multi_patient_specs, weights_dirichlet)
+    sc = WARM_SCALES[args.warm_scale]
+    n_train, n_held = sc["n_train"], sc["n_held"]
+    prm = class_penalty_params()
     specs = multi_patient_specs(n_train + n_held, seed=1904015670 + 11)
-    pats = [make_patient(s["seed"], s["n_catheters"], s["dwell_step"], s["n_points"], s["scale"])
-            for s in specs]
-    Ws = [weights_dirichlet(s["seed"], plans) for s in specs]
-    tr_p, tr_w = pats[:n_train], Ws[:n_train]
-    res = []
-    for c in range(0, n_train, 32):
-        probs = [g.Problem(p.A, p.sid, p.params, precision=args.precision, steps_per_poll=32)
-                 for p in tr_p[c:c + 32]]
-        with g.Multi(probs) as mu:
-            res += mu.solve(tr_w[c:c + 32], max_iters=4000, tol=1e-10, want=("T",))
-        for pr in probs:
-            pr.close()
-    data_s = time.perf_counter() - t0
+
+    def build(k, precision, plans):
+        s = specs[k]
+        geo = Geometry().scaled(s["scale"])
+        pts, sid = g.sample_points(geo, s["n_points"], s["seed"], device=True)
+        dw, cat, _ = dwell_positions(geo, s["n_catheters"], s["dwell_step"])
+        pr = g.Problem.from_geometry(pts, sid, dw, prm, precision=precision, steps_per_poll=32)
+        feat = dwell_features(types.SimpleNamespace(geometry=geo, dwells=dw, catheter=cat))
+        return pr, feat, weights_dirichlet(s["seed"], plans)
+
+    t0 = time.perf_counter()
     feats, wtab, pairs, target = [], [], [], []
     f0 = w0 = 0
-    for p, W, r in zip(tr_p, tr_w, res):
-        F = dwell_features(p)
-        feats.append(F)
-        wtab.append(W)
-        pairs.append(np.stack([np.tile(np.arange(len(F)), len(W)) + f0,
-                               np.repeat(np.arange(len(W)), len(F)) + w0], 1))
-        target.append(r["T"].reshape(-1))
-        f0 += len(F)
-        w0 += len(W)
+    for c in range(0, n_train, 64):
+        built = [build(k, args.precision, sc["plans_train"]) for k in range(c, min(c + 64, n_train))]
+        with g.Multi([b[0] for b in built]) as mu:
+            res = mu.solve([torch.from_numpy(b[2]).cuda() for b in built], max_iters=2000, tol=1e-8,
+                           want=("T",))
+        for (pr, F, W), r in zip(built, res):
+            feats.append(F)
+            wtab.append(W)
+            pairs.append(np.stack([np.tile(np.arange(len(F)), len(W)) + f0,
+                                   np.repeat(np.arange(len(W)), len(F)) + w0], 1).astype(np.int32))
+            target.append(np.asarray(r["T"].cpu().numpy() if hasattr(r["T"], "cpu") else r["T"]).reshape(-1))
+            f0 += len(F)
+            w0 += len(W)
+            pr.close()
+    torch.cuda.synchronize()
+    data_s = time.perf_counter() - t0
 
     def dev(a, dt):
         return torch.from_numpy(np.ascontiguousarray(np.concatenate(a), dtype=dt)).cuda()
     Fd, Wt, Pd, Td = dev(feats, np.float32), dev(wtab, np.float32), dev(pairs, np.int32), dev(target, np.float32)
+    del feats, wtab, pairs, target
     net = g.Mlp(mlp_init_params(0))
     gen = torch.Generator(device="cuda").manual_seed(0)
-    steps, batch = 4000, 16384
+    steps, batch = sc["steps"], 16384
     torch.cuda.synchronize()
     t1 = time.perf_counter()
     losses = []
     for k in range(steps):
         idx = torch.randint(0, Pd.shape[0], (batch,), device="cuda", generator=gen)
-        losses.append(net.train_step(Fd, Wt, Pd[idx].contiguous(), Td[idx].contiguous(),
-                                     lr=2e-3 if k < steps // 2 else 5e-4))
+        lr = 2e-3 if k < steps // 2 else (5e-4 if k < 3 * steps // 4 else 1.25e-4)
+        losses.append(net.train_step(Fd, Wt, Pd[idx].contiguous(), Td[idx].contiguous(), lr=lr))
     torch.cuda.synchronize()
     train_s = time.perf_counter() - t1
-    budgets = (200, 800, 3200)
-    table = {v: {b: {"ms": 0.0, "within_1e-4": 0, "gaps": []} for b in budgets}
-             for v in ("fp32_uniform", f"{args.precision}_uniform", f"{args.precision}_warm")}
-    warm_ms, n_model = 0.0, 0
-    for h in range(n_train, n_train + n_held):
-        p, W = pats[h], Ws[h]
-        F = dwell_features(p)
-        pf = g.Problem(p.A, p.sid, p.params, precision="fp32", steps_per_poll=32)
-        pt = g.Problem(p.A, p.sid, p.params, precision=args.precision, steps_per_poll=32)
-        t2 = time.perf_counter()
-        t0w, flag = g.warm_start(pt, net, F, W, t_floor=0.3)
-        warm_ms += 1000 * (time.perf_counter() - t2)
-        n_model += int(flag.sum())
-        r1 = pt.solve_batch(W, None, max_iters=12000, tol=1e-13, want=("objectives",))["objectives"]
-        r2 = pt.solve_batch(W, t0w, max_iters=12000, tol=1e-13, want=("objectives",))["objectives"]
-        runs = {}
-        for b in budgets:
-            for v, (pr, s0) in {"fp32_uniform": (pf, None), f"{args.precision}_uniform": (pt, None),
-                                f"{args.precision}_warm": (pt, t0w)}.items():
-                torch.cuda.synchronize()
-                t3 = time.perf_counter()
-                o = pr.solve_batch(W, s0, max_iters=b, tol=0.0, want=("objectives",))["objectives"]
-                dt = 1000 * (time.perf_counter() - t3)
-                runs[(v, b)] = (o, dt)
-        Fref = np.minimum(np.minimum(r1, r2), runs[("fp32_uniform", budgets[-1])][0])
-        for (v, b), (o, dt) in runs.items():
-            gap = (o - Fref) / Fref
-            e = table[v][b]
-            e["ms"] += dt
-            e["within_1e-4"] += int(np.sum(gap <= 1e-4))
-            e["gaps"].append(gap)
-        pf.close()
-        pt.close()
+    n_rows = int(Pd.shape[0])
+    del Fd, Wt, Pd, Td
+
+    # held-out patients, both forms
+    held = range(n_train, n_train + n_held)
+    tc = [build(k, args.precision, sc["plans_held"]) for k in held]
+    f32 = [build(k, "fp32", sc["plans_held"])[0] for k in held]
+    Ws = [torch.from_numpy(b[2]).cuda() for b in tc]
+    torch.cuda.synchronize()
+    t2 = time.perf_counter()
+    warm = [g.warm_start(pr, net, torch.from_numpy(F).cuda(), W, t_floor=0.3) for (pr, F, _), W in zip(tc, Ws)]
+    torch.cuda.synchronize()
+    warm_ms = 1000 * (time.perf_counter() - t2)
+    n_model = int(sum(int(f.sum().item()) for _, f in warm))
+    t0w = [t for t, _ in warm]
+    mu_tc = g.Multi([b[0] for b in tc])
+    # the FP32 form has no multi-patient launch: one solve call per patient, times summed
+    variants = {"fp32_uniform": (f32, None), f"{args.precision}_uniform": (mu_tc, None),
+                f"{args.precision}_warm": (mu_tc, t0w)}
+
+    def arr(x):
+        return np.asarray(x.cpu().numpy() if hasattr(x, "cpu") else x).reshape(-1)
+
+    def run(solver, s0, max_iters, tol, want=("objectives",)):
+        torch.cuda.synchronize()
+        a = time.perf_counter()
+        if isinstance(solver, list):
+            r = [pr.solve_batch(W, None if s0 is None else s0[i], max_iters=max_iters, tol=tol, want=want)
+                 for i, (pr, W) in enumerate(zip(solver, Ws))]
+        else:
+            r = solver.solve(Ws, t0=s0, max_iters=max_iters, tol=tol, want=want)
+        torch.cuda.synchronize()
+        out = {k: np.concatenate([arr(x[k]) for x in r]) for k in want}
+        return out, 1000 * (time.perf_counter() - a)
+
+    runs = {}
+    for v, (solver, s0) in variants.items():
+        for b in WARM_LADDER:
+            runs[(v, b)] = run(solver, s0, b, 0.0)
+        runs[(v, "stop")] = run(solver, s0, 3000, 1e-4, want=("objectives", "iters"))
+    # reference: long FP32 solves from both starts
+    ref_long = {}
+    for key, s0 in (("uniform", None), ("warm", t0w)):
+        ref_long[key] = run(f32, s0, 8000, 1e-12)[0]["objectives"]
+    Fref = np.minimum(ref_long["uniform"], ref_long["warm"])
+    for (v, b), (o, _) in runs.items():
+        Fref = np.minimum(Fref, o["objectives"])
+    mu_tc.close()
+    for b in tc:
+        b[0].close()
+    for pr in f32:
+        pr.close()
     net.close()
     out = {}
-    for v, d in table.items():
-        out[v] = {str(b): {"ms": e["ms"] + (warm_ms if v.endswith("warm") else 0.0),
-                           "within_1e-4": e["within_1e-4"],
-                           "median_gap": float(np.median(np.concatenate(e["gaps"])))}
-                  for b, e in d.items()}
+    for v in variants:
+        extra = warm_ms if v.endswith("warm") else 0.0
+        ladder, first = {}, np.full(len(Fref), np.inf)
+        for b in WARM_LADDER:
+            o, ms = runs[(v, b)]
+            gap = o["objectives"] / Fref - 1.0
+            ok = gap <= QUALITY
+            first = np.where(ok & np.isinf(first), b, first)
+            ladder[str(b)] = {"ms": ms + extra, "within_1e-4": int(ok.sum()),
+                              "median_gap": float(np.median(gap))}
+        o, ms = runs[(v, "stop")]
+        gap = o["objectives"] / Fref - 1.0
+        med_first = float(np.median(first))
+        out[v] = {"budgets": ladder,
+                  "iters_to_1e-4": {"median": med_first if np.isfinite(med_first) else None,
+                                    "reached_by_3200": int(np.isfinite(first).sum())},
+                  "stop_rule_1e-4": {"ms": ms + extra, "iters_median": float(np.median(o["iters"])),
+                                     "iters_mean": float(np.mean(o["iters"])),
+                                     "within_1e-4": int(np.sum(gap <= QUALITY)),
+                                     "median_gap": float(np.median(gap))}}
     return {
-        "training": {"patients": n_train, "plans": n_train * plans, "rows": int(Pd.shape[0]),
-                     "data_s": data_s, "steps": steps, "batch": batch, "train_s": train_s,
+        "scale": args.warm_scale,
+        "training": {"patients": n_train, "plans": n_train * sc["plans_train"], "rows": n_rows,
+                     "data_s": data_s, "data_rule": "relative change 1e-8, at most 2000 iterations",
+                     "steps": steps, "batch": batch, "train_s": train_s,
                      "loss_first": float(np.mean(losses[:20])), "loss_last": float(np.mean(losses[-20:]))},
-        "held_out": {"patients": n_held, "plans": n_held * plans,
+        "held_out": {"patients": n_held, "plans": n_held * sc["plans_held"],
                      "plans_started_from_model": n_model, "warm_start_ms": warm_ms},
-        "budgets_iterations": list(budgets),
+        "ladder_iterations": list(WARM_LADDER),
         "by_start": out,
-        "note": "gaps relative to the best objective of long solves (1e-13, 12000 iterations) "
-                "from both starts and of the longest FP32 run; ms = wall time of the solve call "
-                "(warm: plus the prediction and the fallback evaluation)",
+        "note": "gap = F / F_ref - 1, F_ref = lowest objective of every run and of long FP32 "
+                "solves (1e-12, 8000 iterations) from both starts; ms = wall time of one "
+                "multi-patient solve call over the held-out patients (warm: plus the prediction "
+                "and the fallback evaluation); iters_to_1e-4 = first ladder budget at which a "
+                "plan is within 1e-4 of F_ref",
     }
 
 def gsa_section(g, torch, prob, Wd, fstar, iters, lbfgs_ms, stream):
@@ -738,7 +802,10 @@ def section_summary(name, sec):
             return {str(r["refine_iters"]): [r["plans_within_1e-4"], round(r["ms_per_solve"], 1)]
                     for r in sec["rows"]}
         if name == "warm_start":
-            return {v: {b: [round(e["ms"], 1), e["within_1e-4"]] for b, e in d.items()}
+            return {v: {"stop_1e-4": [round(d["stop_rule_1e-4"]["ms"], 1), d["stop_rule_1e-4"]["iters_median"],
+                                      d["stop_rule_1e-4"]["within_1e-4"]],
+                        "iters_to_1e-4": d["iters_to_1e-4"]["median"],
+                        "800": [round(d["budgets"]["800"]["ms"], 1), d["budgets"]["800"]["within_1e-4"]]}
                     for v, d in sec["by_start"].items()}
     except (KeyError, TypeError) as ex:
         return {"summary_error": repr(ex)}

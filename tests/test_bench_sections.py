@@ -94,3 +94,7 @@ def test_section_summary_keeps_key_figures():
     assert bench.section_summary("eps_sweep", sec) == {"0.001": [12.35, 0.5679, 1e-3]}
     assert bench.section_summary("gsa", {"error": "boom"}) == {"error": "boom"}
     assert "summary_error" in bench.section_summary("gsa", {"ms": 1.0})
+    d = {"stop_rule_1e-4": {"ms": 12.34, "iters_median": 700.0, "within_1e-4": 5},
+         "iters_to_1e-4": {"median": 800.0}, "budgets": {"800": {"ms": 3.21, "within_1e-4": 4}}}
+    assert bench.section_summary("warm_start", {"by_start": {"bf16x2_warm": d}}) == {
+        "bf16x2_warm": {"stop_1e-4": [12.3, 700.0, 5], "iters_to_1e-4": 800.0, "800": [3.2, 4]}}
