@@ -68,6 +68,7 @@ def parse_args():
     ap.add_argument("--no-gsa", action="store_true", help="skip the annealing-engine section")
     ap.add_argument("--no-eps-sweep", action="store_true", help="skip the stopping-criterion sweep")
     ap.add_argument("--no-fp32-form", action="store_true", help="skip the FP32-form section")
+    ap.add_argument("--no-mlp-inference", action="store_true", help="skip the network-inference section")
     ap.add_argument("--no-flow", action="store_true", help="skip the on-device planning-flow section")
     ap.add_argument("--no-refine", action="store_true", help="skip the FP32-refinement section")
     ap.add_argument("--refine-list", default="300,1000",
@@ -670,6 +671,44 @@ def gsa_section(g, torch, prob, Wd, fstar, iters, lbfgs_ms, stream):
                         "temperature 1e-2 -> 1e-5 of the start objective, geometric"}
 
 
+def mlp_inference_section(g, torch, bf16_peak):
+    """Throughput of the warm-start network's tcgen05 inference kernel at the held-out scale
+    of the warm-start workload (1000 plans x the dwell positions of a 20-catheter patient of
+    the uneven workload, every row one dwell of one plan), device buffers, CUDA events on the
+    calling stream around `reps` predictions after three warm-up calls.  FLOPs by the
+    network's count per row, 2 (14 x 128 + 2 x 128 x 128 + 128)."""
+    import types
+    from synth import Geometry, dwell_features, dwell_positions, mlp_init_params, weights_dirichlet
+    geo = Geometry().scaled(1.1)
+    dw, cat, _ = dwell_positions(geo, 20, 0.2)
+    F = torch.from_numpy(dwell_features(types.SimpleNamespace(geometry=geo, dwells=dw, catheter=cat))).cuda()
+    out = {"rows_per_plan": int(F.shape[0])}
+    flop_row = 2.0 * (14 * 128 + 2 * 128 * 128 + 128)
+    with g.Mlp(mlp_init_params(0)) as net:
+        for P in (1000, 16000):
+            W = torch.from_numpy(weights_dirichlet(7, P)).cuda()
+            st = torch.cuda.current_stream()
+            for _ in range(3):
+                net.predict(F, W, stream=st)
+            reps = 10
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            torch.cuda.synchronize()
+            a.record(st)
+            for _ in range(reps):
+                net.predict(F, W, stream=st)
+            b.record(st)
+            torch.cuda.synchronize()
+            ms = a.elapsed_time(b) / reps
+            R = P * int(F.shape[0])
+            tf = flop_row * R / (ms * 1e-3) / 1e12
+            out[f"plans_{P}"] = {"rows": R, "ms": ms, "rows_per_s": R / (ms * 1e-3), "tflops": tf,
+                                 "frac_of_bf16_peak": tf / bf16_peak,
+                                 "launches": int(net.last_launch_count())}
+    out["note"] = ("ms per prediction call (one k_mlp_infer_tc launch plus the call's stream "
+                   "handoff); the kernel is bound by its FP32 erf-GELU epilogues, not the MMAs")
+    return out
+
+
 def fp32_form_section(g, torch, args, pat, W, Wd, fstar, stream):
     """The plain method in FP32 (the workload's stated precision) on the headline workload and
     rule: plans within 1e-4 of F* per second, and the FP32 dose kernel against the device's
@@ -798,6 +837,9 @@ def section_summary(name, sec):
             return {"plans_within_1e-4": sec["plans_within_1e-4"],
                     "plans_within_1e-4_per_s": sec["plans_within_1e-4_per_s"],
                     "dose_kernel_frac_of_fp32_peak": sec["roofline"]["frac"]}
+        if name == "mlp_inference":
+            return {k: [round(v["ms"], 3), round(v["tflops"], 1)] for k, v in sec.items()
+                    if k.startswith("plans_")}
         if name == "refine":
             return {str(r["refine_iters"]): [r["plans_within_1e-4"], round(r["ms_per_solve"], 1)]
                     for r in sec["rows"]}
@@ -948,6 +990,8 @@ def run_ours(args):
             sections["refine"] = lambda: refine_section(g, torch, args, pat, Wd, fstar, stream)
         if not args.no_warm:
             sections["warm_start"] = lambda: warm_start_section(g, torch, args)
+        if not args.no_mlp_inference:
+            sections["mlp_inference"] = lambda: mlp_inference_section(g, torch, peaks["bf16_tflops"])
         summary = {}
         for name, fn in sections.items():
             try:

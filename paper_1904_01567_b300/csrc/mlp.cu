@@ -11,7 +11,7 @@
 //   k_mlp_infer_tc          inference on the fifth-generation tensor cores: tcgen05.mma with
 //                           the weights copied into shared memory by the TMA unit, FP32
 //                           accumulators in TMEM, bias + GELU epilogues that write the next
-//                           layer's BF16 operand; persistent grid, two 128-row tiles in
+//                           layer's BF16 operand; persistent grid, three 128-row tiles in
 //                           flight per CTA
 //   k_mlp_train             training forward and backward of 16-row tiles per warp on
 //                           warp-level BF16 MMA (m16n8k16, FP32 accumulators in registers):
@@ -450,10 +450,12 @@ __global__ void k_mlp_adam(float *__restrict__ p, float *__restrict__ m, float *
 // copied whole by the TMA unit; a tile's activations H (128 rows x 128 columns) are two blocks.
 constexpr uint32_t BLK = HID * 128;                           // bytes of one block: 16 KB
 constexpr uint32_t IMG_W1 = 0, IMG_W2 = BLK, IMG_W3 = 3 * BLK, IMG_BYTES = 5 * BLK;
-constexpr int TC_GROUPS = 2;                                  // 128-row tiles in flight per CTA
+constexpr int TC_GROUPS = 3;                                  // 128-row tiles in flight per CTA
 constexpr int TC_THREADS = TC_GROUPS * 128;                   // one thread per row of a tile
 constexpr size_t TC_SMEM = IMG_BYTES + (size_t)TC_GROUPS * 2 * BLK + 1024;   // + alignment
-constexpr uint32_t TC_TMEM_COLS = TC_GROUPS * HID;            // one FP32 accumulator per group
+constexpr uint32_t TC_TMEM_COLS = TC_GROUPS * HID <= 256 ? 256 : 512;   // a power of two holding
+                                                                          // one accumulator per group
+static_assert(TC_GROUPS * HID <= 512, "TMEM columns");
 constexpr long long kMlpWaitNs = 1000000000LL;                // 1 s per wait, then an error
 
 // Byte offset of element (row, col) in a stack of blocks (col / 64 selects the block).
@@ -508,26 +510,28 @@ __device__ __forceinline__ void put_inputs(const RowSrc &s, int64_t r, uint8_t *
 }
 
 // Hidden-layer epilogue of one row: h = GELU(z + b) from the accumulator's 128 columns
-// (TMEM lane = row), BF16 into the tile's blocks as the next layer's A operand.
+// (TMEM lane = row), BF16 into the tile's blocks as the next layer's A operand.  32 columns
+// per pass, the passes not unrolled: the GELUs of the whole row unrolled would not fit the
+// instruction cache.
 __device__ __forceinline__ void epi_hidden(uint32_t taddr, const float *b, uint8_t *sH, uint32_t row)
 {
+#pragma unroll 1
+    for (int c0 = 0; c0 < HID; c0 += 32) {
+        uint32_t v[2][16];
+        gmco::tmem_ld16(taddr + (uint32_t)c0, v[0]);
+        gmco::tmem_ld16(taddr + (uint32_t)c0 + 16, v[1]);
+        tmem_ld_wait16(v[0]);
+        tmem_ld_wait16(v[1]);
 #pragma unroll
-    for (int half = 0; half < 2; ++half) {
-        uint32_t v[4][16];
+        for (int q = 0; q < 4; ++q) {
+            uint32_t h[4];
 #pragma unroll
-        for (int c4 = 0; c4 < 4; ++c4) gmco::tmem_ld16(taddr + (uint32_t)(64 * half + 16 * c4), v[c4]);
-#pragma unroll
-        for (int c4 = 0; c4 < 4; ++c4) tmem_ld_wait16(v[c4]);
-#pragma unroll
-        for (int c4 = 0; c4 < 4; ++c4) {
-            const int c0 = 64 * half + 16 * c4;
-            uint32_t h[8];
-#pragma unroll
-            for (int e = 0; e < 8; ++e)
-                h[e] = pack_bf16(gelu(__uint_as_float(v[c4][2 * e]) + b[c0 + 2 * e]),
-                                 gelu(__uint_as_float(v[c4][2 * e + 1]) + b[c0 + 2 * e + 1]));
-            *reinterpret_cast<uint4 *>(sH + swz(row, (uint32_t)c0)) = make_uint4(h[0], h[1], h[2], h[3]);
-            *reinterpret_cast<uint4 *>(sH + swz(row, (uint32_t)c0 + 8)) = make_uint4(h[4], h[5], h[6], h[7]);
+            for (int e = 0; e < 4; ++e) {
+                const int c = 8 * q + 2 * e;   // column c0 + c of the pass
+                h[e] = pack_bf16(gelu(__uint_as_float(v[c >> 4][c & 15]) + b[c0 + c]),
+                                 gelu(__uint_as_float(v[c >> 4][(c & 15) + 1]) + b[c0 + c + 1]));
+            }
+            *reinterpret_cast<uint4 *>(sH + swz(row, (uint32_t)(c0 + 8 * q))) = make_uint4(h[0], h[1], h[2], h[3]);
         }
     }
 }
@@ -536,20 +540,16 @@ __device__ __forceinline__ void epi_hidden(uint32_t taddr, const float *b, uint8
 __device__ __forceinline__ float epi_out(uint32_t taddr, const float *b3, const float *w4, float b4)
 {
     float o = 0.0f;
+#pragma unroll 1
+    for (int c0 = 0; c0 < HID; c0 += 32) {
+        uint32_t v[2][16];
+        gmco::tmem_ld16(taddr + (uint32_t)c0, v[0]);
+        gmco::tmem_ld16(taddr + (uint32_t)c0 + 16, v[1]);
+        tmem_ld_wait16(v[0]);
+        tmem_ld_wait16(v[1]);
 #pragma unroll
-    for (int half = 0; half < 2; ++half) {
-        uint32_t v[4][16];
-#pragma unroll
-        for (int c4 = 0; c4 < 4; ++c4) gmco::tmem_ld16(taddr + (uint32_t)(64 * half + 16 * c4), v[c4]);
-#pragma unroll
-        for (int c4 = 0; c4 < 4; ++c4) tmem_ld_wait16(v[c4]);
-#pragma unroll
-        for (int c4 = 0; c4 < 4; ++c4)
-#pragma unroll
-            for (int e = 0; e < 16; ++e) {
-                const int c = 64 * half + 16 * c4 + e;
-                o = fmaf(gelu(__uint_as_float(v[c4][e]) + b3[c]), w4[c], o);
-            }
+        for (int c = 0; c < 32; ++c)
+            o = fmaf(gelu(__uint_as_float(v[c >> 4][c & 15]) + b3[c0 + c]), w4[c0 + c], o);
     }
     return o + b4;
 }
@@ -560,8 +560,8 @@ __device__ __forceinline__ float epi_out(uint32_t taddr, const float *b3, const 
 // threads write the inputs, one elected thread issues the layer's tcgen05.mma (M = N = 128,
 // K = 16 for layer 1, 128 for layers 2 and 3) and commits it to the group's mbarrier, the
 // threads read the accumulator with tcgen05.ld, add the bias, apply GELU and write BF16
-// activations for the next layer; the output unit and softplus finish in registers.  The two
-// groups interleave, so one group's MMAs run under the other's epilogue.  Every wait is
+// activations for the next layer; the output unit and softplus finish in registers.  The
+// groups interleave, so one group's MMAs run under the others' epilogues.  Every wait is
 // bounded: a wait that runs out sets *err, the group stops at its next barrier, and the CTA
 // waits (bounded) for its MMAs and copies in flight before freeing TMEM.
 __global__ void __launch_bounds__(TC_THREADS, 1)
