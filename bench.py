@@ -775,7 +775,7 @@ def refine_section(g, torch, args, pat, Wd, fstar, stream):
 
 def eps_sweep_section(g, torch, prob, pat, Wd, max_iters, stream, fstar,
                       eps_list=(1e-7, 1e-6, 1e-5, 1e-4, 1e-3, 1e-2)):
-    """The stopping-criterion sweep of Sec. 2.2.4 (the paper's Fig. 4a, on this workload): for
+    """The stopping-criterion sweep of Sec. 2.2.4 (the paper's Fig. 3a, on this workload): for
     each relative-change tolerance eps, the solve time of the whole batch (CUDA events, after one
     warm-up solve at that eps) and the fraction of non-dominated plans of the pool, judged on
     the per-structure objectives f_s (the unweighted mean penalty of each structure, evaluated
@@ -810,7 +810,7 @@ def eps_sweep_section(g, torch, prob, pat, Wd, max_iters, stream, fstar,
         r["speedup_vs_first"] = rows[0]["ms"] / r["ms"]
     return {"rows": rows, "plans": P,
             "objectives": "per-structure f_s, FP32 evaluation at the solved T",
-            "paper_context": "paper (Fig. 4a): eps = 1e-3 kept as the clinically useful criterion"}
+            "paper_context": "paper (Fig. 3a): eps = 1e-3 kept as the clinically useful criterion"}
 
 
 def section_summary(name, sec):

@@ -61,7 +61,8 @@ def _check_predict(t, ref, label):
 
 
 @pytest.mark.parametrize("n_cath,n_dwell,n_plans", [
-    (18, None, 250),   # 324 dwells x 250 plans = 81000 rows: every CTA loops, ragged last tile
+    (18, None, 999),   # 144 dwells x 999 plans = 143856 rows: 1124 tiles, every CTA's
+                       # groups loop twice or more, ragged last tile
     (12, None, 1),     # fewer rows than one tile: the CTA's second tile group has no work
     (12, 128, 4),      # whole tiles only
     (12, 1, 1),        # a single row
