@@ -47,6 +47,27 @@ constexpr int BUF_COLS = 256;
 constexpr long long kDrainNs = 1000000000LL;   // wind-down waits after a failed wait: 1 s
 
 // ------------------------------------------------------------------ the GEMM kernel
+
+// The MMAs of one stage: k16n K steps (16 each) of the group's NP products, all issued by the
+// elected lane of the converged MMA warp.  NP is a template parameter so that the loop has no
+// per-product predicates.
+template <int NP>
+__device__ __forceinline__ void issue_stage(uint32_t tbuf, uint32_t st_lo, const uint32_t *aq,
+                                            const uint32_t *bq, const uint32_t *iq, int k16n,
+                                            bool fresh)
+{
+#pragma unroll
+    for (int k16 = 0; k16 < 4; ++k16) {
+        if (k16 < k16n) {
+            const uint32_t kk = st_lo + 2u * (uint32_t)k16;
+#pragma unroll
+            for (int q = 0; q < NP; ++q)
+                mma_bf16_elect(tbuf, DESC_FIXED | (kk + aq[q]), DESC_FIXED | (kk + bq[q]), iq[q],
+                               (fresh && k16 == 0 && q == 0) ? 0u : 1u);
+        }
+    }
+}
+
 // One kind of ring stage: the M-side tiles (a_map, 128 rows each) and the N-side slots loaded
 // for one K block, and the products issued on them.  A slot holds one or two boxes of 128
 // rows stacked in shared memory (b_map[slot][0], b_map[slot][1]; -1 = none; b_roff = row
@@ -349,7 +370,9 @@ __global__ void __launch_bounds__(NTHREADS, 1) k_tc(const __grid_constant__ KPar
     } else if (warp == W_MMA) {
         // ---------------- MMA issuer (the whole warp walks the items; one elected lane issues)
         {
-            int it = 0, p = 0, nb = 0;
+            int p = 0, nb = 0;
+            int st_i = 0;            // stage of the ring and the parity of its current use
+            uint32_t st_ph = 0u;
             uint32_t use[2] = {0u, 0u};   // completed uses of each accumulator buffer
             bool ok = true;
             const uint32_t s_lo0 = desc_lo(smem_u32(smem));
@@ -387,9 +410,13 @@ __global__ void __launch_bounds__(NTHREADS, 1) k_tc(const __grid_constant__ KPar
                         bq[q] = (uint32_t)(kp.b_off + g.pair_b[qq] * kp.slot_bytes) >> 4;
                         iq[q] = idesc_bf16(w.half ? 128 : g.pair_n[qq]);
                     }
-                    for (int kb = kb0; kb < kb1; ++kb, ++it) {
-                        const int s = it % kp.n_stages;
-                        const uint32_t ph = (uint32_t)(it / kp.n_stages) & 1u;
+                    for (int kb = kb0; kb < kb1; ++kb) {
+                        const int s = st_i;
+                        const uint32_t ph = st_ph;
+                        if (++st_i == kp.n_stages) {
+                            st_i = 0;
+                            st_ph ^= 1u;
+                        }
                         if (!__all_sync(0xffffffffu, mbar_wait(smem_u32(&full_bar[s]), ph, kp.err, 2, kp.wait_ns))) {
                             ok = false;   // warp-uniform
                             break;
@@ -400,19 +427,15 @@ __global__ void __launch_bounds__(NTHREADS, 1) k_tc(const __grid_constant__ KPar
                         // starts the accumulator
                         const bool fresh = gi == 0 && kb == kb0;
                         const int k16n = min(4, k16_total - kb * 4);
-#pragma unroll
-                        for (int k16 = 0; k16 < 4; ++k16) {
-                            if (k16 < k16n) {
-                                const uint32_t kk = st_lo + 2u * (uint32_t)k16;
-#pragma unroll
-                                for (int q = 0; q < MAX_PAIRS; ++q) {
-                                    if (q < npair) {
-                                        const uint32_t accum = (fresh && k16 == 0 && q == 0) ? 0u : 1u;
-                                        mma_bf16_elect(tbuf, DESC_FIXED | (kk + aq[q]), DESC_FIXED | (kk + bq[q]),
-                                                       iq[q], accum);
-                                    }
-                                }
-                            }
+                        switch (npair) {
+                        case 1: issue_stage<1>(tbuf, st_lo, aq, bq, iq, k16n, fresh); break;
+                        case 2: issue_stage<2>(tbuf, st_lo, aq, bq, iq, k16n, fresh); break;
+                        case 3: issue_stage<3>(tbuf, st_lo, aq, bq, iq, k16n, fresh); break;
+                        case 4: issue_stage<4>(tbuf, st_lo, aq, bq, iq, k16n, fresh); break;
+                        case 5: issue_stage<5>(tbuf, st_lo, aq, bq, iq, k16n, fresh); break;
+                        case 6: issue_stage<6>(tbuf, st_lo, aq, bq, iq, k16n, fresh); break;
+                        case 7: issue_stage<7>(tbuf, st_lo, aq, bq, iq, k16n, fresh); break;
+                        default: issue_stage<8>(tbuf, st_lo, aq, bq, iq, k16n, fresh); break;
                         }
                         mma_commit_elect(smem_u32(&empty_bar[s]));   // stage free once these MMAs finish
                     }

@@ -23,41 +23,42 @@ __device__ __forceinline__ void mbar_expect_tx(uint32_t bar, uint32_t bytes)
                  : "memory");
 }
 
-__device__ __forceinline__ bool mbar_test(uint32_t bar, uint32_t parity)
+// One potentially blocking test of the phase with the given parity: the thread may be
+// suspended until the phase completes, for at most about hint_ns nanoseconds.
+__device__ __forceinline__ bool mbar_test(uint32_t bar, uint32_t parity, uint32_t hint_ns)
 {
     uint32_t ok;
     asm volatile(
         "{\n\t.reg .pred p;\n\t"
-        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2, %3;\n\t"
         "selp.b32 %0, 1, 0, p;\n\t}"
         : "=r"(ok)
-        : "r"(bar), "r"(parity)
+        : "r"(bar), "r"(parity), "r"(hint_ns)
         : "memory");
     return ok != 0;
-}
-
-__device__ __forceinline__ long long global_ns()
-{
-    long long t;
-    asm volatile("mov.u64 %0, %globaltimer;" : "=l"(t));
-    return t;
 }
 
 // Waits for the phase with the given parity; gives up after limit_ns nanoseconds (the
 // problem's wait limit, 1 s by default), records `code` in *err (when err is given) and returns
 // false so that the kernel can still wind down: wait for its own copies and MMAs in flight and
-// free its TMEM.
+// free its TMEM.  A test may suspend the thread until the phase completes, so the time is taken
+// around every test, including one that succeeds: a phase that completes later than the limit
+// counts as run out.  The SM cycle counter measures it (2.2 cycles per nanosecond, above the
+// highest SM clock, so the limit is never cut short; at lower clocks it stretches).
 __device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, int32_t *err, int code,
                                           long long limit_ns)
 {
-    if (mbar_test(bar, parity)) return true;
-    const long long t0 = global_ns();
-    while (!mbar_test(bar, parity)) {
-        if (global_ns() - t0 > limit_ns) {
+    const uint32_t hint = (uint32_t)(limit_ns < 0x7fffffffLL ? limit_ns : 0x7fffffffLL);
+    const long long limit_cyc = limit_ns * 11 / 5;
+    const long long c0 = clock64();
+    bool done;
+    do {
+        done = mbar_test(bar, parity, hint);
+        if (clock64() - c0 > limit_cyc) {
             if (err) atomicExch(err, code);
             return false;
         }
-    }
+    } while (!done);
     return true;
 }
 
