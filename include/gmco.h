@@ -290,7 +290,8 @@ gmco_status gmco_dvh_from_dose(gmco_problem *prob, const float *dose, int64_t P,
 
 /* Measurement aid: times one evaluation of P plans at a line-search trial point
  * (x_trial = 1.01 X, so both the dose and the dose change are computed) `reps` times after
- * one warm-up, with CUDA events between its kernels on the problem's stream.
+ * one warm-up, back to back on the problem's stream (as the solve loop launches them), with
+ * CUDA events between its kernels.  reps is at most 1000.
  *   ms     4 averages (milliseconds): trial-point preparation, dose GEMM with the penalty
  *          epilogue, gradient GEMM, reduction of partial sums
  *   flops  4 values or NULL: algorithmic FLOPs of the dose GEMM (the dose d = A t of

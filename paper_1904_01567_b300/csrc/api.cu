@@ -1519,7 +1519,7 @@ gmco_status gmco_solve_sa(gmco_problem *pr, const float *penalty_weights, int64_
 gmco_status gmco_profile_evaluate(gmco_problem *pr, const float *penalty_weights, int64_t P,
                                   const float *X, int32_t reps, double *ms, double *flops)
 {
-    if (!pr || !penalty_weights || !X || !ms || P < 1 || P > (1 << 20) || reps < 1) {
+    if (!pr || !penalty_weights || !X || !ms || P < 1 || P > (1 << 20) || reps < 1 || reps > 1000) {
         set_error_msg("gmco_profile_evaluate: bad arguments");
         return GMCO_EINVAL;
     }
@@ -1545,22 +1545,24 @@ gmco_status gmco_profile_evaluate(gmco_problem *pr, const float *penalty_weights
     CK(launch_profile_setup(s, pr->stream));
     CK(launch_compact(s, 0, pr->stream));
     const int form = pr->opt.precision == GMCO_PREC_FP32 ? 0 : 1;
-    cudaEvent_t ev[5];
-    for (int k = 0; k < 5; ++k) CK(cudaEventCreate(&ev[k]));
-    double acc[4] = {0, 0, 0, 0};
+    // the repetitions run back to back on the stream, as the solve loop's launches do (no
+    // synchronisation between them, which would add an idle GPU's launch latency to each
+    // kernel's time); one set of events per repetition, the first repetition a warm-up
+    std::vector<cudaEvent_t> ev((size_t)5 * (reps + 1), nullptr);
     gmco_status rs = GMCO_OK;
-    for (int r = 0; r < reps + 1 && rs == GMCO_OK; ++r) {   // first repetition is warm-up
-        rs = launch_eval(pr, s, form, true, pr->stream, ev);
-        if (rs != GMCO_OK) break;
-        if (cudaStreamSynchronize(pr->stream) != cudaSuccess) { rs = GMCO_ECUDA; break; }
-        if (r == 0) continue;
+    for (auto &e : ev)
+        if (cudaEventCreate(&e) != cudaSuccess) rs = GMCO_ECUDA;
+    for (int r = 0; r < reps + 1 && rs == GMCO_OK; ++r) rs = launch_eval(pr, s, form, true, pr->stream, &ev[(size_t)5 * r]);
+    if (rs == GMCO_OK && cudaStreamSynchronize(pr->stream) != cudaSuccess) rs = GMCO_ECUDA;
+    double acc[4] = {0, 0, 0, 0};
+    for (int r = 1; r < reps + 1 && rs == GMCO_OK; ++r)
         for (int k = 0; k < 4; ++k) {
             float t = 0.0f;
-            cudaEventElapsedTime(&t, ev[k], ev[k + 1]);
+            cudaEventElapsedTime(&t, ev[(size_t)5 * r + k], ev[(size_t)5 * r + k + 1]);
             acc[k] += t;
         }
-    }
-    for (int k = 0; k < 5; ++k) cudaEventDestroy(ev[k]);
+    for (auto &e : ev)
+        if (e) cudaEventDestroy(e);
     if (rs != GMCO_OK) return rs;
     for (int k = 0; k < 4; ++k) ms[k] = acc[k] / reps;
     if (flops) {
