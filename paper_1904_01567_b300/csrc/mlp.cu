@@ -7,24 +7,18 @@
 // activations in the products, FP32 accumulation, FP32 master weights.  The paper has no
 // learned component: this is the warm-start extension of its batched solve.
 //
-// Kernels:
-//   k_mlp_infer_tc          inference on the fifth-generation tensor cores: tcgen05.mma with
-//                           the weights copied into shared memory by the TMA unit, FP32
-//                           accumulators in TMEM, bias + GELU epilogues that write the next
-//                           layer's BF16 operand; persistent grid, three 128-row tiles in
-//                           flight per CTA
-//   k_mlp_train             training forward and backward of 16-row tiles per warp on
-//                           warp-level BF16 MMA (m16n8k16, FP32 accumulators in registers):
-//                           activations carried from one layer's accumulators to the next
-//                           layer's operand fragments in registers, weights in shared memory;
-//                           the loss and the backward pass of each tile in registers
-//                           (dz_3 -> dh_2 -> dz_2 -> dh_1 -> dz_1 with the transposed products
-//                           h W^T); writes the layer inputs H_{l-1} and the pre-activation
-//                           gradients dZ_l feature-major for the weight gradients, and per-CTA
-//                           partial sums of the bias gradients
-//   k_mlp_dw                dW_l = H_{l-1}^T dZ_l, split over row ranges, per-CTA partials
-//   k_mlp_reduce            fixed-order sums of the per-CTA partials into the gradient
-//   k_mlp_adam              Adam on the FP32 master weights, then the BF16 copies
+// Kernels (all products on the fifth-generation tensor cores: tcgen05.mma with BF16 operands
+// in shared memory, FP32 accumulators in TMEM; weights copied into shared memory by the TMA unit):
+//   k_mlp_infer_tc          inference, persistent grid, three 128-row tiles in flight per CTA;
+//                           bias + GELU epilogues write the next layer's BF16 operand
+//   k_mlp_train_tc          training forward and backward of 128-row tiles: z_l kept in TMEM,
+//                           dz_3 -> dh_2 = dz_3 W_3^T -> dz_2 -> dh_1 = dz_2 W_2^T -> dz_1;
+//                           writes the layer inputs H_0..H_3, do and dZ_1..dZ_3 feature-major
+//   k_mlp_dw_tc             weight gradients dW_l = H_{l-1}^T dZ_l (with the bias gradient from a
+//                           row of ones), dw_4 = H_3^T do: M = 128 features, K = rows in 64-row
+//                           blocks through a TMA ring, split over row ranges, per-CTA partials
+//   k_mlp_dw_reduce, k_mlp_reduce   fixed-order sums of the per-CTA partials into the gradient
+//   k_mlp_adam              Adam on the FP32 master weights; k_mlp_pack the BF16 images
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
 
@@ -42,27 +36,26 @@
 #include "gmco.h"
 #include "tcgen05.cuh"
 
+namespace gmco {
+bool tc_encode_map(CUtensorMap *m, const void *ptr, uint64_t cols, uint64_t rows, uint32_t box_cols,
+                   uint32_t box_rows);
+}
+
 namespace {
 
 constexpr int NIN = 14, NFEAT = 10, NW = 4, KIN = 16, HID = 128;
-constexpr int WARPS = 8, ROWS_W = 16, ROWS_CTA = WARPS * ROWS_W;
-constexpr int LDH = HID + 8;   // padded row (bf16) of the 128-wide weight copies in smem
-constexpr int LD1 = KIN + 8;   // padded row of W1^T
 // flat FP32 parameter layout (the C ABI's): W1 [14][128], b1, W2 [128][128], b2, W3, b3, w4, b4
 constexpr int OFF_W1 = 0, OFF_B1 = OFF_W1 + NIN * HID, OFF_W2 = OFF_B1 + HID,
               OFF_B2 = OFF_W2 + HID * HID, OFF_W3 = OFF_B2 + HID, OFF_B3 = OFF_W3 + HID * HID,
               OFF_W4 = OFF_B3 + HID, OFF_B4 = OFF_W4 + HID, NPARAM = OFF_B4 + 1;
 static_assert(NPARAM == GMCO_MLP_NPARAM, "parameter count");
-constexpr int NPART = 1 + 4 * HID + 1;   // per-CTA partials: loss, db1, db2, db3, dw4, db4
 constexpr int MAX_CTAS = 148;
 
 // BF16 weights as the kernels read them.
 struct DevWeights {
-    __nv_bfloat16 *Wt1;        // [128][16]  W1^T (n, k), k padded to 16 with zeros
-    __nv_bfloat16 *Wt2, *Wt3;  // [128][128] W^T (n, k): forward operand
-    __nv_bfloat16 *W2, *W3;    // [128][128] W (k, n): backward operand
     float *bias;               // b1, b2, b3, w4 (4 x 128) and b4
-    uint8_t *img;              // shared-memory image of W1^T, W2^T, W3^T for k_mlp_infer_tc
+    uint8_t *img;              // shared-memory image of W1^T, W2^T, W3^T (forward products)
+    uint8_t *imgb;             // shared-memory image of W3, W2 as [k][n] (backward products)
 };
 
 // Rows of one call: dense (row = plan * n_dwell + dwell) or listed (pairs[row] = (feature
@@ -71,6 +64,7 @@ struct RowSrc {
     const float *feat;      // [n_feat][10]
     const float *w;         // [n_w][4] raw penalty weights
     const int32_t *pairs;   // [R][2] or null (dense)
+    int64_t n_feat, n_w;    // listed mode: rows of feat and w (the pairs are checked against them)
     int64_t n_dwell;        // dense mode
     int64_t R;
     const float *target;    // [R] (training)
@@ -79,31 +73,16 @@ struct RowSrc {
 struct TrainOut {
     __nv_bfloat16 *H0, *H1, *H2;      // [16][Rp], [128][Rp], [128][Rp]  layer inputs
     __nv_bfloat16 *dZ1, *dZ2, *dZ3;   // [128][Rp]                      pre-activation grads
+    __nv_bfloat16 *H3, *DO, *ONES;    // [128][Rp] GELU(z_3); [16][Rp] row 0 = do; [16][Rp] row 0 = 1
     int64_t Rp;                       // row stride (R rounded up to 128)
-    float *part;                      // [gridDim][NPART]
+    float *part;                      // [gridDim][2]: sum of squared errors, db_4
     float inv_R;                      // 1 / R (mean squared error)
 };
-
-__device__ __forceinline__ void mma16816(float (&c)[4], const uint32_t (&a)[4], uint32_t b0,
-                                         uint32_t b1)
-{
-    asm volatile(
-        "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, "
-        "{%8,%9}, {%0,%1,%2,%3};"
-        : "+f"(c[0]), "+f"(c[1]), "+f"(c[2]), "+f"(c[3])
-        : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b0), "r"(b1));
-}
 
 __device__ __forceinline__ uint32_t pack_bf16(float lo, float hi)
 {
     const __nv_bfloat162 v = __floats2bfloat162_rn(lo, hi);
     return *reinterpret_cast<const uint32_t *>(&v);
-}
-
-__device__ __forceinline__ float2 unpack_bf16(uint32_t v)
-{
-    const __nv_bfloat162 b = *reinterpret_cast<const __nv_bfloat162 *>(&v);
-    return __bfloat1622float2(b);
 }
 
 __device__ __forceinline__ float gelu(float z) { return 0.5f * z * (1.0f + erff(z * 0.70710678118654752f)); }
@@ -116,305 +95,6 @@ __device__ __forceinline__ float gelu_d(float z)
 
 __device__ __forceinline__ float softplus(float o) { return o > 20.0f ? o : log1pf(expf(o)); }
 __device__ __forceinline__ float sigmoid(float o) { return 1.0f / (1.0f + expf(-o)); }
-
-// Input column c of row r (0 past the row count and in the two padding columns).
-__device__ __forceinline__ float in_val(const RowSrc &s, int64_t r, int c)
-{
-    if (r >= s.R || c >= NIN) return 0.0f;
-    int64_t fr, wr;
-    if (s.pairs) {
-        fr = s.pairs[2 * r];
-        wr = s.pairs[2 * r + 1];
-    } else {
-        fr = r % s.n_dwell;
-        wr = r / s.n_dwell;
-    }
-    if (c < NFEAT) return s.feat[fr * NFEAT + c];
-    return log10f(fmaxf(s.w[wr * NW + (c - NFEAT)], 1e-3f));
-}
-
-// acc (16 rows x 128 columns, C fragments of 16 n-tiles) -> operand fragments of 8 k-steps.
-__device__ __forceinline__ void to_frag(const float (&acc)[16][4], uint32_t (&a)[8][4])
-{
-#pragma unroll
-    for (int s = 0; s < 8; ++s) {
-        a[s][0] = pack_bf16(acc[2 * s][0], acc[2 * s][1]);
-        a[s][1] = pack_bf16(acc[2 * s][2], acc[2 * s][3]);
-        a[s][2] = pack_bf16(acc[2 * s + 1][0], acc[2 * s + 1][1]);
-        a[s][3] = pack_bf16(acc[2 * s + 1][2], acc[2 * s + 1][3]);
-    }
-}
-
-// acc += A (16 x 128, fragments) * B, B[k][n] read from smem rows of a (n, k)-major copy
-// (forward: W^T) or a (k, n)-major one (backward: W, giving A W^T).
-__device__ __forceinline__ void gemm_128(float (&acc)[16][4], const uint32_t (&a)[8][4],
-                                         const __nv_bfloat16 *sB, int g, int t)
-{
-#pragma unroll
-    for (int s = 0; s < 8; ++s) {
-#pragma unroll
-        for (int j = 0; j < 16; ++j) {
-            const __nv_bfloat16 *row = sB + (size_t)(8 * j + g) * LDH + 16 * s + 2 * t;
-            const uint32_t b0 = *reinterpret_cast<const uint32_t *>(row);
-            const uint32_t b1 = *reinterpret_cast<const uint32_t *>(row + 8);
-            mma16816(acc[j], a[s], b0, b1);
-        }
-    }
-}
-
-// Feature-major store of a 16 x 128 fragment set: out[col][row0 + row].
-__device__ __forceinline__ void store_t(__nv_bfloat16 *out, int64_t ld, int64_t row0,
-                                        const float (&v)[16][4], int g, int t)
-{
-#pragma unroll
-    for (int j = 0; j < 16; ++j) {
-        const int c = 8 * j + 2 * t;
-        out[(size_t)c * ld + row0 + g] = __float2bfloat16_rn(v[j][0]);
-        out[(size_t)(c + 1) * ld + row0 + g] = __float2bfloat16_rn(v[j][1]);
-        out[(size_t)c * ld + row0 + g + 8] = __float2bfloat16_rn(v[j][2]);
-        out[(size_t)(c + 1) * ld + row0 + g + 8] = __float2bfloat16_rn(v[j][3]);
-    }
-}
-
-// Column sums over the warp's 16 rows of a fragment set, added to sum[128] (lanes g = 0).
-__device__ __forceinline__ void col_sums(const float (&v)[16][4], float *sum, int g, int t)
-{
-#pragma unroll
-    for (int j = 0; j < 16; ++j) {
-        float s0 = v[j][0] + v[j][2], s1 = v[j][1] + v[j][3];
-#pragma unroll
-        for (int o = 4; o < 32; o <<= 1) {
-            s0 += __shfl_xor_sync(0xffffffffu, s0, o);
-            s1 += __shfl_xor_sync(0xffffffffu, s1, o);
-        }
-        if (g == 0) {
-            sum[8 * j + 2 * t] += s0;
-            sum[8 * j + 2 * t + 1] += s1;
-        }
-    }
-}
-
-__global__ void __launch_bounds__(WARPS * 32, 1) k_mlp_train(DevWeights wt, RowSrc src, TrainOut tr)
-{
-    extern __shared__ __align__(16) uint8_t sm[];
-    __nv_bfloat16 *sWt1 = reinterpret_cast<__nv_bfloat16 *>(sm);       // [128][LD1]
-    __nv_bfloat16 *sWt2 = sWt1 + HID * LD1;                              // [128][LDH]
-    __nv_bfloat16 *sWt3 = sWt2 + HID * LDH;
-    __nv_bfloat16 *sW2 = sWt3 + HID * LDH;                               // backward operands
-    __nv_bfloat16 *sW3 = sW2 + HID * LDH;
-    __nv_bfloat16 *sZ = sW3 + HID * LDH;                                 // [2][8][16][128]
-    __shared__ float sb[4 * HID + 1];
-    __shared__ float sacc[WARPS][4 * HID + 2];   // per warp db1, db2, db3, dw4, db4, loss
-
-    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31, g = lane >> 2, t = lane & 3;
-    for (int i = tid; i < HID * KIN; i += blockDim.x) sWt1[(i / KIN) * LD1 + i % KIN] = wt.Wt1[i];
-    for (int i = tid; i < HID * HID; i += blockDim.x) {
-        const int r = i / HID, c = i % HID;
-        sWt2[r * LDH + c] = wt.Wt2[i];
-        sWt3[r * LDH + c] = wt.Wt3[i];
-        sW2[r * LDH + c] = wt.W2[i];
-        sW3[r * LDH + c] = wt.W3[i];
-    }
-    for (int i = tid; i < 4 * HID + 1; i += blockDim.x) sb[i] = wt.bias[i];
-    for (int i = lane; i < 4 * HID + 2; i += 32) sacc[warp][i] = 0.0f;
-    __syncthreads();
-    const float *b1 = sb, *b2 = sb + HID, *b3 = sb + 2 * HID, *w4 = sb + 3 * HID;
-    const float b4 = sb[4 * HID];
-    __nv_bfloat16 *sZ1 = sZ + (size_t)warp * ROWS_W * HID;
-    __nv_bfloat16 *sZ2 = sZ + (size_t)(WARPS + warp) * ROWS_W * HID;
-
-    const int64_t n_tiles = (src.R + ROWS_CTA - 1) / ROWS_CTA;
-    for (int64_t tile = blockIdx.x; tile < n_tiles; tile += gridDim.x) {
-        const int64_t r0 = tile * ROWS_CTA + warp * ROWS_W;
-        const int64_t rA = r0 + g, rB = r0 + g + 8;
-        float acc[16][4];
-        uint32_t a[8][4];
-        // ---- layer 1 (K = 16: 14 inputs and two zero columns)
-        {
-            float x[4][2];
-            x[0][0] = in_val(src, rA, 2 * t);     x[0][1] = in_val(src, rA, 2 * t + 1);
-            x[1][0] = in_val(src, rB, 2 * t);     x[1][1] = in_val(src, rB, 2 * t + 1);
-            x[2][0] = in_val(src, rA, 2 * t + 8); x[2][1] = in_val(src, rA, 2 * t + 9);
-            x[3][0] = in_val(src, rB, 2 * t + 8); x[3][1] = in_val(src, rB, 2 * t + 9);
-            uint32_t a0[4];
-#pragma unroll
-            for (int q = 0; q < 4; ++q) a0[q] = pack_bf16(x[q][0], x[q][1]);
-            {
-                const int64_t ld = tr.Rp;
-                tr.H0[(size_t)(2 * t) * ld + rA] = __float2bfloat16_rn(x[0][0]);
-                tr.H0[(size_t)(2 * t + 1) * ld + rA] = __float2bfloat16_rn(x[0][1]);
-                tr.H0[(size_t)(2 * t) * ld + rB] = __float2bfloat16_rn(x[1][0]);
-                tr.H0[(size_t)(2 * t + 1) * ld + rB] = __float2bfloat16_rn(x[1][1]);
-                tr.H0[(size_t)(2 * t + 8) * ld + rA] = __float2bfloat16_rn(x[2][0]);
-                tr.H0[(size_t)(2 * t + 9) * ld + rA] = __float2bfloat16_rn(x[2][1]);
-                tr.H0[(size_t)(2 * t + 8) * ld + rB] = __float2bfloat16_rn(x[3][0]);
-                tr.H0[(size_t)(2 * t + 9) * ld + rB] = __float2bfloat16_rn(x[3][1]);
-            }
-#pragma unroll
-            for (int j = 0; j < 16; ++j) {
-                const float c0 = b1[8 * j + 2 * t], c1 = b1[8 * j + 2 * t + 1];
-                acc[j][0] = c0; acc[j][1] = c1; acc[j][2] = c0; acc[j][3] = c1;
-                const __nv_bfloat16 *row = sWt1 + (8 * j + g) * LD1 + 2 * t;
-                mma16816(acc[j], a0, *reinterpret_cast<const uint32_t *>(row),
-                         *reinterpret_cast<const uint32_t *>(row + 8));
-            }
-        }
-        // ---- layers 2 and 3; z_1, z_2 kept (BF16) for the backward pass
-#pragma unroll 1
-        for (int l = 1; l <= 2; ++l) {
-            {
-                __nv_bfloat16 *z = l == 1 ? sZ1 : sZ2;
-#pragma unroll
-                for (int j = 0; j < 16; ++j) {
-                    *reinterpret_cast<uint32_t *>(z + g * HID + 8 * j + 2 * t) = pack_bf16(acc[j][0], acc[j][1]);
-                    *reinterpret_cast<uint32_t *>(z + (g + 8) * HID + 8 * j + 2 * t) = pack_bf16(acc[j][2], acc[j][3]);
-                }
-            }
-#pragma unroll
-            for (int j = 0; j < 16; ++j)
-#pragma unroll
-                for (int q = 0; q < 4; ++q) acc[j][q] = gelu(acc[j][q]);
-            store_t(l == 1 ? tr.H1 : tr.H2, tr.Rp, r0, acc, g, t);
-            to_frag(acc, a);
-            const float *bb = l == 1 ? b2 : b3;
-#pragma unroll
-            for (int j = 0; j < 16; ++j) {
-                const float c0 = bb[8 * j + 2 * t], c1 = bb[8 * j + 2 * t + 1];
-                acc[j][0] = c0; acc[j][1] = c1; acc[j][2] = c0; acc[j][3] = c1;
-            }
-            gemm_128(acc, a, l == 1 ? sWt2 : sWt3, g, t);
-        }
-        // ---- output unit: o = GELU(z_3) . w4 + b4, t = softplus(o)
-        float pA = 0.0f, pB = 0.0f;
-#pragma unroll
-        for (int j = 0; j < 16; ++j) {
-            const float u0 = w4[8 * j + 2 * t], u1 = w4[8 * j + 2 * t + 1];
-            pA = fmaf(gelu(acc[j][0]), u0, fmaf(gelu(acc[j][1]), u1, pA));
-            pB = fmaf(gelu(acc[j][2]), u0, fmaf(gelu(acc[j][3]), u1, pB));
-        }
-        pA += __shfl_xor_sync(0xffffffffu, pA, 1);
-        pA += __shfl_xor_sync(0xffffffffu, pA, 2);
-        pB += __shfl_xor_sync(0xffffffffu, pB, 1);
-        pB += __shfl_xor_sync(0xffffffffu, pB, 2);
-        const float oA = pA + b4, oB = pB + b4;
-        const float yA = softplus(oA), yB = softplus(oB);
-        // ---- loss and backward
-        const bool vA = rA < src.R, vB = rB < src.R;
-        const float eA = vA ? yA - src.target[rA] : 0.0f, eB = vB ? yB - src.target[rB] : 0.0f;
-        const float doA = 2.0f * tr.inv_R * eA * sigmoid(oA), doB = 2.0f * tr.inv_R * eB * sigmoid(oB);
-        {
-            float l2 = (t == 0) ? eA * eA + eB * eB : 0.0f;
-#pragma unroll
-            for (int o = 1; o < 32; o <<= 1) l2 += __shfl_xor_sync(0xffffffffu, l2, o);
-            float d4 = (t == 0) ? doA + doB : 0.0f;
-#pragma unroll
-            for (int o = 1; o < 32; o <<= 1) d4 += __shfl_xor_sync(0xffffffffu, d4, o);
-            if (lane == 0) {
-                sacc[warp][4 * HID] += d4;            // db4
-                sacc[warp][4 * HID + 1] += l2;        // sum of squared errors
-            }
-        }
-        // dw4 = sum_r h3 do, dz3 = do w4 GELU'(z3) (in place of z3)
-        {
-            float hw[16][4];
-#pragma unroll
-            for (int j = 0; j < 16; ++j) {
-                hw[j][0] = gelu(acc[j][0]) * doA; hw[j][1] = gelu(acc[j][1]) * doA;
-                hw[j][2] = gelu(acc[j][2]) * doB; hw[j][3] = gelu(acc[j][3]) * doB;
-            }
-            col_sums(hw, &sacc[warp][3 * HID], g, t);
-        }
-#pragma unroll
-        for (int j = 0; j < 16; ++j) {
-            const float u0 = w4[8 * j + 2 * t], u1 = w4[8 * j + 2 * t + 1];
-            acc[j][0] = doA * u0 * gelu_d(acc[j][0]);
-            acc[j][1] = doA * u1 * gelu_d(acc[j][1]);
-            acc[j][2] = doB * u0 * gelu_d(acc[j][2]);
-            acc[j][3] = doB * u1 * gelu_d(acc[j][3]);
-        }
-#pragma unroll 1
-        for (int l = 3; l >= 2; --l) {
-            col_sums(acc, &sacc[warp][(l - 1) * HID], g, t);   // db_l
-            store_t(l == 3 ? tr.dZ3 : tr.dZ2, tr.Rp, r0, acc, g, t);
-            to_frag(acc, a);
-#pragma unroll
-            for (int j = 0; j < 16; ++j)
-#pragma unroll
-                for (int q = 0; q < 4; ++q) acc[j][q] = 0.0f;
-            gemm_128(acc, a, l == 3 ? sW3 : sW2, g, t);   // dh_{l-1} = dz_l W_l^T
-            const __nv_bfloat16 *z = l == 3 ? sZ2 : sZ1;
-#pragma unroll
-            for (int j = 0; j < 16; ++j) {
-                const float2 zA = unpack_bf16(*reinterpret_cast<const uint32_t *>(z + g * HID + 8 * j + 2 * t));
-                const float2 zB = unpack_bf16(*reinterpret_cast<const uint32_t *>(z + (g + 8) * HID + 8 * j + 2 * t));
-                acc[j][0] *= gelu_d(zA.x);
-                acc[j][1] *= gelu_d(zA.y);
-                acc[j][2] *= gelu_d(zB.x);
-                acc[j][3] *= gelu_d(zB.y);
-            }
-        }
-        col_sums(acc, &sacc[warp][0], g, t);   // db1
-        store_t(tr.dZ1, tr.Rp, r0, acc, g, t);
-    }
-    {
-        __syncthreads();
-        for (int i = tid; i < NPART; i += blockDim.x) {
-            // partial layout: loss, db1, db2, db3, dw4, db4
-            const int src_i = i == 0 ? 4 * HID + 1 : i - 1;
-            float s = 0.0f;
-            for (int w = 0; w < WARPS; ++w) s += sacc[w][src_i];
-            tr.part[(size_t)blockIdx.x * NPART + i] = s;
-        }
-    }
-}
-
-// dW[k][n] partial over the rows [c * chunk, (c + 1) * chunk) of H^T [K][Rp] and dZ^T
-// [128][Rp]: warp w computes rows k of its 16-row M tile (K = 128) or, for K = 16, the 16
-// columns n of its slice.
-__global__ void __launch_bounds__(WARPS * 32) k_mlp_dw(const __nv_bfloat16 *__restrict__ Ht,
-                                                       const __nv_bfloat16 *__restrict__ dZt,
-                                                       int32_t K, int64_t Rp, int64_t chunk,
-                                                       float *__restrict__ part)
-{
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, g = lane >> 2, t = lane & 3;
-    const int m0 = K == HID ? 16 * warp : 0;
-    const int n0 = K == HID ? 0 : 16 * warp;
-    const int nt = K == HID ? 16 : 2;   // n-tiles of 8
-    float acc[16][4];
-#pragma unroll
-    for (int j = 0; j < 16; ++j)
-#pragma unroll
-        for (int q = 0; q < 4; ++q) acc[j][q] = 0.0f;
-    const int64_t beg = blockIdx.x * chunk, end = min(beg + chunk, Rp);
-    for (int64_t r = beg; r < end; r += 16) {
-        uint32_t a[4];
-        const __nv_bfloat16 *ha = Ht + (size_t)(m0 + g) * Rp + r + 2 * t;
-        const __nv_bfloat16 *hb = Ht + (size_t)(m0 + g + 8) * Rp + r + 2 * t;
-        a[0] = *reinterpret_cast<const uint32_t *>(ha);
-        a[1] = *reinterpret_cast<const uint32_t *>(hb);
-        a[2] = *reinterpret_cast<const uint32_t *>(ha + 8);
-        a[3] = *reinterpret_cast<const uint32_t *>(hb + 8);
-#pragma unroll
-        for (int j = 0; j < 16; ++j) {
-            if (j < nt) {
-                const __nv_bfloat16 *bp = dZt + (size_t)(n0 + 8 * j + g) * Rp + r + 2 * t;
-                mma16816(acc[j], a, *reinterpret_cast<const uint32_t *>(bp),
-                         *reinterpret_cast<const uint32_t *>(bp + 8));
-            }
-        }
-    }
-    float *out = part + (size_t)blockIdx.x * K * HID;
-#pragma unroll
-    for (int j = 0; j < 16; ++j) {
-        if (j < nt) {
-            const int c = n0 + 8 * j + 2 * t;
-            out[(size_t)(m0 + g) * HID + c] = acc[j][0];
-            out[(size_t)(m0 + g) * HID + c + 1] = acc[j][1];
-            out[(size_t)(m0 + g + 8) * HID + c] = acc[j][2];
-            out[(size_t)(m0 + g + 8) * HID + c + 1] = acc[j][3];
-        }
-    }
-}
 
 // grad[dst + i] = sum over c < n of part[c * stride + src + i] (fixed order), i < count;
 // rows >= valid_rows of a [rows][128] block are skipped (W1's padding rows 14, 15).
@@ -457,6 +137,7 @@ constexpr uint32_t TC_TMEM_COLS = TC_GROUPS * HID <= 256 ? 256 : 512;   // a pow
                                                                           // one accumulator per group
 static_assert(TC_GROUPS * HID <= 512, "TMEM columns");
 constexpr long long kMlpWaitNs = 1000000000LL;                // 1 s per wait, then an error
+constexpr int32_t kErrPair = 16;                              // status: a pair index out of range
 
 // Byte offset of element (row, col) in a stack of blocks (col / 64 selects the block).
 __host__ __device__ __forceinline__ uint32_t swz(uint32_t row, uint32_t col)
@@ -667,21 +348,421 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
     }
 }
 
+// ------------------------------------------------------------------ tcgen05 training
+// Backward operand image: W3 and W2 as [k][n] (row k, K = n), the B operand of dh = dz W^T.
+constexpr uint32_t IMGB_W3 = 0, IMGB_W2 = 2 * BLK, IMGB_BYTES = 4 * BLK;
+constexpr size_t TR_SMEM = IMG_BYTES + IMGB_BYTES + 2 * BLK + 1024;   // weights, one tile, align
+constexpr int TR_THREADS = 128;
+constexpr uint32_t TR_C0 = 0, TR_C1 = 128, TR_C2 = 256, TR_C3 = 384;   // TMEM column regions
+
+// Feature-major BF16 store of one row's value of feature c: out[c][r].
+__device__ __forceinline__ void fm_store(__nv_bfloat16 *out, int64_t ld, int c, int64_t r, float v)
+{
+    out[(size_t)c * ld + r] = __float2bfloat16_rn(v);
+}
+
+// One MMA phase of the training kernel: the tile's operand writes are fenced for the tensor
+// core, the group barrier also tells whether any thread's previous wait ran out, the first
+// warp issues the layer's products (K = 16 from the first block, or 128 from both) into TMEM
+// column region d, and every thread waits for their completion.  Returns false when the
+// kernel must stop (uniform over the CTA).
+__device__ __forceinline__ bool tr_phase(uint32_t d, uint32_t a_s, uint32_t b_s, bool k16_only, int warp,
+                                         uint32_t bar, uint32_t &parity, bool &pending, int32_t *err)
+{
+    using namespace gmco;
+    fence_proxy_async_smem();
+    fence_before();
+    if (bar_any(1, TR_THREADS, pending)) return false;
+    if (warp == 0) {
+        fence_after();
+        const uint32_t idesc = idesc_bf16(HID);
+        if (k16_only) {
+            mma_bf16_elect(d, DESC_FIXED | desc_lo(a_s), DESC_FIXED | desc_lo(b_s), idesc, 0u);
+        } else {
+#pragma unroll
+            for (int k = 0; k < HID / 16; ++k) {
+                const uint32_t off = (uint32_t)(k >> 2) * BLK + (uint32_t)(k & 3) * 32;
+                mma_bf16_elect(d, DESC_FIXED | desc_lo(a_s + off), DESC_FIXED | desc_lo(b_s + off), idesc,
+                               k > 0 ? 1u : 0u);
+            }
+        }
+        mma_commit_elect(bar);
+    }
+    pending = !mbar_wait(bar, parity, err, 2, kMlpWaitNs);
+    parity ^= 1u;
+    fence_after();
+    return true;
+}
+
+// Training forward and backward of 128-row tiles on the fifth-generation tensor cores, one
+// thread per row (= TMEM lane).  Per tile: the three forward layers (z_l kept in TMEM regions
+// C0..C2, FP32), the output unit, the loss and do = dL/do, then dz_3 = do w_4 GELU'(z_3),
+// dh_2 = dz_3 W_3^T (region C3), dz_2 = dh_2 GELU'(z_2), dh_1 = dz_2 W_2^T (region C2, z_3 no
+// longer needed), dz_1 = dh_1 GELU'(z_1).  The BF16 activations of the next product go
+// through the tile's shared-memory blocks; the layer inputs H_0..H_3, do and dZ_1..dZ_3 are
+// written feature-major for the weight-gradient GEMMs (H_0's column 14 holds 1, so that the
+// bias gradient b_1 comes out of the same product).  Per-CTA partials: the sum of squared
+// errors and of do (db_4).
+__global__ void __launch_bounds__(TR_THREADS, 1)
+    k_mlp_train_tc(const uint8_t *__restrict__ img, const uint8_t *__restrict__ imgb,
+                   const float *__restrict__ bias, RowSrc src, TrainOut tr, int32_t *__restrict__ err)
+{
+    using namespace gmco;
+    extern __shared__ uint8_t dyn[];
+    __shared__ float sb[4 * HID + 1];
+    __shared__ float red[2][TR_THREADS / 32];
+    __shared__ __align__(8) uint64_t w_bar, mma_bar, drain_bar;
+    __shared__ uint32_t tmem_holder;
+    uint8_t *base = reinterpret_cast<uint8_t *>(((uintptr_t)dyn + 1023) & ~(uintptr_t)1023);
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const uint32_t row = (uint32_t)tid;
+    const uint32_t s_img = smem_u32(base), s_imgb = s_img + IMG_BYTES;
+    uint8_t *sH = base + IMG_BYTES + IMGB_BYTES;
+    const uint32_t s_h = smem_u32(sH);
+    if (tid == 0) {
+        mbar_init(smem_u32(&w_bar), 1);
+        mbar_init(smem_u32(&mma_bar), 1);
+        mbar_init(smem_u32(&drain_bar), 1);
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    if (warp == 0) tmem_alloc(smem_u32(&tmem_holder), 512);
+    for (int i = tid; i < 4 * HID + 1; i += TR_THREADS) sb[i] = bias[i];
+    fence_before();
+    __syncthreads();
+    fence_after();
+    const uint32_t tmem = tmem_holder;
+    if (tid == 0) {
+        mbar_expect_tx(smem_u32(&w_bar), IMG_BYTES + IMGB_BYTES);
+        for (uint32_t c = 0; c < IMG_BYTES / BLK; ++c) bulk_load(s_img + c * BLK, img + c * BLK, BLK, smem_u32(&w_bar));
+        for (uint32_t c = 0; c < IMGB_BYTES / BLK; ++c) bulk_load(s_imgb + c * BLK, imgb + c * BLK, BLK, smem_u32(&w_bar));
+    }
+    const bool w_ok = mbar_wait(smem_u32(&w_bar), 0u, err, 1, kMlpWaitNs);
+    const bool w_fail = __syncthreads_or(!w_ok);
+    if (w_fail && tid == 0) mbar_wait(smem_u32(&w_bar), 0u, nullptr, 0, kMlpWaitNs);
+
+    const uint32_t t_lane = tmem + ((uint32_t)(32 * warp) << 16);
+    const float *b1 = sb, *b2 = sb + HID, *b3 = sb + 2 * HID, *w4 = sb + 3 * HID;
+    const float b4 = sb[4 * HID];
+    const uint32_t bar = smem_u32(&mma_bar);
+    const int64_t n_tiles = (src.R + 127) / 128, ld = tr.Rp;
+    uint32_t parity = 0;
+    bool pending = false, failed = w_fail;
+    float loss = 0.0f, db4 = 0.0f;
+    for (int64_t tile = blockIdx.x; !failed && tile < n_tiles; tile += gridDim.x) {
+        const int64_t r = tile * 128 + row;
+        bool valid = r < src.R;
+        // ---- inputs: BF16 into the tile's first block; H_0 (with the ones column 14)
+        {
+            float x[16];
+#pragma unroll
+            for (int c = 0; c < 16; ++c) x[c] = 0.0f;
+            int64_t fr = 0, wr = 0;
+            if (valid) {
+                if (src.pairs) {
+                    fr = src.pairs[2 * r];
+                    wr = src.pairs[2 * r + 1];
+                    if (fr < 0 || fr >= src.n_feat || wr < 0 || wr >= src.n_w) {
+                        atomicExch(err, kErrPair);   // a bad pair: the row reads as zeros
+                        valid = false;
+                    }
+                } else {
+                    fr = r % src.n_dwell;
+                    wr = r / src.n_dwell;
+                }
+            }
+            if (valid) {
+#pragma unroll
+                for (int c = 0; c < NFEAT; ++c) x[c] = src.feat[fr * NFEAT + c];
+#pragma unroll
+                for (int c = 0; c < NW; ++c) x[NFEAT + c] = log10f(fmaxf(src.w[wr * NW + c], 1e-3f));
+            }
+            uint4 lo, hi;
+            lo.x = pack_bf16(x[0], x[1]);   lo.y = pack_bf16(x[2], x[3]);
+            lo.z = pack_bf16(x[4], x[5]);   lo.w = pack_bf16(x[6], x[7]);
+            hi.x = pack_bf16(x[8], x[9]);   hi.y = pack_bf16(x[10], x[11]);
+            hi.z = pack_bf16(x[12], x[13]); hi.w = pack_bf16(x[14], x[15]);
+            *reinterpret_cast<uint4 *>(sH + swz(row, 0)) = lo;
+            *reinterpret_cast<uint4 *>(sH + swz(row, 8)) = hi;
+#pragma unroll
+            for (int c = 0; c < 16; ++c) fm_store(tr.H0, ld, c, r, c == 14 ? 1.0f : x[c]);
+        }
+        // ---- forward
+        if (!tr_phase(tmem + TR_C0, s_h, s_img + IMG_W1, true, warp, bar, parity, pending, err)) { failed = true; break; }
+#pragma unroll 1
+        for (int l = 0; l < 2; ++l) {
+            const uint32_t cz = l == 0 ? TR_C0 : TR_C1;
+            const float *bl = l == 0 ? b1 : b2;
+            __nv_bfloat16 *Hout = l == 0 ? tr.H1 : tr.H2;
+#pragma unroll 1
+            for (int c0 = 0; c0 < HID; c0 += 32) {
+                uint32_t v[2][16];
+                tmem_ld16(t_lane + cz + (uint32_t)c0, v[0]);
+                tmem_ld16(t_lane + cz + (uint32_t)c0 + 16, v[1]);
+                tmem_ld_wait16(v[0]);
+                tmem_ld_wait16(v[1]);
+#pragma unroll
+                for (int q = 0; q < 4; ++q) {
+                    uint32_t h[4];
+#pragma unroll
+                    for (int e = 0; e < 4; ++e) {
+                        const int c = 8 * q + 2 * e;
+                        const float h0 = gelu(__uint_as_float(v[c >> 4][c & 15]) + bl[c0 + c]);
+                        const float h1 = gelu(__uint_as_float(v[c >> 4][(c & 15) + 1]) + bl[c0 + c + 1]);
+                        h[e] = pack_bf16(h0, h1);
+                        fm_store(Hout, ld, c0 + c, r, h0);
+                        fm_store(Hout, ld, c0 + c + 1, r, h1);
+                    }
+                    *reinterpret_cast<uint4 *>(sH + swz(row, (uint32_t)(c0 + 8 * q))) = make_uint4(h[0], h[1], h[2], h[3]);
+                }
+            }
+            if (!tr_phase(tmem + (l == 0 ? TR_C1 : TR_C2), s_h, s_img + (l == 0 ? IMG_W2 : IMG_W3), false, warp, bar,
+                          parity, pending, err)) { failed = true; break; }
+        }
+        if (failed) break;
+        // ---- output unit, loss, do
+        float o = 0.0f;
+#pragma unroll 1
+        for (int c0 = 0; c0 < HID; c0 += 32) {
+            uint32_t v[2][16];
+            tmem_ld16(t_lane + TR_C2 + (uint32_t)c0, v[0]);
+            tmem_ld16(t_lane + TR_C2 + (uint32_t)c0 + 16, v[1]);
+            tmem_ld_wait16(v[0]);
+            tmem_ld_wait16(v[1]);
+#pragma unroll
+            for (int c = 0; c < 32; ++c) o = fmaf(gelu(__uint_as_float(v[c >> 4][c & 15]) + b3[c0 + c]), w4[c0 + c], o);
+        }
+        o += b4;
+        const float e = valid ? softplus(o) - src.target[r] : 0.0f;
+        const float d_o = valid ? 2.0f * tr.inv_R * e * sigmoid(o) : 0.0f;
+        loss += e * e;
+        db4 += d_o;
+        fm_store(tr.DO, ld, 0, r, d_o);
+        // ---- dz_3 = do w_4 GELU'(z_3); H_3 = GELU(z_3) for dw_4
+#pragma unroll 1
+        for (int c0 = 0; c0 < HID; c0 += 32) {
+            uint32_t v[2][16];
+            tmem_ld16(t_lane + TR_C2 + (uint32_t)c0, v[0]);
+            tmem_ld16(t_lane + TR_C2 + (uint32_t)c0 + 16, v[1]);
+            tmem_ld_wait16(v[0]);
+            tmem_ld_wait16(v[1]);
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                uint32_t h[4];
+#pragma unroll
+                for (int e2 = 0; e2 < 4; ++e2) {
+                    const int c = 8 * q + 2 * e2;
+                    float dz[2];
+#pragma unroll
+                    for (int u = 0; u < 2; ++u) {
+                        const float z = __uint_as_float(v[(c + u) >> 4][(c + u) & 15]) + b3[c0 + c + u];
+                        fm_store(tr.H3, ld, c0 + c + u, r, gelu(z));
+                        dz[u] = d_o * w4[c0 + c + u] * gelu_d(z);
+                        fm_store(tr.dZ3, ld, c0 + c + u, r, dz[u]);
+                    }
+                    h[e2] = pack_bf16(dz[0], dz[1]);
+                }
+                *reinterpret_cast<uint4 *>(sH + swz(row, (uint32_t)(c0 + 8 * q))) = make_uint4(h[0], h[1], h[2], h[3]);
+            }
+        }
+        // ---- dh_2 = dz_3 W_3^T, dz_2 = dh_2 GELU'(z_2); dh_1 = dz_2 W_2^T, dz_1 = dh_1 GELU'(z_1)
+#pragma unroll 1
+        for (int l = 0; l < 2; ++l) {
+            const uint32_t cd = l == 0 ? TR_C3 : TR_C2;   // dh_2, then dh_1
+            const uint32_t cz = l == 0 ? TR_C1 : TR_C0;   // z_2, then z_1
+            const float *bl = l == 0 ? b2 : b1;
+            __nv_bfloat16 *dZout = l == 0 ? tr.dZ2 : tr.dZ1;
+            if (!tr_phase(tmem + cd, s_h, s_imgb + (l == 0 ? IMGB_W3 : IMGB_W2), false, warp, bar, parity, pending,
+                          err)) { failed = true; break; }
+#pragma unroll 1
+            for (int c0 = 0; c0 < HID; c0 += 32) {
+                uint32_t dv[2][16], zv[2][16];
+                tmem_ld16(t_lane + cd + (uint32_t)c0, dv[0]);
+                tmem_ld16(t_lane + cd + (uint32_t)c0 + 16, dv[1]);
+                tmem_ld16(t_lane + cz + (uint32_t)c0, zv[0]);
+                tmem_ld16(t_lane + cz + (uint32_t)c0 + 16, zv[1]);
+                tmem_ld_wait16(dv[0]);
+                tmem_ld_wait16(dv[1]);
+                tmem_ld_wait16(zv[0]);
+                tmem_ld_wait16(zv[1]);
+#pragma unroll
+                for (int q = 0; q < 4; ++q) {
+                    uint32_t h[4];
+#pragma unroll
+                    for (int e2 = 0; e2 < 4; ++e2) {
+                        const int c = 8 * q + 2 * e2;
+                        float dz[2];
+#pragma unroll
+                        for (int u = 0; u < 2; ++u) {
+                            const int cc = c + u;
+                            dz[u] = __uint_as_float(dv[cc >> 4][cc & 15]) *
+                                    gelu_d(__uint_as_float(zv[cc >> 4][cc & 15]) + bl[c0 + cc]);
+                            fm_store(dZout, ld, c0 + cc, r, dz[u]);
+                        }
+                        h[e2] = pack_bf16(dz[0], dz[1]);
+                    }
+                    if (l == 0)
+                        *reinterpret_cast<uint4 *>(sH + swz(row, (uint32_t)(c0 + 8 * q))) = make_uint4(h[0], h[1], h[2], h[3]);
+                }
+            }
+        }
+    }
+    // per-CTA partials in a fixed order: warp sums, then the warps in order
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        loss += __shfl_xor_sync(0xffffffffu, loss, o);
+        db4 += __shfl_xor_sync(0xffffffffu, db4, o);
+    }
+    if (lane == 0) {
+        red[0][warp] = loss;
+        red[1][warp] = db4;
+    }
+    fence_before();
+    if (!failed) failed = bar_any(1, TR_THREADS, pending);
+    if (failed && !w_fail && warp == 0) {
+        mma_commit_elect(smem_u32(&drain_bar));
+        mbar_wait(smem_u32(&drain_bar), 0u, nullptr, 0, kMlpWaitNs);
+    }
+    fence_before();
+    __syncthreads();
+    if (tid == 0) {
+        float sl = 0.0f, sd = 0.0f;
+        for (int w = 0; w < TR_THREADS / 32; ++w) {
+            sl += red[0][w];
+            sd += red[1][w];
+        }
+        tr.part[(size_t)blockIdx.x * 2 + 0] = sl;
+        tr.part[(size_t)blockIdx.x * 2 + 1] = sd;
+    }
+    if (warp == 0) {
+        fence_after();
+        tmem_dealloc(tmem, 512);
+    }
+}
+
+// Weight-gradient GEMM on the tensor cores: D[m][j] = sum over the CTA's rows r of A[m][r] B[j][r]
+// (A 128 features, B N_b rows, plus N_2 rows from a second map when n_2 > 0, all feature-major
+// BF16 with rows r contiguous), M = 128, N = N_b + n_2, K = rows in blocks of 64 through a
+// four-stage ring: a producer thread (warp 0), an MMA thread (warp 1), the accumulator read
+// back by all four warps into the CTA's FP32 partial part[cta][128][N].
+constexpr int DW_STAGES = 4;
+constexpr uint32_t DW_A = 0, DW_B = BLK, DW_B2 = 2 * BLK, DW_STAGE = 2 * BLK + 2048;   // 34 KB
+constexpr size_t DW_SMEM = (size_t)DW_STAGES * DW_STAGE + 1024;
+
+__global__ void __launch_bounds__(128, 1)
+    k_mlp_dw_tc(const __grid_constant__ CUtensorMap ma, const __grid_constant__ CUtensorMap mb,
+                const __grid_constant__ CUtensorMap mb2, int32_t n_b, int32_t n_2, int64_t kb_total,
+                int64_t kb_chunk, float *__restrict__ part, int32_t *__restrict__ err)
+{
+    using namespace gmco;
+    extern __shared__ uint8_t dyn[];
+    __shared__ __align__(8) uint64_t full_bar[DW_STAGES], empty_bar[DW_STAGES], done_bar;
+    __shared__ uint32_t tmem_holder;
+    uint8_t *base = reinterpret_cast<uint8_t *>(((uintptr_t)dyn + 1023) & ~(uintptr_t)1023);
+    const uint32_t s0 = smem_u32(base);
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int N = n_b + n_2;
+    const int64_t kb0 = blockIdx.x * kb_chunk, kb1 = min(kb0 + kb_chunk, kb_total);
+    if (tid == 0) {
+        for (int s = 0; s < DW_STAGES; ++s) {
+            mbar_init(smem_u32(&full_bar[s]), 1);
+            mbar_init(smem_u32(&empty_bar[s]), 1);
+        }
+        mbar_init(smem_u32(&done_bar), 1);
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    if (warp == 0) tmem_alloc(smem_u32(&tmem_holder), 256);
+    fence_before();
+    __syncthreads();
+    fence_after();
+    const uint32_t tmem = tmem_holder;
+    __shared__ int s_fail;
+    if (tid == 0) s_fail = 0;
+    __syncthreads();
+    int armed = 0;   // producer: stages armed, for the wind-down
+    if (warp == 0 && lane == 0) {
+        const uint32_t bytes = (uint32_t)(BLK + n_b * 128 + n_2 * 128);
+        for (int64_t kb = kb0; kb < kb1; ++kb, ++armed) {
+            const int it = (int)(kb - kb0), s = it % DW_STAGES;
+            const uint32_t ph = (uint32_t)(it / DW_STAGES) & 1u;
+            if (!mbar_wait(smem_u32(&empty_bar[s]), ph ^ 1u, err, 1, kMlpWaitNs)) { s_fail = 1; break; }
+            const uint32_t st = s0 + (uint32_t)s * DW_STAGE, fb = smem_u32(&full_bar[s]);
+            mbar_expect_tx(fb, bytes);
+            tma_load_2d(st + DW_A, &ma, (int)(kb * 64), 0, fb);
+            tma_load_2d(st + DW_B, &mb, (int)(kb * 64), 0, fb);
+            if (n_2 > 0) tma_load_2d(st + DW_B2, &mb2, (int)(kb * 64), 0, fb);
+        }
+    } else if (warp == 1) {
+        const uint32_t idesc = idesc_bf16(N);
+        bool ok = true;
+        for (int64_t kb = kb0; kb < kb1 && ok; ++kb) {
+            const int it = (int)(kb - kb0), s = it % DW_STAGES;
+            const uint32_t ph = (uint32_t)(it / DW_STAGES) & 1u;
+            if (!__all_sync(0xffffffffu, mbar_wait(smem_u32(&full_bar[s]), ph, err, 2, kMlpWaitNs))) {
+                ok = false;
+                break;
+            }
+            fence_after();
+            const uint32_t st = s0 + (uint32_t)s * DW_STAGE;
+#pragma unroll
+            for (int k = 0; k < 4; ++k)
+                mma_bf16_elect(tmem, DESC_FIXED | desc_lo(st + DW_A + 32u * k), DESC_FIXED | desc_lo(st + DW_B + 32u * k),
+                               idesc, (kb == kb0 && k == 0) ? 0u : 1u);
+            mma_commit_elect(smem_u32(&empty_bar[s]));
+        }
+        if (!ok && lane == 0) s_fail = 1;
+        mma_commit_elect(smem_u32(&done_bar));   // completes once every MMA issued has finished
+    }
+    const bool done = mbar_wait(smem_u32(&done_bar), 0u, err, 3, kMlpWaitNs);
+    if (!done) {
+        if (tid == 0) s_fail = 1;
+        mbar_wait(smem_u32(&done_bar), 0u, nullptr, 0, kMlpWaitNs);
+    }
+    fence_after();
+    __syncthreads();
+    if (warp == 0 && lane == 0 && s_fail) {
+        // copies this thread armed may still be landing: wait (bounded) for their phases
+        for (int s = 0; s < DW_STAGES; ++s) {
+            if (armed <= s) continue;
+            const int last = armed - 1 - ((armed - 1 - s) % DW_STAGES);
+            mbar_wait(smem_u32(&full_bar[s]), (uint32_t)(last / DW_STAGES) & 1u, nullptr, 0, kMlpWaitNs);
+        }
+    }
+    if (!s_fail && kb1 > kb0) {
+        const int m = 32 * warp + lane;
+        float *out = part + ((size_t)blockIdx.x * 128 + m) * N;
+        for (int c = 0; c < N; c += 16) {
+            uint32_t v[16];
+            tmem_ld16(tmem + ((uint32_t)(32 * warp) << 16) + (uint32_t)c, v);
+            tmem_ld_wait16(v);
+#pragma unroll
+            for (int j = 0; j < 16; ++j) out[c + j] = __uint_as_float(v[j]);
+        }
+    }
+    fence_before();
+    __syncthreads();
+    if (warp == 0) {
+        fence_after();
+        tmem_dealloc(tmem, 256);
+    }
+}
+
+// grad[dst + j * sj + m * sm] = sum over CTAs c < n (in order) of part[c][m][j0 + j], for
+// m < 128 and j < nj (N columns per partial row).
+__global__ void k_mlp_dw_reduce(const float *__restrict__ part, int32_t n, int32_t N, int32_t j0, int32_t nj,
+                                float *__restrict__ grad, int64_t dst, int64_t sj, int64_t sm)
+{
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= 128 * nj) return;
+    const int m = i % 128, j = i / 128;
+    float s = 0.0f;
+    for (int c = 0; c < n; ++c) s += part[((size_t)c * 128 + m) * N + j0 + j];
+    grad[dst + j * sj + m * sm] = s;
+}
+
 // BF16 copies of the FP32 master parameters in the kernels' layouts.
 __global__ void k_mlp_pack(const float *__restrict__ p, DevWeights w)
 {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i < HID * HID) {
-        const int k = i / HID, n = i % HID;   // W[k][n]
-        w.W2[i] = __float2bfloat16_rn(p[OFF_W2 + i]);
-        w.W3[i] = __float2bfloat16_rn(p[OFF_W3 + i]);
-        w.Wt2[n * HID + k] = __float2bfloat16_rn(p[OFF_W2 + i]);
-        w.Wt3[n * HID + k] = __float2bfloat16_rn(p[OFF_W3 + i]);
-    }
-    if (i < HID * KIN) {
-        const int n = i / KIN, k = i % KIN;   // Wt1[n][k]
-        w.Wt1[i] = __float2bfloat16_rn(k < NIN ? p[OFF_W1 + k * HID + n] : 0.0f);
-    }
     if (i < HID * 64) {
         const int n = i / 64, k = i % 64;     // one 64-column block of W1^T, columns 14.. zero
         img_put(w.img, IMG_W1, n, k, k < NIN ? p[OFF_W1 + k * HID + n] : 0.0f);
@@ -690,6 +771,8 @@ __global__ void k_mlp_pack(const float *__restrict__ p, DevWeights w)
         const int k = i / HID, n = i % HID;
         img_put(w.img, IMG_W2, n, k, p[OFF_W2 + i]);
         img_put(w.img, IMG_W3, n, k, p[OFF_W3 + i]);
+        img_put(w.imgb, IMGB_W2, k, n, p[OFF_W2 + i]);
+        img_put(w.imgb, IMGB_W3, k, n, p[OFF_W3 + i]);
     }
     if (i < 4 * HID + 1) {
         // bias[] = b1, b2, b3, w4 (128 each), then b4
@@ -697,11 +780,6 @@ __global__ void k_mlp_pack(const float *__restrict__ p, DevWeights w)
         const int srcs[4] = {OFF_B1, OFF_B2, OFF_B3, OFF_W4};
         w.bias[i] = i == 4 * HID ? p[OFF_B4] : p[srcs[blk] + o];
     }
-}
-
-size_t train_smem()
-{
-    return (size_t)HID * LD1 * 2 + 4 * (size_t)HID * LDH * 2 + 2 * (size_t)WARPS * ROWS_W * HID * 2;
 }
 
 thread_local std::string g_mlp_err;
@@ -808,13 +886,20 @@ gmco_status finish(gmco_mlp *q, void *user_stream)
     return GMCO_OK;
 }
 
-int n_ctas(int64_t R) { return (int)std::min<int64_t>(MAX_CTAS, std::max<int64_t>(1, (R + ROWS_CTA - 1) / ROWS_CTA)); }
+__global__ void k_mlp_fill_ones(__nv_bfloat16 *ones, int64_t n)
+{
+    const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i < n) ones[i] = __float2bfloat16_rn(1.0f);
+}
 
-// Loss and gradient (into q->grad) of the batch at the current BF16 weights.
-gmco_status gradient(gmco_mlp *q, const RowSrc &src, float *loss_out)
+// Loss and gradient (into q->grad) of the batch at the current BF16 weights, on the tensor
+// cores: k_mlp_train_tc for the forward and backward of every row, four weight-gradient GEMMs
+// (W_1 with b_1, W_2 with b_2, W_3 with b_3, w_4) and fixed-order reductions of the per-CTA
+// partials.
+gmco_status gradient_tc(gmco_mlp *q, const RowSrc &src, float *loss_out)
 {
     const int64_t R = src.R;
-    const int64_t Rp = (R + ROWS_CTA - 1) / ROWS_CTA * ROWS_CTA;
+    const int64_t Rp = (R + 127) / 128 * 128;
     if (Rp > q->cap_rows) {
         MCK(cudaStreamSynchronize(q->stream));
         free_ws(q);
@@ -822,53 +907,93 @@ gmco_status gradient(gmco_mlp *q, const RowSrc &src, float *loss_out)
         MCK(dalloc(q, &t.H0, (size_t)KIN * Rp, true));
         MCK(dalloc(q, &t.H1, (size_t)HID * Rp, true));
         MCK(dalloc(q, &t.H2, (size_t)HID * Rp, true));
+        MCK(dalloc(q, &t.H3, (size_t)HID * Rp, true));
         MCK(dalloc(q, &t.dZ1, (size_t)HID * Rp, true));
         MCK(dalloc(q, &t.dZ2, (size_t)HID * Rp, true));
         MCK(dalloc(q, &t.dZ3, (size_t)HID * Rp, true));
-        MCK(dalloc(q, &t.part, (size_t)MAX_CTAS * NPART, true));
-        MCK(dalloc(q, &q->dwpart, (size_t)MAX_CTAS * HID * HID, true));
+        MCK(dalloc(q, &t.DO, (size_t)16 * Rp, true));
+        MCK(dalloc(q, &t.ONES, (size_t)16 * Rp, true));
+        MCK(dalloc(q, &t.part, (size_t)MAX_CTAS * 2, true));
+        MCK(dalloc(q, &q->dwpart, (size_t)MAX_CTAS * 128 * 144, true));
+        // rows 1..15 of DO and ONES stay zero; row 0 of ONES is one
+        MCK(cudaMemsetAsync(t.DO, 0, (size_t)16 * Rp * sizeof(__nv_bfloat16), q->stream));
+        MCK(cudaMemsetAsync(t.ONES, 0, (size_t)16 * Rp * sizeof(__nv_bfloat16), q->stream));
+        k_mlp_fill_ones<<<(unsigned)((Rp + 255) / 256), 256, 0, q->stream>>>(t.ONES, Rp);
+        MCK(cudaGetLastError());
         q->cap_rows = Rp;
     }
     TrainOut tr = q->tr;
     tr.Rp = Rp;
     tr.inv_R = 1.0f / (float)R;
-    // rows R..Rp of the feature-major arrays are written by the kernel (tiles cover Rp)
-    const int ctas = n_ctas(R);
-    const size_t smem = train_smem();
-    MCK(cudaFuncSetAttribute(k_mlp_train, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-    RowSrc s2 = src;
-    k_mlp_train<<<ctas, WARPS * 32, smem, q->stream>>>(q->w, s2, tr);
+    int n_sm = 0;
+    MCK(cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, q->device));
+    const int ctas = (int)std::min<int64_t>(std::min(n_sm, MAX_CTAS), Rp / 128);
+    MCK(cudaFuncSetAttribute(k_mlp_train_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)TR_SMEM));
+    k_mlp_train_tc<<<ctas, TR_THREADS, TR_SMEM, q->stream>>>(q->w.img, q->w.imgb, q->w.bias, src, tr, q->err);
     MCK(cudaGetLastError());
     q->launches++;
-    // bias and output-unit gradients, loss
+    // weight gradients: D = A B^T over row ranges of 64-row blocks
+    const int64_t kb_total = Rp / 64;
+    const int64_t kb_chunk = std::max<int64_t>(4, (kb_total + n_sm - 1) / n_sm);
+    const int n_dw = (int)((kb_total + kb_chunk - 1) / kb_chunk);   // every CTA has a block
+    struct Job {
+        const __nv_bfloat16 *A, *B, *B2;
+        int n_b, n_2;
+        int64_t w_off, b_off;   // weight block (j = k < nk) and bias column (j = n_b), -1: none
+        int nk;
+    };
+    const Job jobs[4] = {
+        {tr.dZ1, tr.H0, nullptr, 16, 0, OFF_W1, OFF_B1, NIN},     // column 14 of H0 is one
+        {tr.dZ2, tr.H1, tr.ONES, 128, 16, OFF_W2, OFF_B2, HID},
+        {tr.dZ3, tr.H2, tr.ONES, 128, 16, OFF_W3, OFF_B3, HID},
+        {tr.H3, tr.DO, nullptr, 16, 0, OFF_W4, -1, 1},
+    };
+    MCK(cudaFuncSetAttribute(k_mlp_dw_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)DW_SMEM));
     const int rb = 256;
-    k_mlp_reduce<<<(HID + rb - 1) / rb, rb, 0, q->stream>>>(tr.part, ctas, NPART, 1, HID, q->grad, OFF_B1);
-    k_mlp_reduce<<<(HID + rb - 1) / rb, rb, 0, q->stream>>>(tr.part, ctas, NPART, 1 + HID, HID, q->grad, OFF_B2);
-    k_mlp_reduce<<<(HID + rb - 1) / rb, rb, 0, q->stream>>>(tr.part, ctas, NPART, 1 + 2 * HID, HID, q->grad, OFF_B3);
-    k_mlp_reduce<<<(HID + 1 + rb - 1) / rb, rb, 0, q->stream>>>(tr.part, ctas, NPART, 1 + 3 * HID, HID + 1, q->grad, OFF_W4);
-    MCK(cudaGetLastError());
-    q->launches += 4;
-    // weight gradients, split over row ranges
-    const int64_t chunk = std::max<int64_t>(16, (Rp / MAX_CTAS + 15) / 16 * 16);
-    const int nd = (int)((Rp + chunk - 1) / chunk);
-    struct L { const __nv_bfloat16 *H, *dZ; int K; int off; };
-    const L layers[3] = {{tr.H0, tr.dZ1, KIN, OFF_W1}, {tr.H1, tr.dZ2, HID, OFF_W2}, {tr.H2, tr.dZ3, HID, OFF_W3}};
-    for (const L &l : layers) {
-        k_mlp_dw<<<nd, WARPS * 32, 0, q->stream>>>(l.H, l.dZ, l.K, Rp, chunk, q->dwpart);
-        const int64_t cnt = (int64_t)(l.K == KIN ? NIN : HID) * HID;   // W1: rows 0..13 only
-        k_mlp_reduce<<<(unsigned)((cnt + rb - 1) / rb), rb, 0, q->stream>>>(q->dwpart, nd, (int64_t)l.K * HID,
-                                                                           0, cnt, q->grad, l.off);
+    for (const Job &jb : jobs) {
+        CUtensorMap ma, mb, mb2;
+        if (!gmco::tc_encode_map(&ma, jb.A, (uint64_t)Rp, 128, 64, 128) ||
+            !gmco::tc_encode_map(&mb, jb.B, (uint64_t)Rp, (uint64_t)jb.n_b, 64, (uint32_t)jb.n_b) ||
+            !gmco::tc_encode_map(&mb2, jb.B2 ? jb.B2 : jb.B, (uint64_t)Rp, 16, 64, 16)) {
+            g_mlp_err = "gradient: tensor map encoding failed";
+            return GMCO_ECUDA;
+        }
+        const int N = jb.n_b + jb.n_2;
+        k_mlp_dw_tc<<<n_dw, 128, DW_SMEM, q->stream>>>(ma, mb, mb2, jb.n_b, jb.n_2, kb_total, kb_chunk, q->dwpart, q->err);
         MCK(cudaGetLastError());
+        // D[m = n][j = k]: the weight W[k][n] at w_off + k * 128 + n (for w_4: w_off + n)
+        const int64_t sj = jb.nk == 1 ? 0 : HID;
+        k_mlp_dw_reduce<<<(unsigned)((128 * jb.nk + rb - 1) / rb), rb, 0, q->stream>>>(q->dwpart, n_dw, N, 0, jb.nk,
+                                                                                     q->grad, jb.w_off, sj, 1);
         q->launches += 2;
-    }
-    if (loss_out) {
-        k_mlp_reduce<<<1, 32, 0, q->stream>>>(tr.part, ctas, NPART, 0, 1, q->grad + NPARAM, 0);
+        if (jb.b_off >= 0) {
+            const int jb_col = jb.n_2 > 0 ? jb.n_b : 14;   // the ones row: ONES row 0, or H0 column 14
+            k_mlp_dw_reduce<<<1, 128, 0, q->stream>>>(q->dwpart, n_dw, N, jb_col, 1, q->grad, jb.b_off, 0, 1);
+            q->launches++;
+        }
         MCK(cudaGetLastError());
-        q->launches++;
-        MCK(cudaMemcpyAsync(q->h_pinned, q->grad + NPARAM, sizeof(float), cudaMemcpyDeviceToHost, q->stream));
-        MCK(cudaStreamSynchronize(q->stream));
-        *loss_out = q->h_pinned[0] / (float)R;
     }
+    // db_4 and the loss from the per-CTA partials (loss, db_4)
+    k_mlp_reduce<<<1, 32, 0, q->stream>>>(tr.part, ctas, 2, 1, 1, q->grad, OFF_B4);
+    k_mlp_reduce<<<1, 32, 0, q->stream>>>(tr.part, ctas, 2, 0, 1, q->grad + NPARAM, 0);
+    MCK(cudaGetLastError());
+    q->launches += 2;
+    MCK(cudaMemcpyAsync(q->h_pinned + 1, q->err, sizeof(int32_t), cudaMemcpyDeviceToHost, q->stream));
+    if (loss_out) MCK(cudaMemcpyAsync(q->h_pinned, q->grad + NPARAM, sizeof(float), cudaMemcpyDeviceToHost, q->stream));
+    MCK(cudaStreamSynchronize(q->stream));
+    int32_t code = 0;
+    memcpy(&code, q->h_pinned + 1, sizeof code);
+    if (code != 0) {
+        cudaMemsetAsync(q->err, 0, sizeof(int32_t), q->stream);
+        cudaStreamSynchronize(q->stream);
+        if (code == kErrPair) {
+            g_mlp_err = "pair index out of range";
+            return GMCO_EINVAL;
+        }
+        g_mlp_err = "gradient: a tensor-core wait of the training kernels ran out (code " + std::to_string(code) + ")";
+        return GMCO_ECUDA;
+    }
+    if (loss_out) *loss_out = q->h_pinned[0] / (float)R;
     return GMCO_OK;
 }
 
@@ -886,15 +1011,10 @@ gmco_status batch_args(gmco_mlp *q, Staged &st, const float *feat, int64_t n_fea
     if ((r = stage(q, st, w, (size_t)n_w * NW, &s.w)) != GMCO_OK) return r;
     if ((r = stage(q, st, pairs, (size_t)R * 2, &s.pairs)) != GMCO_OK) return r;
     if ((r = stage(q, st, target, (size_t)R, &s.target)) != GMCO_OK) return r;
-    // index check on the host copy of the pairs
-    std::vector<int32_t> hp((size_t)R * 2);
-    MCK(cudaMemcpyAsync(hp.data(), s.pairs, hp.size() * sizeof(int32_t), cudaMemcpyDeviceToHost, q->stream));
-    MCK(cudaStreamSynchronize(q->stream));
-    for (int64_t i = 0; i < R; ++i)
-        if (hp[2 * i] < 0 || hp[2 * i] >= n_feat || hp[2 * i + 1] < 0 || hp[2 * i + 1] >= n_w) {
-            g_mlp_err = "pair index out of range";
-            return GMCO_EINVAL;
-        }
+    // the training kernel checks every pair against these counts before it reads a row
+    // (a row out of range is read as zeros and the call fails with GMCO_EINVAL)
+    s.n_feat = n_feat;
+    s.n_w = n_w;
     s.n_dwell = 0;
     s.R = R;
     *src = s;
@@ -959,10 +1079,9 @@ gmco_status gmco_mlp_create(const float *params, gmco_mlp **out)
         return fail(GMCO_ECUDA);
     if (dalloc(q, &q->p, NPARAM) != cudaSuccess || dalloc(q, &q->m, NPARAM) != cudaSuccess ||
         dalloc(q, &q->v, NPARAM) != cudaSuccess || dalloc(q, &q->grad, NPARAM + 1) != cudaSuccess ||
-        dalloc(q, &q->w.Wt1, HID * KIN) != cudaSuccess || dalloc(q, &q->w.Wt2, HID * HID) != cudaSuccess ||
-        dalloc(q, &q->w.Wt3, HID * HID) != cudaSuccess || dalloc(q, &q->w.W2, HID * HID) != cudaSuccess ||
-        dalloc(q, &q->w.W3, HID * HID) != cudaSuccess || dalloc(q, &q->w.bias, 4 * HID + 1) != cudaSuccess ||
-        dalloc(q, &q->w.img, IMG_BYTES) != cudaSuccess || dalloc(q, &q->err, 1) != cudaSuccess)
+        dalloc(q, &q->w.bias, 4 * HID + 1) != cudaSuccess ||
+        dalloc(q, &q->w.img, IMG_BYTES) != cudaSuccess || dalloc(q, &q->w.imgb, IMGB_BYTES) != cudaSuccess ||
+        dalloc(q, &q->err, 1) != cudaSuccess)
         return fail(GMCO_ENOMEM);
     if (cudaMemcpy(q->p, hp.data(), NPARAM * sizeof(float), cudaMemcpyHostToDevice) != cudaSuccess ||
         cudaMemset(q->m, 0, NPARAM * sizeof(float)) != cudaSuccess ||
@@ -1151,7 +1270,7 @@ gmco_status gmco_mlp_gradient(gmco_mlp *q, const float *features, int64_t n_feat
     if ((r = batch_args(q, st, features, n_feat, penalty_weights, n_w, pairs, target, R, &s)) != GMCO_OK)
         return r;
     float l = 0.0f;
-    if ((r = gradient(q, s, &l)) != GMCO_OK) return r;
+    if ((r = gradient_tc(q, s, &l)) != GMCO_OK) return r;
     if (loss) *loss = l;
     MCK(cudaMemcpyAsync(grad, q->grad, NPARAM * sizeof(float), cudaMemcpyDefault, q->stream));
     return finish(q, cuda_stream);
@@ -1174,7 +1293,7 @@ gmco_status gmco_mlp_train_step(gmco_mlp *q, const float *features, int64_t n_fe
     if ((r = batch_args(q, st, features, n_feat, penalty_weights, n_w, pairs, target, R, &s)) != GMCO_OK)
         return r;
     float l = 0.0f;
-    if ((r = gradient(q, s, loss ? &l : nullptr)) != GMCO_OK) return r;
+    if ((r = gradient_tc(q, s, loss ? &l : nullptr)) != GMCO_OK) return r;
     q->step++;
     const float b1 = 0.9f, b2 = 0.999f, eps = 1e-8f;
     const float c1 = 1.0f - (float)pow((double)b1, (double)q->step);

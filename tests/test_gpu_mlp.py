@@ -179,3 +179,21 @@ def test_checkpoint_resumes_training_bit_for_bit(gmco_mod, tmp_path):
             assert np.array_equal(back.params(), net.params())
     hdr = path.read_bytes().split(b"\n", 2)
     assert hdr[0] == b"GMCO-MLP" and b'"step": 3' in hdr[1]
+
+
+def test_bad_pairs_refused_without_update(gmco_mod):
+    """A pair index out of range is caught by the training kernel before it reads the row: the
+    call fails with GMCO_EINVAL and the parameters and the Adam step are unchanged; the next
+    valid step runs."""
+    F, W, pairs, target = _batch(15, 2000)
+    p = _params(10)
+    with gmco_mod.Mlp(p) as net:
+        for bad in ((0, len(F)), (1, len(W)), (0, -1)):
+            pb = pairs.copy()
+            pb[777, bad[0]] = bad[1]
+            with pytest.raises(gmco_mod.GmcoError) as e:
+                net.train_step(F, W, pb, target, lr=1e-3)
+            assert e.value.status == gmco_mod.EINVAL
+            assert np.array_equal(net.params(), p)
+        net.train_step(F, W, pairs, target, lr=1e-3)
+        assert not np.array_equal(net.params(), p)
