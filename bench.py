@@ -78,6 +78,26 @@ def parse_args():
     return ap.parse_args()
 
 
+def exact_objectives(torch, pat, W, T):
+    """Eq. (obj) with Eq. (1) and Eq. (dose) at the returned dwell times T (P x n_dwell),
+    evaluated in FP64 on the device with torch: the objective that the quality bar compares
+    with F*, free of the kernels' own FP32 re-evaluation error (up to about 3e-5 relative at
+    12 000 points, which would otherwise let plans just above the bar count)."""
+    dev = "cuda"
+    A = torch.as_tensor(np.asarray(pat.A, dtype=np.float64), device=dev)
+    sid = torch.as_tensor(np.asarray(pat.sid, dtype=np.int64), device=dev)
+    prm = torch.as_tensor(np.asarray(pat.params, dtype=np.float64), device=dev)
+    Wt = torch.as_tensor(np.asarray(W.cpu().numpy() if hasattr(W, "cpu") else W, dtype=np.float64), device=dev)
+    Tt = (T if hasattr(T, "cpu") else torch.as_tensor(np.asarray(T))).to(device=dev, dtype=torch.float64)
+    N = torch.bincount(sid, minlength=prm.shape[0]).to(torch.float64)
+    c = Wt[:, sid] / N[sid].clamp(min=1.0)            # w_ps / N_s per point
+    D = Tt @ A.T                                       # doses, P x n_pnt
+    under = (prm[sid, 1] - D).clamp(min=0.0)
+    over = (D - prm[sid, 2]).clamp(min=0.0)
+    F = (c * (prm[sid, 0] * under * under + prm[sid, 3] * over * over)).sum(dim=1)
+    return F.cpu().numpy()
+
+
 def read_fstar(name):
     path = os.path.join(ROOT, "tests", "golden", f"fstar_{name}.txt")
     vals = {}
@@ -221,7 +241,8 @@ def workload_config(args, pat, P):
             "max_iters": args.max_iters, "max_evals": args.max_evals, "stop_window": args.stop_window,
             "refine_iters_fp32": args.refine_iters, "grad_split_kb": args.grad_split_kb,
             "start": "uniform t = 1 s",
-            "quality": f"F <= F*(1+{QUALITY:g}), F* = exact FP64 optimum per plan",
+            "quality": f"F(T) <= F*(1+{QUALITY:g}), F(T) = Eq. (obj) at the returned dwell times in FP64, "
+                       f"F* = exact FP64 optimum per plan",
             "l2": "flushed between timed steps (256 MB write)" if not args.no_flush else "not flushed",
             "precision_form": args.precision}
 
@@ -726,7 +747,7 @@ def fp32_form_section(g, torch, args, pat, W, Wd, fstar, stream):
         torch.cuda.synchronize()
         ms = a.elapsed_time(b)
         launches = p32.last_launch_count()
-        gap = out["objectives"].cpu().numpy() / fstar - 1.0
+        gap = exact_objectives(torch, pat, W, out["T"]) / fstar - 1.0
         X = np.sqrt(out["T"].cpu().numpy()).astype(np.float32)
         prof = p32.profile_evaluate(W, X, reps=max(2, args.profile_reps // 2))
     ok = int(np.sum(gap <= QUALITY))
@@ -761,7 +782,7 @@ def fp32_accuracy_tensor_form(g, torch, args, pat, Wd, fstar, stream):
         b.record(stream)
         torch.cuda.synchronize()
         ms = a.elapsed_time(b)
-    gap = out["objectives"].cpu().numpy() / fstar - 1.0
+    gap = exact_objectives(torch, pat, Wd, out["T"]) / fstar - 1.0
     ok = int(np.sum(gap <= QUALITY))
     return {"precision_form": "bf16x3", "plans_within_1e-4": ok, "ms_per_solve": ms,
             "plans_within_1e-4_per_s": ok / (ms * 1e-3), "median_gap_vs_fstar": float(np.median(gap))}
@@ -783,7 +804,7 @@ def refine_section(g, torch, args, pat, Wd, fstar, stream):
                                  allow_timeout=True)
             b.record(stream)
             torch.cuda.synchronize()
-        gap = out["objectives"].cpu().numpy() / fstar - 1.0
+        gap = exact_objectives(torch, pat, Wd, out["T"]) / fstar - 1.0
         ms = a.elapsed_time(b)
         ok = int(np.sum(gap <= QUALITY))
         rows.append({"refine_iters": R, "plans_within_1e-4": ok, "ms_per_solve": ms,
@@ -795,13 +816,15 @@ def refine_section(g, torch, args, pat, Wd, fstar, stream):
 
 
 def eps_sweep_section(g, torch, prob, pat, Wd, max_iters, stream, fstar,
-                      eps_list=(1e-7, 1e-6, 1e-5, 1e-4, 1e-3, 1e-2)):
+                      eps_list=(1e-7, 1e-6, 1e-5, 1e-4, 1e-3, 1e-2), fobj=None):
     """The stopping-criterion sweep of Sec. 2.2.4 (the paper's Fig. 3a, on this workload): for
     each relative-change tolerance eps, the solve time of the whole batch (CUDA events, after one
     warm-up solve at that eps) and the fraction of non-dominated plans of the pool, judged on
     the per-structure objectives f_s (the unweighted mean penalty of each structure, evaluated
     with the FP32 form at the solved dwell times, one evaluation per structure with one-hot
-    weights) by the library's non-dominated filter."""
+    weights) by the library's non-dominated filter.  fobj(out) gives the objectives the gaps to
+    F* are taken on (default: Eq. (obj) at the returned dwell times in FP64).
+    """
     P, S = int(Wd.shape[0]), int(pat.params.shape[0])
     rows = []
     with g.Problem(pat.A, pat.sid, pat.params, precision="fp32") as p32:
@@ -821,7 +844,8 @@ def eps_sweep_section(g, torch, prob, pat, Wd, max_iters, stream, fstar,
                 Wk[:, k] = 1.0
                 f[:, k] = p32.evaluate(Wk, X, objectives=True, grad=False)["objectives"].cpu().numpy()
             nd = g.pareto_filter(f)
-            gap = out["objectives"].cpu().numpy() / fstar - 1.0
+            Fx = fobj(out) if fobj else exact_objectives(torch, pat, Wd, out["T"])
+            gap = Fx / fstar - 1.0
             rows.append({"eps": eps, "ms": a.elapsed_time(b), "frac_nondominated": float(np.mean(nd)),
                          "median_iters": float(np.median(out["iters"].cpu().numpy())),
                          "median_gap_vs_fstar": float(np.median(gap)),
@@ -937,8 +961,9 @@ def run_ours(args):
     iters = out["iters"].cpu().numpy()
     status = out["status"].cpu().numpy()
     dvh = out["dvh"].cpu().numpy()
-    rel = obj / fstar - 1.0
+    rel = exact_objectives(torch, pat, W, out["T"]) / fstar - 1.0
     ok = int(np.sum(rel <= QUALITY))
+    ok_reported = int(np.sum(obj / fstar - 1.0 <= QUALITY))
     total_ok = sum_over_ranks(dist, torch, ok)
     value = total_ok / (step_ms / 1000.0)
 
@@ -951,7 +976,7 @@ def run_ours(args):
             host = prob.solve_batch(W, max_iters=args.max_iters, tol=args.tol, allow_timeout=True)
             times.append(time.perf_counter() - t0)
         e2e_s = max_over_ranks(dist, torch, float(np.mean(times)))
-        ok_h = int(np.sum(host["objectives"] / fstar - 1.0 <= QUALITY))
+        ok_h = int(np.sum(exact_objectives(torch, pat, W, host["T"]) / fstar - 1.0 <= QUALITY))
         h2d = W.nbytes
         d2h = sum(v.nbytes for k, v in host.items() if hasattr(v, "nbytes"))
         e2e = {"value": sum_over_ranks(dist, torch, ok_h) / e2e_s, "unit": UNIT,
@@ -1031,6 +1056,7 @@ def run_ours(args):
                                              "dose rates, Dirichlet(1) x 10 hidden weights)",
             "config": dict(workload_config(args, pat, P), parallelism=f"replicas{world}"),
             "plans_within_1e-4": ok, "plans": P,
+            "plans_within_1e-4_by_reported_objective": ok_reported,
             "iters": {"median": float(np.median(iters)), "max": int(iters.max()),
                       "status_counts": {int(s): int(np.sum(status == s)) for s in np.unique(status)}},
             "rel_gap_vs_fstar": {"median": float(np.median(rel)), "p90": float(np.percentile(rel, 90)),

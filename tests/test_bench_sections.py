@@ -70,7 +70,7 @@ def test_eps_sweep_section_host_logic():
     solver = _Solver()
     fstar = np.array([2.0, 2.0, 1.0, 2.0, 2.0])
     r = bench.eps_sweep_section(g, _fake_torch, solver, pat, torch.zeros(5, 4), 10, None, fstar,
-                                eps_list=(1e-7, 1e-3))
+                                eps_list=(1e-7, 1e-3), fobj=lambda out: out["objectives"].cpu().numpy())
     assert [row["eps"] for row in r["rows"]] == [1e-7, 1e-3]
     assert solver.tols == [1e-7, 1e-7, 1e-3, 1e-3]           # one warm-up and one timed solve each
     assert all(row["frac_nondominated"] == 0.4 and row["speedup_vs_first"] == 1.0 for row in r["rows"])
