@@ -73,8 +73,8 @@ struct EvalArgs {
     const float *dT;         // cap x nd_pad change of dwell times vs the base point, or null
     const float *Wc;         // cap x n_struct, w_ps / N_s
     float *G;                // cap x np_pad, dF/dd per point (mode G) or dose (mode D)
-    float *Fpart;            // n_ptiles x cap, per point tile partial of F
-    float *dFpart;           // n_ptiles x cap, partial of F(trial) - F(base)
+    float *Fpart;            // cap x n_ptiles, per point tile partial of F (a row's contiguous)
+    float *dFpart;           // cap x n_ptiles, partial of F(trial) - F(base)
     float *gpart;            // n_split x rows x nd_pad, partial of A^T G (rows = *n_rows)
     SplitPlan sp;            // split plan of the gradient GEMM that wrote gpart
 };
@@ -102,7 +102,7 @@ struct SolverState {
 // Inputs of a fused solver step: the evaluation's partial sums and where the next step's
 // compact rows go.
 struct StepArgs {
-    const float *Fpart, *dFpart;     // n_ptiles x cap
+    const float *Fpart, *dFpart;     // cap x n_ptiles
     const float *gpart;              // n_split x rows x nd_pad
     int32_t n_ptiles, cap;
     SplitPlan sp;

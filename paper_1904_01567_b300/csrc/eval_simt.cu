@@ -191,8 +191,8 @@ __global__ void __launch_bounds__(NT, 2) k_gemm1(EvalArgs e, int32_t mode)
         }
         const int row = row0 + tr * 4 + r;
         if (tc == 0 && row < n_rows) {
-            e.Fpart[(size_t)blockIdx.x * e.cap + row] = v;
-            if (e.dFpart) e.dFpart[(size_t)blockIdx.x * e.cap + row] = HAS_DT ? dv : 0.0f;
+            e.Fpart[(size_t)row * gridDim.x + blockIdx.x] = v;   // [row][point tile]
+            if (e.dFpart) e.dFpart[(size_t)row * gridDim.x + blockIdx.x] = HAS_DT ? dv : 0.0f;
         }
     }
 }

@@ -82,7 +82,7 @@ __global__ void k_na_finish(const float *__restrict__ X, const float *__restrict
     }
     if (threadIdx.x == 0 && F) {
         double f = 0.0;
-        for (int t = 0; t < n_ptiles; ++t) f += (double)Fpart[(size_t)t * P + i];
+        for (int t = 0; t < n_ptiles; ++t) f += (double)Fpart[(size_t)i * n_ptiles + t];
         F[i] = f;
     }
 }

@@ -183,8 +183,8 @@ __global__ void k_finish(SolverState s, EvalArgs e, int32_t n_ptiles)
     __shared__ double red[2][128];
     double f = 0.0, df = 0.0;
     for (int t = threadIdx.x; t < n_ptiles; t += blockDim.x) {
-        f += (double)e.Fpart[(size_t)t * e.cap + i];
-        if (e.dFpart) df += (double)e.dFpart[(size_t)t * e.cap + i];
+        f += (double)e.Fpart[(size_t)i * n_ptiles + t];
+        if (e.dFpart) df += (double)e.dFpart[(size_t)i * n_ptiles + t];
     }
     red[0][threadIdx.x] = f;
     red[1][threadIdx.x] = df;
@@ -384,8 +384,8 @@ __device__ __forceinline__ void step_plan(const SolverState &s, const UpdatePara
     double fsum = 0.0, dfsum = 0.0;
 #pragma unroll 4
     for (int t = lane; t < a.n_ptiles; t += 32) {
-        fsum += (double)a.Fpart[(size_t)t * a.cap + slot];
-        if (st == ST_TRIAL) dfsum += (double)a.dFpart[(size_t)t * a.cap + slot];
+        fsum += (double)a.Fpart[(size_t)slot * a.n_ptiles + t];   // a row's partials are contiguous
+        if (st == ST_TRIAL) dfsum += (double)a.dFpart[(size_t)slot * a.n_ptiles + t];
     }
     const double Ft = warp_sum_d(fsum);
     const double dF = warp_sum_d(dfsum);

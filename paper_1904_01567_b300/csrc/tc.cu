@@ -723,10 +723,10 @@ __global__ void __launch_bounds__(NTHREADS, 1) k_tc(const __grid_constant__ KPar
                 if (threadIdx.x < BM && ok) {   // fixed-order sum of the four lane quarters
                     const int rr = threadIdx.x, row = w.ptile * BM + rr;
                     if (row < n_rows) {
-                        d.Fpart[(size_t)w.sub * d.cap + row] =
+                        d.Fpart[(size_t)row * d.n_ptiles + w.sub] =
                             ((s_part[0][0][rr] + s_part[0][1][rr]) + s_part[0][2][rr]) + s_part[0][3][rr];
                         if (kp.has_dT)
-                            d.dFpart[(size_t)w.sub * d.cap + row] =
+                            d.dFpart[(size_t)row * d.n_ptiles + w.sub] =
                                 ((s_part[1][0][rr] + s_part[1][1][rr]) + s_part[1][2][rr]) + s_part[1][3][rr];
                     }
                 }

@@ -37,7 +37,7 @@ struct TcDoseProb {
     const float *Wc;            // cap x n_struct, w / N_s per compact row
     __nv_bfloat16 *G[3];        // row r at G[j] + r * ld_g: split terms of dF/dd
     float *dose_out;            // row r at dose_out + r * ld_g (dose mode)
-    float *Fpart, *dFpart;      // [point tile][cap]
+    float *Fpart, *dFpart;      // [cap][point tile]
     int32_t a_row;              // first row of this problem's points in the A maps
     int32_t t_row;              // first row of its plans in the T / dT maps
     int32_t kb;                 // K blocks of 64 dwells
