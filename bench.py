@@ -271,7 +271,9 @@ def run_reference(args):
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": 0,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1000 * t,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-            "data": "synthetic", "config": workload_config(args, pat, n),
+            # the workload's config as the GPU arm states it; each step times a bounded
+            # sample of it (cpu_baseline.sample)
+            "data": "synthetic", "config": workload_config(args, pat, W.shape[0]),
             "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
                              "sample": f"first {n} plans of {args.workload}, same tol, "
                                        f"max_iters and max_evals, one plan per OpenMP thread; {model}",
