@@ -235,6 +235,9 @@ def cpu_baseline(pat, W, fstar, settings, n_sample, tol, max_iters, threads=0, m
     return wall, ok, r
 
 
+DATA = "synthetic (seeded prostate geometry, point-source dose rates, Dirichlet(1) x 10 hidden weights)"
+
+
 def workload_config(args, pat, P):
     return {"workload": args.workload, "n_pnt": int(pat.n_pnt), "n_dwell": int(pat.n_dwell),
             "n_struct": 4, "plans_per_gpu": int(P), "m": 10, "tol": args.tol,
@@ -273,7 +276,7 @@ def run_reference(args):
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
             # the workload's config as the GPU arm states it; each step times a bounded
             # sample of it (cpu_baseline.sample)
-            "data": "synthetic", "config": workload_config(args, pat, W.shape[0]),
+            "data": DATA, "config": dict(workload_config(args, pat, W.shape[0]), parallelism=f"replicas{world}"),
             "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
                              "sample": f"first {n} plans of {args.workload}, same tol, "
                                        f"max_iters and max_evals, one plan per OpenMP thread; {model}",
@@ -1059,8 +1062,7 @@ def run_ours(args):
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": step_ms,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-            "dtype": args.precision, "data": "synthetic (seeded prostate geometry, point-source "
-                                             "dose rates, Dirichlet(1) x 10 hidden weights)",
+            "dtype": args.precision, "data": DATA,
             "config": dict(workload_config(args, pat, P), parallelism=f"replicas{world}"),
             "plans_within_1e-4": ok, "plans": P,
             "plans_within_1e-4_by_reported_objective": ok_reported,

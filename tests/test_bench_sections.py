@@ -1,6 +1,7 @@
 """Host logic of the benchmark's annealing and stopping-criterion sections, run on the CPU with
 stand-ins for the library and the CUDA events (no device): the keys of their JSON objects, the
-ratios they derive and the per-structure one-hot weights they evaluate with."""
+ratios they derive and the per-structure one-hot weights they evaluate with; and the reference
+arm's line (the oracle on host cores), which states the GPU arm's workload config."""
 import sys
 import types
 import os
@@ -98,3 +99,31 @@ def test_section_summary_keeps_key_figures():
          "iters_to_1e-4": {"median": 800.0}, "budgets": {"800": {"ms": 3.21, "within_1e-4": 4}}}
     assert bench.section_summary("warm_start", {"by_start": {"bf16x2_warm": d}}) == {
         "bf16x2_warm": {"stop_1e-4": [12.3, 700.0, 5], "iters_to_1e-4": 800.0, "800": [3.2, 4]}}
+
+
+def test_reference_arm_states_the_gpu_arms_config():
+    """The reference arm (the FP64 oracle on host cores, timed on a bounded sample) prints the
+    same workload config as the GPU arm would for the same arguments, and describes its sample
+    in cpu_baseline.sample."""
+    import json
+    import subprocess
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    out = subprocess.run([sys.executable, os.path.join(root, "bench.py"), "--impl", "reference",
+                          "--workload", "prostate-2k-8plans", "--steps", "1", "--warmup", "0",
+                          "--cpu-sample", "2"],
+                         capture_output=True, text=True, timeout=600, cwd=root)
+    assert out.returncode == 0, out.stderr[-2000:]
+    line = json.loads(out.stdout.strip().splitlines()[-1])
+    from synth import workload
+    pat, W, _ = workload("prostate-2k-8plans")
+    saved = sys.argv
+    try:
+        sys.argv = ["bench.py", "--workload", "prostate-2k-8plans"]
+        args = bench.parse_args()
+    finally:
+        sys.argv = saved
+    want = dict(bench.workload_config(args, pat, W.shape[0]), parallelism="replicas1")
+    assert line["config"] == want
+    assert line["data"] == bench.DATA
+    assert line["impl"] == "reference" and line["cpu_baseline"]["kind"] == "oracle"
+    assert "first 2 plans" in line["cpu_baseline"]["sample"]
