@@ -358,9 +358,14 @@ __device__ __forceinline__ void step_plan(const SolverState &s, const UpdatePara
     if (hS) {   // rows of nd_pad floats: 16-byte aligned, a multiple of 16 bytes
         if (lane == 0) {
             hbar_expect(hbar, (uint32_t)cnt * 2u * (uint32_t)nd * 4u);
-            for (int k = 0, i = nw; k < cnt; ++k, i = i == 0 ? m - 1 : i - 1) {   // newest first
-                bulk_to_smem(hS + (size_t)i * nd, HS + (size_t)i * nd, (uint32_t)nd * 4u, hbar);
-                bulk_to_smem(hY + (size_t)i * nd, HY + (size_t)i * nd, (uint32_t)nd * 4u, hbar);
+            if (cnt == m) {   // a full ring is contiguous here and there: one copy each for s and y
+                bulk_to_smem(hS, HS, (uint32_t)m * (uint32_t)nd * 4u, hbar);
+                bulk_to_smem(hY, HY, (uint32_t)m * (uint32_t)nd * 4u, hbar);
+            } else {
+                for (int k = 0, i = nw; k < cnt; ++k, i = i == 0 ? m - 1 : i - 1) {   // newest first
+                    bulk_to_smem(hS + (size_t)i * nd, HS + (size_t)i * nd, (uint32_t)nd * 4u, hbar);
+                    bulk_to_smem(hY + (size_t)i * nd, HY + (size_t)i * nd, (uint32_t)nd * 4u, hbar);
+                }
             }
         }
         *hbar_used = true;
